@@ -1,0 +1,354 @@
+"""Seeded synthetic conic-QP instances (inputs only; no solver arithmetic).
+
+Both the FP64 CPU oracle and the CUDA path consume these instances; this module
+computes nothing that the method computes.  Every random number comes from
+Philox-4x32-10, the counter-based generator of Salmon, Moraes, Dror and Shaw,
+"Parallel random numbers: as easy as 1, 2, 3" (SC 2011), implemented here from
+that published definition (10 rounds of the 4x32 Philox S-box with the two
+published multipliers and Weyl key increments).
+
+An instance is a plain dict of numpy arrays describing
+
+    min 1/2 x'Qx + c'x   s.t.  A x = b,  x in K = K_1 x ... x K_J,
+
+with A in CSR form (rowptr int64, colind int64, val float64), Q given in the
+structured form Q = diag(q) + P + R' D R (any part may be absent), and K given
+as a list of contiguous cone blocks (type, start, dim, alpha) that partition
+0..n-1.  Cone types: 0 free, 1 nonnegative, 2 second-order (v, t) with t last,
+3 rotated second-order (v, s, t) with ||v||^2 <= 2 s t, 4 exponential (r, s, t)
+with s exp(r/s) <= t, 5 three-dimensional power (r, s, t) with
+r^alpha s^(1-alpha) >= |t|.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+CONE_FREE, CONE_NONNEG, CONE_SOC, CONE_RSOC, CONE_EXP, CONE_POW = 0, 1, 2, 3, 4, 5
+
+_M0 = np.uint64(0xD2511F53)
+_M1 = np.uint64(0xCD9E8D57)
+_W0 = np.uint32(0x9E3779B9)
+_W1 = np.uint32(0xBB67AE85)
+_MASK32 = np.uint64(0xFFFFFFFF)
+
+
+def philox4x32_10(ctr: np.ndarray, key: np.ndarray) -> np.ndarray:
+    """Philox-4x32-10 block function.
+
+    ctr: uint32 array of shape (N, 4); key: uint32 array of shape (2,) or (N, 2).
+    Returns uint32 array (N, 4).
+    """
+    c = np.array(ctr, dtype=np.uint32, copy=True).reshape(-1, 4)
+    k = np.broadcast_to(np.asarray(key, dtype=np.uint32), (c.shape[0], 2)).copy()
+    c0, c1, c2, c3 = (c[:, i].astype(np.uint64) for i in range(4))
+    k0 = k[:, 0].astype(np.uint64)
+    k1 = k[:, 1].astype(np.uint64)
+    for rnd in range(10):
+        if rnd > 0:
+            k0 = (k0 + np.uint64(_W0)) & _MASK32
+            k1 = (k1 + np.uint64(_W1)) & _MASK32
+        p0 = _M0 * c0
+        p1 = _M1 * c2
+        hi0, lo0 = p0 >> np.uint64(32), p0 & _MASK32
+        hi1, lo1 = p1 >> np.uint64(32), p1 & _MASK32
+        c0, c1, c2, c3 = hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0
+    return np.stack([c0, c1, c2, c3], axis=1).astype(np.uint32)
+
+
+class Stream:
+    """A Philox stream keyed by (seed, stream id); counters advance sequentially."""
+
+    def __init__(self, seed: int, stream: int = 0):
+        self.key = np.array([seed & 0xFFFFFFFF, stream & 0xFFFFFFFF], dtype=np.uint32)
+        self.counter = 0
+
+    def u32(self, n: int) -> np.ndarray:
+        nblk = (n + 3) // 4
+        idx = np.arange(self.counter, self.counter + nblk, dtype=np.uint64)
+        self.counter += nblk
+        ctr = np.zeros((nblk, 4), dtype=np.uint32)
+        ctr[:, 0] = (idx & _MASK32).astype(np.uint32)
+        ctr[:, 1] = (idx >> np.uint64(32)).astype(np.uint32)
+        return philox4x32_10(ctr, self.key).reshape(-1)[:n]
+
+    def uniform(self, n: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
+        """Doubles in [lo, hi) with 53 random bits each (two 32-bit draws)."""
+        w = self.u32(2 * n).astype(np.uint64).reshape(n, 2)
+        m = ((w[:, 0] >> np.uint64(5)) << np.uint64(26)) | (w[:, 1] >> np.uint64(6))
+        u = m.astype(np.float64) * (1.0 / 9007199254740992.0)
+        return lo + (hi - lo) * u
+
+    def normal(self, n: int, mean: float = 0.0, std: float = 1.0) -> np.ndarray:
+        """Box-Muller normals."""
+        h = (n + 1) // 2
+        u1 = self.uniform(h)
+        u2 = self.uniform(h)
+        r = np.sqrt(-2.0 * np.log1p(-u1))
+        z = np.concatenate([r * np.cos(2 * np.pi * u2), r * np.sin(2 * np.pi * u2)])[:n]
+        return mean + std * z
+
+    def integers(self, n: int, lo: int, hi: int) -> np.ndarray:
+        """Integers uniform in [lo, hi) (hi - lo < 2**31)."""
+        span = hi - lo
+        return lo + np.minimum((self.uniform(n) * span).astype(np.int64), span - 1)
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+def _coo_to_csr(m, n, rows, cols, vals):
+    """Sum duplicates and return CSR arrays with sorted column indices."""
+    rows = np.asarray(rows, dtype=np.int64)
+    cols = np.asarray(cols, dtype=np.int64)
+    vals = np.asarray(vals, dtype=np.float64)
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    if rows.size:
+        key = rows * n + cols
+        first = np.ones(key.size, dtype=bool)
+        first[1:] = key[1:] != key[:-1]
+        grp = np.cumsum(first) - 1
+        vals = np.bincount(grp, weights=vals)
+        rows, cols = rows[first], cols[first]
+    rowptr = np.zeros(m + 1, dtype=np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    return rowptr, cols, vals
+
+
+def csr_matvec(rowptr, colind, val, x):
+    """Plain CSR product used only to build right-hand sides b = A x0."""
+    m = rowptr.size - 1
+    prod = val * x[colind]
+    out = np.zeros(m)
+    nz = np.diff(rowptr)
+    rows = np.repeat(np.arange(m), nz)
+    np.add.at(out, rows, prod)
+    return out
+
+
+def blocks_from_list(blist):
+    """blist: list of (type, dim, alpha) in order -> block arrays."""
+    t = np.array([b[0] for b in blist], dtype=np.int32)
+    d = np.array([b[1] for b in blist], dtype=np.int64)
+    a = np.array([b[2] for b in blist], dtype=np.float64)
+    s = np.zeros_like(d)
+    if d.size:
+        s[1:] = np.cumsum(d)[:-1]
+    return t, s, d, a
+
+
+def interior_point(stream: Stream, btype, bstart, bdim, balpha, n):
+    """A point strictly inside K (used as a feasible x0 so that b = A x0)."""
+    x = np.zeros(n)
+    for t, s, d, al in zip(btype, bstart, bdim, balpha):
+        s, d = int(s), int(d)
+        if t == CONE_FREE:
+            x[s:s + d] = stream.normal(d)
+        elif t == CONE_NONNEG:
+            x[s:s + d] = np.abs(stream.normal(d)) + 0.01
+        elif t == CONE_SOC:
+            v = stream.normal(d - 1)
+            x[s:s + d - 1] = v
+            x[s + d - 1] = np.linalg.norm(v) + abs(stream.normal(1)[0]) + 0.1
+        elif t == CONE_RSOC:
+            v = stream.normal(d - 2)
+            sv = abs(stream.normal(1)[0]) + 0.5
+            x[s:s + d - 2] = v
+            x[s + d - 2] = sv
+            x[s + d - 1] = v @ v / (2 * sv) + abs(stream.normal(1)[0]) + 0.1
+        elif t == CONE_EXP:
+            r = stream.normal(1)[0]
+            sv = abs(stream.normal(1)[0]) + 0.5
+            x[s:s + 3] = [r, sv, sv * np.exp(r / sv) + abs(stream.normal(1)[0]) + 0.1]
+        elif t == CONE_POW:
+            r = abs(stream.normal(1)[0]) + 0.5
+            sv = abs(stream.normal(1)[0]) + 0.5
+            bound = r ** al * sv ** (1 - al)
+            x[s:s + 3] = [r, sv, 0.5 * bound * (2 * stream.uniform(1)[0] - 1)]
+    return x
+
+
+def make_instance(name, m, n, a_rowptr, a_colind, a_val, c, b, btype, bstart, bdim, balpha,
+                  q_diag=None, p_csr=None, q_R=None, q_D=None, **extra):
+    inst = dict(name=name, m=int(m), n=int(n),
+                a_rowptr=np.ascontiguousarray(a_rowptr, dtype=np.int64),
+                a_colind=np.ascontiguousarray(a_colind, dtype=np.int64),
+                a_val=np.ascontiguousarray(a_val, dtype=np.float64),
+                c=np.ascontiguousarray(c, dtype=np.float64),
+                b=np.ascontiguousarray(b, dtype=np.float64),
+                blk_type=np.ascontiguousarray(btype, dtype=np.int32),
+                blk_start=np.ascontiguousarray(bstart, dtype=np.int64),
+                blk_dim=np.ascontiguousarray(bdim, dtype=np.int64),
+                blk_alpha=np.ascontiguousarray(balpha, dtype=np.float64),
+                q_diag=None if q_diag is None else np.ascontiguousarray(q_diag, dtype=np.float64),
+                p_rowptr=None, p_colind=None, p_val=None,
+                q_R=None if q_R is None else np.ascontiguousarray(q_R, dtype=np.float64),
+                q_D=None if q_D is None else np.ascontiguousarray(q_D, dtype=np.float64))
+    if p_csr is not None:
+        inst["p_rowptr"] = np.ascontiguousarray(p_csr[0], dtype=np.int64)
+        inst["p_colind"] = np.ascontiguousarray(p_csr[1], dtype=np.int64)
+        inst["p_val"] = np.ascontiguousarray(p_csr[2], dtype=np.float64)
+    inst.update(extra)
+    return inst
+
+
+def _random_sparse(stream, m, n, density):
+    """Bernoulli(density) pattern with N(0,1) values, sampled column by column."""
+    mask = stream.uniform(m * n) < density
+    idx = np.nonzero(mask)[0]
+    rows, cols = idx // n, idx % n
+    vals = stream.normal(idx.size)
+    return rows, cols, vals
+
+
+# ---------------------------------------------------------------------------
+# the five benchmark configurations (seed 1000 + config number)
+# ---------------------------------------------------------------------------
+
+def sparse_qp_nonneg(n=1000, m=500, a_density=0.01, m_rows=200, m_density=0.02, seed=1001):
+    """Config 1: plain sparse QP over the nonnegative orthant.
+
+    A (m x n) 1% dense N(0,1); Q = M'M + 1e-2 I with M (m_rows x n) 2% dense
+    N(0,1), passed as one sparse symmetric P; c ~ N(0,1); b = A x0 with
+    x0 = |N(0,1)|.
+    """
+    st = Stream(seed, 0)
+    ar, ac, av = _random_sparse(st, m, n, a_density)
+    a_rowptr, a_colind, a_val = _coo_to_csr(m, n, ar, ac, av)
+    mr, mc, mv = _random_sparse(st, m_rows, n, m_density)
+    Md = np.zeros((m_rows, n))
+    Md[mr, mc] = mv
+    Qd = Md.T @ Md + 1e-2 * np.eye(n)
+    pr, pc = np.nonzero(Qd)
+    p_csr = _coo_to_csr(n, n, pr, pc, Qd[pr, pc])
+    c = st.normal(n)
+    x0 = np.abs(st.normal(n))
+    b = csr_matvec(a_rowptr, a_colind, a_val, x0)
+    btype, bstart, bdim, balpha = blocks_from_list([(CONE_NONNEG, n, 0.0)])
+    return make_instance("sparse_qp_nonneg_n%d_m%d" % (n, m), m, n, a_rowptr, a_colind, a_val, c, b,
+                         btype, bstart, bdim, balpha, p_csr=p_csr, x_feasible=x0)
+
+
+def socp_mix(n=200_000, n_nonneg=100_000, n_soc=2000, soc_dim=(10, 50), n_rsoc=500, rsoc_dim=(3, 20),
+             m=100_000, nnz_per_col=10, rank=20, seed=1002):
+    """Config 2: SOCP/QCQP mix with diagonal-plus-low-rank Q.
+
+    Blocks in order: n_nonneg nonnegative coordinates, n_soc SOCs of dimension
+    U[soc_dim], n_rsoc rotated SOCs of dimension U[rsoc_dim], then free
+    coordinates up to n.  A has about nnz_per_col N(0,1) entries per column and
+    every row at least one entry; Q = diag(lognormal(0,1)) + R'R with R (rank x n)
+    N(0, 1/n); c ~ N(0,1); b = A x0 with x0 strictly inside K.
+    """
+    st = Stream(seed, 0)
+    blist = [(CONE_NONNEG, n_nonneg, 0.0)]
+    sd = st.integers(n_soc, soc_dim[0], soc_dim[1] + 1)
+    rd = st.integers(n_rsoc, rsoc_dim[0], rsoc_dim[1] + 1)
+    blist += [(CONE_SOC, int(d), 0.0) for d in sd]
+    blist += [(CONE_RSOC, int(d), 0.0) for d in rd]
+    used = sum(b[1] for b in blist)
+    if used > n:
+        raise ValueError("cone blocks exceed n")
+    if n - used > 0:
+        blist.append((CONE_FREE, n - used, 0.0))
+    btype, bstart, bdim, balpha = blocks_from_list(blist)
+    cols = np.repeat(np.arange(n, dtype=np.int64), nnz_per_col)
+    rows = st.integers(cols.size, 0, m)
+    vals = st.normal(cols.size)
+    present = np.zeros(m, dtype=bool)
+    present[rows] = True
+    empty = np.nonzero(~present)[0]
+    if empty.size:
+        rows = np.concatenate([rows, empty])
+        cols = np.concatenate([cols, st.integers(empty.size, 0, n)])
+        vals = np.concatenate([vals, st.normal(empty.size)])
+    a_rowptr, a_colind, a_val = _coo_to_csr(m, n, rows, cols, vals)
+    q_diag = np.exp(st.normal(n))
+    q_R = st.normal(rank * n, 0.0, 1.0 / np.sqrt(n)).reshape(rank, n)
+    q_D = np.eye(rank)
+    c = st.normal(n)
+    x0 = interior_point(st, btype, bstart, bdim, balpha, n)
+    b = csr_matvec(a_rowptr, a_colind, a_val, x0)
+    return make_instance("socp_mix_n%d_m%d" % (n, m), m, n, a_rowptr, a_colind, a_val, c, b,
+                         btype, bstart, bdim, balpha, q_diag=q_diag, q_R=q_R, q_D=q_D, x_feasible=x0)
+
+
+def fisher_market(n_buyers=10_000, n_goods=1000, density=0.05, seed=1003, pow_fraction=0.5):
+    """Config 3: quasilinear Fisher market with exponential and power cones.
+
+    Variables, in order: allocations x_ij on the valuation graph E (nonneg),
+    retained money delta_i (nonneg), then one 3-D cone block per buyer:
+    exponential (z_i, s_i, t_i) with s_i exp(z_i/s_i) <= t_i, or power
+    (t_i, s_i, z_i) with t_i^a s_i^(1-a) >= |z_i|.  Rows: supply
+    sum_i x_ij = 1 (one per good), utility t_i - sum_j u_ij x_ij - delta_i = 0
+    (one per buyer), and s_i = 1 (one per buyer).  Objective
+    sum_i (delta_i - w_i z_i), Q = 0.  Valuations lognormal(0,1) at the given
+    density, budgets w_i ~ U[0.5, 2], supplies 1, alpha ~ U[0.2, 0.8].
+    """
+    st = Stream(seed, 0)
+    nb, ng = n_buyers, n_goods
+    mask = st.uniform(nb * ng) < density
+    idx = np.nonzero(mask)[0]
+    bi, gj = idx // ng, idx % ng
+    # every good needs at least one buyer and every buyer at least one good
+    missing_g = np.setdiff1d(np.arange(ng), gj)
+    if missing_g.size:
+        bi = np.concatenate([bi, st.integers(missing_g.size, 0, nb)])
+        gj = np.concatenate([gj, missing_g])
+    missing_b = np.setdiff1d(np.arange(nb), bi)
+    if missing_b.size:
+        bi = np.concatenate([bi, missing_b])
+        gj = np.concatenate([gj, st.integers(missing_b.size, 0, ng)])
+    order = np.lexsort((gj, bi))
+    bi, gj = bi[order], gj[order]
+    e = bi.size
+    u = np.exp(st.normal(e))
+    w = st.uniform(nb, 0.5, 2.0)
+    is_pow = st.uniform(nb) < pow_fraction
+    alpha = st.uniform(nb, 0.2, 0.8)
+    n = e + nb + 3 * nb
+    off_delta = e
+    off_cone = e + nb
+    blist = [(CONE_NONNEG, e + nb, 0.0)]
+    for i in range(nb):
+        blist.append((CONE_POW, 3, float(alpha[i])) if is_pow[i] else (CONE_EXP, 3, 0.0))
+    btype, bstart, bdim, balpha = blocks_from_list(blist)
+    # coordinate of z_i, s_i, t_i inside block i
+    zc = np.where(is_pow, 2, 0)
+    tc = np.where(is_pow, 0, 2)
+    z_idx = off_cone + 3 * np.arange(nb) + zc
+    s_idx = off_cone + 3 * np.arange(nb) + 1
+    t_idx = off_cone + 3 * np.arange(nb) + tc
+    m = ng + 2 * nb
+    rows = [gj, ng + bi, ng + np.arange(nb), ng + np.arange(nb), ng + nb + np.arange(nb)]
+    cols = [np.arange(e), np.arange(e), t_idx, off_delta + np.arange(nb), s_idx]
+    vals = [np.ones(e), -u, np.ones(nb), -np.ones(nb), np.ones(nb)]
+    a_rowptr, a_colind, a_val = _coo_to_csr(m, n, np.concatenate(rows), np.concatenate(cols),
+                                            np.concatenate(vals))
+    b = np.concatenate([np.ones(ng), np.zeros(nb), np.ones(nb)])
+    c = np.zeros(n)
+    c[off_delta:off_delta + nb] = 1.0
+    c[z_idx] = -w
+    return make_instance("fisher_b%d_g%d" % (nb, ng), m, n, a_rowptr, a_colind, a_val, c, b,
+                         btype, bstart, bdim, balpha, q_diag=np.zeros(n),
+                         fisher=dict(n_buyers=nb, n_goods=ng, edges=e, buyer=bi, good=gj, u=u, w=w,
+                                     is_pow=is_pow, alpha=alpha, z_idx=z_idx, t_idx=t_idx, s_idx=s_idx))
+
+
+CONFIGS = {
+    1: lambda: sparse_qp_nonneg(),
+    2: lambda: socp_mix(),
+    3: lambda: fisher_market(),
+}
+
+
+def small_config(k: int):
+    """Scaled-down copies with the same structure, for oracle-speed parity tests."""
+    if k == 1:
+        return sparse_qp_nonneg(n=200, m=100, seed=2001)
+    if k == 2:
+        return socp_mix(n=3000, n_nonneg=1500, n_soc=30, n_rsoc=10, m=1500, seed=2002)
+    if k == 3:
+        return fisher_market(n_buyers=200, n_goods=40, density=0.1, seed=2003)
+    raise KeyError(k)

@@ -1,0 +1,54 @@
+"""Input generators: Philox-4x32-10 known answers and instance structure."""
+import numpy as np
+
+import instances as I
+
+
+def test_philox_known_answers():
+    # Known-answer vectors published with the Philox definition (Salmon et al., SC 2011; Random123 KAT file)
+    z = I.philox4x32_10(np.zeros((1, 4), np.uint32), np.zeros(2, np.uint32))[0]
+    assert [int(v) for v in z] == [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]
+    f = I.philox4x32_10(np.full((1, 4), 0xFFFFFFFF, np.uint32), np.full(2, 0xFFFFFFFF, np.uint32))[0]
+    assert [int(v) for v in f] == [0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD]
+    pi = I.philox4x32_10(np.array([[0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344]], np.uint32),
+                         np.array([0xA4093822, 0x299F31D0], np.uint32))[0]
+    assert [int(v) for v in pi] == [0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1]
+
+
+def test_stream_reproducible_and_distributions():
+    a = I.Stream(7, 3).uniform(50000)
+    b = I.Stream(7, 3).uniform(50000)
+    assert np.array_equal(a, b)
+    assert 0.0 <= a.min() and a.max() < 1.0
+    assert abs(a.mean() - 0.5) < 0.01
+    z = I.Stream(8, 0).normal(100000)
+    assert abs(z.mean()) < 0.02 and abs(z.std() - 1.0) < 0.02
+
+
+def _check_structure(inst):
+    n, m = inst["n"], inst["m"]
+    assert inst["a_rowptr"].size == m + 1 and inst["a_rowptr"][0] == 0
+    assert inst["a_colind"].min() >= 0 and inst["a_colind"].max() < n
+    # blocks partition 0..n-1 contiguously
+    s, d = inst["blk_start"], inst["blk_dim"]
+    assert s[0] == 0 and np.all(s[1:] == s[:-1] + d[:-1]) and s[-1] + d[-1] == n
+    assert inst["c"].size == n and inst["b"].size == m
+
+
+def test_small_configs_structure_and_feasibility():
+    for k in (1, 2, 3):
+        inst = I.small_config(k)
+        _check_structure(inst)
+        if "x_feasible" in inst:
+            x0 = inst["x_feasible"]
+            assert np.allclose(I.csr_matvec(inst["a_rowptr"], inst["a_colind"], inst["a_val"], x0), inst["b"])
+
+
+def test_fisher_rows():
+    inst = I.small_config(3)
+    f = inst["fisher"]
+    nb, ng = f["n_buyers"], f["n_goods"]
+    assert inst["m"] == ng + 2 * nb
+    assert inst["n"] == f["edges"] + 4 * nb
+    # every supply row and utility row is non-empty
+    assert np.all(np.diff(inst["a_rowptr"]) > 0)
