@@ -890,9 +890,16 @@ static int prox_bb(const wprob* w, double tau, const double* v, const double* u0
   double* q = dalloc(n);
   double* trial = dalloc(n);
   double jmax = 0.0;
+  /* J = diag(Q) + I/tau with the full diagonal of Q = diag(q) + P + R'DR (eq. jacobi-inner-metric) */
   for (int64_t i = 0; i < n; ++i) {
-    J[i] = jacobi ? w->qd[i] + 1.0 / tau : 1.0;
-    if (w->qd[i] + 1.0 / tau > jmax) jmax = w->qd[i] + 1.0 / tau;
+    double qi = w->qd[i];
+    if (w->pr)
+      for (int64_t t = w->pr[i]; t < w->pr[i + 1]; ++t)
+        if (w->pc[t] == i) qi += w->pv[t];
+    for (int64_t l = 0; l < w->k; ++l)
+      for (int64_t l2 = 0; l2 < w->k; ++l2) qi += w->R[l * n + i] * w->D[l * w->k + l2] * w->R[l2 * n + i];
+    J[i] = jacobi ? qi + 1.0 / tau : 1.0;
+    if (qi + 1.0 / tau > jmax) jmax = qi + 1.0 / tau;
   }
   memcpy(u, u0, (size_t)n * sizeof(double));
   w_q_apply(w, u, q);
