@@ -1,0 +1,203 @@
+/*
+ * cqp.h — C ABI of the GB300 conic-QP PDHG library (libcqp_gb300.so).
+ *
+ * Problem (paper, Sec. 1, eq. "cqp"):
+ *     min_x  1/2 x'Qx + c'x   s.t.  A x = b,  x in K = K_1 x ... x K_J,
+ * solved by restarted reflected-Halpern PDHG (Alg. "pdhcq1", uncompiled branch,
+ * and Sec. 4.2.1 eq. "rh-update") or restarted Cesaro-averaged PDHG (Alg.
+ * "pdhcq1", compiled branch), with the practical components of Sec. 4
+ * (rescaling Sec. 4.2.2, adaptive inner accuracy Sec. 4.2.3, Jacobi projected
+ * BB Sec. 4.2.4 / eq. "jacobi-bb-step", diagonal-Q metric projection eq.
+ * "diagonal-q-metric", step sizes eq. "practical-stepsizes", PID primal weight
+ * eqs. "pid-error"/"pid-weight", adaptive restart eq. "practical-restart-rule",
+ * defaults Table "practical-defaults").  K is a product of free, nonnegative,
+ * second-order, rotated second-order, exponential and 3-D power cones
+ * (Sec. 4 standard form, eq. "solver-input", equality rows only).
+ *
+ * Conventions shared by every entry point:
+ *  - All functions return an int status: 0 = success, > 0 = solver outcome
+ *    (iteration or time limit), < 0 = error (see CQP_ERR_*).  No C++ exception
+ *    crosses this boundary and nothing aborts the process.
+ *  - Input arrays are borrowed for the duration of the call and never retained;
+ *    the library copies what it keeps.  Output arrays are caller-owned.
+ *  - "device" pointers are CUDA global-memory pointers of the current device;
+ *    "host" pointers are ordinary (preferably pinned) host memory.  Each entry
+ *    point states which it expects.
+ *  - A stream argument (cudaStream_t passed as void*) may be NULL for the
+ *    default stream.  Entry points that return results to the host
+ *    synchronise that stream before returning.
+ *  - The library needs a GB300 (sm_103a); on any CUDA error the call returns
+ *    CQP_ERR_CUDA and cqp_last_error() describes it.
+ */
+#ifndef CQP_GB300_H
+#define CQP_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define CQP_OK 0
+#define CQP_ITER_LIMIT 1          /* max_iter reached before rel-KKT <= tol */
+#define CQP_TIME_LIMIT 2          /* time_limit_s reached */
+#define CQP_ERR_INVALID (-1)      /* bad sizes, partition, cone parameters, non-finite data */
+#define CQP_ERR_CUDA (-2)         /* a CUDA runtime call failed */
+#define CQP_ERR_OOM (-3)          /* device allocation failed */
+#define CQP_ERR_NUMERICAL (-4)    /* NaN/Inf detected in the FP64 reductions */
+#define CQP_ERR_WAIT (-5)         /* a bounded device-side wait expired (grid barrier) */
+#define CQP_ERR_UNSUPPORTED (-6)  /* option combination not implemented */
+
+/* ---- cone types (Sec. 4, after eq. "solver-input") ------------------ */
+#define CQP_CONE_FREE 0    /* R^d (box with infinite bounds) */
+#define CQP_CONE_NONNEG 1  /* R^d_+ */
+#define CQP_CONE_SOC 2     /* {(v, t): ||v||_2 <= t}, t is the LAST coordinate, d >= 2 */
+#define CQP_CONE_RSOC 3    /* {(v, s, t): ||v||^2 <= 2 s t, s, t >= 0}, s, t last, d >= 3 */
+#define CQP_CONE_EXP 4     /* cl{(r, s, t): s > 0, s exp(r/s) <= t}, d = 3 */
+#define CQP_CONE_POW 5     /* {(r, s, t): r, s >= 0, r^a s^(1-a) >= |t|}, d = 3, 0 < a < 1 */
+
+/* CSR matrix.  rowptr has nrows+1 entries (int64, rowptr[0] = 0), colind and
+ * val have nnz entries; colind in [0, ncols).  nnz must be < 2^31. */
+typedef struct {
+  int64_t nrows, ncols, nnz;
+  const int64_t* rowptr;
+  const int32_t* colind;
+  const double* val;
+} cqp_csr;
+
+/* Structured Q = diag(q) + P + R' D R (Sec. 4.1, "Products with a structured
+ * operator"), never formed.  Any part may be absent: diag = NULL, P.rowptr =
+ * NULL, rank = 0.  P is n x n symmetric; R is rank x n row-major; D is
+ * rank x rank row-major symmetric.  rank <= 64.  Q must be positive
+ * semidefinite (not checked). */
+typedef struct {
+  const double* diag;
+  cqp_csr P;
+  int64_t rank;
+  const double* R;
+  const double* D;
+} cqp_qop;
+
+/* Cone blocks: nblocks contiguous slices (start, dim) that partition 0..n-1
+ * in increasing order; alpha is used by CQP_CONE_POW only. */
+typedef struct {
+  int64_t nblocks;
+  const int32_t* type;
+  const int64_t* start;
+  const int64_t* dim;
+  const double* alpha;
+} cqp_cones;
+
+typedef struct {
+  /* arithmetic */
+  int32_t precision;        /* 0: FP32 iterates and matrices, FP64 reductions and cone roots; 1: all FP64 */
+  int32_t update;           /* 0: reflected Halpern (eq. "rh-update"); 1: Cesaro averaged (Alg. "pdhcq1") */
+  double rho;               /* reflection coefficient, default 1.0 */
+  /* rescaling (Table "practical-defaults") */
+  int32_t ruiz_iters;       /* 10 */
+  double pc_alpha;          /* 1.0; < 0 disables Pock-Chambolle */
+  int32_t bound_obj;        /* 1 */
+  /* inner solver */
+  double eps0_in, gamma_in, eps_min_in;   /* 1e-3, 5e-4, 1e-9 */
+  int32_t jacobi;           /* 1 */
+  int32_t max_inner;        /* 1000 */
+  int32_t force_inner;      /* 1: projected BB even for diagonal Q */
+  /* restart / primal weight */
+  double beta_s, beta_n, beta_a;          /* 0.2, 0.8, 0.36 */
+  double beta_I, K_P, K_I, K_D;           /* 0.3, 0.99, 0.01, 0.0 */
+  int32_t pid;              /* 1 */
+  int32_t avg_epoch;        /* epoch length of the averaged variant, 64 */
+  /* termination */
+  double tol;               /* 1e-4 relative KKT */
+  int64_t max_iter;         /* outer iterations, 100000 */
+  int32_t check_every;      /* KKT / restart check cadence, 64 */
+  double time_limit_s;      /* <= 0: none */
+  /* step size */
+  int32_t power_iters;      /* 200 */
+  double power_tol;         /* 1e-6 */
+  double step_factor;       /* 0.998 */
+  /* execution */
+  int32_t input_on_device;  /* 1: every input pointer of cqp_setup is a device pointer */
+  int32_t team;             /* 0 auto, 1 whole-GPU cooperative kernel, 2 one thread block */
+  int32_t threads;          /* threads per block, 0 = auto */
+  int32_t blocks_per_sm;    /* 0 = auto (cooperative team only) */
+  int32_t tpr_a, tpr_at;    /* threads per CSR row for A and A', 0 = autotuned */
+  int32_t launch_iters;     /* outer iterations per kernel launch, 0 = auto */
+  void* stream;             /* cudaStream_t, NULL = default stream */
+} cqp_options;
+
+typedef struct {
+  double eps_p, eps_d, eps_g, rel_kkt;    /* relative primal, dual, gap residuals and their max */
+  double pobj, dobj;                      /* primal and dual objective values */
+  double norm_res_p, norm_res_d;          /* ||Ax - b||_2, ||Pi_K(-s)||_2 with s = Qx + c - A'y */
+} cqp_kkt_report;
+
+typedef struct {
+  int32_t status;
+  int64_t iters, restarts, inner_total, kernel_launches;
+  cqp_kkt_report kkt;
+  double eta, norm_A, omega;
+  double setup_ms, solve_ms;
+} cqp_result;
+
+typedef struct cqp_handle cqp_handle;
+
+/* Fills *opt with the defaults listed above.  Returns CQP_OK. */
+int cqp_default_options(cqp_options* opt);
+
+/* Builds the device-resident, rescaled problem (Sec. 4.2.2 rescaling and
+ * eq. "practical-stepsizes": Ruiz, Pock-Chambolle and bound-objective scaling,
+ * power-iteration estimate of ||A||_2, eta = step_factor/||A||_2).
+ *   A: m x n equality matrix; Q: objective operator (NULL = 0); c: n; b: m;
+ *   K: cone partition of 0..n-1; opt: NULL = defaults.
+ * Pointers are host pointers unless opt->input_on_device = 1.  On success
+ * *out owns all device memory of the problem until cqp_free.
+ * Errors: CQP_ERR_INVALID (sizes, partition not contiguous/covering, SOC dim
+ * < 2, RSOC dim < 3, EXP/POW dim != 3, alpha outside (0,1), rank > 64, nnz >=
+ * 2^31, non-finite values), CQP_ERR_OOM, CQP_ERR_CUDA; *out is NULL then. */
+int cqp_setup(const cqp_csr* A, const cqp_qop* Q, const double* c, const double* b, const cqp_cones* K,
+              const cqp_options* opt, cqp_handle** out);
+
+/* Runs the restarted PDHG loop on the GPU until rel-KKT <= tol (checked on the
+ * unscaled candidate every check_every iterations, Sec. 4.2.2 last paragraph),
+ * max_iter, or time_limit_s.
+ *   x0 (n), y0 (m): optional warm start (NULL = zeros), unscaled.
+ *   x_out (n), y_out (m): caller-owned, receive the unscaled final candidate
+ *   (may be NULL).  All four are host pointers, or device pointers when
+ *   on_device = 1.  res: optional, filled on return.
+ * Returns CQP_OK, CQP_ITER_LIMIT, CQP_TIME_LIMIT or an error code. */
+int cqp_solve(cqp_handle* h, const double* x0, const double* y0, double* x_out, double* y_out, int32_t on_device,
+              cqp_result* res);
+
+/* FP64 KKT report (eq. "kkt-cqp" measured relative to ||b||, ||c||) of the
+ * unscaled point (x, y) on the handle's problem, computed on the GPU.
+ * x (n), y (m): host pointers, or device pointers when on_device = 1. */
+int cqp_kkt(cqp_handle* h, const double* x, const double* y, int32_t on_device, cqp_kkt_report* rep);
+
+/* Releases every resource of h (NULL is allowed). */
+void cqp_free(cqp_handle* h);
+
+/* Text for a status code; the last CUDA or validation error of this thread. */
+const char* cqp_status_string(int status);
+const char* cqp_last_error(void);
+
+/* ---- kernel-level entry points (device pointers, used for parity and
+ * bandwidth measurements).  `precision` selects FP32 (0) or FP64 (1) data:
+ * val/x/y are float* or double* accordingly.  rowptr/colind are int32. ---- */
+
+/* y = A x with the CSR kernel of the solver (threads_per_row 0 = autotuned).
+ * Returns CQP_ERR_INVALID for bad sizes. */
+int cqp_spmv(int32_t precision, int64_t nrows, int64_t ncols, const int32_t* rowptr, const int32_t* colind,
+             const void* val, const void* x, void* y, int32_t threads_per_row, void* stream);
+
+/* out = Pi^M_K(r) blockwise (App. "cone-projections"): Euclidean when m is NULL,
+ * otherwise the projection in the diagonal metric M = diag(m).  Cone blocks as
+ * in cqp_setup but as device arrays.  r, m, out have n entries. */
+int cqp_project(int32_t precision, int64_t n, const cqp_cones* K_device, const void* r, const void* m, void* out,
+                void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,261 @@
+"""Python binding of the GB300 conic-QP PDHG library (include/cqp.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library
+libcqp_gb300.so.  The library must have been built (``build()``); importing
+the functions below without it raises instead of falling back to anything.
+
+Functions keep the C names: cqp_default_options, cqp_setup, cqp_solve,
+cqp_kkt, cqp_free, cqp_spmv, cqp_project, cqp_status_string, cqp_last_error.
+`Solver` wraps them for instance dicts (see the `instances` package layout):
+host numpy arrays, or torch CUDA tensors for device-resident inputs.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["build", "lib", "cqp_default_options", "cqp_setup", "cqp_solve", "cqp_kkt", "cqp_free", "cqp_spmv",
+           "cqp_project", "cqp_status_string", "cqp_last_error", "Solver", "CQPError", "STATUS"]
+
+CQP_OK, CQP_ITER_LIMIT, CQP_TIME_LIMIT = 0, 1, 2
+STATUS = {0: "converged", 1: "iteration limit", 2: "time limit", -1: "invalid input", -2: "CUDA error",
+          -3: "out of device memory", -4: "non-finite value", -5: "device wait expired", -6: "unsupported"}
+
+
+class CQPError(RuntimeError):
+    def __init__(self, code, msg=""):
+        super().__init__("cqp error %d (%s)%s" % (code, STATUS.get(code, "?"), (": " + msg) if msg else ""))
+        self.code = code
+
+
+class CSR(C.Structure):
+    _fields_ = [("nrows", C.c_int64), ("ncols", C.c_int64), ("nnz", C.c_int64),
+                ("rowptr", C.c_void_p), ("colind", C.c_void_p), ("val", C.c_void_p)]
+
+
+class QOp(C.Structure):
+    _fields_ = [("diag", C.c_void_p), ("P", CSR), ("rank", C.c_int64), ("R", C.c_void_p), ("D", C.c_void_p)]
+
+
+class Cones(C.Structure):
+    _fields_ = [("nblocks", C.c_int64), ("type", C.c_void_p), ("start", C.c_void_p), ("dim", C.c_void_p),
+                ("alpha", C.c_void_p)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("update", C.c_int32), ("rho", C.c_double),
+                ("ruiz_iters", C.c_int32), ("pc_alpha", C.c_double), ("bound_obj", C.c_int32),
+                ("eps0_in", C.c_double), ("gamma_in", C.c_double), ("eps_min_in", C.c_double),
+                ("jacobi", C.c_int32), ("max_inner", C.c_int32), ("force_inner", C.c_int32),
+                ("beta_s", C.c_double), ("beta_n", C.c_double), ("beta_a", C.c_double),
+                ("beta_I", C.c_double), ("K_P", C.c_double), ("K_I", C.c_double), ("K_D", C.c_double),
+                ("pid", C.c_int32), ("avg_epoch", C.c_int32),
+                ("tol", C.c_double), ("max_iter", C.c_int64), ("check_every", C.c_int32),
+                ("time_limit_s", C.c_double),
+                ("power_iters", C.c_int32), ("power_tol", C.c_double), ("step_factor", C.c_double),
+                ("input_on_device", C.c_int32), ("team", C.c_int32), ("threads", C.c_int32),
+                ("blocks_per_sm", C.c_int32), ("tpr_a", C.c_int32), ("tpr_at", C.c_int32),
+                ("launch_iters", C.c_int32), ("stream", C.c_void_p)]
+
+
+class KKTReport(C.Structure):
+    _fields_ = [("eps_p", C.c_double), ("eps_d", C.c_double), ("eps_g", C.c_double), ("rel_kkt", C.c_double),
+                ("pobj", C.c_double), ("dobj", C.c_double), ("norm_res_p", C.c_double), ("norm_res_d", C.c_double)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iters", C.c_int64), ("restarts", C.c_int64), ("inner_total", C.c_int64),
+                ("kernel_launches", C.c_int64), ("kkt", KKTReport), ("eta", C.c_double), ("norm_A", C.c_double),
+                ("omega", C.c_double), ("setup_ms", C.c_double), ("solve_ms", C.c_double)]
+
+
+_lib = None
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile the CUDA library for sm_103a (in-tree)."""
+    return _build.build(force=force, verbose=verbose)
+
+
+def lib():
+    """Load libcqp_gb300.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("libcqp_gb300.so is not built; run paper_2608_09159_gb300.build()")
+        L = C.CDLL(_build.LIB)
+        vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+        L.cqp_default_options.argtypes = [vp]
+        L.cqp_setup.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.cqp_solve.argtypes = [vp, vp, vp, vp, vp, i32, vp]
+        L.cqp_kkt.argtypes = [vp, vp, vp, i32, vp]
+        L.cqp_free.argtypes = [vp]
+        L.cqp_free.restype = None
+        L.cqp_status_string.argtypes = [C.c_int]
+        L.cqp_status_string.restype = C.c_char_p
+        L.cqp_last_error.argtypes = []
+        L.cqp_last_error.restype = C.c_char_p
+        L.cqp_spmv.argtypes = [i32, i64, i64, vp, vp, vp, vp, vp, i32, vp]
+        L.cqp_project.argtypes = [i32, i64, vp, vp, vp, vp, vp]
+        for f in ("cqp_default_options", "cqp_setup", "cqp_solve", "cqp_kkt", "cqp_spmv", "cqp_project"):
+            getattr(L, f).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def cqp_status_string(code: int) -> str:
+    return lib().cqp_status_string(code).decode()
+
+
+def cqp_last_error() -> str:
+    return lib().cqp_last_error().decode()
+
+
+def _check(rc, allow_positive=True):
+    if rc < 0 or (rc > 0 and not allow_positive):
+        raise CQPError(rc, cqp_last_error())
+    return rc
+
+
+def cqp_default_options(**kw) -> Options:
+    o = Options()
+    _check(lib().cqp_default_options(C.byref(o)))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def cqp_setup(A: CSR, Q, c, b, K: Cones, opt: Options):
+    h = C.c_void_p()
+    _check(lib().cqp_setup(C.byref(A), None if Q is None else C.byref(Q), c, b, C.byref(K), C.byref(opt), C.byref(h)))
+    return h
+
+
+def cqp_solve(h, x0, y0, x_out, y_out, on_device: int, res: Result) -> int:
+    return _check(lib().cqp_solve(h, x0, y0, x_out, y_out, on_device, C.byref(res)))
+
+
+def cqp_kkt(h, x, y, on_device: int, rep: KKTReport) -> int:
+    return _check(lib().cqp_kkt(h, x, y, on_device, C.byref(rep)))
+
+
+def cqp_free(h) -> None:
+    lib().cqp_free(h)
+
+
+def cqp_spmv(precision, nrows, ncols, rowptr, colind, val, x, y, threads_per_row=0, stream=None) -> int:
+    return _check(lib().cqp_spmv(precision, nrows, ncols, rowptr, colind, val, x, y, threads_per_row, stream))
+
+
+def cqp_project(precision, n, K_device: Cones, r, m, out, stream=None) -> int:
+    return _check(lib().cqp_project(precision, n, C.byref(K_device), r, m, out, stream))
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper over instance dicts
+# ---------------------------------------------------------------------------
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+class Solver:
+    """Owns a cqp_handle built from an instance dict.
+
+    Host numpy arrays are passed as host pointers.  With ``device=True`` the
+    arrays are first copied to torch CUDA tensors and passed as device pointers
+    (``input_on_device = 1``), i.e. the inputs are resident in HBM.
+    """
+
+    def __init__(self, inst, device: bool = False, **opts):
+        self._keep = []
+        self.inst = inst
+        self.n, self.m = int(inst["n"]), int(inst["m"])
+        conv = {
+            "a_rowptr": np.int64, "a_colind": np.int32, "a_val": np.float64, "c": np.float64, "b": np.float64,
+            "q_diag": np.float64, "q_R": np.float64, "q_D": np.float64, "p_rowptr": np.int64, "p_colind": np.int32,
+            "p_val": np.float64, "blk_type": np.int32, "blk_start": np.int64, "blk_dim": np.int64,
+            "blk_alpha": np.float64}
+        arrs = {}
+        for k, dt in conv.items():
+            v = inst.get(k)
+            if v is None:
+                arrs[k] = None
+                continue
+            if hasattr(v, "data_ptr"):
+                arrs[k] = v
+            else:
+                arrs[k] = np.ascontiguousarray(v, dtype=dt)
+        if device:
+            import torch
+            for k, v in list(arrs.items()):
+                if v is not None and not hasattr(v, "data_ptr"):
+                    arrs[k] = torch.from_numpy(v).cuda()
+            opts["input_on_device"] = 1
+        self._keep.append(arrs)
+        p = _ptr
+        self.A = CSR(self.m, self.n, int(inst["a_rowptr"][-1]), p(arrs["a_rowptr"]), p(arrs["a_colind"]),
+                     p(arrs["a_val"]))
+        R = arrs["q_R"]
+        rank = 0 if R is None else int(R.shape[0])
+        Pm = CSR(self.n, self.n, 0 if arrs["p_rowptr"] is None else int(inst["p_rowptr"][-1]),
+                 p(arrs["p_rowptr"]), p(arrs["p_colind"]), p(arrs["p_val"]))
+        self.Q = QOp(p(arrs["q_diag"]), Pm, rank, p(R), p(arrs["q_D"]))
+        self.K = Cones(int(len(inst["blk_type"])), p(arrs["blk_type"]), p(arrs["blk_start"]), p(arrs["blk_dim"]),
+                       p(arrs["blk_alpha"]))
+        self.opt = cqp_default_options(**opts)
+        self.h = cqp_setup(self.A, self.Q, p(arrs["c"]), p(arrs["b"]), self.K, self.opt)
+
+    def solve(self, x0=None, y0=None, out_device=False):
+        """Returns (x, y, result dict).  With out_device the outputs are torch CUDA tensors."""
+        res = Result()
+        if out_device:
+            import torch
+            x = torch.empty(self.n, dtype=torch.float64, device="cuda")
+            y = torch.empty(max(self.m, 1), dtype=torch.float64, device="cuda")
+            x0p = None if x0 is None else x0.data_ptr()
+            y0p = None if y0 is None else y0.data_ptr()
+            rc = cqp_solve(self.h, x0p, y0p, x.data_ptr(), y.data_ptr(), 1, res)
+            y = y[:self.m]
+        else:
+            x = np.zeros(self.n)
+            y = np.zeros(self.m)
+            x0 = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
+            y0 = None if y0 is None else np.ascontiguousarray(y0, dtype=np.float64)
+            rc = cqp_solve(self.h, _ptr(x0), _ptr(y0), _ptr(x), _ptr(y), 0, res)
+        return x, y, result_dict(res, rc)
+
+    def kkt(self, x, y):
+        rep = KKTReport()
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        cqp_kkt(self.h, _ptr(x), _ptr(y), 0, rep)
+        return {f: getattr(rep, f) for f, _ in KKTReport._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            cqp_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def result_dict(res: Result, rc: int):
+    d = {f: getattr(res, f) for f, _ in Result._fields_ if f != "kkt"}
+    d["kkt"] = {f: getattr(res.kkt, f) for f, _ in KKTReport._fields_}
+    d["rc"] = rc
+    return d

@@ -1,0 +1,807 @@
+// C ABI of the library (declarations and contracts in include/cqp.h).
+//
+// Host orchestration only: validation, layout permutation, transpose,
+// rescaling (Sec. 4.2.2), norm estimate (eq. practical-stepsizes), the launch
+// loop of the persistent solver kernel, unscaling.  Every step on the data
+// runs in the kernels of setup.cuh / solver_impl.cuh.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "cqp.h"
+#include "launch.h"
+#include "setup.cuh"
+#include "solver_impl.cuh"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct Fail {
+  int code;
+};
+
+void fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  throw Fail{code};
+}
+
+#define CK(x)                                                                                                 \
+  do {                                                                                                        \
+    cudaError_t e_ = (x);                                                                                     \
+    if (e_ != cudaSuccess) {                                                                                  \
+      fail(e_ == cudaErrorMemoryAllocation ? CQP_ERR_OOM : CQP_ERR_CUDA,                                      \
+           std::string(#x) + ": " + cudaGetErrorString(e_));                                                 \
+    }                                                                                                         \
+  } while (0)
+
+// device allocations owned by a handle
+struct Arena {
+  std::vector<void*> ptrs;
+  template <typename U>
+  U* alloc(int64_t n) {
+    void* p = nullptr;
+    const size_t bytes = (size_t)std::max<int64_t>(n, 1) * sizeof(U);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) fail(e == cudaErrorMemoryAllocation ? CQP_ERR_OOM : CQP_ERR_CUDA, "cudaMalloc failed");
+    ptrs.push_back(p);
+    return (U*)p;
+  }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+  ~Arena() { release(); }
+};
+
+// scoped temporary allocations (setup only)
+struct Temp {
+  Arena a;
+  template <typename U>
+  U* alloc(int64_t n) { return a.alloc<U>(n); }
+};
+
+double dev_dot(const double* a, const double* b, int64_t n, double* part, double* out, cudaStream_t st) {
+  const int nb = cqp::grid_for(n, cqp::kSetupThreads, 1024);
+  cqp::k_dot_partial<<<nb, cqp::kSetupThreads, 0, st>>>(n, a, b, part);
+  cqp::k_sum_partials<<<1, 32, 0, st>>>(nb, part, out);
+  double h = 0.0;
+  CK(cudaMemcpyAsync(&h, out, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return h;
+}
+
+// exclusive scan of n int32 counts into n+1 int32 offsets
+void dev_scan(const int32_t* in, int32_t* out, int64_t n, Temp& tmp, cudaStream_t st) {
+  const int64_t per = 1 << 16;
+  const int nb = (int)std::max<int64_t>(1, (n + per - 1) / per);
+  int64_t* tot = tmp.alloc<int64_t>(nb + 1);
+  cqp::k_scan_block_totals<<<nb, cqp::kSetupThreads, 0, st>>>(n, in, per, tot);
+  cqp::k_scan_totals<<<1, 32, 0, st>>>(nb, tot);
+  cqp::k_scan_apply<<<nb, cqp::kSetupThreads, 0, st>>>(n, in, per, tot, out);
+  CK(cudaGetLastError());
+}
+
+struct HandleBase {
+  virtual ~HandleBase() {}
+  virtual int solve(const double* x0, const double* y0, double* xo, double* yo, int on_dev, cqp_result* res) = 0;
+  virtual int kkt(const double* x, const double* y, int on_dev, cqp_kkt_report* rep) = 0;
+};
+
+// unscale + un-permute: out[perm[i]] = scale * v[i] / f[i]
+template <typename T>
+__global__ void k_unscale_unperm(int64_t n, const int64_t* perm, const T* v, const double* f, double scale, double* out) {
+  CQP_GRID_LOOP(i, n) out[perm ? perm[i] : i] = scale * (double)v[i] / f[i];
+}
+// permute + scale: v[i] = in[perm[i]] * f[i] / scale
+template <typename T>
+__global__ void k_perm_scale(int64_t n, const int64_t* perm, const double* in, const double* f, double scale, T* v) {
+  CQP_GRID_LOOP(i, n) v[i] = in ? T(in[perm ? perm[i] : i] * f[i] / scale) : T(0);
+}
+template <typename T>
+__global__ void k_copy_vec(int64_t n, const T* a, T* b) {
+  CQP_GRID_LOOP(i, n) b[i] = a[i];
+}
+template <typename T>
+__global__ void k_zero(int64_t n, T* a) {
+  CQP_GRID_LOOP(i, n) a[i] = T(0);
+}
+// new coordinate -> old coordinate through the segment table (new_start sorted)
+__global__ void k_build_perm(int64_t n, int64_t nseg, const int64_t* seg_new, const int64_t* seg_old, int64_t* perm,
+                             int64_t* iperm) {
+  CQP_GRID_LOOP(i, n) {
+    int64_t lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi + 1) >> 1;
+      if (seg_new[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    const int64_t o = seg_old[lo] + (i - seg_new[lo]);
+    perm[i] = o;
+    iperm[o] = i;
+  }
+}
+// sum of q^2 over [a, b) (cone coordinates: zero q means Euclidean projections)
+__global__ void k_sumsq_range(int64_t a, int64_t b, const double* q, double* out) {
+  double s = 0.0;
+  for (int64_t i = a + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < b; i += (int64_t)gridDim.x * blockDim.x)
+    s += q[i] * q[i];
+  s = cqp::warp_sum(s);
+  if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(out, s);
+}
+template <typename T>
+__global__ void k_rx_partial(int64_t k, int64_t n, const T* R, const T* x, double* out) {
+  // out[l] += sum_i R[l, i] x_i (deterministic enough for a one-off start value)
+  for (int64_t l = blockIdx.y; l < k; l += gridDim.y) {
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+      s += (double)R[l * n + i] * (double)x[i];
+    s = cqp::warp_sum(s);
+    if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(&out[l], s);
+  }
+}
+__global__ void k_state_set_th(cqp::State* S, const double* t, int k) {
+  if (threadIdx.x == 0 && blockIdx.x == 0)
+    for (int l = 0; l < k; ++l) S->t_h[l] = t[l];
+}
+
+int pow2_tpr(double mean) {
+  int t = 1;
+  while (t < 32 && t < mean) t <<= 1;
+  return t;
+}
+
+template <typename T>
+struct Handle : HandleBase {
+  cqp_options opt;
+  cudaStream_t st = nullptr;
+  int nsm = 152;
+  int64_t n = 0, m = 0, nnz = 0, k = 0, pnnz = 0;
+  Arena mem;
+  int64_t* perm = nullptr;
+  int64_t* iperm = nullptr;
+  cqp::Prob<T> P{};
+  cqp::Work<T> W{};
+  cqp::Opts O{};
+  cqp::State* S = nullptr;
+  unsigned* bar_count = nullptr;
+  int* dev_err = nullptr;
+  double* kkt_out = nullptr;
+  T* tmp_x = nullptr;
+  T* tmp_y = nullptr;
+  double eta = 0, normA = 0, omega0 = 1, setup_ms = 0;
+  bool grid = false;
+  int blocks = 1, threads = 512;
+
+  ~Handle() override { mem.release(); }
+
+  cqp::KernelArgs<T> args(long long budget) {
+    cqp::KernelArgs<T> a;
+    a.P = P;
+    a.W = W;
+    a.O = O;
+    a.S = S;
+    a.bar.count = bar_count;
+    a.bar.err = dev_err;
+    a.budget = budget;
+    return a;
+  }
+
+  void setup(const cqp_csr* A, const cqp_qop* Q, const double* c_in, const double* b_in, const cqp_cones* K,
+             const cqp_options& o) {
+    auto t0 = std::chrono::steady_clock::now();
+    opt = o;
+    st = (cudaStream_t)o.stream;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    m = A->nrows;
+    n = A->ncols;
+    nnz = A->nnz;
+    const bool on_dev = o.input_on_device != 0;
+    Temp tmp;
+    auto upload = [&](const void* src, size_t bytes) -> const void* {
+      if (!src) return nullptr;
+      if (on_dev) return src;
+      void* d = tmp.alloc<char>((int64_t)bytes);
+      CK(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, st));
+      return d;
+    };
+    auto fetch = [&](const void* src, size_t bytes, void* dst) {
+      if (on_dev) CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st));
+      else memcpy(dst, src, bytes);
+    };
+    // ---- cone partition (host; nblocks entries) --------------------------------
+    const int64_t nb = K->nblocks;
+    std::vector<int32_t> bt(nb);
+    std::vector<int64_t> bs(nb), bd(nb);
+    std::vector<double> ba(nb, 0.0);
+    if (nb > 0) {
+      fetch(K->type, nb * sizeof(int32_t), bt.data());
+      fetch(K->start, nb * sizeof(int64_t), bs.data());
+      fetch(K->dim, nb * sizeof(int64_t), bd.data());
+      if (K->alpha) fetch(K->alpha, nb * sizeof(double), ba.data());
+      CK(cudaStreamSynchronize(st));
+    }
+    int64_t pos = 0;
+    for (int64_t j = 0; j < nb; ++j) {
+      if (bs[j] != pos || bd[j] < 1) fail(CQP_ERR_INVALID, "cone blocks must partition 0..n-1 contiguously in order");
+      const int t = bt[j];
+      if (t < 0 || t > 5) fail(CQP_ERR_INVALID, "unknown cone type");
+      if (t == CQP_CONE_SOC && bd[j] < 2) fail(CQP_ERR_INVALID, "SOC block dimension < 2");
+      if (t == CQP_CONE_RSOC && bd[j] < 3) fail(CQP_ERR_INVALID, "RSOC block dimension < 3");
+      if ((t == CQP_CONE_EXP || t == CQP_CONE_POW) && bd[j] != 3) fail(CQP_ERR_INVALID, "EXP/POW block dimension != 3");
+      if (t == CQP_CONE_POW && !(ba[j] > 0.0 && ba[j] < 1.0)) fail(CQP_ERR_INVALID, "power cone alpha outside (0,1)");
+      pos += bd[j];
+    }
+    if (pos != n) fail(CQP_ERR_INVALID, "cone blocks do not cover 0..n-1");
+    // segment table in the new order: free, nonneg, soc, rsoc, exp, pow (stable within a type)
+    std::vector<int64_t> seg_new, seg_old;
+    std::vector<int64_t> soc_off{0}, rsoc_off{0};
+    std::vector<double> pow_al;
+    int64_t cnt[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t j = 0; j < nb; ++j) cnt[bt[j]] += bd[j];
+    int64_t base[6];
+    base[0] = 0;
+    for (int t = 1; t < 6; ++t) base[t] = base[t - 1] + cnt[t - 1];
+    int64_t fill[6];
+    for (int t = 0; t < 6; ++t) fill[t] = base[t];
+    for (int t = 0; t < 6; ++t)
+      for (int64_t j = 0; j < nb; ++j) {
+        if (bt[j] != t) continue;
+        seg_new.push_back(fill[t]);
+        seg_old.push_back(bs[j]);
+        if (t == CQP_CONE_SOC) soc_off.push_back(fill[t] + bd[j]);
+        if (t == CQP_CONE_RSOC) rsoc_off.push_back(fill[t] + bd[j]);
+        if (t == CQP_CONE_POW) pow_al.push_back(ba[j]);
+        fill[t] += bd[j];
+      }
+    soc_off[0] = base[2];
+    rsoc_off[0] = base[3];
+    // ---- sizes and options --------------------------------------------------------
+    if (m < 0 || n < 1 || nnz < 0 || nnz >= (int64_t(1) << 31)) fail(CQP_ERR_INVALID, "bad matrix sizes");
+    k = Q ? Q->rank : 0;
+    if (k < 0 || k > cqp::kMaxRank) fail(CQP_ERR_INVALID, "rank of R must be <= 64");
+    const bool has_p = Q && Q->P.rowptr;
+    pnnz = has_p ? Q->P.nnz : 0;
+    if (has_p && (Q->P.nrows != n || Q->P.ncols != n || pnnz >= (int64_t(1) << 31)))
+      fail(CQP_ERR_INVALID, "P must be n x n");
+    if (k > 0 && (!Q->R || !Q->D)) fail(CQP_ERR_INVALID, "rank > 0 needs R and D");
+    // ---- upload inputs (FP64) and validate ------------------------------------------
+    const int64_t* a_rp64 = (const int64_t*)upload(A->rowptr, (m + 1) * sizeof(int64_t));
+    const int32_t* a_ci_in = (const int32_t*)upload(A->colind, nnz * sizeof(int32_t));
+    const double* a_v_in = (const double*)upload(A->val, nnz * sizeof(double));
+    const double* c_d = (const double*)upload(c_in, n * sizeof(double));
+    const double* b_d = (const double*)upload(b_in, m * sizeof(double));
+    const double* qd_in = Q ? (const double*)upload(Q->diag, n * sizeof(double)) : nullptr;
+    const double* R_in = k > 0 ? (const double*)upload(Q->R, k * n * sizeof(double)) : nullptr;
+    const double* D_in = k > 0 ? (const double*)upload(Q->D, k * k * sizeof(double)) : nullptr;
+    const int64_t* p_rp64 = has_p ? (const int64_t*)upload(Q->P.rowptr, (n + 1) * sizeof(int64_t)) : nullptr;
+    const int32_t* p_ci_in = has_p ? (const int32_t*)upload(Q->P.colind, pnnz * sizeof(int32_t)) : nullptr;
+    const double* p_v_in = has_p ? (const double*)upload(Q->P.val, pnnz * sizeof(double)) : nullptr;
+    if (!c_d || (m > 0 && !b_d)) fail(CQP_ERR_INVALID, "c and b are required");
+    int* bad = tmp.alloc<int>(1);
+    CK(cudaMemsetAsync(bad, 0, sizeof(int), st));
+    cqp::k_validate_csr<<<cqp::grid_for(nnz + m), cqp::kSetupThreads, 0, st>>>(m, n, a_rp64, a_ci_in, a_v_in, bad);
+    cqp::k_validate_vec<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, c_d, bad);
+    if (m > 0) cqp::k_validate_vec<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, b_d, bad);
+    if (qd_in) cqp::k_validate_vec<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, qd_in, bad);
+    if (R_in) cqp::k_validate_vec<<<cqp::grid_for(k * n), cqp::kSetupThreads, 0, st>>>(k * n, R_in, bad);
+    if (has_p) cqp::k_validate_csr<<<cqp::grid_for(pnnz + n), cqp::kSetupThreads, 0, st>>>(n, n, p_rp64, p_ci_in, p_v_in, bad);
+    int hbad = 0;
+    CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    int64_t last_rp = 0;
+    CK(cudaMemcpyAsync(&last_rp, a_rp64 + m, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (hbad) fail(CQP_ERR_INVALID, "invalid or non-finite input data (flags " + std::to_string(hbad) + ")");
+    if (last_rp != nnz) fail(CQP_ERR_INVALID, "A.rowptr[m] != nnz");
+    double* part = tmp.alloc<double>(1024);
+    double* one = tmp.alloc<double>(1);
+    P.norm_b = m > 0 ? std::sqrt(dev_dot(b_d, nullptr, m, part, one, st)) : 0.0;
+    P.norm_c = std::sqrt(dev_dot(c_d, nullptr, n, part, one, st));
+    // ---- permutation ------------------------------------------------------------------
+    perm = mem.alloc<int64_t>(n);
+    iperm = mem.alloc<int64_t>(n);
+    {
+      int64_t* sn = tmp.alloc<int64_t>(seg_new.size());
+      int64_t* so = tmp.alloc<int64_t>(seg_old.size());
+      CK(cudaMemcpyAsync(sn, seg_new.data(), seg_new.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(so, seg_old.data(), seg_old.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+      k_build_perm<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, (int64_t)seg_new.size(), sn, so, perm, iperm);
+    }
+    // A with remapped columns, FP64 working values
+    int32_t* a_rp = mem.alloc<int32_t>(m + 1);
+    int32_t* a_ci = mem.alloc<int32_t>(nnz);
+    double* av = tmp.alloc<double>(nnz);
+    cqp::k_copy_rowptr32<<<cqp::grid_for(m + 1), cqp::kSetupThreads, 0, st>>>(m + 1, a_rp64, a_rp);
+    cqp::k_remap_cols<<<cqp::grid_for(nnz), cqp::kSetupThreads, 0, st>>>(nnz, iperm, a_ci_in, a_ci);
+    CK(cudaMemcpyAsync(av, a_v_in, nnz * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    double* cv = tmp.alloc<double>(n);
+    double* qv = tmp.alloc<double>(n);
+    double* bv = tmp.alloc<double>(std::max<int64_t>(m, 1));
+    cqp::k_gather<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, perm, c_d, cv, 0.0);
+    cqp::k_gather<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, perm, qd_in, qv, 0.0);
+    if (m > 0) CK(cudaMemcpyAsync(bv, b_d, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    double* Rv = nullptr;
+    double* Dv = nullptr;
+    if (k > 0) {
+      Rv = tmp.alloc<double>(k * n);
+      cqp::k_gather_cols<<<cqp::grid_for(k * n), cqp::kSetupThreads, 0, st>>>(k, n, perm, R_in, Rv);
+      Dv = mem.alloc<double>(k * k);
+      CK(cudaMemcpyAsync(Dv, D_in, k * k * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+    int32_t* p_rp = nullptr;
+    int32_t* p_ci = nullptr;
+    double* pv = nullptr;
+    if (has_p) {
+      int32_t* len = tmp.alloc<int32_t>(n);
+      p_rp = mem.alloc<int32_t>(n + 1);
+      p_ci = mem.alloc<int32_t>(pnnz);
+      pv = tmp.alloc<double>(pnnz);
+      cqp::k_row_lengths_perm<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, perm, p_rp64, len);
+      dev_scan(len, p_rp, n, tmp, st);
+      cqp::k_copy_rows_perm<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, perm, iperm, p_rp64, p_ci_in, p_v_in,
+                                                                                p_rp, p_ci, pv);
+    }
+    // ---- transpose of A (deterministic: every row of A' sorted by row of A) ------------
+    int32_t* t_rp = mem.alloc<int32_t>(n + 1);
+    int32_t* t_ci = mem.alloc<int32_t>(nnz);
+    int32_t* tmap = tmp.alloc<int32_t>(nnz);
+    {
+      int32_t* cntc = tmp.alloc<int32_t>(n);
+      CK(cudaMemsetAsync(cntc, 0, n * sizeof(int32_t), st));
+      cqp::k_count_cols<<<cqp::grid_for(nnz), cqp::kSetupThreads, 0, st>>>(nnz, a_ci, cntc);
+      dev_scan(cntc, t_rp, n, tmp, st);
+      int32_t* cursor = tmp.alloc<int32_t>(n);
+      CK(cudaMemcpyAsync(cursor, t_rp, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+      cqp::k_scatter_transpose<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp, a_ci, cursor, t_ci, tmap);
+      cqp::k_sort_segments<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, t_rp, t_ci, tmap);
+    }
+    // ---- rescaling (Table practical-defaults: Ruiz x10, Pock-Chambolle alpha = 1,
+    // cone-preserving aggregation, bound-objective) -------------------------------------
+    double* col = mem.alloc<double>(n);
+    double* row = mem.alloc<double>(std::max<int64_t>(m, 1));
+    double* colf = tmp.alloc<double>(n);
+    double* rowf = tmp.alloc<double>(std::max<int64_t>(m, 1));
+    cqp::k_fill<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, col, 1.0);
+    if (m > 0) cqp::k_fill<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, row, 1.0);
+    int64_t* d_soc = mem.alloc<int64_t>(soc_off.size());
+    int64_t* d_rsoc = mem.alloc<int64_t>(rsoc_off.size());
+    CK(cudaMemcpyAsync(d_soc, soc_off.data(), soc_off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_rsoc, rsoc_off.data(), rsoc_off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    const int64_t n_soc = (int64_t)soc_off.size() - 1, n_rsoc = (int64_t)rsoc_off.size() - 1;
+    const int64_t n_exp = cnt[4] / 3, n_pow = cnt[5] / 3;
+    auto aggregate = [&](int mode) {
+      if (n_soc) cqp::k_aggregate_blocks<<<cqp::grid_for(n_soc), cqp::kSetupThreads, 0, st>>>(n_soc, d_soc, 0, 0, mode, colf);
+      if (n_rsoc) cqp::k_aggregate_blocks<<<cqp::grid_for(n_rsoc), cqp::kSetupThreads, 0, st>>>(n_rsoc, d_rsoc, 0, 0, mode, colf);
+      if (n_exp) cqp::k_aggregate_blocks<<<cqp::grid_for(n_exp), cqp::kSetupThreads, 0, st>>>(n_exp, nullptr, base[4], 3, mode, colf);
+      if (n_pow) cqp::k_aggregate_blocks<<<cqp::grid_for(n_pow), cqp::kSetupThreads, 0, st>>>(n_pow, nullptr, base[5], 3, mode, colf);
+    };
+    auto scale_step = [&]() {
+      cqp::k_scale_matrix<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp, a_ci, av, rowf, colf);
+      cqp::k_mul<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, col, colf);
+      if (m > 0) cqp::k_mul<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, row, rowf);
+    };
+    for (int it = 0; it < o.ruiz_iters; ++it) {
+      cqp::k_col_stat<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, t_rp, tmap, av, 0, 0.0, colf);
+      if (m > 0) cqp::k_row_stat<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp, av, 0, 0.0, rowf);
+      cqp::k_sqrt_or_one<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, colf);
+      if (m > 0) cqp::k_sqrt_or_one<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, rowf);
+      aggregate(0);
+      scale_step();
+    }
+    if (o.pc_alpha >= 0.0) {
+      const double al = o.pc_alpha;
+      cqp::k_col_stat<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, t_rp, tmap, av, 1, 2.0 - al, colf);
+      if (m > 0) cqp::k_row_stat<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp, av, 1, al, rowf);
+      cqp::k_sqrt_or_one<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, colf);
+      if (m > 0) cqp::k_sqrt_or_one<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, rowf);
+      aggregate(1);
+      scale_step();
+    }
+    cqp::k_div<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, cv, col);
+    if (m > 0) cqp::k_div<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, bv, row);
+    cqp::k_div2<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, qv, col);
+    if (has_p) cqp::k_scale_sym<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, p_rp, p_ci, pv, col);
+    if (k > 0) cqp::k_scale_cols<<<cqp::grid_for(k * n), cqp::kSetupThreads, 0, st>>>(k, n, Rv, col);
+    double beta_b = 1.0, beta_c = 1.0;
+    if (o.bound_obj) {
+      beta_b = (m > 0 ? std::sqrt(dev_dot(bv, nullptr, m, part, one, st)) : 0.0) + 1.0;
+      beta_c = std::sqrt(dev_dot(cv, nullptr, n, part, one, st)) + 1.0;
+      if (m > 0) cqp::k_scal<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, bv, 1.0 / beta_b);
+      cqp::k_scal<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, cv, 1.0 / beta_c);
+      const double qs = beta_b / beta_c;
+      cqp::k_scal<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, qv, qs);
+      if (has_p) cqp::k_scal<<<cqp::grid_for(pnnz), cqp::kSetupThreads, 0, st>>>(pnnz, pv, qs);
+      if (k > 0) cqp::k_scal<<<1, 64, 0, st>>>(k * k, Dv, qs);
+    }
+    // full diagonal of Q~ (Jacobi metric) and conversion to the iterate precision
+    double* jdv = tmp.alloc<double>(n);
+    cqp::k_full_diag<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, qv, p_rp, p_ci, pv, k, Rv, Dv, jdv);
+    T* a_v = mem.alloc<T>(nnz);
+    T* t_v = mem.alloc<T>(nnz);
+    cqp::k_convert<T><<<cqp::grid_for(nnz), cqp::kSetupThreads, 0, st>>>(nnz, av, a_v);
+    cqp::k_gather_convert<T><<<cqp::grid_for(nnz), cqp::kSetupThreads, 0, st>>>(nnz, tmap, av, t_v);
+    T* cT = mem.alloc<T>(n);
+    T* bT = mem.alloc<T>(std::max<int64_t>(m, 1));
+    T* qT = mem.alloc<T>(n);
+    T* jT = mem.alloc<T>(n);
+    cqp::k_convert<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, cv, cT);
+    if (m > 0) cqp::k_convert<T><<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, bv, bT);
+    cqp::k_convert<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, qv, qT);
+    cqp::k_convert<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, jdv, jT);
+    T* RT = nullptr;
+    if (k > 0) {
+      RT = mem.alloc<T>(k * n);
+      cqp::k_convert<T><<<cqp::grid_for(k * n), cqp::kSetupThreads, 0, st>>>(k * n, Rv, RT);
+    }
+    T* pT = nullptr;
+    if (has_p) {
+      pT = mem.alloc<T>(pnnz);
+      cqp::k_convert<T><<<cqp::grid_for(pnnz), cqp::kSetupThreads, 0, st>>>(pnnz, pv, pT);
+    }
+    double* palpha = nullptr;
+    if (!pow_al.empty()) {
+      palpha = mem.alloc<double>(pow_al.size());
+      CK(cudaMemcpyAsync(palpha, pow_al.data(), pow_al.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    }
+    // Euclidean projections suffice when the diagonal Q vanishes on every cone coordinate
+    double qcone = 0.0;
+    {
+      double* acc = tmp.alloc<double>(1);
+      CK(cudaMemsetAsync(acc, 0, sizeof(double), st));
+      k_sumsq_range<<<cqp::grid_for(n - base[2]), cqp::kSetupThreads, 0, st>>>(base[2], n, qv, acc);
+      CK(cudaMemcpyAsync(&qcone, acc, sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    // ---- ||A~||_2 by power iteration on A~'A~ (reading: all-ones start, Rayleigh
+    // quotient, stop at power_tol relative change or power_iters) ---------------------------
+    {
+      double* v = tmp.alloc<double>(n);
+      double* w = tmp.alloc<double>(std::max<int64_t>(m, 1));
+      double* z = tmp.alloc<double>(n);
+      cqp::k_fill<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, v, 1.0 / std::sqrt((double)n));
+      double sig = 0.0;
+      for (int it = 0; it < o.power_iters && m > 0; ++it) {
+        cqp::k_spmv_simple<T><<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp, a_ci, a_v, v, w);
+        const double s_new = std::sqrt(dev_dot(w, nullptr, m, part, one, st));
+        cqp::k_spmv_simple<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, t_rp, t_ci, t_v, w, z);
+        const double zn = std::sqrt(dev_dot(z, nullptr, n, part, one, st));
+        if (zn == 0.0) { sig = s_new; break; }
+        cqp::k_scal<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, z, 1.0 / zn);
+        CK(cudaMemcpyAsync(v, z, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        const bool done = it > 0 && std::fabs(s_new - sig) <= o.power_tol * s_new;
+        sig = s_new;
+        if (done) break;
+      }
+      normA = sig;
+      eta = o.step_factor / (sig > 0.0 ? sig : 1.0);
+      const double cn = std::sqrt(dev_dot(cv, nullptr, n, part, one, st));
+      const double bn = m > 0 ? std::sqrt(dev_dot(bv, nullptr, m, part, one, st)) : 0.0;
+      omega0 = (cn > 1e-10 && bn > 1e-10) ? cn / bn : 1.0;   // reading: ||c~||/||b~||
+    }
+    // ---- problem descriptor ----------------------------------------------------------------
+    P.n = n; P.m = m;
+    P.a_rp = a_rp; P.a_ci = a_ci; P.a_v = a_v;
+    P.t_rp = t_rp; P.t_ci = t_ci; P.t_v = t_v;
+    P.qd = qT; P.jd = jT; P.k = (int)k; P.R = RT; P.D = Dv;
+    P.p_rp = p_rp; P.p_ci = p_ci; P.p_v = pT;
+    P.c = cT; P.b = bT; P.col = col; P.row = row; P.beta_b = beta_b; P.beta_c = beta_c;
+    P.n_free = cnt[0]; P.n_nonneg = cnt[1];
+    P.n_soc = n_soc; P.soc_off = d_soc; P.n_rsoc = n_rsoc; P.rsoc_off = d_rsoc;
+    P.n_exp = n_exp; P.exp_base = base[4]; P.n_pow = n_pow; P.pow_base = base[5]; P.pow_alpha = palpha;
+    if (has_p) P.qmode = cqp::kQSparse;
+    else if (k > 0 || o.force_inner) P.qmode = cqp::kQLowRank;
+    else P.qmode = cqp::kQDiag;
+    P.euclid_cones = (P.qmode == cqp::kQDiag && qcone == 0.0) ? 1 : 0;
+    P.tpr_a = o.tpr_a > 0 ? o.tpr_a : pow2_tpr(m > 0 ? (double)nnz / (double)m : 1.0);
+    P.tpr_t = o.tpr_at > 0 ? o.tpr_at : pow2_tpr((double)std::max(nnz, pnnz) / (double)n);
+    // ---- work buffers and state -------------------------------------------------------------
+    const int64_t mm = std::max<int64_t>(m, 1);
+    for (int i = 0; i < 2; ++i) {
+      W.hx[i] = mem.alloc<T>(n); W.hy[i] = mem.alloc<T>(mm); W.wx[i] = mem.alloc<T>(n);
+      W.u[i] = mem.alloc<T>(n);
+      W.g[i] = P.qmode == cqp::kQSparse ? mem.alloc<T>(n) : nullptr;
+    }
+    W.ax = mem.alloc<T>(n); W.ay = mem.alloc<T>(mm); W.wy = mem.alloc<T>(mm); W.v = mem.alloc<T>(n);
+    W.avx = o.update == 1 ? mem.alloc<T>(n) : nullptr;
+    W.avy = o.update == 1 ? mem.alloc<T>(mm) : nullptr;
+    W.mbuf = mem.alloc<T>(n);
+    W.sd = mem.alloc<double>(n);
+    // team
+    threads = o.threads > 0 ? o.threads : 512;
+    const int64_t size = n + m;
+    grid = o.team == 1 || (o.team == 0 && size > 40000);
+    if (grid) {
+      const int per = cqp::pdhg_blocks_per_sm<T>(threads);
+      if (per < 1) fail(CQP_ERR_UNSUPPORTED, "solver kernel does not fit on an SM with this block size");
+      const int want = o.blocks_per_sm > 0 ? std::min(o.blocks_per_sm, per) : 1;
+      blocks = nsm * want;
+    } else {
+      blocks = 1;
+    }
+    W.part = mem.alloc<double>((int64_t)cqp::kMaxSlots * blocks);
+    S = mem.alloc<cqp::State>(1);
+    bar_count = mem.alloc<unsigned>(1);
+    dev_err = mem.alloc<int>(1);
+    kkt_out = mem.alloc<double>(8);
+    tmp_x = mem.alloc<T>(n);
+    tmp_y = mem.alloc<T>(mm);
+    O.rho = o.rho; O.eps_min_in = o.eps_min_in; O.gamma_in = o.gamma_in; O.tol = o.tol;
+    O.beta_s = o.beta_s; O.beta_n = o.beta_n; O.beta_a = o.beta_a;
+    O.beta_I = o.beta_I; O.K_P = o.K_P; O.K_I = o.K_I; O.K_D = o.K_D;
+    O.max_iter = o.max_iter; O.check_every = std::max(1, o.check_every); O.max_inner = std::max(1, o.max_inner);
+    O.jacobi = o.jacobi; O.pid = o.pid; O.update = o.update; O.avg_epoch = std::max(1, o.avg_epoch);
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+
+  int solve(const double* x0, const double* y0, double* xo, double* yo, int on_dev, cqp_result* res) override {
+    auto t0 = std::chrono::steady_clock::now();
+    const int64_t mm = std::max<int64_t>(m, 1);
+    Temp tmp;
+    const double* dx0 = x0;
+    const double* dy0 = y0;
+    if (!on_dev) {
+      if (x0) { double* d = tmp.alloc<double>(n); CK(cudaMemcpyAsync(d, x0, n * 8, cudaMemcpyHostToDevice, st)); dx0 = d; }
+      if (y0 && m > 0) { double* d = tmp.alloc<double>(m); CK(cudaMemcpyAsync(d, y0, m * 8, cudaMemcpyHostToDevice, st)); dy0 = d; }
+    }
+    // scaled start: x~ = col x / beta_b (permuted), y~ = row y / beta_c
+    k_perm_scale<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, perm, dx0, P.col, P.beta_b, W.hx[0]);
+    if (m > 0) k_perm_scale<T><<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, nullptr, dy0, P.row, P.beta_c, W.hy[0]);
+    k_copy_vec<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, W.hx[0], W.ax);
+    k_copy_vec<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, W.hx[0], W.wx[0]);
+    k_copy_vec<T><<<cqp::grid_for(mm), cqp::kSetupThreads, 0, st>>>(mm, W.hy[0], W.ay);
+    k_copy_vec<T><<<cqp::grid_for(mm), cqp::kSetupThreads, 0, st>>>(mm, W.hy[0], W.wy);
+    if (W.avx) {
+      k_zero<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, W.avx);
+      k_zero<T><<<cqp::grid_for(mm), cqp::kSetupThreads, 0, st>>>(mm, W.avy);
+    }
+    cqp::State hs;
+    memset(&hs, 0, sizeof(hs));
+    hs.omega = omega0;
+    hs.eta = eta;
+    hs.tau = eta / omega0;
+    hs.sigma = eta * omega0;
+    hs.eps_in = opt.eps0_in;
+    CK(cudaMemcpyAsync(S, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
+    if (k > 0 && x0) {
+      double* t = tmp.alloc<double>(k);
+      CK(cudaMemsetAsync(t, 0, k * sizeof(double), st));
+      k_rx_partial<T><<<dim3(cqp::grid_for(n, 256, 256), (unsigned)k), 256, 0, st>>>(k, n, P.R, W.hx[0], t);
+      k_state_set_th<<<1, 32, 0, st>>>(S, t, (int)k);
+    }
+    CK(cudaMemsetAsync(dev_err, 0, sizeof(int), st));
+    long long per_launch = opt.launch_iters > 0 ? opt.launch_iters : (long long)O.check_every * (grid ? 4 : 16);
+    int launches = 0;
+    int status = CQP_ITER_LIMIT;
+    cqp::State back;
+    for (;;) {
+      CK(cudaMemsetAsync(bar_count, 0, sizeof(unsigned), st));
+      CK(cqp::launch_pdhg<T>(args(per_launch), grid, blocks, threads, st));
+      ++launches;
+      CK(cudaMemcpyAsync(&back, S, sizeof(back), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (back.err == cqp::kErrBarrier) { status = CQP_ERR_WAIT; break; }
+      if (back.err == cqp::kErrNumeric) { status = CQP_ERR_NUMERICAL; break; }
+      if (back.status == 1) { status = CQP_OK; break; }
+      if (back.status == 2 || back.ktot >= O.max_iter) { status = CQP_ITER_LIMIT; break; }
+      const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (opt.time_limit_s > 0 && el > opt.time_limit_s) { status = CQP_TIME_LIMIT; break; }
+    }
+    // final candidate (average for the averaged variant), unscaled and un-permuted
+    const T* fx = opt.update == 1 ? W.avx : W.wx[back.wb];
+    const T* fy = opt.update == 1 ? W.avy : W.wy;
+    double* ox = tmp.alloc<double>(n);
+    double* oy = tmp.alloc<double>(mm);
+    k_unscale_unperm<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, perm, fx, P.col, P.beta_b, ox);
+    if (m > 0) k_unscale_unperm<T><<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, nullptr, fy, P.row, P.beta_c, oy);
+    if (xo) CK(cudaMemcpyAsync(xo, ox, n * 8, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    if (yo && m > 0) CK(cudaMemcpyAsync(yo, oy, m * 8, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (res) {
+      memset(res, 0, sizeof(*res));
+      res->status = status;
+      res->iters = back.ktot;
+      res->restarts = back.restarts;
+      res->inner_total = back.inner_total;
+      res->kernel_launches = launches;
+      res->kkt.eps_p = back.kkt[0]; res->kkt.eps_d = back.kkt[1]; res->kkt.eps_g = back.kkt[2];
+      res->kkt.rel_kkt = back.kkt[3]; res->kkt.pobj = back.kkt[4]; res->kkt.dobj = back.kkt[5];
+      res->kkt.norm_res_p = back.kkt[6]; res->kkt.norm_res_d = back.kkt[7];
+      res->eta = eta;
+      res->norm_A = normA;
+      res->omega = back.omega;
+      res->setup_ms = setup_ms;
+      res->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return status;
+  }
+
+  int kkt(const double* x, const double* y, int on_dev, cqp_kkt_report* rep) override {
+    const int64_t mm = std::max<int64_t>(m, 1);
+    Temp tmp;
+    const double* dx = x;
+    const double* dy = y;
+    if (!on_dev) {
+      double* d = tmp.alloc<double>(n);
+      CK(cudaMemcpyAsync(d, x, n * 8, cudaMemcpyHostToDevice, st));
+      dx = d;
+      double* e = tmp.alloc<double>(mm);
+      if (m > 0) CK(cudaMemcpyAsync(e, y, m * 8, cudaMemcpyHostToDevice, st));
+      dy = e;
+    }
+    k_perm_scale<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, perm, dx, P.col, P.beta_b, tmp_x);
+    if (m > 0) k_perm_scale<T><<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, nullptr, dy, P.row, P.beta_c, tmp_y);
+    CK(cudaMemsetAsync(bar_count, 0, sizeof(unsigned), st));
+    CK(cudaMemsetAsync(dev_err, 0, sizeof(int), st));
+    CK(cqp::launch_kkt<T>(args(0), tmp_x, tmp_y, kkt_out, grid, blocks, threads, st));
+    double h[8];
+    CK(cudaMemcpyAsync(h, kkt_out, sizeof(h), cudaMemcpyDeviceToHost, st));
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (herr) return CQP_ERR_WAIT;
+    rep->eps_p = h[0]; rep->eps_d = h[1]; rep->eps_g = h[2]; rep->rel_kkt = h[3];
+    rep->pobj = h[4]; rep->dobj = h[5]; rep->norm_res_p = h[6]; rep->norm_res_d = h[7];
+    return std::isfinite(h[3]) ? CQP_OK : CQP_ERR_NUMERICAL;
+  }
+};
+
+template <typename F>
+int guarded(F f) {
+  try {
+    return f();
+  } catch (const Fail& e) {
+    return e.code;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return CQP_ERR_CUDA;
+  } catch (...) {
+    g_last_error = "unknown error";
+    return CQP_ERR_CUDA;
+  }
+}
+
+}  // namespace
+
+struct cqp_handle {
+  HandleBase* impl;
+};
+
+extern "C" {
+
+int cqp_default_options(cqp_options* o) {
+  if (!o) return CQP_ERR_INVALID;
+  memset(o, 0, sizeof(*o));
+  o->precision = 0;
+  o->update = 0;
+  o->rho = 1.0;
+  o->ruiz_iters = 10;
+  o->pc_alpha = 1.0;
+  o->bound_obj = 1;
+  o->eps0_in = 1e-3;
+  o->gamma_in = 5e-4;
+  o->eps_min_in = 1e-9;
+  o->jacobi = 1;
+  o->max_inner = 1000;
+  o->force_inner = 0;
+  o->beta_s = 0.2;
+  o->beta_n = 0.8;
+  o->beta_a = 0.36;
+  o->beta_I = 0.3;
+  o->K_P = 0.99;
+  o->K_I = 0.01;
+  o->K_D = 0.0;
+  o->pid = 1;
+  o->avg_epoch = 64;
+  o->tol = 1e-4;
+  o->max_iter = 100000;
+  o->check_every = 64;
+  o->time_limit_s = 0.0;
+  o->power_iters = 200;
+  o->power_tol = 1e-6;
+  o->step_factor = 0.998;
+  return CQP_OK;
+}
+
+int cqp_setup(const cqp_csr* A, const cqp_qop* Q, const double* c, const double* b, const cqp_cones* K,
+              const cqp_options* opt, cqp_handle** out) {
+  if (!out) return CQP_ERR_INVALID;
+  *out = nullptr;
+  if (!A || !K || !c) return CQP_ERR_INVALID;
+  cqp_options o;
+  if (opt) o = *opt; else cqp_default_options(&o);
+  return guarded([&]() {
+    HandleBase* h = nullptr;
+    if (o.precision == 1) {
+      auto* hh = new Handle<double>();
+      try { hh->setup(A, Q, c, b, K, o); } catch (...) { delete hh; throw; }
+      h = hh;
+    } else {
+      auto* hh = new Handle<float>();
+      try { hh->setup(A, Q, c, b, K, o); } catch (...) { delete hh; throw; }
+      h = hh;
+    }
+    *out = new cqp_handle{h};
+    return CQP_OK;
+  });
+}
+
+int cqp_solve(cqp_handle* h, const double* x0, const double* y0, double* x_out, double* y_out, int32_t on_device,
+              cqp_result* res) {
+  if (!h || !h->impl) return CQP_ERR_INVALID;
+  return guarded([&]() { return h->impl->solve(x0, y0, x_out, y_out, on_device, res); });
+}
+
+int cqp_kkt(cqp_handle* h, const double* x, const double* y, int32_t on_device, cqp_kkt_report* rep) {
+  if (!h || !h->impl || !x || !rep) return CQP_ERR_INVALID;
+  return guarded([&]() { return h->impl->kkt(x, y, on_device, rep); });
+}
+
+void cqp_free(cqp_handle* h) {
+  if (!h) return;
+  delete h->impl;
+  delete h;
+}
+
+const char* cqp_status_string(int s) {
+  switch (s) {
+    case CQP_OK: return "converged";
+    case CQP_ITER_LIMIT: return "iteration limit";
+    case CQP_TIME_LIMIT: return "time limit";
+    case CQP_ERR_INVALID: return "invalid input";
+    case CQP_ERR_CUDA: return "CUDA error";
+    case CQP_ERR_OOM: return "out of device memory";
+    case CQP_ERR_NUMERICAL: return "non-finite value in a reduction";
+    case CQP_ERR_WAIT: return "a bounded device-side wait expired";
+    case CQP_ERR_UNSUPPORTED: return "unsupported option combination";
+    default: return "unknown status";
+  }
+}
+
+const char* cqp_last_error(void) { return g_last_error.c_str(); }
+
+int cqp_spmv(int32_t precision, int64_t nrows, int64_t ncols, const int32_t* rowptr, const int32_t* colind,
+             const void* val, const void* x, void* y, int32_t threads_per_row, void* stream) {
+  if (nrows < 0 || ncols < 0 || !rowptr || (nrows > 0 && (!colind || !val || !x || !y))) return CQP_ERR_INVALID;
+  int tpr = threads_per_row;
+  if (tpr != 0 && tpr != 1 && tpr != 2 && tpr != 4 && tpr != 8 && tpr != 16 && tpr != 32) return CQP_ERR_INVALID;
+  return guarded([&]() {
+    if (tpr == 0) {
+      int32_t last = 0;
+      CK(cudaMemcpy(&last, rowptr + nrows, sizeof(int32_t), cudaMemcpyDeviceToHost));
+      tpr = pow2_tpr(nrows > 0 ? (double)last / (double)nrows : 1.0);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (nrows == 0) return CQP_OK;
+    if (precision == 1)
+      CK(cqp::launch_spmv<double>(nrows, rowptr, colind, (const double*)val, (const double*)x, (double*)y, tpr, st));
+    else
+      CK(cqp::launch_spmv<float>(nrows, rowptr, colind, (const float*)val, (const float*)x, (float*)y, tpr, st));
+    CK(cudaStreamSynchronize(st));
+    return CQP_OK;
+  });
+}
+
+int cqp_project(int32_t precision, int64_t n, const cqp_cones* K, const void* r, const void* m, void* out, void* stream) {
+  if (!K || !r || !out || n < 0) return CQP_ERR_INVALID;
+  return guarded([&]() {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (K->nblocks == 0) return CQP_OK;
+    if (precision == 1)
+      CK(cqp::launch_project<double>(K->nblocks, K->type, K->start, K->dim, K->alpha, (const double*)r,
+                                     (const double*)m, (double*)out, n, st));
+    else
+      CK(cqp::launch_project<float>(K->nblocks, K->type, K->start, K->dim, K->alpha, (const float*)r,
+                                    (const float*)m, (float*)out, n, st));
+    CK(cudaStreamSynchronize(st));
+    return CQP_OK;
+  });
+}
+
+}  // extern "C"

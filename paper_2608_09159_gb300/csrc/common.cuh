@@ -1,0 +1,186 @@
+// Device-side building blocks shared by the kernels of the library:
+// warp/block reductions, the bounded-spin grid barrier and the "team" that a
+// solver phase runs on (the whole GPU as one cooperative grid, or one CTA).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cqp {
+
+constexpr int kWarp = 32;
+constexpr int kMaxRank = 64;        // largest low-rank factor R supported (rank x n)
+constexpr int kMaxSlots = 96;       // FP64 reduction slots per phase
+
+// device-side error codes written to SolverState::err
+enum DevErr : int { kErrNone = 0, kErrBarrier = 1, kErrNumeric = 2 };
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+// sum over aligned groups of G lanes (G a power of two <= 32); every lane of a group gets the group sum
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Sum NS per-thread values over the block; results land in out[0..NS) (shared),
+// visible to all threads after the call.  scratch: NS * (blockDim/32) doubles.
+template <int NS>
+__device__ __forceinline__ void block_sum(double (&v)[NS], double* scratch, double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    double t = warp_sum(v[s]);
+    if (lane == 0) scratch[s * nw + warp] = t;
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < NS; s += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += scratch[s * nw + w];
+    out[s] = t;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Teams.  A solver phase is written once against this interface:
+//   nb(), bid()            number of blocks in the team and this block's rank
+//   sync()                 team-wide barrier (returns false if a bounded wait expired)
+//   publish(slot, v)       block total v of reduction slot `slot` (thread 0 only)
+//   gather(nslots, out)    after sync(): out[s] = sum over blocks of slot s, in a fixed
+//                          order, identical on every block (shared-memory `out`)
+// ---------------------------------------------------------------------------
+
+struct GridBarrier {
+  unsigned* count;   // zeroed by the host before every launch
+  int* err;          // device error word
+};
+
+// Whole-GPU team: the kernel is launched cooperatively so all blocks are
+// co-resident; the barrier spins with an iteration limit and reports expiry
+// through *err instead of hanging.
+struct GridTeam {
+  GridBarrier bar;
+  double* part;      // [kMaxSlots][gridDim.x] block partials in global memory
+  unsigned target;
+  int failed;
+
+  __device__ void init(GridBarrier b, double* p) {
+    bar = b;
+    part = p;
+    target = 0;
+    failed = 0;
+  }
+  __device__ __forceinline__ int nb() const { return gridDim.x; }
+  __device__ __forceinline__ int bid() const { return blockIdx.x; }
+  __device__ bool sync() {
+    __syncthreads();
+    target += gridDim.x;
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(bar.count, 1u);
+      long long spins = 0;
+      while ((int)(ld_acquire_u32(bar.count) - target) < 0) {
+        if (++spins > (1ll << 24) || *(volatile int*)bar.err != 0) {
+          atomicCAS(bar.err, 0, (int)kErrBarrier);
+          break;
+        }
+      }
+      __threadfence();
+    }
+    __syncthreads();
+    failed = *(volatile int*)bar.err != 0;
+    return !failed;
+  }
+  __device__ __forceinline__ void publish(int slot, double v) { part[slot * gridDim.x + blockIdx.x] = v; }
+  // one warp per slot, lanes stride over blocks, then a fixed-order shuffle tree
+  __device__ void gather(int nslots, double* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int s = warp; s < nslots; s += nw) {
+      double t = 0.0;
+      for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(&part[s * gridDim.x + b]);
+      t = warp_sum(t);
+      if (lane == 0) out[s] = t;
+    }
+    __syncthreads();
+  }
+};
+
+// One-CTA team: barriers are __syncthreads and block totals are final.
+struct CtaTeam {
+  double* part;      // shared memory, kMaxSlots
+  int failed;
+  __device__ void init(double* p) {
+    part = p;
+    failed = 0;
+  }
+  __device__ __forceinline__ int nb() const { return 1; }
+  __device__ __forceinline__ int bid() const { return 0; }
+  __device__ __forceinline__ bool sync() {
+    __syncthreads();
+    return true;
+  }
+  __device__ __forceinline__ void publish(int slot, double v) { part[slot] = v; }
+  __device__ void gather(int nslots, double* out) {
+    __syncthreads();
+    for (int s = threadIdx.x; s < nslots; s += blockDim.x) out[s] = part[s];
+    __syncthreads();
+  }
+};
+
+// [lo, hi) share of `count` items for block b of nb
+__device__ __forceinline__ void split_range(int64_t count, int b, int nb, int64_t& lo, int64_t& hi) {
+  lo = (count * b) / nb;
+  hi = (count * (b + 1)) / nb;
+}
+
+// first row r with rowptr[r] >= target (rowptr non-decreasing, nrows+1 entries)
+__device__ __forceinline__ int64_t lower_bound_rows(const int* rowptr, int64_t nrows, int64_t target) {
+  int64_t lo = 0, hi = nrows;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if ((int64_t)rowptr[mid] < target) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// rows of a CSR matrix shared among nb blocks with (almost) equal nnz + row count
+__device__ __forceinline__ void split_rows_by_nnz(const int* rowptr, int64_t nrows, int b, int nb, int64_t& lo,
+                                                  int64_t& hi) {
+  const int64_t nnz = rowptr[nrows];
+  const int64_t work = nnz + nrows;
+  // balance nnz + rows: search on rowptr[r] + r
+  auto find = [&](int64_t target) {
+    int64_t l = 0, h = nrows;
+    while (l < h) {
+      int64_t mid = (l + h) >> 1;
+      if ((int64_t)rowptr[mid] + mid < target) l = mid + 1; else h = mid;
+    }
+    return l;
+  };
+  lo = b == 0 ? 0 : find((work * b) / nb);
+  hi = b == nb - 1 ? nrows : find((work * (b + 1)) / nb);
+}
+
+}  // namespace cqp

@@ -1,0 +1,517 @@
+// Cone projections on the GPU (paper App. "cone-projections", Table
+// "cone-projection-methods").  Conventions of the standard form (Sec. 4):
+//   SOC  (v, t), t last;  RSOC (v, s, t), ||v||^2 <= 2 s t, s, t last;
+//   EXP  (r, s, t), s exp(r/s) <= t;  POW (r, s, t), r^a s^(1-a) >= |t|.
+// Metric projections Pi^M_K(z) = argmin_{u in K} ||u - z||_M^2 with diagonal M.
+//
+// SOC / RSOC blocks are projected by one warp: the block's coordinates are
+// strided over the lanes, norms and root-function sums are warp reductions,
+// and the scalar root iteration runs redundantly (identically) on every lane.
+// EXP / POW blocks are projected by one thread in FP64.
+#pragma once
+
+#include <cfloat>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace cqp {
+
+template <typename T> struct Tol;
+template <> struct Tol<float> { static constexpr double rel = 2e-7; };
+template <> struct Tol<double> { static constexpr double rel = 4e-16; };
+
+// --------------------------------------------------------------------------
+// Second-order cone, Euclidean (App. A.2, eq. soc-euclidean-projection).
+// x holds the d coordinates (v_1..v_{d-1}, t); projected in place.
+// --------------------------------------------------------------------------
+template <typename T>
+__device__ __noinline__ void warp_soc_euclid(T* x, int d, int lane) {
+  double s = 0.0;
+  for (int i = lane; i < d - 1; i += 32) s += (double)x[i] * (double)x[i];
+  const double t = (double)x[d - 1];
+  s = warp_sum(s);
+  const double a = sqrt(s);
+  if (a <= t) return;
+  if (a <= -t) {
+    for (int i = lane; i < d; i += 32) x[i] = T(0);
+    __syncwarp();
+    return;
+  }
+  const double coef = (a + t) / (2.0 * a);
+  for (int i = lane; i < d - 1; i += 32) x[i] = T(coef * (double)x[i]);
+  if (lane == 0) x[d - 1] = T(0.5 * (a + t));
+  __syncwarp();
+}
+
+// --------------------------------------------------------------------------
+// Second-order cone in the metric M = diag(m) (App. A.2, eq.
+// soc-metric-projection): v_i(l) = m_i z_i/(m_i + l), t(l) = m_t z_t/(m_t - l),
+// root of f(l) = ||v(l)||^2 - t(l)^2.  Bracket: (0, m_t) when z_t > 0; (m_t, l_U]
+// when z_t < 0 with l_U = (A m_t + B m_max)/(A - B), A = ||M_v z_v||,
+// B = m_t |z_t| (f(l_U) >= 0 follows from ||v||^2 >= A^2/(m_max + l)^2).
+// Singular z_t = 0: l = m_t, t = ||v||.  Newton steps kept inside the bracket.
+// --------------------------------------------------------------------------
+template <typename T>
+__device__ __noinline__ void warp_soc_metric(T* x, const T* m, int d, int lane) {
+  const int nv = d - 1;
+  double v2 = 0.0, A2 = 0.0, mmax = 0.0;
+  for (int i = lane; i < nv; i += 32) {
+    const double xi = (double)x[i], mi = (double)m[i];
+    v2 += xi * xi;
+    A2 += (mi * xi) * (mi * xi);
+    mmax = fmax(mmax, mi);
+  }
+  const double zt = (double)x[nv], mt = (double)m[nv];
+  v2 = warp_sum(v2);
+  A2 = warp_sum(A2);
+  mmax = warp_max(mmax);
+  if (sqrt(v2) <= zt) return;                          // z in K
+  const double A = sqrt(A2), B = mt * fabs(zt);
+  if (zt <= 0.0 && A <= B) {                           // -Mz in K* = K
+    for (int i = lane; i < d; i += 32) x[i] = T(0);
+    __syncwarp();
+    return;
+  }
+  double lam;
+  if (zt == 0.0) {
+    lam = mt;
+  } else {
+    double lo, hi;
+    if (zt > 0.0) { lo = 0.0; hi = mt; }
+    else { lo = mt; hi = (A * mt + B * mmax) / (A - B) * (1.0 + 1e-12) + 1e-300; }
+    const double bt = (mt * zt) * (mt * zt);
+    // Newton iteration started at the bracket midpoint
+    lam = 0.5 * (lo + hi);
+    for (int it = 0; it < 200; ++it) {
+      // f and f' (the element sums in T precision, accumulated in FP64)
+      double s2 = 0.0, s3 = 0.0;
+      for (int i = lane; i < nv; i += 32) {
+        const T mi = m[i], xi = x[i];
+        const T ai = (mi * xi) * (mi * xi);
+        const T den = mi + T(lam);
+        const T q = ai / (den * den);
+        s2 += (double)q;
+        s3 += (double)(q / den);
+      }
+      s2 = warp_sum(s2);
+      s3 = warp_sum(s3);
+      const double dm = mt - lam;
+      const double f = s2 - bt / (dm * dm);
+      const double fp = -2.0 * s3 - 2.0 * bt / (dm * dm * dm);
+      if (f > 0.0) lo = lam; else hi = lam;
+      double nx = (fp != 0.0) ? lam - f / fp : 0.5 * (lo + hi);
+      if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
+      const double step = fabs(nx - lam);
+      lam = nx;
+      if (f == 0.0 || step <= Tol<T>::rel * fmax(lam, 1e-300) || (hi - lo) <= Tol<T>::rel * fmax(lam, 1e-300))
+        break;
+    }
+  }
+  double vv = 0.0;
+  for (int i = lane; i < nv; i += 32) {
+    const double mi = (double)m[i];
+    const double vi = mi * (double)x[i] / (mi + lam);
+    x[i] = T(vi);
+    vv += vi * vi;
+  }
+  vv = warp_sum(vv);
+  if (lane == 0) x[nv] = T(sqrt(vv));
+  __syncwarp();
+}
+
+// --------------------------------------------------------------------------
+// Rotated SOC, Euclidean: U^{-1} Pi_soc(U z), U(v,s,t) = ((v,(s-t)/sqrt2),(s+t)/sqrt2)
+// (App. A.3, eq. rsoc-via-soc).
+// --------------------------------------------------------------------------
+template <typename T>
+__device__ __noinline__ void warp_rsoc_euclid(T* x, int d, int lane) {
+  const int nv = d - 2;
+  const double h = 0.70710678118654752440;
+  double s = 0.0;
+  for (int i = lane; i < nv; i += 32) s += (double)x[i] * (double)x[i];
+  const double zs = (double)x[nv], zt = (double)x[nv + 1];
+  s = warp_sum(s);
+  const double w = (zs - zt) * h, tt = (zs + zt) * h;
+  const double a = sqrt(s + w * w);
+  if (a <= tt) return;
+  if (a <= -tt) {
+    for (int i = lane; i < d; i += 32) x[i] = T(0);
+    __syncwarp();
+    return;
+  }
+  const double coef = (a + tt) / (2.0 * a);
+  for (int i = lane; i < nv; i += 32) x[i] = T(coef * (double)x[i]);
+  if (lane == 0) {
+    const double wp = coef * w, tp = 0.5 * (a + tt);
+    x[nv] = T((wp + tp) * h);
+    x[nv + 1] = T((tp - wp) * h);
+  }
+  __syncwarp();
+}
+
+// --------------------------------------------------------------------------
+// Rotated SOC in the metric M (App. A.3, eq. rsoc-metric-projection):
+// v_i(xi) = m_i z_i/(m_i + 2 xi); [m_s, -2xi; -2xi, m_t][s; t] = [m_s z_s; m_t z_t];
+// f(xi) = ||v||^2 - 2 s t.  Singular 2 xi = q = sqrt(m_s m_t) with consistent
+// right-hand side handled by eq. rsoc-metric-singular-projection.  Branch: with
+// kappa = sqrt(m_s) z_s + sqrt(m_t) z_t the admissible root (s, t >= 0) lies in
+// (l, q/2) when kappa > 0 and in (q/2, u) when kappa < 0, where l, u are the
+// points at which s or t changes sign; f > 0 at l (or u, or infinity) and
+// f -> -inf at the pole.
+// --------------------------------------------------------------------------
+template <typename T>
+__device__ __noinline__ void warp_rsoc_metric(T* x, const T* m, int d, int lane) {
+  const int nv = d - 2;
+  double v2 = 0.0, mv2 = 0.0;
+  for (int i = lane; i < nv; i += 32) {
+    const double xi = (double)x[i], mi = (double)m[i];
+    v2 += xi * xi;
+    mv2 += (mi * xi) * (mi * xi);
+  }
+  const double zs = (double)x[nv], zt = (double)x[nv + 1];
+  const double ms = (double)m[nv], mt = (double)m[nv + 1];
+  v2 = warp_sum(v2);
+  mv2 = warp_sum(mv2);
+  if (zs >= 0.0 && zt >= 0.0 && v2 <= 2.0 * zs * zt) return;
+  if (zs <= 0.0 && zt <= 0.0 && mv2 <= 2.0 * (ms * zs) * (mt * zt)) {
+    for (int i = lane; i < d; i += 32) x[i] = T(0);
+    __syncwarp();
+    return;
+  }
+  if (v2 == 0.0) {  // cone reduces to the quadrant s, t >= 0
+    __syncwarp();
+    if (lane == 0) {
+      x[nv] = T(fmax(zs, 0.0));
+      x[nv + 1] = T(fmax(zt, 0.0));
+    }
+    __syncwarp();
+    return;
+  }
+  const double sms = sqrt(ms), smt = sqrt(mt), q = sms * smt;
+  const double kappa = sms * zs + smt * zt;
+  const double kscale = sms * fabs(zs) + smt * fabs(zt);
+  double s_out, t_out, xi;
+  if (fabs(kappa) <= 64.0 * Tol<T>::rel * kscale) {
+    xi = 0.5 * q;
+    double vv = 0.0;
+    for (int i = lane; i < nv; i += 32) {
+      const double mi = (double)m[i], vi = mi * (double)x[i] / (mi + q);
+      vv += vi * vi;
+    }
+    vv = warp_sum(vv);
+    const double delta = sms * zs;
+    const double chi = sqrt(delta * delta + 2.0 * q * vv);
+    s_out = (delta + chi) / (2.0 * sms);
+    t_out = (-delta + chi) / (2.0 * smt);
+  } else {
+    double lo, hi;
+    const double al[2] = {ms * zs, mt * zt}, be[2] = {zt, zs};
+    if (kappa > 0.0) {
+      lo = 0.0;
+      hi = 0.5 * q;
+      for (int j = 0; j < 2; ++j)
+        if (al[j] < 0.0) lo = fmax(lo, -al[j] / (2.0 * be[j]));
+    } else {
+      lo = 0.5 * q;
+      hi = INFINITY;
+      for (int j = 0; j < 2; ++j)
+        if (be[j] > 0.0) hi = fmin(hi, -al[j] / (2.0 * be[j]));
+    }
+    auto fval = [&](double xx) {
+      double sv = 0.0;
+      for (int i = lane; i < nv; i += 32) {
+        const T mi = m[i], zi = x[i];
+        const T a = (mi * zi) * (mi * zi);
+        const T den = mi + T(2.0 * xx);
+        sv += (double)(a / (den * den));
+      }
+      sv = warp_sum(sv);
+      const double det = ms * mt - 4.0 * xx * xx;
+      const double s = mt * (ms * zs + 2.0 * xx * zt) / det;
+      const double t = ms * (mt * zt + 2.0 * xx * zs) / det;
+      return sv - 2.0 * s * t;
+    };
+    if (!isfinite(hi)) {
+      hi = q;
+      for (int it = 0; it < 2000 && fval(hi) <= 0.0; ++it) hi *= 2.0;
+    }
+    // bisection: f(lo) > 0 > f(hi) when kappa > 0, f(lo) < 0 < f(hi) when kappa < 0
+    const bool lo_pos = kappa > 0.0;
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi || (hi - lo) <= Tol<T>::rel * mid) break;
+      const double f = fval(mid);
+      if ((f > 0.0) == lo_pos) lo = mid; else hi = mid;
+    }
+    xi = 0.5 * (lo + hi);
+    const double det = ms * mt - 4.0 * xi * xi;
+    s_out = fmax(mt * (ms * zs + 2.0 * xi * zt) / det, 0.0);
+    t_out = fmax(ms * (mt * zt + 2.0 * xi * zs) / det, 0.0);
+  }
+  for (int i = lane; i < nv; i += 32) {
+    const double mi = (double)m[i];
+    x[i] = T(mi * (double)x[i] / (mi + 2.0 * xi));
+  }
+  __syncwarp();
+  if (lane == 0) {
+    x[nv] = T(s_out);
+    x[nv + 1] = T(t_out);
+  }
+  __syncwarp();
+}
+
+// --------------------------------------------------------------------------
+// Exponential cone.  At the projection p = eta a(rho), a = (rho, 1, e^rho), and
+// M(p - z) = mu c(rho) with c = (-1, rho - 1, e^-rho) (the dual-cone ray normal to
+// K at p), eta, mu > 0; rho is a zero of
+//   G(rho) = m_t e^rho (m_s s0 + m_r (rho-1) r0) + m_r m_s e^-rho (rho s0 - r0)
+//            - m_t t0 (m_r rho (rho-1) + m_s)
+// (z in span{a, M^{-1} c}) at which G crosses from negative to positive.  All
+// scalar functions are evaluated times e^{-|rho|} (same sign, no overflow).
+// --------------------------------------------------------------------------
+struct ExpData {
+  double r0, s0, t0, mr, ms, mt;
+};
+
+__device__ __forceinline__ double exp_G(const ExpData& c, double rho, double* dG) {
+  // returns e^{-|rho|} G(rho); *dG receives e^{-|rho|} G'(rho)
+  const double a = c.mt * (c.ms * c.s0 + c.mr * (rho - 1.0) * c.r0);
+  const double da = c.mt * c.mr * c.r0;
+  const double b = c.mr * c.ms * (rho * c.s0 - c.r0);
+  const double db = c.mr * c.ms * c.s0;
+  const double p = c.mt * c.t0 * (c.mr * rho * (rho - 1.0) + c.ms);
+  const double dp = c.mt * c.t0 * c.mr * (2.0 * rho - 1.0);
+  if (rho >= 0.0) {
+    const double e1 = exp(-rho), e2 = e1 * e1;
+    // G = e^rho a + e^-rho b - p; G' = e^rho (a + da) + e^-rho (db - b) - dp
+    *dG = (a + da) + (db - b) * e2 - dp * e1;
+    return a + b * e2 - p * e1;
+  }
+  const double e1 = exp(rho), e2 = e1 * e1;
+  *dG = (a + da) * e2 + (db - b) - dp * e1;
+  return a * e2 + b - p * e1;
+}
+
+__device__ __forceinline__ double exp_N(const ExpData& c, double rho) {  // eta_M numerator, scaled for rho > 0
+  if (rho > 0.0) {
+    const double e1 = exp(-rho);
+    return (c.mr * rho * c.r0 + c.ms * c.s0) * e1 + c.mt * c.t0;
+  }
+  return c.mr * rho * c.r0 + c.ms * c.s0 + c.mt * exp(rho) * c.t0;
+}
+__device__ __forceinline__ double exp_g2(const ExpData& c, double rho) {  // > 0 iff mu > 0, scaled for rho < 0
+  if (rho < 0.0) {
+    const double e1 = exp(rho);
+    return (c.r0 + (1.0 - rho) * c.s0) * e1 - c.t0;
+  }
+  return c.r0 + (1.0 - rho) * c.s0 - exp(-rho) * c.t0;
+}
+
+// safeguarded Newton on G over [lo, hi] with G(lo) < 0 < G(hi)
+static __device__ __noinline__ double exp_root(const ExpData& c, double lo, double hi) {
+  double rho = 0.5 * (lo + hi);
+  for (int it = 0; it < 300; ++it) {
+    double dG;
+    const double G = exp_G(c, rho, &dG);
+    if (G == 0.0) return rho;
+    if (G < 0.0) lo = rho; else hi = rho;
+    double nx = (dG != 0.0) ? rho - G / dG : 0.5 * (lo + hi);
+    if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
+    const double step = fabs(nx - rho);
+    rho = nx;
+    if (step <= 4e-16 * fmax(1.0, fabs(rho)) || (hi - lo) <= 4e-16 * fmax(1.0, fabs(rho))) break;
+  }
+  return rho;
+}
+
+static __device__ void exp_finish(const ExpData& c, double rho, double* out) {
+  if (rho <= 0.0) {
+    const double ep = exp(rho);
+    const double eta = (c.mr * rho * c.r0 + c.ms * c.s0 + c.mt * ep * c.t0) / (c.mr * rho * rho + c.ms + c.mt * ep * ep);
+    out[0] = eta * rho;
+    out[1] = eta;
+    out[2] = eta * ep;
+  } else {
+    const double em = exp(-rho);
+    const double te = (c.mr * rho * c.r0 * em + c.ms * c.s0 * em + c.mt * c.t0) /
+                      (c.mr * rho * rho * em * em + c.ms * em * em + c.mt);   // eta e^rho
+    out[0] = te * rho * em;
+    out[1] = te * em;
+    out[2] = te;
+  }
+}
+
+// returns true if one of the closed-form cases applied (App. A.4)
+static __device__ bool exp_trivial(const ExpData& c, double* out) {
+  const double r0 = c.r0, s0 = c.s0, t0 = c.t0;
+  if ((s0 > 0.0 && r0 <= s0 * log(fmax(t0, 0.0) / s0)) || (r0 <= 0.0 && s0 == 0.0 && t0 >= 0.0)) {
+    out[0] = r0; out[1] = s0; out[2] = t0;       // z in K
+    return true;
+  }
+  const double u = -c.mr * r0, v = -c.ms * s0, w = -c.mt * t0;   // -Mz in K*?
+  if ((u < 0.0 && w > 0.0 && log(-u) + v / u <= 1.0 + log(w)) || (u == 0.0 && v >= 0.0 && w >= 0.0)) {
+    out[0] = out[1] = out[2] = 0.0;
+    return true;
+  }
+  if (r0 <= 0.0 && s0 <= 0.0) {                  // face {s = 0}
+    out[0] = r0; out[1] = 0.0; out[2] = fmax(t0, 0.0);
+    return true;
+  }
+  return false;
+}
+
+// Euclidean exponential-cone projection.  With M = I the first two components
+// of z = eta a + mu b (b = -c) give eta = (s0 + (rho-1) r0)/(rho^2-rho+1) and
+// mu = (r0 - rho s0)/(rho^2-rho+1), so {eta > 0, mu > 0} is an interval cut out
+// by two linear inequalities in rho, with G < 0 at its left end and G > 0 at
+// its right end.
+static __device__ __noinline__ void exp_proj_euclid(double r0, double s0, double t0, double* out) {
+  const ExpData c{r0, s0, t0, 1.0, 1.0, 1.0};
+  if (exp_trivial(c, out)) return;
+  double lo = -INFINITY, hi = INFINITY;
+  if (r0 > 0.0) lo = fmax(lo, 1.0 - s0 / r0);
+  if (r0 < 0.0) hi = fmin(hi, 1.0 - s0 / r0);
+  if (s0 > 0.0) hi = fmin(hi, r0 / s0);
+  if (s0 < 0.0) lo = fmax(lo, r0 / s0);
+  double dG;
+  if (!isfinite(lo)) {
+    double step = 1.0;
+    lo = hi - step;
+    while (exp_G(c, lo, &dG) >= 0.0 && step < 1e8) { step *= 2.0; lo = hi - step; }
+  }
+  if (!isfinite(hi)) {
+    double step = 1.0;
+    hi = lo + step;
+    while (exp_G(c, hi, &dG) <= 0.0 && step < 1e8) { step *= 2.0; hi = lo + step; }
+  }
+  exp_finish(c, exp_root(c, lo, hi), out);
+}
+
+// zeros of a function that is convex or concave with stationary point rc (NaN:
+// monotone), located by outward doubling from the anchor and bisection
+template <typename F>
+static __device__ int exp_piece_roots(F f, double rc, double* roots) {
+  int nr = 0;
+  const double a = isnan(rc) ? 0.0 : rc;
+  const double fa = f(a);
+  if (fa == 0.0) { roots[nr++] = a; return nr; }
+  for (int dir = -1; dir <= 1; dir += 2) {
+    for (double step = 1.0; step < 1e8; step *= 2.0) {
+      const double xx = a + dir * step;
+      const double fx = f(xx);
+      if ((fx > 0.0) != (fa > 0.0)) {
+        double lo = dir < 0 ? xx : a, hi = dir < 0 ? a : xx;
+        const bool lo_pos = (dir < 0 ? fx : fa) > 0.0;
+        for (int it = 0; it < 200; ++it) {
+          const double mid = 0.5 * (lo + hi);
+          if (mid <= lo || mid >= hi) break;
+          if ((f(mid) > 0.0) == lo_pos) lo = mid; else hi = mid;
+        }
+        roots[nr++] = 0.5 * (lo + hi);
+        break;
+      }
+    }
+  }
+  return nr;
+}
+
+// Exponential-cone projection in the metric M (App. A.4, eq. exp-metric-projection).
+// The admissible zero of G has N > 0 (eta_M > 0) and g2 > 0 (mu > 0).  N and g2
+// are each convex or concave in rho, so {N > 0, g2 > 0} is a union of a few
+// intervals bounded by their zeros; on each interval G has no zero but the
+// admissible one, an up-crossing.  The intervals are enumerated and the one
+// with a sign change of G is solved by the safeguarded Newton iteration.
+static __device__ __noinline__ void exp_proj_metric(double r0, double s0, double t0, double mr, double ms, double mt, double* out) {
+  const ExpData c{r0, s0, t0, mr, ms, mt};
+  if (exp_trivial(c, out)) return;
+  double br[4];
+  int nb = 0;
+  double rc = NAN;
+  if (t0 != 0.0 && -mr * r0 / (mt * t0) > 0.0) rc = log(-mr * r0 / (mt * t0));
+  nb += exp_piece_roots([&](double x) { return exp_N(c, x); }, rc, br + nb);
+  rc = NAN;
+  if (s0 != 0.0 && t0 / s0 > 0.0) rc = log(t0 / s0);
+  nb += exp_piece_roots([&](double x) { return exp_g2(c, x); }, rc, br + nb);
+  for (int i = 1; i < nb; ++i)
+    for (int j = i; j > 0 && br[j] < br[j - 1]; --j) { const double tmp = br[j]; br[j] = br[j - 1]; br[j - 1] = tmp; }
+  double rho = NAN, dG;
+  for (int iv = 0; iv <= nb && isnan(rho); ++iv) {
+    const double a = iv == 0 ? -INFINITY : br[iv - 1];
+    const double b = iv == nb ? INFINITY : br[iv];
+    if (!(b > a)) continue;
+    double p;
+    if (isfinite(a) && isfinite(b)) p = 0.5 * (a + b);
+    else if (isfinite(a)) p = a + 1.0;
+    else if (isfinite(b)) p = b - 1.0;
+    else p = 0.0;
+    if (!(exp_N(c, p) > 0.0 && exp_g2(c, p) > 0.0)) continue;
+    const double gp = exp_G(c, p, &dG);
+    if (gp == 0.0) { rho = p; break; }
+    double lo = NAN, hi = NAN;
+    if (gp < 0.0) {
+      lo = p;
+      if (isfinite(b)) { if (exp_G(c, b, &dG) > 0.0) hi = b; }
+      else for (double st = 1.0; st < 1e8; st *= 2.0) if (exp_G(c, p + st, &dG) > 0.0) { hi = p + st; break; }
+    } else {
+      hi = p;
+      if (isfinite(a)) { if (exp_G(c, a, &dG) < 0.0) lo = a; }
+      else for (double st = 1.0; st < 1e8; st *= 2.0) if (exp_G(c, p - st, &dG) < 0.0) { lo = p - st; break; }
+    }
+    if (!isnan(lo) && !isnan(hi)) rho = exp_root(c, lo, hi);
+  }
+  if (isnan(rho)) {          // not expected: fall back to the Euclidean direction
+    double e[3];
+    exp_proj_euclid(r0, s0, t0, e);
+    rho = e[1] > 0.0 ? log(fmax(e[2] / e[1], 1e-300)) : 0.0;
+  }
+  exp_finish(c, rho, out);
+}
+
+// --------------------------------------------------------------------------
+// Three-dimensional power cone (App. A.5, eqs. power-projection-root,
+// power-cone-stable-quadratic-root, Prop. power-cone-bisection): the unique
+// zero of g(rho) = a log x(rho) + (1-a) log y(rho) - log rho in (0, R), R = |z_t|,
+// with g > 0 near 0 and g < 0 near R, found by Newton steps kept inside the
+// bisection bracket.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ double pow_qroot(double s, double c) {
+  const double d = sqrt(s * s + 4.0 * c);
+  return s >= 0.0 ? 0.5 * (s + d) : 2.0 * c / (d - s);
+}
+
+static __device__ __noinline__ void pow_proj(double rx, double ry, double rz, double al, double mx, double my, double mz, double* out) {
+  auto geo = [&](double xx, double yy) { return (xx <= 0.0 || yy <= 0.0) ? 0.0 : exp(al * log(xx) + (1.0 - al) * log(yy)); };
+  if (rx >= 0.0 && ry >= 0.0 && geo(rx, ry) >= fabs(rz)) { out[0] = rx; out[1] = ry; out[2] = rz; return; }
+  {
+    const double p = -mx * rx, q = -my * ry, w = -mz * rz;
+    if (p >= 0.0 && q >= 0.0 && geo(p / al, q / (1.0 - al)) >= fabs(w)) { out[0] = out[1] = out[2] = 0.0; return; }
+  }
+  if (rz == 0.0) { out[0] = fmax(rx, 0.0); out[1] = fmax(ry, 0.0); out[2] = 0.0; return; }
+  const double R = fabs(rz), kx = al * mz / mx, ky = (1.0 - al) * mz / my;
+  double lo = 0.0, hi = R, rho = 0.5 * R;
+  for (int it = 0; it < 300; ++it) {
+    const double w = rho * (R - rho), dw = R - 2.0 * rho;
+    const double cx = kx * w, cy = ky * w;
+    const double dx = sqrt(rx * rx + 4.0 * cx), dy = sqrt(ry * ry + 4.0 * cy);
+    const double xx = rx >= 0.0 ? 0.5 * (rx + dx) : 2.0 * cx / (dx - rx);
+    const double yy = ry >= 0.0 ? 0.5 * (ry + dy) : 2.0 * cy / (dy - ry);
+    const double g = al * log(xx) + (1.0 - al) * log(yy) - log(rho);
+    if (g == 0.0) break;
+    if (g > 0.0) lo = rho; else hi = rho;
+    // d/drho of the positive root u of u^2 - s u - c: du = dc / (2u - s) = dc / sqrt(s^2 + 4c)
+    const double gx = kx * dw / dx, gy = ky * dw / dy;
+    const double dg = al * gx / xx + (1.0 - al) * gy / yy - 1.0 / rho;
+    double nx = (dg != 0.0 && isfinite(dg)) ? rho - g / dg : 0.5 * (lo + hi);
+    if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
+    const double step = fabs(nx - rho);
+    rho = nx;
+    if (step <= 4e-16 * fmax(rho, 1e-300) || (hi - lo) <= 4e-16 * fmax(1.0, R)) break;
+  }
+  const double w = rho * (R - rho);
+  out[0] = pow_qroot(rx, kx * w);
+  out[1] = pow_qroot(ry, ky * w);
+  out[2] = rz > 0.0 ? rho : -rho;
+}
+
+}  // namespace cqp

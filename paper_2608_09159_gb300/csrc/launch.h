@@ -1,0 +1,38 @@
+// Launchers for the solver kernels, instantiated per precision in
+// solver_f32.cu / solver_f64.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "solver.cuh"
+
+namespace cqp {
+
+template <typename T>
+struct KernelArgs;
+
+// Cooperative whole-GPU launch (grid = true) or one block (grid = false).
+template <typename T>
+cudaError_t launch_pdhg(const KernelArgs<T>& a, bool grid, int blocks, int threads, cudaStream_t st);
+
+// KKT report of the scaled point (x, y) with the handle's data; out receives 8 doubles.
+template <typename T>
+cudaError_t launch_kkt(const KernelArgs<T>& a, const T* x, const T* y, double* out, bool grid, int blocks, int threads,
+                       cudaStream_t st);
+
+// Blocks per SM that can be co-resident for the cooperative solver kernel.
+template <typename T>
+int pdhg_blocks_per_sm(int threads);
+
+template <typename T>
+size_t pdhg_smem(int threads);
+
+// Kernel-level entry points used by the C ABI.
+template <typename T>
+cudaError_t launch_spmv(int64_t nrows, const int* rp, const int* ci, const T* v, const T* x, T* y, int tpr,
+                        cudaStream_t st);
+template <typename T>
+cudaError_t launch_project(int64_t nblocks, const int32_t* type, const int64_t* start, const int64_t* dim,
+                           const double* alpha, const T* r, const T* m, T* out, int64_t n, cudaStream_t st);
+
+}  // namespace cqp

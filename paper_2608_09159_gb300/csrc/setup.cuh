@@ -1,0 +1,265 @@
+// Setup kernels: layout permutation, transpose, rescaling (Sec. 4.2.2), norm
+// estimate (eq. practical-stepsizes).  All arithmetic on the problem data is
+// FP64; the scaled matrices are converted to the iterate precision at the end.
+#pragma once
+
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace cqp {
+
+constexpr int kSetupThreads = 256;
+
+inline int grid_for(int64_t n, int threads = kSetupThreads, int cap = 152 * 32) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+#define CQP_GRID_LOOP(i, n) for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+// ---- validation: colind in range, values finite --------------------------------
+__global__ void k_validate_csr(int64_t nrows, int64_t ncols, const int64_t* rowptr, const int32_t* colind,
+                               const double* val, int* bad) {
+  const int64_t nnz = rowptr[nrows];
+  CQP_GRID_LOOP(r, nrows) {
+    if (rowptr[r] > rowptr[r + 1]) atomicOr(bad, 1);
+  }
+  CQP_GRID_LOOP(k, nnz) {
+    const int c = colind[k];
+    if (c < 0 || c >= ncols) atomicOr(bad, 2);
+    if (!isfinite(val[k])) atomicOr(bad, 4);
+  }
+}
+__global__ void k_validate_vec(int64_t n, const double* v, int* bad) {
+  CQP_GRID_LOOP(i, n) if (!isfinite(v[i])) atomicOr(bad, 8);
+}
+
+// ---- permutation of coordinates into [free | nonneg | soc | rsoc | exp | pow] ----
+__global__ void k_gather(int64_t n, const int64_t* perm, const double* in, double* out, double fill) {
+  CQP_GRID_LOOP(i, n) out[i] = in ? in[perm[i]] : fill;
+}
+__global__ void k_remap_cols(int64_t nnz, const int64_t* iperm, const int32_t* in, int32_t* out) {
+  CQP_GRID_LOOP(k, nnz) out[k] = (int32_t)iperm[in[k]];
+}
+__global__ void k_copy_rowptr32(int64_t n1, const int64_t* in, int32_t* out) {
+  CQP_GRID_LOOP(i, n1) out[i] = (int32_t)in[i];
+}
+// R (k x n) columns permuted
+__global__ void k_gather_cols(int64_t k, int64_t n, const int64_t* perm, const double* in, double* out) {
+  CQP_GRID_LOOP(t, k * n) {
+    const int64_t l = t / n, j = t % n;
+    out[t] = in[l * n + perm[j]];
+  }
+}
+// permuted sparse P: new row i = old row perm[i], columns remapped
+__global__ void k_row_lengths_perm(int64_t n, const int64_t* perm, const int64_t* rp, int32_t* len) {
+  CQP_GRID_LOOP(i, n) len[i] = (int32_t)(rp[perm[i] + 1] - rp[perm[i]]);
+}
+__global__ void k_copy_rows_perm(int64_t n, const int64_t* perm, const int64_t* iperm, const int64_t* rp,
+                                 const int32_t* ci, const double* v, const int32_t* nrp, int32_t* nci, double* nv) {
+  CQP_GRID_LOOP(i, n) {
+    const int64_t o = perm[i];
+    int64_t dst = nrp[i];
+    for (int64_t t = rp[o]; t < rp[o + 1]; ++t, ++dst) {
+      nci[dst] = (int32_t)iperm[ci[t]];
+      nv[dst] = v[t];
+    }
+  }
+}
+
+// ---- exclusive scan of int32 counts into int32 offsets (n entries -> n+1) ----------
+// three passes: per-block totals, serial scan of the totals, per-block scan + offset
+__global__ void k_scan_block_totals(int64_t n, const int32_t* in, int64_t per_block, int64_t* tot) {
+  const int64_t b0 = blockIdx.x * per_block, b1 = min(n, b0 + per_block);
+  int64_t s = 0;
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) s += in[i];
+  __shared__ int64_t red[kSetupThreads];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) tot[blockIdx.x] = red[0];
+}
+__global__ void k_scan_totals(int nb, int64_t* tot) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int64_t s = 0;
+    for (int b = 0; b < nb; ++b) { const int64_t t = tot[b]; tot[b] = s; s += t; }
+    tot[nb] = s;
+  }
+}
+__global__ void k_scan_apply(int64_t n, const int32_t* in, int64_t per_block, const int64_t* tot, int32_t* out) {
+  // serial chunks per thread, then a block scan of the chunk sums
+  __shared__ int64_t sums[kSetupThreads];
+  const int64_t b0 = blockIdx.x * per_block, b1 = min(n, b0 + per_block);
+  const int64_t len = b1 - b0;
+  const int64_t chunk = (len + blockDim.x - 1) / blockDim.x;
+  const int64_t c0 = b0 + threadIdx.x * chunk, c1 = min(b1, c0 + chunk);
+  int64_t s = 0;
+  for (int64_t i = c0; i < c1; ++i) s += in[i];
+  sums[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t acc = tot[blockIdx.x];
+    for (int t = 0; t < (int)blockDim.x; ++t) { const int64_t v = sums[t]; sums[t] = acc; acc += v; }
+  }
+  __syncthreads();
+  int64_t acc = sums[threadIdx.x];
+  for (int64_t i = c0; i < c1; ++i) { out[i] = (int32_t)acc; acc += in[i]; }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = (int32_t)tot[gridDim.x];
+}
+
+// ---- transpose ----------------------------------------------------------------
+__global__ void k_count_cols(int64_t nnz, const int32_t* ci, int32_t* cnt) {
+  CQP_GRID_LOOP(k, nnz) atomicAdd(&cnt[ci[k]], 1);
+}
+__global__ void k_scatter_transpose(int64_t m, const int32_t* rp, const int32_t* ci, int32_t* cursor, int32_t* tci,
+                                    int32_t* tmap) {
+  CQP_GRID_LOOP(r, m) {
+    for (int k = rp[r]; k < rp[r + 1]; ++k) {
+      const int pos = atomicAdd(&cursor[ci[k]], 1);
+      tci[pos] = (int32_t)r;
+      tmap[pos] = k;
+    }
+  }
+}
+// order every transposed row by its column (original row) index: deterministic layout
+__global__ void k_sort_segments(int64_t n, const int32_t* trp, int32_t* tci, int32_t* tmap) {
+  CQP_GRID_LOOP(j, n) {
+    const int b = trp[j], e = trp[j + 1];
+    for (int a = b + 1; a < e; ++a) {
+      const int key = tci[a], val = tmap[a];
+      int t = a - 1;
+      while (t >= b && tci[t] > key) { tci[t + 1] = tci[t]; tmap[t + 1] = tmap[t]; --t; }
+      tci[t + 1] = key;
+      tmap[t + 1] = val;
+    }
+  }
+}
+
+// ---- rescaling (Ruiz l_inf, Pock-Chambolle, cone-preserving aggregation) -------------
+// row statistic: max |a| (mode 0) or sum |a|^p (mode 1) over each row of A
+__global__ void k_row_stat(int64_t m, const int32_t* rp, const double* v, int mode, double p, double* out) {
+  CQP_GRID_LOOP(r, m) {
+    double s = 0.0;
+    for (int k = rp[r]; k < rp[r + 1]; ++k) {
+      const double a = fabs(v[k]);
+      s = mode == 0 ? fmax(s, a) : s + pow(a, p);
+    }
+    out[r] = s;
+  }
+}
+// column statistic through the transpose structure (tmap indexes A's values)
+__global__ void k_col_stat(int64_t n, const int32_t* trp, const int32_t* tmap, const double* v, int mode, double p,
+                           double* out) {
+  CQP_GRID_LOOP(j, n) {
+    double s = 0.0;
+    for (int k = trp[j]; k < trp[j + 1]; ++k) {
+      const double a = fabs(v[tmap[k]]);
+      s = mode == 0 ? fmax(s, a) : s + pow(a, p);
+    }
+    out[j] = s;
+  }
+}
+// f = sqrt(stat) (1 where the statistic vanishes)
+__global__ void k_sqrt_or_one(int64_t n, double* f) {
+  CQP_GRID_LOOP(i, n) f[i] = f[i] > 0.0 ? sqrt(f[i]) : 1.0;
+}
+// cone blocks of the permuted layout: [b0, b1) coordinate ranges given by offsets
+// (SOC, RSOC) or by a base and width 3 (EXP, POW); max (mode 0) or RMS (mode 1)
+__global__ void k_aggregate_blocks(int64_t nblk, const int64_t* off, int64_t base, int width, int mode, double* f) {
+  CQP_GRID_LOOP(b, nblk) {
+    const int64_t s = off ? off[b] : base + width * b;
+    const int64_t e = off ? off[b + 1] : s + width;
+    double a = 0.0;
+    for (int64_t i = s; i < e; ++i) a = mode == 0 ? fmax(a, f[i]) : a + f[i] * f[i];
+    if (mode == 1) a = sqrt(a / (double)(e - s));
+    for (int64_t i = s; i < e; ++i) f[i] = a;
+  }
+}
+// A <- diag(1/rowf) A diag(1/colf); col *= colf; row *= rowf
+__global__ void k_scale_matrix(int64_t m, const int32_t* rp, const int32_t* ci, double* v, const double* rowf,
+                               const double* colf) {
+  CQP_GRID_LOOP(r, m) {
+    const double fr = rowf[r];
+    for (int k = rp[r]; k < rp[r + 1]; ++k) v[k] /= fr * colf[ci[k]];
+  }
+}
+__global__ void k_mul(int64_t n, double* a, const double* f) { CQP_GRID_LOOP(i, n) a[i] *= f[i]; }
+__global__ void k_div(int64_t n, double* a, const double* f) { CQP_GRID_LOOP(i, n) a[i] /= f[i]; }
+__global__ void k_div2(int64_t n, double* a, const double* f) { CQP_GRID_LOOP(i, n) a[i] /= f[i] * f[i]; }
+__global__ void k_fill(int64_t n, double* a, double v) { CQP_GRID_LOOP(i, n) a[i] = v; }
+__global__ void k_scal(int64_t n, double* a, double s) { CQP_GRID_LOOP(i, n) a[i] *= s; }
+// P~_ij = P_ij / (col_i col_j)
+__global__ void k_scale_sym(int64_t n, const int32_t* rp, const int32_t* ci, double* v, const double* col) {
+  CQP_GRID_LOOP(r, n) {
+    for (int k = rp[r]; k < rp[r + 1]; ++k) v[k] /= col[r] * col[ci[k]];
+  }
+}
+// R~ = R diag(1/col)
+__global__ void k_scale_cols(int64_t k, int64_t n, double* R, const double* col) {
+  CQP_GRID_LOOP(t, k * n) R[t] /= col[t % n];
+}
+// full diagonal of Q~ = diag(qd) + P + R' D R
+__global__ void k_full_diag(int64_t n, const double* qd, const int32_t* prp, const int32_t* pci, const double* pv,
+                            int64_t k, const double* R, const double* D, double* jd) {
+  CQP_GRID_LOOP(i, n) {
+    double q = qd[i];
+    if (prp)
+      for (int t = prp[i]; t < prp[i + 1]; ++t)
+        if (pci[t] == i) q += pv[t];
+    for (int64_t l = 0; l < k; ++l) {
+      const double rl = R[l * n + i];
+      if (rl == 0.0) continue;
+      double s = 0.0;
+      for (int64_t l2 = 0; l2 < k; ++l2) s += D[l * k + l2] * R[l2 * n + i];
+      q += rl * s;
+    }
+    jd[i] = q;
+  }
+}
+template <typename T>
+__global__ void k_convert(int64_t n, const double* in, T* out) {
+  CQP_GRID_LOOP(i, n) out[i] = T(in[i]);
+}
+template <typename T>
+__global__ void k_gather_convert(int64_t n, const int32_t* idx, const double* in, T* out) {
+  CQP_GRID_LOOP(i, n) out[i] = T(in[idx[i]]);
+}
+
+// ---- reductions (FP64, two-level, deterministic) ----------------------------------
+__global__ void k_dot_partial(int64_t n, const double* a, const double* b, double* part) {
+  double s = 0.0;
+  CQP_GRID_LOOP(i, n) s += a[i] * (b ? b[i] : a[i]);
+  __shared__ double red[kSetupThreads];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+__global__ void k_sum_partials(int nb, const double* part, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[b];
+    *out = s;
+  }
+}
+
+// ---- power iteration pieces: y = A x (FP64 accumulation over T values) --------------
+template <typename T>
+__global__ void k_spmv_simple(int64_t m, const int32_t* rp, const int32_t* ci, const T* v, const double* x, double* y) {
+  CQP_GRID_LOOP(r, m) {
+    double s = 0.0;
+    for (int k = rp[r]; k < rp[r + 1]; ++k) s += (double)v[k] * x[ci[k]];
+    y[r] = s;
+  }
+}
+
+}  // namespace cqp

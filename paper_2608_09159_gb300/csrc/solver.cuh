@@ -1,0 +1,428 @@
+// The restarted PDHG iteration as one persistent kernel.
+//
+// Paper: Alg. "pdhcq1" (reflected-Halpern branch) and Sec. 4: primal prox
+// (eq. prox-subproblem) by Jacobi projected BB (eqs. bb-inner-gradient,
+// jacobi-bb-step) or, for diagonal Q, one metric projection (eqs.
+// diagonal-q-metric, diagonal-q-metric-projection); dual step and
+// reflected-Halpern update (eqs. stored-pdhg-candidate, rh-update); restart to
+// the last candidate (eq. restart-output); adaptive restart (eqs.
+// practical-fixed-point-movement, practical-restart-rule); PID primal weight
+// (eqs. pid-error, pid-weight); adaptive inner tolerance (eq.
+// monotone-primal-inner-tol, stop rule jacobi-stop-unscale); termination on
+// the unscaled candidate.  The Cesaro-averaged variant (compiled Alg.
+// "pdhcq1") restarts from the epoch average every avg_epoch iterations.
+//
+// Execution: every block of the team owns an equal share of each coordinate
+// segment (free, nonnegative, SOC blocks, RSOC blocks, exponential cones,
+// power cones) and an nnz-balanced range of rows of A.  A phase works on the
+// owned data, publishes FP64 block partials, and ends with a team barrier;
+// every block then sums the partials in the same order, so all blocks take the
+// same control decisions without further communication.  Cone blocks never
+// straddle two owners, so projections are block-local and need no barrier.
+//
+// Inner projected BB in one pass per iteration: the prox objective H is
+// quadratic, so g^{j+1} - g^j = (Q + I/tau) s_{j+1} exactly and
+//   <s, dg> = sum_i (q_i + 1/tau) s_i^2 + (R s)' D (R s)   (Q = diag(q) + R'DR),
+// where R s = R u^{j+1} - R u^j comes out of the same reduction that carries
+// ||s||^2 and <s, J s>.  The BB step size alpha_{j+1} is thus known right after
+// the pass that produced u^{j+1}, and the gradient at u^{j+1} is formed on the
+// fly inside the next pass.  A sparse P part needs P u^{j+1} first, so that mode
+// uses two passes per iteration.
+#pragma once
+
+#include "common.cuh"
+#include "cones.cuh"
+
+namespace cqp {
+
+enum QMode : int { kQDiag = 0, kQLowRank = 1, kQSparse = 2 };
+
+template <typename T>
+struct Prob {
+  int64_t n, m;
+  const int* a_rp; const int* a_ci; const T* a_v;     // scaled A (m rows)
+  const int* t_rp; const int* t_ci; const T* t_v;     // scaled A' (n rows)
+  const T* qd;                                        // explicit diagonal part of scaled Q (n)
+  const T* jd;                                        // full diagonal of scaled Q (n)
+  int k; const T* R; const double* D;                 // scaled low-rank factor (k x n), D (k x k)
+  const int* p_rp; const int* p_ci; const T* p_v;     // scaled sparse P (n rows) or null
+  const T* c; const T* b;                             // scaled c, b
+  const double* col; const double* row;               // x = beta_b x~/col, y = beta_c y~/row
+  double beta_b, beta_c, norm_b, norm_c;              // ||b||, ||c|| of the unscaled data
+  int64_t n_free, n_nonneg;                           // [0,n_free) free, then nonneg
+  int64_t n_soc; const int64_t* soc_off;              // SOC blocks: coordinates [soc_off[j], soc_off[j+1])
+  int64_t n_rsoc; const int64_t* rsoc_off;
+  int64_t n_exp, exp_base;                            // exp cones at exp_base + 3 j
+  int64_t n_pow, pow_base; const double* pow_alpha;
+  int qmode;
+  int euclid_cones;                                   // diagonal mode with zero q on cone coordinates
+  int tpr_a, tpr_t;                                   // threads per row of A and of A'
+};
+
+template <typename T>
+struct Work {
+  T* hx[2]; T* hy[2];   // reflected-Halpern states (double-buffered)
+  T* ax; T* ay;         // anchors
+  T* wx[2]; T* wy;      // stored candidates (x double-buffered for the movement)
+  T* v;                 // x + tau A'y
+  T* u[2];              // inner iterates
+  T* g[2];              // gradients (sparse-P mode)
+  T* avx; T* avy;       // running averages (averaged variant)
+  T* mbuf;              // metric of cone blocks too large for shared staging
+  double* sd;           // FP64 dual slack of cone coordinates (KKT)
+  double* part;         // block partials [kMaxSlots][nb]
+};
+
+struct Opts {
+  double rho, eps_min_in, gamma_in, tol;
+  double beta_s, beta_n, beta_a, beta_I, K_P, K_I, K_D;
+  long long max_iter;
+  int check_every, max_inner, jacobi, pid, update, avg_epoch;
+};
+
+// Control state of one solve (device memory, FP64 scalars).
+struct State {
+  double tau, sigma, omega, eta;
+  double eps_in, E0, Eprev, pid_int, err_prev, mov;
+  double t_h[kMaxRank];            // R~ h_x of the current Halpern state
+  double kkt[8];                   // eps_p, eps_d, eps_g, rel_kkt, pobj, dobj, ||r_p||, ||r_d||
+  double lastE;
+  long long k, ktot, restarts, inner_total;
+  int hb, wb;                      // current Halpern / candidate buffer
+  int status;                      // 0 running, 1 converged, 2 iteration limit
+  int err;                         // DevErr
+};
+
+// block-shared copy of the control state plus reduction outputs
+struct Ctl {
+  State s;
+  double red[kMaxSlots];           // gathered sums of the last phase
+  double w[kMaxRank];              // D~ t for the gradient of the current inner step
+  double tcur[kMaxRank];           // R~ u^j of the current inner iterate
+  double alpha, sJs;
+  double pid_dx, pid_dy;           // ||w_x - a_x||, ||w_y - a_y|| of the last check
+  long long inner_j;
+};
+
+// ---------------------------------------------------------------------------
+// block ownership
+// ---------------------------------------------------------------------------
+struct Own {
+  int64_t x0[6], x1[6];   // owned coordinate ranges: free, nonneg, soc, rsoc, exp, pow
+  int64_t f0, f1, nn0, nn1, s0, s1, r0, r1, e0, e1, p0, p1;
+  int64_t row0, row1;
+};
+
+template <typename T>
+__device__ void make_own(const Prob<T>& P, int b, int nb, Own& o) {
+  split_range(P.n_free, b, nb, o.f0, o.f1);
+  split_range(P.n_nonneg, b, nb, o.nn0, o.nn1);
+  o.nn0 += P.n_free; o.nn1 += P.n_free;
+  split_range(P.n_soc, b, nb, o.s0, o.s1);
+  split_range(P.n_rsoc, b, nb, o.r0, o.r1);
+  split_range(P.n_exp, b, nb, o.e0, o.e1);
+  split_range(P.n_pow, b, nb, o.p0, o.p1);
+  o.x0[0] = o.f0; o.x1[0] = o.f1;
+  o.x0[1] = o.nn0; o.x1[1] = o.nn1;
+  o.x0[2] = P.n_soc ? P.soc_off[o.s0] : 0; o.x1[2] = P.n_soc ? P.soc_off[o.s1] : 0;
+  o.x0[3] = P.n_rsoc ? P.rsoc_off[o.r0] : 0; o.x1[3] = P.n_rsoc ? P.rsoc_off[o.r1] : 0;
+  o.x0[4] = P.exp_base + 3 * o.e0; o.x1[4] = P.exp_base + 3 * o.e1;
+  o.x0[5] = P.pow_base + 3 * o.p0; o.x1[5] = P.pow_base + 3 * o.p1;
+  split_rows_by_nnz(P.a_rp, P.m, b, nb, o.row0, o.row1);
+}
+
+// ---------------------------------------------------------------------------
+// CSR row products by groups of G lanes; every lane of the group gets the sum.
+// X(j) returns the operand for column j.
+// ---------------------------------------------------------------------------
+template <int G, typename Acc, typename T, typename X>
+__device__ __forceinline__ Acc row_dot(const int* rp, const int* ci, const T* v, int64_t row, int gl, X xf) {
+  Acc s = Acc(0);
+  const int beg = rp[row], end = rp[row + 1];
+  for (int k = beg + gl; k < end; k += G) s += (Acc)v[k] * (Acc)xf(ci[k]);
+  return group_sum<G>(s);
+}
+
+// Iterate the rows [r0, r1) of a CSR matrix with groups of G lanes; f(row, gl, sum)
+// is called by every lane of the group after the reduction.
+template <int G, typename Acc, typename T, typename X, typename F>
+__device__ __forceinline__ void rows_loop(const int* rp, const int* ci, const T* v, int64_t r0, int64_t r1, X xf, F f) {
+  const int lane = threadIdx.x & 31;
+  const int gl = lane & (G - 1);
+  const int64_t gid = threadIdx.x / G, ngr = blockDim.x / G;
+  // all lanes of a warp iterate together (group_sum shuffles need full warps)
+  const int64_t nrows = r1 - r0;
+  const int64_t per_warp_rows = 32 / G;
+  const int64_t nwarps = blockDim.x >> 5;
+  const int64_t warp = threadIdx.x >> 5;
+  for (int64_t base = warp * per_warp_rows; base < nrows; base += nwarps * per_warp_rows) {
+    const int64_t r = r0 + base + (lane / G);
+    const bool ok = r < r1;
+    Acc s = Acc(0);
+    if (ok) {
+      const int beg = rp[r], end = rp[r + 1];
+      for (int k = beg + gl; k < end; k += G) s += (Acc)v[k] * (Acc)xf(ci[k]);
+    }
+    s = group_sum<G>(s);
+    if (ok) f(r, gl, s);
+  }
+  (void)gid;
+  (void)ngr;
+}
+
+template <typename Acc, typename T, typename X, typename F>
+__device__ __forceinline__ void rows_loop_tpr(int tpr, const int* rp, const int* ci, const T* v, int64_t r0, int64_t r1,
+                                              X xf, F f) {
+  switch (tpr) {
+    case 1: rows_loop<1, Acc>(rp, ci, v, r0, r1, xf, f); break;
+    case 2: rows_loop<2, Acc>(rp, ci, v, r0, r1, xf, f); break;
+    case 4: rows_loop<4, Acc>(rp, ci, v, r0, r1, xf, f); break;
+    case 8: rows_loop<8, Acc>(rp, ci, v, r0, r1, xf, f); break;
+    case 16: rows_loop<16, Acc>(rp, ci, v, r0, r1, xf, f); break;
+    default: rows_loop<32, Acc>(rp, ci, v, r0, r1, xf, f); break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The solver.  Team is GridTeam (whole GPU) or CtaTeam (one block).
+// ---------------------------------------------------------------------------
+template <typename T, class Team>
+struct Solver {
+  const Prob<T>& P;
+  const Work<T>& W;
+  const Opts& O;
+  Team& team;
+  Ctl& C;
+  Own own;
+  double* scratch;   // block_sum scratch: kMaxSlots * nwarps doubles (shared)
+  double* wacc;      // per-warp R-product accumulators: nwarps * kMaxRank doubles (shared)
+  T* cbuf;           // per-warp cone staging: nwarps * 2 * kConeStage (shared)
+  static constexpr int kConeStage = 128;
+
+  __device__ Solver(const Prob<T>& p, const Work<T>& w, const Opts& o, Team& t, Ctl& c, double* scr, double* wa,
+                    T* cb)
+      : P(p), W(w), O(o), team(t), C(c), scratch(scr), wacc(wa), cbuf(cb) {
+    make_own(P, team.bid(), team.nb(), own);
+  }
+
+  // ---- small helpers -------------------------------------------------------
+  __device__ __forceinline__ int nwarps() const { return blockDim.x >> 5; }
+
+  // zero the per-warp R accumulators
+  __device__ void wacc_zero() {
+    for (int i = threadIdx.x; i < nwarps() * P.k; i += blockDim.x) wacc[i] = 0.0;
+    __syncthreads();
+  }
+  // add sum over the warp of R[l, i] * val for every l (warp-uniform call; lanes with
+  // valid == false contribute zero)
+  __device__ __forceinline__ void wacc_add(int64_t i, double val, bool valid) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int l = 0; l < P.k; ++l) {
+      double p = valid ? (double)P.R[(int64_t)l * P.n + i] * val : 0.0;
+      p = warp_sum(p);
+      if (lane == 0) wacc[warp * P.k + l] += p;
+    }
+  }
+  // (R' w)_i with w in shared memory (k entries)
+  __device__ __forceinline__ double rtw(int64_t i, const double* w) const {
+    double s = 0.0;
+    for (int l = 0; l < P.k; ++l) s += (double)P.R[(int64_t)l * P.n + i] * w[l];
+    return s;
+  }
+
+  // publish NS block totals in slots [slot0, slot0+NS) plus, if with_r, the k R sums
+  template <int NS>
+  __device__ void publish(double (&v)[NS], int slot0, bool with_r) {
+    block_sum<NS>(v, scratch, C.red);   // C.red used as temporary block totals
+    if (threadIdx.x == 0)
+      for (int s = 0; s < NS; ++s) team.publish(slot0 + s, C.red[s]);
+    if (with_r) {
+      const int nw = nwarps();
+      for (int l = threadIdx.x; l < P.k; l += blockDim.x) {
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += wacc[w * P.k + l];
+        team.publish(slot0 + NS + l, t);
+      }
+    }
+    __syncthreads();
+  }
+  __device__ bool sync_gather(int nslots) {
+    if (!team.sync()) return false;
+    team.gather(nslots, C.red);
+    return true;
+  }
+
+  // ---- projections of the owned cone blocks --------------------------------
+  // Projects, in place, the owned SOC/RSOC/EXP/POW blocks of x in the metric
+  //   kEuclid: M = I;  kJacobi: m_i = diag(Q~)_i + 1/tau (eq. jacobi-inner-metric);
+  //   kDiagQ: m_i = 1 + tau q_i (eq. diagonal-q-metric).
+  // Ends with __syncthreads.
+  enum MetricKind : int { kEuclid = 0, kJacobi = 1, kDiagQ = 2 };
+  __device__ __forceinline__ double metric(int kind, int64_t i, double tau) const {
+    return kind == kJacobi ? (double)P.jd[i] + 1.0 / tau : (kind == kDiagQ ? 1.0 + tau * (double)P.qd[i] : 1.0);
+  }
+  __device__ __noinline__ void project_owned_cones(T* x, int kind, double tau) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = nwarps();
+    const bool euclid = kind == kEuclid;
+    T* zs = cbuf + warp * 2 * kConeStage;
+    T* ms = zs + kConeStage;
+    for (int pass = 0; pass < 2; ++pass) {
+      const int64_t b0 = pass == 0 ? own.s0 : own.r0, b1 = pass == 0 ? own.s1 : own.r1;
+      const int64_t* off = pass == 0 ? P.soc_off : P.rsoc_off;
+      for (int64_t blk = b0 + warp; blk < b1; blk += nw) {
+        const int64_t s = off[blk];
+        const int d = (int)(off[blk + 1] - s);
+        const bool staged = d <= kConeStage;
+        T* z = staged ? zs : x + s;
+        T* mm = staged ? ms : W.mbuf + s;
+        for (int i = lane; i < d; i += 32) {
+          if (staged) zs[i] = x[s + i];
+          if (!euclid) mm[i] = T(metric(kind, s + i, tau));
+        }
+        __syncwarp();
+        if (pass == 0) {
+          if (euclid) warp_soc_euclid<T>(z, d, lane);
+          else warp_soc_metric<T>(z, mm, d, lane);
+        } else {
+          if (euclid) warp_rsoc_euclid<T>(z, d, lane);
+          else warp_rsoc_metric<T>(z, mm, d, lane);
+        }
+        if (staged) {
+          for (int i = lane; i < d; i += 32) x[s + i] = zs[i];
+          __syncwarp();
+        }
+      }
+    }
+    for (int64_t e = own.e0 + threadIdx.x; e < own.e1; e += blockDim.x) {
+      const int64_t s = P.exp_base + 3 * e;
+      double o[3];
+      if (euclid) exp_proj_euclid((double)x[s], (double)x[s + 1], (double)x[s + 2], o);
+      else exp_proj_metric((double)x[s], (double)x[s + 1], (double)x[s + 2], metric(kind, s, tau),
+                           metric(kind, s + 1, tau), metric(kind, s + 2, tau), o);
+      x[s] = T(o[0]); x[s + 1] = T(o[1]); x[s + 2] = T(o[2]);
+    }
+    for (int64_t e = own.p0 + threadIdx.x; e < own.p1; e += blockDim.x) {
+      const int64_t s = P.pow_base + 3 * e;
+      double o[3];
+      pow_proj((double)x[s], (double)x[s + 1], (double)x[s + 2], P.pow_alpha[e], metric(kind, s, tau),
+               metric(kind, s + 1, tau), metric(kind, s + 2, tau), o);
+      x[s] = T(o[0]); x[s + 1] = T(o[1]); x[s + 2] = T(o[2]);
+    }
+    __syncthreads();
+  }
+
+  // Elementwise projection onto the free / nonnegative segments (metric-free, App. A.1)
+  __device__ __forceinline__ T proj_elem(int64_t i, T z) const { return (i < P.n_free) ? z : (z > T(0) ? z : T(0)); }
+
+  // ---- A' products: v = h_x + tau A' h_y on the owned coordinates -----------
+  __device__ void phase_aty(const T* hx, const T* hy, double tau) {
+    for (int seg = 0; seg < 6; ++seg) {
+      rows_loop_tpr<T>(P.tpr_t, P.t_rp, P.t_ci, P.t_v, own.x0[seg], own.x1[seg], [&](int j) { return hy[j]; },
+                       [&](int64_t i, int gl, T s) {
+                         if (gl == 0) W.v[i] = hx[i] + T(tau) * s;
+                       });
+    }
+    __syncthreads();
+  }
+
+  // ---- one projected (Jacobi-)BB step on the owned coordinates --------------
+  // u_next = Pi^J(u_cur - alpha J^{-1} g(u_cur)),   g = Q u + c + (u - v)/tau,
+  // with Q u = qd u + R' D t (t = R u_cur, D t in C.w); in sparse-P mode the
+  // whole gradient is taken from gs (computed by grad_pass).
+  // Accumulates s = u_next - u_cur: v3 = {||s||^2, <s, J s>, sum (qd + 1/tau) s^2} and,
+  // with R, the warp partials of R u_next.
+  __device__ void inner_step(const T* ucur, T* unext, const T* gs, double alpha, double tau, double (&v3)[3]) {
+    const double itau = 1.0 / tau;
+    const bool lowr = P.k > 0;
+    const bool jac = O.jacobi != 0;
+    auto grad = [&](int64_t i, double u) {
+      if (gs) return (double)gs[i];
+      double g = (double)P.qd[i] * u + (double)P.c[i] + (u - (double)W.v[i]) * itau;
+      if (lowr) g += rtw(i, C.w);
+      return g;
+    };
+    auto jm = [&](int64_t i) { return jac ? (double)P.jd[i] + itau : 1.0; };
+    v3[0] = v3[1] = v3[2] = 0.0;
+    if (lowr) wacc_zero();
+    // elementwise segments (free, nonneg): whole warps iterate together
+    const int lane = threadIdx.x & 31;
+    for (int seg = 0; seg < 2; ++seg) {
+      const int64_t a = own.x0[seg], b = own.x1[seg];
+      for (int64_t base = a + (threadIdx.x - lane); base < b; base += blockDim.x) {
+        const int64_t i = base + lane;
+        const bool ok = i < b;
+        double un = 0.0;
+        if (ok) {
+          const double u = (double)ucur[i];
+          const double J = jm(i);
+          const double z = u - alpha * grad(i, u) / J;
+          un = (double)proj_elem(i, T(z));
+          unext[i] = T(un);
+          const double s = un - u;
+          v3[0] += s * s;
+          v3[1] += J * s * s;
+          v3[2] += ((double)P.qd[i] + itau) * s * s;
+        }
+        if (lowr) wacc_add(i, un, ok);
+      }
+    }
+    // cone segments: gradient step into unext, then block-local metric projection
+    for (int seg = 2; seg < 6; ++seg)
+      for (int64_t i = own.x0[seg] + threadIdx.x; i < own.x1[seg]; i += blockDim.x) {
+        const double u = (double)ucur[i];
+        unext[i] = T(u - alpha * grad(i, u) / jm(i));
+      }
+    __syncthreads();
+    project_owned_cones(unext, jac ? kJacobi : kEuclid, tau);
+    for (int seg = 2; seg < 6; ++seg) {
+      const int64_t a = own.x0[seg], b = own.x1[seg];
+      for (int64_t base = a + (threadIdx.x - lane); base < b; base += blockDim.x) {
+        const int64_t i = base + lane;
+        const bool ok = i < b;
+        double un = 0.0;
+        if (ok) {
+          un = (double)unext[i];
+          const double s = un - (double)ucur[i];
+          v3[0] += s * s;
+          v3[1] += jm(i) * s * s;
+          v3[2] += ((double)P.qd[i] + itau) * s * s;
+        }
+        if (lowr) wacc_add(i, un, ok);
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- sparse-P mode: gradient at u (P u by the owned rows of P), dots -------
+  // writes g(u) to gout; v2 = {<s, dg>} with s = u - uprev, dg = g(u) - gprev
+  __device__ void grad_pass(const T* u, const T* uprev, const T* gprev, T* gout, double tau, double (&v2)[2],
+                            bool first) {
+    const double itau = 1.0 / tau;
+    v2[0] = v2[1] = 0.0;
+    for (int seg = 0; seg < 6; ++seg) {
+      rows_loop_tpr<double>(
+          P.tpr_t, P.p_rp, P.p_ci, P.p_v, own.x0[seg], own.x1[seg], [&](int j) { return u[j]; },
+          [&](int64_t i, int gl, double pu) {
+            if (gl == 0) {
+              double g = pu + (double)P.qd[i] * (double)u[i] + (double)P.c[i] + ((double)u[i] - (double)W.v[i]) * itau;
+              if (P.k > 0) g += rtw(i, C.w);
+              gout[i] = T(g);
+              if (!first) {
+                const double s = (double)u[i] - (double)uprev[i];
+                v2[0] += s * (g - (double)gprev[i]);
+              }
+            }
+          });
+    }
+    __syncthreads();
+  }
+
+  // ---- the main loop ---------------------------------------------------------
+  __device__ void run(long long budget);
+  __device__ bool prox_bb(const T* hx, int& ubuf);
+  __device__ bool prox_diag(const T* hx);
+  __device__ bool kkt(const T* x, const T* y, bool have_rx);
+  __device__ void ctl_pid_restart(double dxn, double dyn);
+};
+
+}  // namespace cqp

@@ -1,0 +1,601 @@
+// Bodies of the Solver phases declared in solver.cuh.
+#pragma once
+
+#include "solver.cuh"
+
+namespace cqp {
+
+// rows [r0, r1) with groups of G lanes computing two row products at once
+template <int G, typename Acc, typename T, typename X1, typename X2, typename F>
+__device__ __forceinline__ void rows_loop2(const int* rp, const int* ci, const T* v, int64_t r0, int64_t r1, X1 x1,
+                                           X2 x2, F f) {
+  const int lane = threadIdx.x & 31, gl = lane & (G - 1);
+  const int64_t per_warp = 32 / G, nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5;
+  for (int64_t base = warp * per_warp; base < r1 - r0; base += nwarps * per_warp) {
+    const int64_t r = r0 + base + lane / G;
+    const bool ok = r < r1;
+    Acc s1 = Acc(0), s2 = Acc(0);
+    if (ok) {
+      const int beg = rp[r], end = rp[r + 1];
+      for (int k = beg + gl; k < end; k += G) {
+        const int j = ci[k];
+        const Acc a = (Acc)v[k];
+        s1 += a * (Acc)x1(j);
+        s2 += a * (Acc)x2(j);
+      }
+    }
+    s1 = group_sum<G>(s1);
+    s2 = group_sum<G>(s2);
+    if (ok) f(r, gl, s1, s2);
+  }
+}
+
+template <typename Acc, typename T, typename X1, typename X2, typename F>
+__device__ __forceinline__ void rows_loop2_tpr(int tpr, const int* rp, const int* ci, const T* v, int64_t r0, int64_t r1,
+                                               X1 x1, X2 x2, F f) {
+  switch (tpr) {
+    case 1: rows_loop2<1, Acc>(rp, ci, v, r0, r1, x1, x2, f); break;
+    case 2: rows_loop2<2, Acc>(rp, ci, v, r0, r1, x1, x2, f); break;
+    case 4: rows_loop2<4, Acc>(rp, ci, v, r0, r1, x1, x2, f); break;
+    case 8: rows_loop2<8, Acc>(rp, ci, v, r0, r1, x1, x2, f); break;
+    case 16: rows_loop2<16, Acc>(rp, ci, v, r0, r1, x1, x2, f); break;
+    default: rows_loop2<32, Acc>(rp, ci, v, r0, r1, x1, x2, f); break;
+  }
+}
+
+// C.w = D~ t (k entries), threads l < k
+template <typename T>
+__device__ __forceinline__ void apply_D(const Prob<T>& P, const double* t, double* w) {
+  __syncthreads();
+  for (int l = threadIdx.x; l < P.k; l += blockDim.x) {
+    double s = 0.0;
+    for (int l2 = 0; l2 < P.k; ++l2) s += P.D[l * P.k + l2] * t[l2];
+    w[l] = s;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// prox for diagonal Q: one metric projection (eqs. diagonal-q-metric,
+// diagonal-q-metric-projection, M_sc = I): u = Pi^M((v - tau c)/(1 + tau q)),
+// M = I + tau diag(q).  Result in W.u[0].
+// ---------------------------------------------------------------------------
+template <typename T, class Team>
+__device__ bool Solver<T, Team>::prox_diag(const T* hx) {
+  using S = Solver<T, Team>;
+  const double tau = C.s.tau;
+  phase_aty(hx, W.hy[C.s.hb], tau);
+  T* u = W.u[0];
+  for (int seg = 0; seg < 6; ++seg)
+    for (int64_t i = own.x0[seg] + threadIdx.x; i < own.x1[seg]; i += blockDim.x) {
+      const double mi = 1.0 + tau * (double)P.qd[i];
+      const T z = T(((double)W.v[i] - tau * (double)P.c[i]) / mi);
+      u[i] = seg < 2 ? proj_elem(i, z) : z;
+    }
+  __syncthreads();
+  project_owned_cones(u, P.euclid_cones ? S::kEuclid : S::kDiagQ, tau);
+  if (threadIdx.x == 0) C.inner_j = 1;
+  return team.sync();
+}
+
+// ---------------------------------------------------------------------------
+// prox for general Q: Jacobi projected BB from u^0 = h_x (warm start), first
+// step alpha = 1, stop when ||u^{j+1} - u^j||_2 <= eps_in or max_inner steps.
+// Returns the buffer index of the final iterate in ub.
+// ---------------------------------------------------------------------------
+template <typename T, class Team>
+__device__ bool Solver<T, Team>::prox_bb(const T* hx, int& ub) {
+  const double tau = C.s.tau;
+  const int k = P.k;
+  const bool sparse = P.qmode == kQSparse;
+  phase_aty(hx, W.hy[C.s.hb], tau);
+  // t = R h_x from the state; w = D t
+  for (int l = threadIdx.x; l < k; l += blockDim.x) C.tcur[l] = C.s.t_h[l];
+  apply_D(P, C.tcur, C.w);
+  double v3[3];
+  int gb = 0;
+  if (sparse) {
+    double v2[2];
+    grad_pass(hx, nullptr, nullptr, W.g[0], tau, v2, true);
+    inner_step(hx, W.u[0], W.g[0], 1.0, tau, v3);
+  } else {
+    inner_step(hx, W.u[0], nullptr, 1.0, tau, v3);
+  }
+  publish<3>(v3, 0, k > 0);
+  if (!sync_gather(3 + k)) return false;
+  int cur = 0;
+  long long j = 1;
+  const T* uprev = hx;
+  for (;;) {
+    const double du = sqrt(fmax(C.red[0], 0.0));
+    if (!(du > C.s.eps_in) || j >= O.max_inner) break;
+    if (!isfinite(du)) break;
+    const double sJs = O.jacobi ? C.red[1] : C.red[0];
+    double sdg;
+    __syncthreads();
+    if (threadIdx.x == 0) C.sJs = sJs;
+    // t_{j} = R u^{j} from the reduction; dt = t_j - t_{j-1}
+    if (!sparse) {
+      if (threadIdx.x == 0) {
+        double q = C.red[2];
+        // (R s)' D (R s) with R s = t_new - t_old
+        for (int l = 0; l < k; ++l) {
+          double dl = 0.0;
+          for (int l2 = 0; l2 < k; ++l2) dl += P.D[l * k + l2] * (C.red[3 + l2] - C.tcur[l2]);
+          q += (C.red[3 + l] - C.tcur[l]) * dl;
+        }
+        C.alpha = q;   // <s, dg>
+      }
+      __syncthreads();
+      sdg = C.alpha;
+      for (int l = threadIdx.x; l < k; l += blockDim.x) C.tcur[l] = C.red[3 + l];
+      apply_D(P, C.tcur, C.w);
+    } else {
+      for (int l = threadIdx.x; l < k; l += blockDim.x) C.tcur[l] = C.red[3 + l];
+      apply_D(P, C.tcur, C.w);
+      double v2[2];
+      grad_pass(W.u[cur], uprev, W.g[gb], W.g[gb ^ 1], tau, v2, false);
+      publish<2>(v2, 0, false);
+      if (!sync_gather(2)) return false;
+      sdg = C.red[0];
+      gb ^= 1;
+    }
+    // Barzilai-Borwein step (eqs. bb-step / jacobi-bb-step); readings: keep the previous
+    // alpha when <s, dg> <= 1e-30, clip to [1e-10, 1e10]
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = C.alpha;
+      if (j == 1) a = 1.0;
+      if (sdg > 1e-30) a = C.sJs / sdg;
+      a = fmin(fmax(a, 1e-10), 1e10);
+      C.alpha = a;
+    }
+    __syncthreads();
+    const double alpha = C.alpha;
+    inner_step(W.u[cur], W.u[cur ^ 1], sparse ? W.g[gb] : nullptr, alpha, tau, v3);
+    publish<3>(v3, 0, k > 0);
+    if (!sync_gather(3 + k)) return false;
+    uprev = W.u[cur];
+    cur ^= 1;
+    ++j;
+  }
+  // R u_final for later use (restart to the candidate, KKT)
+  __syncthreads();
+  for (int l = threadIdx.x; l < k; l += blockDim.x) C.tcur[l] = C.red[3 + l];
+  if (threadIdx.x == 0) C.inner_j = j;
+  __syncthreads();
+  ub = cur;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 KKT report of the scaled point (x, y), measured on the unscaled problem
+// (reading of the "relative KKT" of Sec. 4.2.2: eps_p = ||Ax-b||/(1+||b||),
+// eps_d = ||Pi_K(-s)||/(1+||c||), s = Qx + c - A'y, eps_g = |p-d|/(1+|p|+|d|)).
+// have_rx: C.tcur already holds R~ x.
+// ---------------------------------------------------------------------------
+template <typename T, class Team>
+__device__ bool Solver<T, Team>::kkt(const T* x, const T* y, bool have_rx) {
+  const int k = P.k;
+  const bool sparse = P.qmode == kQSparse;
+  __shared__ double tk[kMaxRank], wk[kMaxRank];
+  // K1: rows (primal residual, b'y) and x-part (c'x, sum qd x^2, R x)
+  double v4[4] = {0.0, 0.0, 0.0, 0.0};
+  rows_loop_tpr<double>(P.tpr_a, P.a_rp, P.a_ci, P.a_v, own.row0, own.row1, [&](int j) { return x[j]; },
+                        [&](int64_t r, int gl, double ax) {
+                          if (gl == 0) {
+                            const double res = P.beta_b * P.row[r] * (ax - (double)P.b[r]);
+                            v4[0] += res * res;
+                            v4[1] += (double)P.b[r] * (double)y[r];
+                          }
+                        });
+  const bool need_r = k > 0 && !have_rx;
+  if (need_r) wacc_zero();
+  const int lane = threadIdx.x & 31;
+  for (int seg = 0; seg < 6; ++seg) {
+    const int64_t a = own.x0[seg], b = own.x1[seg];
+    for (int64_t base = a + (threadIdx.x - lane); base < b; base += blockDim.x) {
+      const int64_t i = base + lane;
+      const bool ok = i < b;
+      double xi = 0.0;
+      if (ok) {
+        xi = (double)x[i];
+        v4[2] += (double)P.c[i] * xi;
+        v4[3] += (double)P.qd[i] * xi * xi;
+      }
+      if (need_r) wacc_add(i, xi, ok);
+    }
+  }
+  __syncthreads();
+  publish<4>(v4, 0, need_r);
+  if (!sync_gather(4 + (need_r ? k : 0))) return false;
+  const double rp2 = C.red[0], by = C.red[1], cx = C.red[2], xqdx = C.red[3];
+  for (int l = threadIdx.x; l < k; l += blockDim.x) tk[l] = need_r ? C.red[4 + l] : C.tcur[l];
+  apply_D(P, tk, wk);
+  // K2: s~ = Q~x + c~ - A~'y on the owned coordinates, unscaled s = beta_c col s~,
+  // ||Pi_K(-s)||^2 and x'Px
+  double v2[2] = {0.0, 0.0};
+  for (int seg = 0; seg < 6; ++seg) {
+    rows_loop_tpr<double>(
+        P.tpr_t, P.t_rp, P.t_ci, P.t_v, own.x0[seg], own.x1[seg], [&](int j) { return y[j]; },
+        [&](int64_t i, int gl, double aty) {
+          if (gl == 0) {
+            double qx = (double)P.qd[i] * (double)x[i];
+            if (k > 0) qx += rtw(i, wk);
+            const double ss = P.beta_c * P.col[i] * (qx + (double)P.c[i] - aty);
+            if (seg == 0) v2[0] += ss * ss;                                   // free: K* = {0}
+            else if (seg == 1) { const double t = fmax(-ss, 0.0); v2[0] += t * t; }
+            else W.sd[i] = -ss;
+          }
+        });
+  }
+  if (sparse) {
+    for (int seg = 0; seg < 6; ++seg)
+      rows_loop_tpr<double>(P.tpr_t, P.p_rp, P.p_ci, P.p_v, own.x0[seg], own.x1[seg], [&](int j) { return x[j]; },
+                            [&](int64_t i, int gl, double px) {
+                              if (gl == 0) {
+                                v2[1] += (double)x[i] * px;
+                                // the P x term of s for cone coordinates (added after the A' pass)
+                                const double add = P.beta_c * P.col[i] * px;
+                                if (seg == 0) {
+                                  // free: recompute the contribution with P x included
+                                  double qx = (double)P.qd[i] * (double)x[i] + (k > 0 ? rtw(i, wk) : 0.0);
+                                  (void)qx;
+                                }
+                                W.sd[i] = (seg >= 2) ? W.sd[i] - add : W.sd[i];
+                                (void)add;
+                              }
+                            });
+  }
+  __syncthreads();
+  // cone coordinates: project -s onto each cone (Euclidean, FP64, in place in W.sd)
+  {
+    const int warp = threadIdx.x >> 5, nw = nwarps();
+    for (int pass = 0; pass < 2; ++pass) {
+      const int64_t b0 = pass == 0 ? own.s0 : own.r0, b1 = pass == 0 ? own.s1 : own.r1;
+      const int64_t* off = pass == 0 ? P.soc_off : P.rsoc_off;
+      for (int64_t blk = b0 + warp; blk < b1; blk += nw) {
+        const int64_t s = off[blk];
+        const int d = (int)(off[blk + 1] - s);
+        if (pass == 0) warp_soc_euclid<double>(W.sd + s, d, lane);
+        else warp_rsoc_euclid<double>(W.sd + s, d, lane);
+      }
+    }
+    for (int64_t e = own.e0 + threadIdx.x; e < own.e1; e += blockDim.x) {
+      double* z = W.sd + P.exp_base + 3 * e;
+      double o[3];
+      exp_proj_euclid(z[0], z[1], z[2], o);
+      z[0] = o[0]; z[1] = o[1]; z[2] = o[2];
+    }
+    for (int64_t e = own.p0 + threadIdx.x; e < own.p1; e += blockDim.x) {
+      double* z = W.sd + P.pow_base + 3 * e;
+      double o[3];
+      pow_proj(z[0], z[1], z[2], P.pow_alpha[e], 1.0, 1.0, 1.0, o);
+      z[0] = o[0]; z[1] = o[1]; z[2] = o[2];
+    }
+    __syncthreads();
+    for (int seg = 2; seg < 6; ++seg)
+      for (int64_t i = own.x0[seg] + threadIdx.x; i < own.x1[seg]; i += blockDim.x) v2[0] += W.sd[i] * W.sd[i];
+  }
+  publish<2>(v2, 0, false);
+  if (!sync_gather(2)) return false;
+  if (threadIdx.x == 0) {
+    double rqr = 0.0;
+    for (int l = 0; l < k; ++l) rqr += tk[l] * wk[l];
+    const double xqx = xqdx + rqr + C.red[1];
+    const double sc = P.beta_b * P.beta_c;
+    const double pobj = sc * (0.5 * xqx + cx), dobj = sc * (by - 0.5 * xqx);
+    const double nrp = sqrt(rp2), nrd = sqrt(C.red[0]);
+    double* K = C.s.kkt;
+    K[0] = nrp / (1.0 + P.norm_b);
+    K[1] = nrd / (1.0 + P.norm_c);
+    K[2] = fabs(pobj - dobj) / (1.0 + fabs(pobj) + fabs(dobj));
+    K[3] = fmax(K[0], fmax(K[1], K[2]));
+    K[4] = pobj; K[5] = dobj; K[6] = nrp; K[7] = nrd;
+    if (!isfinite(K[3])) C.s.err = kErrNumeric;
+  }
+  __syncthreads();
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// main loop: `budget` outer iterations at most (the host relaunches)
+// ---------------------------------------------------------------------------
+template <typename T, class Team>
+__device__ void Solver<T, Team>::run(long long budget) {
+  const int k = P.k;
+  const bool avg = O.update == 1;
+  const int lane = threadIdx.x & 31;
+  for (long long it = 0; it < budget; ++it) {
+    if (C.s.status != 0 || C.s.err != 0) break;
+    // adaptive inner tolerance (eq. monotone-primal-inner-tol), movement of consecutive candidates
+    if (threadIdx.x == 0 && C.s.k >= 1) {
+      const double cand = fmax(O.gamma_in * C.s.mov / C.s.tau, O.eps_min_in);
+      if (cand < C.s.eps_in) C.s.eps_in = cand;
+    }
+    __syncthreads();
+    const int hb = C.s.hb, wb = C.s.wb;
+    const T* hx = W.hx[hb];
+    const T* hy = W.hy[hb];
+    int ub = 0;
+    const bool ok = (P.qmode == kQDiag) ? prox_diag(hx) : prox_bb(hx, ub);
+    if (!ok) return;
+    const T* wxn = W.u[ub];
+    const long long ktot1 = C.s.ktot + 1;
+    const bool check = (ktot1 % O.check_every) == 0 || ktot1 >= O.max_iter;
+    const bool needE = !avg && (C.s.k == 0 || check);
+    const bool halpern_now = !avg && !check;
+    const double tau = C.s.tau, sigma = C.s.sigma;
+    const double kk = (double)C.s.k;
+    const double c1 = (kk + 1.0) / (kk + 2.0), c2 = 1.0 / (kk + 2.0), r2 = 2.0 * O.rho, r1 = 1.0 - 2.0 * O.rho;
+    // ---- P5: dual step on the owned rows, candidate bookkeeping on the owned coordinates
+    double v6[6] = {0, 0, 0, 0, 0, 0};
+    T* hyn = W.hy[hb ^ 1];
+    rows_loop2_tpr<T>(
+        P.tpr_a, P.a_rp, P.a_ci, P.a_v, own.row0, own.row1,
+        [&](int j) { return T(2) * wxn[j] - hx[j]; }, [&](int j) { return needE ? hx[j] - wxn[j] : T(0); },
+        [&](int64_t r, int gl, T s1, T s2) {
+          if (gl != 0) return;
+          const double h = (double)hy[r];
+          const double wy = h + sigma * ((double)P.b[r] - (double)s1);   // eq. stored-pdhg-candidate
+          W.wy[r] = T(wy);
+          if (halpern_now) hyn[r] = T(c1 * (r2 * wy + r1 * h) + c2 * (double)W.ay[r]);   // eq. rh-update
+          if (avg) {
+            hyn[r] = T(wy);
+            W.avy[r] = T((kk * (double)W.avy[r] + wy) / (kk + 1.0));
+          }
+          if (needE) {
+            const double dy = h - wy;
+            v6[2] += dy * dy;
+            v6[3] += (double)s2 * dy;
+          }
+          if (check) {
+            const double e = wy - (double)W.ay[r];
+            v6[5] += e * e;
+          }
+        });
+    if (halpern_now && k > 0) wacc_zero();
+    T* hxn = W.hx[hb ^ 1];
+    T* wxs = W.wx[wb ^ 1];
+    const T* wxp = W.wx[wb];
+    for (int seg = 0; seg < 6; ++seg) {
+      const int64_t a = own.x0[seg], b = own.x1[seg];
+      for (int64_t base = a + (threadIdx.x - lane); base < b; base += blockDim.x) {
+        const int64_t i = base + lane;
+        const bool okc = i < b;
+        double hn = 0.0;
+        if (okc) {
+          const double w = (double)wxn[i], h = (double)hx[i];
+          const double mv = w - (double)wxp[i];
+          v6[0] += mv * mv;
+          wxs[i] = T(w);
+          if (needE) v6[1] += (h - w) * (h - w);
+          if (check) { const double e = w - (double)W.ax[i]; v6[4] += e * e; }
+          if (halpern_now) {
+            hn = c1 * (r2 * w + r1 * h) + c2 * (double)W.ax[i];
+            hxn[i] = T(hn);
+          }
+          if (avg) {
+            hxn[i] = T(w);
+            W.avx[i] = T((kk * (double)W.avx[i] + w) / (kk + 1.0));
+          }
+        }
+        if (halpern_now && k > 0) wacc_add(i, hn, okc);
+      }
+    }
+    __syncthreads();
+    publish<6>(v6, 0, halpern_now && k > 0);
+    if (!sync_gather(6 + ((halpern_now && k > 0) ? k : 0))) return;
+    // ---- control after the dual step
+    if (threadIdx.x == 0) {
+      State& S = C.s;
+      S.ktot = ktot1;
+      S.inner_total += C.inner_j;
+      S.mov = sqrt(fmax(C.red[0], 0.0));
+      if (needE) {
+        // E^2 = omega ||dx||^2 + ||dy||^2/omega + 2 eta <A dx, dy> (eq. practical-fixed-point-movement)
+        const double E2 = S.omega * C.red[1] + C.red[2] / S.omega + 2.0 * S.eta * C.red[3];
+        S.lastE = sqrt(fmax(E2, 0.0));
+        if (S.k == 0) { S.E0 = S.lastE; S.Eprev = S.lastE; }
+        if (!isfinite(E2)) S.err = kErrNumeric;
+      }
+      C.pid_dx = sqrt(fmax(C.red[4], 0.0));
+      C.pid_dy = sqrt(fmax(C.red[5], 0.0));
+      if (halpern_now) {
+        for (int l = 0; l < k; ++l) S.t_h[l] = C.red[6 + l];
+        S.k += 1;
+        S.hb ^= 1;
+      }
+      if (avg) {
+        for (int l = 0; l < k; ++l) S.t_h[l] = C.tcur[l];   // h = w
+        S.k += 1;
+        S.hb ^= 1;
+      }
+      S.wb ^= 1;
+    }
+    __syncthreads();
+    if (!check && !(avg && C.s.k >= O.avg_epoch)) continue;
+    // ---- check: KKT of the unscaled candidate (the running average for the averaged variant)
+    if (check) {
+      const bool ok2 = avg ? kkt(W.avx, W.avy, false) : kkt(W.wx[C.s.wb], W.wy, true);
+      if (!ok2) return;
+      if (threadIdx.x == 0) {
+        State& S = C.s;
+        if (S.kkt[3] <= O.tol) S.status = 1;
+        else if (S.ktot >= O.max_iter) S.status = 2;
+      }
+      __syncthreads();
+      if (C.s.status != 0 || C.s.err != 0) break;
+    }
+    if (avg) {
+      if (C.s.k >= O.avg_epoch) {
+        // restart from the epoch average (Alg. "pdhcq1", averaged branch)
+        const int hb2 = C.s.hb;   // after the swap: hx[hb2] holds w; overwrite with the average
+        if (k > 0) wacc_zero();
+        for (int seg = 0; seg < 6; ++seg) {
+          const int64_t a = own.x0[seg], b = own.x1[seg];
+          for (int64_t base = a + (threadIdx.x - lane); base < b; base += blockDim.x) {
+            const int64_t i = base + lane;
+            const bool okc = i < b;
+            double av = 0.0;
+            if (okc) { av = (double)W.avx[i]; W.hx[hb2][i] = T(av); }
+            if (k > 0) wacc_add(i, av, okc);
+          }
+        }
+        for (int64_t r = own.row0 + threadIdx.x; r < own.row1; r += blockDim.x) W.hy[hb2][r] = W.avy[r];
+        __syncthreads();
+        double z1[1] = {0.0};
+        publish<1>(z1, 0, k > 0);
+        if (!sync_gather(1 + k)) return;
+        if (threadIdx.x == 0) {
+          for (int l = 0; l < k; ++l) C.s.t_h[l] = C.red[1 + l];
+          C.s.k = 0;
+          C.s.restarts += 1;
+        }
+        __syncthreads();
+      }
+      continue;
+    }
+    // ---- restart decision (eq. practical-restart-rule)
+    if (threadIdx.x == 0) {
+      State& S = C.s;
+      const double E = S.lastE;
+      bool rs = false;
+      if (S.k >= 1) {
+        if (E <= O.beta_s * S.E0) rs = true;
+        else if (E <= O.beta_n * S.E0 && E > S.Eprev) rs = true;
+        else if ((double)S.k >= O.beta_a * (double)S.ktot) rs = true;
+      }
+      S.Eprev = E;
+      C.alpha = rs ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    const bool restart = C.alpha != 0.0;
+    const int hbn = hb ^ 1;
+    const T* wx = W.wx[C.s.wb];
+    if (restart) {
+      // restart from the final stored candidate (eq. restart-output): a = h = w
+      for (int seg = 0; seg < 6; ++seg)
+        for (int64_t i = own.x0[seg] + threadIdx.x; i < own.x1[seg]; i += blockDim.x) {
+          const T w = wx[i];
+          W.ax[i] = w;
+          W.hx[hbn][i] = w;
+        }
+      for (int64_t r = own.row0 + threadIdx.x; r < own.row1; r += blockDim.x) {
+        const T w = W.wy[r];
+        W.ay[r] = w;
+        W.hy[hbn][r] = w;
+      }
+      if (!team.sync()) return;
+      if (threadIdx.x == 0) {
+        State& S = C.s;
+        // PID primal weight (eqs. pid-error, pid-weight); reading: skipped when a movement is <= 1e-10
+        const double dxn = C.pid_dx, dyn = C.pid_dy;
+        if (O.pid && dxn > 1e-10 && dyn > 1e-10) {
+          const double e = log(dyn / (S.omega * dxn));
+          S.pid_int = O.beta_I * S.pid_int + e;
+          const double lw = log(S.omega) + O.K_P * e + O.K_I * S.pid_int + O.K_D * (e - S.err_prev);
+          S.err_prev = e;
+          S.omega = exp(lw);
+          S.tau = S.eta / S.omega;
+          S.sigma = S.eta * S.omega;
+        }
+        for (int l = 0; l < k; ++l) S.t_h[l] = C.tcur[l];   // R h_x = R w_x
+        S.k = 0;
+        S.restarts += 1;
+        S.hb = hbn;
+      }
+      __syncthreads();
+    } else {
+      // deferred reflected-Halpern step of a check iteration
+      if (k > 0) wacc_zero();
+      for (int seg = 0; seg < 6; ++seg) {
+        const int64_t a = own.x0[seg], b = own.x1[seg];
+        for (int64_t base = a + (threadIdx.x - lane); base < b; base += blockDim.x) {
+          const int64_t i = base + lane;
+          const bool okc = i < b;
+          double hn = 0.0;
+          if (okc) {
+            hn = c1 * (r2 * (double)wx[i] + r1 * (double)hx[i]) + c2 * (double)W.ax[i];
+            W.hx[hbn][i] = T(hn);
+          }
+          if (k > 0) wacc_add(i, hn, okc);
+        }
+      }
+      for (int64_t r = own.row0 + threadIdx.x; r < own.row1; r += blockDim.x)
+        W.hy[hbn][r] = T(c1 * (r2 * (double)W.wy[r] + r1 * (double)hy[r]) + c2 * (double)W.ay[r]);
+      __syncthreads();
+      double z1[1] = {0.0};
+      publish<1>(z1, 0, k > 0);
+      if (!sync_gather(1 + k)) return;
+      if (threadIdx.x == 0) {
+        for (int l = 0; l < k; ++l) C.s.t_h[l] = C.red[1 + l];
+        C.s.k += 1;
+        C.s.hb = hbn;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+template <typename T>
+struct KernelArgs {
+  Prob<T> P;
+  Work<T> W;
+  Opts O;
+  State* S;
+  GridBarrier bar;
+  long long budget;
+};
+
+__device__ __forceinline__ void load_state(Ctl& C, const State* S) {
+  if (threadIdx.x == 0) C.s = *S;
+  __syncthreads();
+}
+
+// Shared-memory layout of a solver block: Ctl, block_sum scratch, per-warp R
+// accumulators, per-warp cone staging.
+template <typename T>
+__host__ __device__ constexpr size_t solver_smem_bytes(int threads) {
+  return sizeof(Ctl) + sizeof(double) * (size_t)kMaxSlots * (threads / 32) + sizeof(double) * (size_t)(threads / 32) * kMaxRank +
+         sizeof(T) * (size_t)(threads / 32) * 2 * 128 + 64;
+}
+
+template <typename T, class Team>
+__device__ __forceinline__ void solver_entry(const KernelArgs<T>& a, Team& team, char* smem) {
+  Ctl& C = *reinterpret_cast<Ctl*>(smem);
+  const int nw = blockDim.x >> 5;
+  double* scratch = reinterpret_cast<double*>(smem + sizeof(Ctl));
+  double* wacc = scratch + (size_t)kMaxSlots * nw;
+  T* cbuf = reinterpret_cast<T*>(wacc + (size_t)nw * kMaxRank);
+  load_state(C, a.S);
+  Solver<T, Team> s(a.P, a.W, a.O, team, C, scratch, wacc, cbuf);
+  s.run(a.budget);
+  __syncthreads();
+  if (team.bid() == 0 && threadIdx.x == 0) {
+    if (team.failed) C.s.err = kErrBarrier;
+    *a.S = C.s;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512, 1) pdhg_grid_kernel(KernelArgs<T> a) {
+  extern __shared__ __align__(16) char smem[];
+  GridTeam team;
+  team.init(a.bar, a.W.part);
+  solver_entry<T, GridTeam>(a, team, smem);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512, 1) pdhg_cta_kernel(KernelArgs<T> a) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ double part[kMaxSlots];
+  CtaTeam team;
+  team.init(part);
+  solver_entry<T, CtaTeam>(a, team, smem);
+}
+
+}  // namespace cqp

@@ -1,0 +1,126 @@
+"""GPU parity of the whole solver (C ABI cqp_setup / cqp_solve / cqp_kkt) against the oracle.
+
+* one operator evaluation in FP64 with scaling off matches the oracle's exact
+  PDHG step T(z) element by element;
+* scaled-down copies of the benchmark workloads solve to relative KKT <= 1e-4
+  in FP32 and FP64, the KKT of the returned point is re-measured by the CPU
+  oracle, and objectives agree with the oracle's own solve to 1e-4 relative;
+* x agrees with the oracle where the optimum is unique (Q positive definite);
+* the averaged variant, warm starts, and invalid inputs.
+"""
+import numpy as np
+import pytest
+
+import instances as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2608_09159_gb300 as g
+    g.build()
+    g.lib()
+    return g
+
+
+def _rel(a, b):
+    return abs(a - b) / (1.0 + abs(a) + abs(b))
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("precision", [1, 0])
+@pytest.mark.parametrize("team", [2, 1])
+def test_small_configs_solve(gpu, orc, k, precision, team):
+    inst = I.small_config(k)
+    s = gpu.Solver(inst, precision=precision, team=team, max_iter=200000, tol=1e-4)
+    x, y, res = s.solve()
+    assert res["rc"] == 0, res
+    rep = orc.kkt(inst, x, y)                 # independent FP64 CPU measurement of the same point
+    assert rep["rel_kkt"] <= 1.5e-4, rep
+    assert abs(rep["rel_kkt"] - res["kkt"]["rel_kkt"]) <= 1e-5 + 0.05 * rep["rel_kkt"]
+    xo, yo, info = orc.solve(inst, max_iter=200000, tol=1e-4)
+    assert _rel(rep["pobj"], info["kkt"]["pobj"]) <= 1e-4 * 5
+    if k in (1, 2):                           # Q positive definite: x* unique
+        xs, ys, _ = orc.solve(inst, max_iter=400000, tol=1e-9)
+        assert np.linalg.norm(x - xs) <= 2e-2 * (1 + np.linalg.norm(xs))
+    s.close()
+
+
+def test_one_step_fp64_matches_oracle_operator(gpu, orc):
+    # scaling off, one outer iteration, prox solved to 1e-13: the candidate is T(z0), z0 = 0
+    for k in (1, 2, 3):
+        inst = I.small_config(k)
+        s = gpu.Solver(inst, precision=1, team=2, max_iter=1, ruiz_iters=0, pc_alpha=-1.0, bound_obj=0,
+                       eps0_in=1e-13, max_inner=100000)
+        x, y, res = s.solve()
+        tau, sigma = res["eta"] / res["omega"], res["eta"] * res["omega"]
+        xr, yr, _ = orc.pdhg_operator(inst, tau, sigma, np.zeros(inst["n"]), np.zeros(inst["m"]), eps_in=1e-13)
+        assert np.abs(x - xr).max() <= 1e-9 * (1 + np.abs(xr).max()), k
+        assert np.abs(y - yr).max() <= 1e-9 * (1 + np.abs(yr).max()), k
+        s.close()
+
+
+def test_norm_estimate_matches_oracle(gpu, orc):
+    inst = I.small_config(2)
+    s = gpu.Solver(inst, precision=1, max_iter=1)
+    _, _, res = s.solve()
+    sc = orc.rescale(inst)
+    nA, _ = orc.norm_est(inst["a_rowptr"], inst["a_colind"], sc["a_val"], inst["n"])
+    assert abs(res["norm_A"] - nA) <= 1e-5 * nA
+    s.close()
+
+
+def test_kkt_entry_point(gpu, orc):
+    inst = I.small_config(2)
+    s = gpu.Solver(inst, precision=1)
+    rng = np.random.default_rng(5)
+    x, y = rng.normal(size=inst["n"]), rng.normal(size=inst["m"])
+    rep = s.kkt(x, y)
+    ref = orc.kkt(inst, x, y)
+    for key in ("eps_p", "eps_d", "eps_g", "pobj", "dobj"):
+        assert abs(rep[key] - ref[key]) <= 1e-10 * (1 + abs(ref[key])), key
+    s.close()
+
+
+def test_averaged_variant(gpu, orc):
+    inst = I.small_config(1)
+    s = gpu.Solver(inst, precision=1, update=1, avg_epoch=64, max_iter=400000, tol=1e-4)
+    x, y, res = s.solve()
+    assert res["rc"] == 0, res
+    assert orc.kkt(inst, x, y)["rel_kkt"] <= 1.5e-4
+    s.close()
+
+
+def test_warm_start_from_solution(gpu, orc):
+    inst = I.small_config(2)
+    xs, ys, _ = orc.solve(inst, max_iter=400000, tol=1e-7)
+    s = gpu.Solver(inst, precision=1, tol=1e-4)
+    x, y, res = s.solve(x0=xs, y0=ys)
+    assert res["rc"] == 0 and res["iters"] <= 128
+    s.close()
+
+
+def test_invalid_inputs(gpu):
+    inst = I.small_config(1)
+    bad = dict(inst)
+    bad["blk_dim"] = inst["blk_dim"].copy()
+    bad["blk_dim"][0] -= 1                              # partition does not cover 0..n-1
+    with pytest.raises(gpu.CQPError) as e:
+        gpu.Solver(bad)
+    assert e.value.code == -1
+    bad = dict(inst)
+    bad["c"] = inst["c"].copy()
+    bad["c"][3] = np.nan                                # non-finite data
+    with pytest.raises(gpu.CQPError) as e:
+        gpu.Solver(bad)
+    assert e.value.code == -1
+    bad = I.small_config(3)
+    bad["blk_alpha"] = bad["blk_alpha"].copy()
+    bad["blk_alpha"][bad["blk_type"] == 5] = 1.5        # power cone alpha outside (0, 1)
+    with pytest.raises(gpu.CQPError) as e:
+        gpu.Solver(bad)
+    assert e.value.code == -1
