@@ -124,6 +124,7 @@ typedef struct {
   int32_t blocks_per_sm;    /* 0 = auto (cooperative team only) */
   int32_t tpr_a, tpr_at;    /* threads per CSR row for A and A', 0 = autotuned */
   int32_t launch_iters;     /* outer iterations per kernel launch, 0 = auto */
+  int32_t profile;          /* 1: record per-phase device time in cqp_result.phase_ms */
   void* stream;             /* cudaStream_t, NULL = default stream */
 } cqp_options;
 
@@ -139,6 +140,10 @@ typedef struct {
   cqp_kkt_report kkt;
   double eta, norm_A, omega;
   double setup_ms, solve_ms;
+  /* with opt.profile: device time (block 0) per phase of the iteration: A'y product,
+   * prox work, prox barriers, dual step, its barrier, KKT checks, restart/Halpern at
+   * checks, whole loop */
+  double phase_ms[8];
 } cqp_result;
 
 typedef struct cqp_handle cqp_handle;

@@ -59,7 +59,7 @@ class Options(C.Structure):
                 ("power_iters", C.c_int32), ("power_tol", C.c_double), ("step_factor", C.c_double),
                 ("input_on_device", C.c_int32), ("team", C.c_int32), ("threads", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("tpr_a", C.c_int32), ("tpr_at", C.c_int32),
-                ("launch_iters", C.c_int32), ("stream", C.c_void_p)]
+                ("launch_iters", C.c_int32), ("profile", C.c_int32), ("stream", C.c_void_p)]
 
 
 class KKTReport(C.Structure):
@@ -70,7 +70,8 @@ class KKTReport(C.Structure):
 class Result(C.Structure):
     _fields_ = [("status", C.c_int32), ("iters", C.c_int64), ("restarts", C.c_int64), ("inner_total", C.c_int64),
                 ("kernel_launches", C.c_int64), ("kkt", KKTReport), ("eta", C.c_double), ("norm_A", C.c_double),
-                ("omega", C.c_double), ("setup_ms", C.c_double), ("solve_ms", C.c_double)]
+                ("omega", C.c_double), ("setup_ms", C.c_double), ("solve_ms", C.c_double),
+                ("phase_ms", C.c_double * 8)]
 
 
 _lib = None
@@ -255,7 +256,8 @@ class Solver:
 
 
 def result_dict(res: Result, rc: int):
-    d = {f: getattr(res, f) for f, _ in Result._fields_ if f != "kkt"}
+    d = {f: getattr(res, f) for f, _ in Result._fields_ if f not in ("kkt", "phase_ms")}
+    d["phase_ms"] = list(res.phase_ms)
     d["kkt"] = {f: getattr(res.kkt, f) for f, _ in KKTReport._fields_}
     d["rc"] = rc
     return d

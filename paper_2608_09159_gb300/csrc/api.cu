@@ -535,6 +535,7 @@ struct Handle : HandleBase {
     O.beta_I = o.beta_I; O.K_P = o.K_P; O.K_I = o.K_I; O.K_D = o.K_D;
     O.max_iter = o.max_iter; O.check_every = std::max(1, o.check_every); O.max_inner = std::max(1, o.max_inner);
     O.jacobi = o.jacobi; O.pid = o.pid; O.update = o.update; O.avg_epoch = std::max(1, o.avg_epoch);
+    O.profile = o.profile;
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
     setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -618,6 +619,7 @@ struct Handle : HandleBase {
       res->omega = back.omega;
       res->setup_ms = setup_ms;
       res->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      for (int i = 0; i < 8; ++i) res->phase_ms[i] = back.prof[i] * 1e-6;
     }
     return status;
   }

@@ -99,13 +99,14 @@ __device__ __noinline__ void warp_soc_metric(T* x, const T* m, int d, int lane) 
       const double dm = mt - lam;
       const double f = s2 - bt / (dm * dm);
       const double fp = -2.0 * s3 - 2.0 * bt / (dm * dm * dm);
-      if (f > 0.0) lo = lam; else hi = lam;
+      if (f == 0.0) break;                               // exact root: keep lam
+      // z_t > 0: f(lo) > 0 > f(hi);  z_t < 0: f(lo) < 0 < f(hi)
+      if ((f > 0.0) == (zt > 0.0)) lo = lam; else hi = lam;
       double nx = (fp != 0.0) ? lam - f / fp : 0.5 * (lo + hi);
       if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
       const double step = fabs(nx - lam);
       lam = nx;
-      if (f == 0.0 || step <= Tol<T>::rel * fmax(lam, 1e-300) || (hi - lo) <= Tol<T>::rel * fmax(lam, 1e-300))
-        break;
+      if (step <= Tol<T>::rel * fmax(lam, 1e-300) || (hi - lo) <= Tol<T>::rel * fmax(lam, 1e-300)) break;
     }
   }
   double vv = 0.0;

@@ -78,6 +78,7 @@ struct Opts {
   double beta_s, beta_n, beta_a, beta_I, K_P, K_I, K_D;
   long long max_iter;
   int check_every, max_inner, jacobi, pid, update, avg_epoch;
+  int profile;                     // accumulate per-phase wall time (block 0) into State::prof
 };
 
 // Control state of one solve (device memory, FP64 scalars).
@@ -87,6 +88,8 @@ struct State {
   double t_h[kMaxRank];            // R~ h_x of the current Halpern state
   double kkt[8];                   // eps_p, eps_d, eps_g, rel_kkt, pobj, dobj, ||r_p||, ||r_d||
   double lastE;
+  double prof[8];                  // ns per phase: A'y, prox work, prox barriers, dual step, its barrier,
+                                   // KKT, restart/Halpern at checks, whole loop
   long long k, ktot, restarts, inner_total;
   int hb, wb;                      // current Halpern / candidate buffer
   int status;                      // 0 running, 1 converged, 2 iteration limit
@@ -102,6 +105,7 @@ struct Ctl {
   double alpha, sJs;
   double pid_dx, pid_dy;           // ||w_x - a_x||, ||w_y - a_y|| of the last check
   long long inner_j;
+  unsigned long long t_last;       // profiling clock
 };
 
 // ---------------------------------------------------------------------------
@@ -207,6 +211,19 @@ struct Solver {
 
   // ---- small helpers -------------------------------------------------------
   __device__ __forceinline__ int nwarps() const { return blockDim.x >> 5; }
+  static __device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+  }
+  // adds the time since the previous tick to phase `slot` (block 0, thread 0, when profiling)
+  __device__ __forceinline__ void tick(int slot) {
+    if (O.profile && team.bid() == 0 && threadIdx.x == 0) {
+      const unsigned long long t = now_ns();
+      C.s.prof[slot] += (double)(t - C.t_last);
+      C.t_last = t;
+    }
+  }
 
   // zero the per-warp R accumulators
   __device__ void wacc_zero() {
@@ -246,9 +263,11 @@ struct Solver {
     }
     __syncthreads();
   }
-  __device__ bool sync_gather(int nslots) {
+  __device__ bool sync_gather(int nslots, int prof_work = -1, int prof_wait = -1) {
+    if (prof_work >= 0) tick(prof_work);
     if (!team.sync()) return false;
     team.gather(nslots, C.red);
+    if (prof_wait >= 0) tick(prof_wait);
     return true;
   }
 
@@ -331,7 +350,7 @@ struct Solver {
   // whole gradient is taken from gs (computed by grad_pass).
   // Accumulates s = u_next - u_cur: v3 = {||s||^2, <s, J s>, sum (qd + 1/tau) s^2} and,
   // with R, the warp partials of R u_next.
-  __device__ void inner_step(const T* ucur, T* unext, const T* gs, double alpha, double tau, double (&v3)[3]) {
+  __device__ void inner_step(const T* ucur, T* unext, const T* gs, double alpha, double tau, double (&v3)[4]) {
     const double itau = 1.0 / tau;
     const bool lowr = P.k > 0;
     const bool jac = O.jacobi != 0;
@@ -342,7 +361,7 @@ struct Solver {
       return g;
     };
     auto jm = [&](int64_t i) { return jac ? (double)P.jd[i] + itau : 1.0; };
-    v3[0] = v3[1] = v3[2] = 0.0;
+    v3[0] = v3[1] = v3[2] = v3[3] = 0.0;
     if (lowr) wacc_zero();
     // elementwise segments (free, nonneg): whole warps iterate together
     const int lane = threadIdx.x & 31;
@@ -362,6 +381,7 @@ struct Solver {
           v3[0] += s * s;
           v3[1] += J * s * s;
           v3[2] += ((double)P.qd[i] + itau) * s * s;
+          v3[3] += un * un;
         }
         if (lowr) wacc_add(i, un, ok);
       }
@@ -386,6 +406,7 @@ struct Solver {
           v3[0] += s * s;
           v3[1] += jm(i) * s * s;
           v3[2] += ((double)P.qd[i] + itau) * s * s;
+          v3[3] += un * un;
         }
         if (lowr) wacc_add(i, un, ok);
       }

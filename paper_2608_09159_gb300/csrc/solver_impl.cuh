@@ -65,6 +65,7 @@ __device__ bool Solver<T, Team>::prox_diag(const T* hx) {
   using S = Solver<T, Team>;
   const double tau = C.s.tau;
   phase_aty(hx, W.hy[C.s.hb], tau);
+  tick(0);
   T* u = W.u[0];
   for (int seg = 0; seg < 6; ++seg)
     for (int64_t i = own.x0[seg] + threadIdx.x; i < own.x1[seg]; i += blockDim.x) {
@@ -75,7 +76,10 @@ __device__ bool Solver<T, Team>::prox_diag(const T* hx) {
   __syncthreads();
   project_owned_cones(u, P.euclid_cones ? S::kEuclid : S::kDiagQ, tau);
   if (threadIdx.x == 0) C.inner_j = 1;
-  return team.sync();
+  tick(1);
+  const bool ok = team.sync();
+  tick(2);
+  return ok;
 }
 
 // ---------------------------------------------------------------------------
@@ -89,11 +93,15 @@ __device__ bool Solver<T, Team>::prox_bb(const T* hx, int& ub) {
   const int k = P.k;
   const bool sparse = P.qmode == kQSparse;
   phase_aty(hx, W.hy[C.s.hb], tau);
+  tick(0);
   // t = R h_x from the state; w = D t
   for (int l = threadIdx.x; l < k; l += blockDim.x) C.tcur[l] = C.s.t_h[l];
   apply_D(P, C.tcur, C.w);
-  double v3[3];
+  double v3[4];
   int gb = 0;
+  // ||u^{j+1} - u^j|| cannot fall below the rounding level of u: the stop test compares it
+  // with max(eps_in, 4 eps_T ||u||) (precision floor; eps_T = 2^-24 or 2^-53)
+  const double eps_T = sizeof(T) == 4 ? 5.9604644775390625e-08 : 1.1102230246251565e-16;
   if (sparse) {
     double v2[2];
     grad_pass(hx, nullptr, nullptr, W.g[0], tau, v2, true);
@@ -101,14 +109,15 @@ __device__ bool Solver<T, Team>::prox_bb(const T* hx, int& ub) {
   } else {
     inner_step(hx, W.u[0], nullptr, 1.0, tau, v3);
   }
-  publish<3>(v3, 0, k > 0);
-  if (!sync_gather(3 + k)) return false;
+  publish<4>(v3, 0, k > 0);
+  if (!sync_gather(4 + k, 1, 2)) return false;
   int cur = 0;
   long long j = 1;
   const T* uprev = hx;
   for (;;) {
     const double du = sqrt(fmax(C.red[0], 0.0));
-    if (!(du > C.s.eps_in) || j >= O.max_inner) break;
+    const double floor_u = 4.0 * eps_T * sqrt(fmax(C.red[3], 0.0));
+    if (!(du > fmax(C.s.eps_in, floor_u)) || j >= O.max_inner) break;
     if (!isfinite(du)) break;
     const double sJs = O.jacobi ? C.red[1] : C.red[0];
     double sdg;
@@ -121,22 +130,22 @@ __device__ bool Solver<T, Team>::prox_bb(const T* hx, int& ub) {
         // (R s)' D (R s) with R s = t_new - t_old
         for (int l = 0; l < k; ++l) {
           double dl = 0.0;
-          for (int l2 = 0; l2 < k; ++l2) dl += P.D[l * k + l2] * (C.red[3 + l2] - C.tcur[l2]);
-          q += (C.red[3 + l] - C.tcur[l]) * dl;
+          for (int l2 = 0; l2 < k; ++l2) dl += P.D[l * k + l2] * (C.red[4 + l2] - C.tcur[l2]);
+          q += (C.red[4 + l] - C.tcur[l]) * dl;
         }
         C.alpha = q;   // <s, dg>
       }
       __syncthreads();
       sdg = C.alpha;
-      for (int l = threadIdx.x; l < k; l += blockDim.x) C.tcur[l] = C.red[3 + l];
+      for (int l = threadIdx.x; l < k; l += blockDim.x) C.tcur[l] = C.red[4 + l];
       apply_D(P, C.tcur, C.w);
     } else {
-      for (int l = threadIdx.x; l < k; l += blockDim.x) C.tcur[l] = C.red[3 + l];
+      for (int l = threadIdx.x; l < k; l += blockDim.x) C.tcur[l] = C.red[4 + l];
       apply_D(P, C.tcur, C.w);
       double v2[2];
       grad_pass(W.u[cur], uprev, W.g[gb], W.g[gb ^ 1], tau, v2, false);
       publish<2>(v2, 0, false);
-      if (!sync_gather(2)) return false;
+      if (!sync_gather(2, 1, 2)) return false;
       sdg = C.red[0];
       gb ^= 1;
     }
@@ -153,15 +162,15 @@ __device__ bool Solver<T, Team>::prox_bb(const T* hx, int& ub) {
     __syncthreads();
     const double alpha = C.alpha;
     inner_step(W.u[cur], W.u[cur ^ 1], sparse ? W.g[gb] : nullptr, alpha, tau, v3);
-    publish<3>(v3, 0, k > 0);
-    if (!sync_gather(3 + k)) return false;
+    publish<4>(v3, 0, k > 0);
+    if (!sync_gather(4 + k, 1, 2)) return false;
     uprev = W.u[cur];
     cur ^= 1;
     ++j;
   }
   // R u_final for later use (restart to the candidate, KKT)
   __syncthreads();
-  for (int l = threadIdx.x; l < k; l += blockDim.x) C.tcur[l] = C.red[3 + l];
+  for (int l = threadIdx.x; l < k; l += blockDim.x) C.tcur[l] = C.red[4 + l];
   if (threadIdx.x == 0) C.inner_j = j;
   __syncthreads();
   ub = cur;
@@ -206,14 +215,26 @@ __device__ bool Solver<T, Team>::kkt(const T* x, const T* y, bool have_rx) {
       if (need_r) wacc_add(i, xi, ok);
     }
   }
+  double v5[5] = {v4[0], v4[1], v4[2], v4[3], 0.0};
+  if (sparse) {
+    // (P~ x)_i on the owned coordinates, kept in W.sd until K2 reads it
+    for (int seg = 0; seg < 6; ++seg)
+      rows_loop_tpr<double>(P.tpr_t, P.p_rp, P.p_ci, P.p_v, own.x0[seg], own.x1[seg], [&](int j) { return x[j]; },
+                            [&](int64_t i, int gl, double px) {
+                              if (gl == 0) {
+                                W.sd[i] = px;
+                                v5[4] += (double)x[i] * px;
+                              }
+                            });
+  }
   __syncthreads();
-  publish<4>(v4, 0, need_r);
-  if (!sync_gather(4 + (need_r ? k : 0))) return false;
-  const double rp2 = C.red[0], by = C.red[1], cx = C.red[2], xqdx = C.red[3];
-  for (int l = threadIdx.x; l < k; l += blockDim.x) tk[l] = need_r ? C.red[4 + l] : C.tcur[l];
+  publish<5>(v5, 0, need_r);
+  if (!sync_gather(5 + (need_r ? k : 0))) return false;
+  const double rp2 = C.red[0], by = C.red[1], cx = C.red[2], xqdx = C.red[3], xpx = C.red[4];
+  for (int l = threadIdx.x; l < k; l += blockDim.x) tk[l] = need_r ? C.red[5 + l] : C.tcur[l];
   apply_D(P, tk, wk);
   // K2: s~ = Q~x + c~ - A~'y on the owned coordinates, unscaled s = beta_c col s~,
-  // ||Pi_K(-s)||^2 and x'Px
+  // ||Pi_K(-s)||^2 (free: K* = {0}; nonneg: max(-s, 0); cones below)
   double v2[2] = {0.0, 0.0};
   for (int seg = 0; seg < 6; ++seg) {
     rows_loop_tpr<double>(
@@ -222,30 +243,13 @@ __device__ bool Solver<T, Team>::kkt(const T* x, const T* y, bool have_rx) {
           if (gl == 0) {
             double qx = (double)P.qd[i] * (double)x[i];
             if (k > 0) qx += rtw(i, wk);
+            if (sparse) qx += W.sd[i];
             const double ss = P.beta_c * P.col[i] * (qx + (double)P.c[i] - aty);
-            if (seg == 0) v2[0] += ss * ss;                                   // free: K* = {0}
+            if (seg == 0) v2[0] += ss * ss;
             else if (seg == 1) { const double t = fmax(-ss, 0.0); v2[0] += t * t; }
             else W.sd[i] = -ss;
           }
         });
-  }
-  if (sparse) {
-    for (int seg = 0; seg < 6; ++seg)
-      rows_loop_tpr<double>(P.tpr_t, P.p_rp, P.p_ci, P.p_v, own.x0[seg], own.x1[seg], [&](int j) { return x[j]; },
-                            [&](int64_t i, int gl, double px) {
-                              if (gl == 0) {
-                                v2[1] += (double)x[i] * px;
-                                // the P x term of s for cone coordinates (added after the A' pass)
-                                const double add = P.beta_c * P.col[i] * px;
-                                if (seg == 0) {
-                                  // free: recompute the contribution with P x included
-                                  double qx = (double)P.qd[i] * (double)x[i] + (k > 0 ? rtw(i, wk) : 0.0);
-                                  (void)qx;
-                                }
-                                W.sd[i] = (seg >= 2) ? W.sd[i] - add : W.sd[i];
-                                (void)add;
-                              }
-                            });
   }
   __syncthreads();
   // cone coordinates: project -s onto each cone (Euclidean, FP64, in place in W.sd)
@@ -282,7 +286,7 @@ __device__ bool Solver<T, Team>::kkt(const T* x, const T* y, bool have_rx) {
   if (threadIdx.x == 0) {
     double rqr = 0.0;
     for (int l = 0; l < k; ++l) rqr += tk[l] * wk[l];
-    const double xqx = xqdx + rqr + C.red[1];
+    const double xqx = xqdx + rqr + xpx;
     const double sc = P.beta_b * P.beta_c;
     const double pobj = sc * (0.5 * xqx + cx), dobj = sc * (by - 0.5 * xqx);
     const double nrp = sqrt(rp2), nrd = sqrt(C.red[0]);
@@ -306,6 +310,8 @@ __device__ void Solver<T, Team>::run(long long budget) {
   const int k = P.k;
   const bool avg = O.update == 1;
   const int lane = threadIdx.x & 31;
+  if (O.profile && team.bid() == 0 && threadIdx.x == 0) C.t_last = now_ns();
+  const unsigned long long t_begin = C.t_last;
   for (long long it = 0; it < budget; ++it) {
     if (C.s.status != 0 || C.s.err != 0) break;
     // adaptive inner tolerance (eq. monotone-primal-inner-tol), movement of consecutive candidates
@@ -385,7 +391,7 @@ __device__ void Solver<T, Team>::run(long long budget) {
     }
     __syncthreads();
     publish<6>(v6, 0, halpern_now && k > 0);
-    if (!sync_gather(6 + ((halpern_now && k > 0) ? k : 0))) return;
+    if (!sync_gather(6 + ((halpern_now && k > 0) ? k : 0), 3, 4)) return;
     // ---- control after the dual step
     if (threadIdx.x == 0) {
       State& S = C.s;
@@ -419,6 +425,7 @@ __device__ void Solver<T, Team>::run(long long budget) {
     if (check) {
       const bool ok2 = avg ? kkt(W.avx, W.avy, false) : kkt(W.wx[C.s.wb], W.wy, true);
       if (!ok2) return;
+      tick(5);
       if (threadIdx.x == 0) {
         State& S = C.s;
         if (S.kkt[3] <= O.tol) S.status = 1;
@@ -506,6 +513,7 @@ __device__ void Solver<T, Team>::run(long long budget) {
         S.hb = hbn;
       }
       __syncthreads();
+      tick(6);
     } else {
       // deferred reflected-Halpern step of a check iteration
       if (k > 0) wacc_zero();
@@ -534,8 +542,10 @@ __device__ void Solver<T, Team>::run(long long budget) {
         C.s.hb = hbn;
       }
       __syncthreads();
+      tick(6);
     }
   }
+  if (O.profile && team.bid() == 0 && threadIdx.x == 0) C.s.prof[7] += (double)(now_ns() - t_begin);
 }
 
 // ---------------------------------------------------------------------------

@@ -36,7 +36,7 @@ def _rel(a, b):
 @pytest.mark.parametrize("team", [2, 1])
 def test_small_configs_solve(gpu, orc, k, precision, team):
     inst = I.small_config(k)
-    s = gpu.Solver(inst, precision=precision, team=team, max_iter=200000, tol=1e-4)
+    s = gpu.Solver(inst, precision=precision, team=team, max_iter=200000, tol=1e-4, time_limit_s=120.0)
     x, y, res = s.solve()
     assert res["rc"] == 0, res
     rep = orc.kkt(inst, x, y)                 # independent FP64 CPU measurement of the same point
@@ -88,7 +88,7 @@ def test_kkt_entry_point(gpu, orc):
 
 def test_averaged_variant(gpu, orc):
     inst = I.small_config(1)
-    s = gpu.Solver(inst, precision=1, update=1, avg_epoch=64, max_iter=400000, tol=1e-4)
+    s = gpu.Solver(inst, precision=1, update=1, avg_epoch=64, max_iter=400000, tol=1e-4, time_limit_s=120.0)
     x, y, res = s.solve()
     assert res["rc"] == 0, res
     assert orc.kkt(inst, x, y)["rel_kkt"] <= 1.5e-4
@@ -98,7 +98,7 @@ def test_averaged_variant(gpu, orc):
 def test_warm_start_from_solution(gpu, orc):
     inst = I.small_config(2)
     xs, ys, _ = orc.solve(inst, max_iter=400000, tol=1e-7)
-    s = gpu.Solver(inst, precision=1, tol=1e-4)
+    s = gpu.Solver(inst, precision=1, tol=1e-4, time_limit_s=60.0)
     x, y, res = s.solve(x0=xs, y0=ys)
     assert res["rc"] == 0 and res["iters"] <= 128
     s.close()
