@@ -1,0 +1,383 @@
+#!/usr/bin/env python3
+"""Time to 1e-4 relative KKT on one GB300 (and the FP64 plain-PDHG comparison).
+
+Workload (default): the SOCP/QCQP mix -- n = 200,000 coordinates (100,000
+nonnegative, 2,000 second-order cones of dimension U[10,50], 500 rotated
+second-order cones of dimension U[3,20], the rest free), m = 100,000 equality
+rows with about 10 N(0,1) entries per column, Q = diag(lognormal(0,1)) + R'R
+with R 20 x n, feasible b.  Seeded synthetic data (Philox, seed 1002).
+
+A step is one complete solve through the C ABI: cqp_setup (rescaling,
+transpose, norm estimate) from device-resident FP64 inputs, then cqp_solve to
+relative KKT <= 1e-4 (FP32 iterates, FP64 reductions and cone roots), outputs
+left on the device.  `value` is the mean time per solve (seconds, lower is
+better).  L2 is flushed (256 MB write) before every step, outside the timed
+event pair.  `e2e` repeats the solve from pinned host buffers with the
+host->device copies of the inputs and the device->host copy of (x, y) inside
+the timed region.  The FP64 plain-PDHG run (same code, precision = all FP64,
+cold start) is timed once as the comparison the metric names.
+
+With --gpus N under torchrun each rank solves its own instance (seed + rank):
+replicas, no collectives; rank 0 prints the max-over-ranks time.
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to 1e-4 rel KKT vs FP64 plain PDHG on 1 GB300; SpMV+prox HBM GB/s"
+WORKLOAD = ("socp_mix: n=200000 (100000 nonneg, 2000 SOC dim U[10,50], 500 RSOC dim U[3,20], free rest), "
+            "m=100000, ~10 nnz/col N(0,1), Q=diag(lognormal)+R'R rank 20, seed 1002")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx = float(p[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes(inst, res, esize=4, isize=4):
+    """Bytes the method must move per solve (each array element touched once per pass),
+    from the iteration counts the solve reports:
+      A'y pass    : A' values + indices + row pointers, h_y gathered once, h_x read, v written
+      inner step  : u, v, c, q, diag(Q) read, u_next written, R (k x n) read
+      dual pass   : A values + indices + row pointers, w_x and h_x gathered once, h_y, b, a_y read,
+                    w_y, h_y written; w_x, h_x, a_x, w_x_prev read, w_x copy and h_x written
+      KKT check   : two products with A / A' and ten vectors, every check_every iterations."""
+    n, m = inst["n"], inst["m"]
+    nnz = int(inst["a_rowptr"][-1])
+    k = 0 if inst.get("q_R") is None else int(inst["q_R"].shape[0])
+    aty = nnz * (esize + isize) + (n + 1) * isize + m * esize + 2 * n * esize
+    inner = (6 + k) * n * esize
+    dual = nnz * (esize + isize) + (m + 1) * isize + 2 * n * esize + 5 * m * esize + 6 * n * esize
+    kkt = 2 * nnz * (esize + isize) + (n + m + 2) * isize + 10 * (n + m) * esize
+    checks = res["iters"] // 64 + 1
+    return res["iters"] * (aty + dual) + res["inner_total"] * inner + checks * kkt
+
+
+def _source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2608_09159_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic():
+    """DRAM bytes per solve of the solver kernel from the committed ncu summary, if it was
+    captured on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "pdhg_kernel_socp_mix.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("source_hash") != _source_hash():
+        return None
+    return d.get("dram_bytes_per_solve")
+
+
+def _device_inst(inst, torch):
+    out = {}
+    for k, v in inst.items():
+        if hasattr(v, "dtype") and hasattr(v, "shape") and k in (
+                "a_rowptr", "a_colind", "a_val", "c", "b", "q_diag", "q_R", "q_D", "p_rowptr", "p_colind", "p_val",
+                "blk_type", "blk_start", "blk_dim", "blk_alpha"):
+            import numpy as np
+            dt = {"a_colind": np.int32, "p_colind": np.int32, "blk_type": np.int32}.get(k, v.dtype)
+            out[k] = torch.from_numpy(np.ascontiguousarray(v, dtype=dt)).cuda()
+        else:
+            out[k] = v
+    return out
+
+
+def _pinned_inst(inst, torch):
+    import numpy as np
+    out = dict(inst)
+    for k in ("a_rowptr", "a_colind", "a_val", "c", "b", "q_diag", "q_R", "q_D", "blk_type", "blk_start", "blk_dim",
+              "blk_alpha"):
+        v = inst.get(k)
+        if v is None:
+            continue
+        dt = {"a_colind": np.int32, "blk_type": np.int32}.get(k, v.dtype)
+        t = torch.from_numpy(np.ascontiguousarray(v, dtype=dt)).pin_memory()
+        out[k] = t.numpy()
+        out["_pin_" + k] = t
+    return out
+
+
+def make_instance(args, rank):
+    import instances
+    if args.small:
+        return instances.socp_mix(n=20000, n_nonneg=10000, n_soc=200, n_rsoc=50, m=10000, seed=1002 + 1000 * rank)
+    return instances.socp_mix(seed=1002 + 1000 * rank)
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    import paper_2608_09159_gb300 as g
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    g.build()
+    g.lib()
+    inst = make_instance(args, rank)
+    dinst = _device_inst(inst, torch)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    opts = dict(precision=0, tol=1e-4, max_iter=200000, time_limit_s=600.0)
+
+    def one_solve(src, device, out_device, **kw):
+        s = g.Solver(src, device=device, **{**opts, **kw})
+        x, y, res = s.solve(out_device=out_device)
+        s.close()
+        return x, y, res
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        one_solve(dinst, False, True)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    times, results = [], []
+    launches0 = g.cqp_kernel_launches()
+    barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x, y, res = one_solve(dinst, False, True)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        results.append(res)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - t_wall
+    launches = g.cqp_kernel_launches() - launches0
+    clk = clocks.stop()
+    step_s = statistics.mean(times)
+    if world > 1:
+        t = torch.tensor([step_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        step_s = float(t.item())
+    res = results[-1]
+    # parity of the timed solution, measured independently on the host (rank 0, FP64 oracle)
+    kkt_check = None
+    if rank == 0 and not args.no_oracle:
+        import oracle
+        kkt_check = oracle.kkt(inst, x.double().cpu().numpy(), y.double().cpu().numpy())["rel_kkt"]
+
+    # e2e: the same solve from pinned host buffers, copies inside the timed region
+    pinst = _pinned_inst(inst, torch)
+    e2e_times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xe, ye, rese = one_solve(pinst, False, False)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    n, m = inst["n"], inst["m"]
+    nnz = int(inst["a_rowptr"][-1])
+    k = int(inst["q_R"].shape[0])
+    h2d = (m + 1) * 8 + nnz * (4 + 8) + 2 * n * 8 + m * 8 + k * n * 8 + k * k * 8 + \
+        len(inst["blk_type"]) * (4 + 8 + 8 + 8)
+    d2h = (n + m) * 8
+
+    # FP64 plain PDHG (same code, all FP64, cold start)
+    fp64 = None
+    if args.fp64_steps > 0:
+        ft = []
+        for _ in range(args.fp64_steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, _, r64 = one_solve(dinst, False, True, precision=1)
+            e1.record(stream)
+            e1.synchronize()
+            ft.append(e0.elapsed_time(e1) / 1e3)
+        fp64 = {"time_s": statistics.mean(ft), "iters": r64["iters"], "inner": r64["inner_total"],
+                "rel_kkt": r64["kkt"]["rel_kkt"], "rc": r64["rc"]}
+
+    peaks, src = _peaks()
+    alg = algorithmic_bytes(inst, res)
+    kern_s = res["kernel_ms"] / 1e3
+    achieved = alg / kern_s / 1e9 if kern_s > 0 else None
+    traffic = _ncu_traffic()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": (achieved / peaks["hbm_gbs"]) if achieved else None, "traffic": traffic,
+            "peak_source": src, "kernel": "pdhg_grid_kernel<float>", "algorithmic_bytes_per_solve": alg,
+            "kernel_s_per_solve": kern_s}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(inst, fp64["iters"] if fp64 else res["iters"], args)
+
+    line = {
+        "metric": METRIC, "value": step_s, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": step_s * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (FP64 reductions, KKT and cone roots)", "data": "synthetic (Philox-seeded)",
+        "config": {"workload": WORKLOAD, "n": n, "m": m, "nnz": nnz, "tol": 1e-4, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed before every step (256 MB write)", "inputs": "device-resident FP64 (HBM)"},
+        "e2e": {"value": statistics.mean(e2e_times), "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "fp64_plain_pdhg": fp64,
+        "speedup_vs_fp64": (fp64["time_s"] / step_s) if fp64 else None,
+        "solve": {"iters": res["iters"], "restarts": res["restarts"], "inner_total": res["inner_total"],
+                  "rel_kkt": res["kkt"]["rel_kkt"], "oracle_rel_kkt": kkt_check, "setup_ms": res["setup_ms"],
+                  "solve_ms": res["solve_ms"], "kernel_ms": res["kernel_ms"], "iters_per_s": res["iters"] / step_s,
+                  "step_times_s": times, "wall_s": wall},
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(inst, iters_to_tol, args):
+    """The FP64 oracle (single thread) on a bounded sample of the same workload: setup plus
+    `sample_iters` outer iterations, extrapolated to the iteration count the FP64 method needs
+    on this instance (the FP64 trajectory of the GPU code, which follows the oracle's)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.solve(inst, max_iter=1)
+    t_setup = time.perf_counter() - t0
+    M = args.cpu_iters
+    t0 = time.perf_counter()
+    oracle.solve(inst, max_iter=M)
+    t_m = time.perf_counter() - t0
+    per_iter = max(t_m - t_setup, 0.0) / max(M - 1, 1)
+    est = t_setup + per_iter * iters_to_tol
+    return {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": "setup + %d outer iterations of the full instance (%.1f s); time to 1e-4 extrapolated to %d "
+                      "iterations at %.3f s/iteration" % (M, t_m, iters_to_tol, per_iter),
+            "s_per_iter": per_iter, "setup_s": t_setup}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import instances  # noqa: F401
+    inst = make_instance(args, 0)
+    vals = []
+    for _ in range(args.warmup + args.steps):
+        cb = cpu_baseline(inst, args.ref_iters, args)
+        vals.append(cb)
+    tim = vals[args.warmup:] or vals
+    v = statistics.mean(c["value"] for c in tim)
+    line = {"metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic (Philox-seeded)", "impl": "reference",
+            "config": {"workload": WORKLOAD, "tol": 1e-4},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": tim[-1]["sample"], "value": v, "unit": "s"},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--cpu-iters", type=int, default=20)
+    ap.add_argument("--ref-iters", type=int, default=256,
+                    help="outer iterations the FP64 method needs on the default workload (reference arm)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-oracle", action="store_true")
+    ap.add_argument("--small", action="store_true", help="10x smaller instance (quick checks)")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        torch.distributed.init_process_group(backend="nccl")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+    if world > 1 and args.impl == "ours":
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -144,6 +144,8 @@ typedef struct {
    * prox work, prox barriers, dual step, its barrier, KKT checks, restart/Halpern at
    * checks, whole loop */
   double phase_ms[8];
+  double kernel_ms;                /* CUDA-event time of the solver kernel launches of this solve */
+  int64_t setup_launches;          /* kernels launched by cqp_setup for this handle */
 } cqp_result;
 
 typedef struct cqp_handle cqp_handle;
@@ -186,6 +188,10 @@ void cqp_free(cqp_handle* h);
 /* Text for a status code; the last CUDA or validation error of this thread. */
 const char* cqp_status_string(int status);
 const char* cqp_last_error(void);
+
+/* Number of kernels this library has launched from the calling thread so far
+ * (setup, solver, KKT and kernel-level entry points). */
+long long cqp_kernel_launches(void);
 
 /* ---- kernel-level entry points (device pointers, used for parity and
  * bandwidth measurements).  `precision` selects FP32 (0) or FP64 (1) data:

@@ -19,7 +19,8 @@ import numpy as np
 from . import _build
 
 __all__ = ["build", "lib", "cqp_default_options", "cqp_setup", "cqp_solve", "cqp_kkt", "cqp_free", "cqp_spmv",
-           "cqp_project", "cqp_status_string", "cqp_last_error", "Solver", "CQPError", "STATUS"]
+           "cqp_project", "cqp_status_string", "cqp_last_error", "cqp_kernel_launches", "Solver", "CQPError",
+           "STATUS"]
 
 CQP_OK, CQP_ITER_LIMIT, CQP_TIME_LIMIT = 0, 1, 2
 STATUS = {0: "converged", 1: "iteration limit", 2: "time limit", -1: "invalid input", -2: "CUDA error",
@@ -71,7 +72,7 @@ class Result(C.Structure):
     _fields_ = [("status", C.c_int32), ("iters", C.c_int64), ("restarts", C.c_int64), ("inner_total", C.c_int64),
                 ("kernel_launches", C.c_int64), ("kkt", KKTReport), ("eta", C.c_double), ("norm_A", C.c_double),
                 ("omega", C.c_double), ("setup_ms", C.c_double), ("solve_ms", C.c_double),
-                ("phase_ms", C.c_double * 8)]
+                ("phase_ms", C.c_double * 8), ("kernel_ms", C.c_double), ("setup_launches", C.c_int64)]
 
 
 _lib = None
@@ -102,6 +103,8 @@ def lib():
         L.cqp_last_error.restype = C.c_char_p
         L.cqp_spmv.argtypes = [i32, i64, i64, vp, vp, vp, vp, vp, i32, vp]
         L.cqp_project.argtypes = [i32, i64, vp, vp, vp, vp, vp]
+        L.cqp_kernel_launches.argtypes = []
+        L.cqp_kernel_launches.restype = C.c_longlong
         for f in ("cqp_default_options", "cqp_setup", "cqp_solve", "cqp_kkt", "cqp_spmv", "cqp_project"):
             getattr(L, f).restype = C.c_int
         _lib = L
@@ -114,6 +117,10 @@ def cqp_status_string(code: int) -> str:
 
 def cqp_last_error() -> str:
     return lib().cqp_last_error().decode()
+
+
+def cqp_kernel_launches() -> int:
+    return int(lib().cqp_kernel_launches())
 
 
 def _check(rc, allow_positive=True):
@@ -202,6 +209,7 @@ class Solver:
             for k, v in list(arrs.items()):
                 if v is not None and not hasattr(v, "data_ptr"):
                     arrs[k] = torch.from_numpy(v).cuda()
+        if device or any(getattr(v, "is_cuda", False) for v in arrs.values() if v is not None):
             opts["input_on_device"] = 1
         self._keep.append(arrs)
         p = _ptr

@@ -21,6 +21,9 @@
 namespace {
 
 thread_local std::string g_last_error;
+// kernels launched by this library in the calling thread (setup, solve, KKT, entry points)
+thread_local long long g_launches = 0;
+inline void count_launch() { ++g_launches; }
 
 struct Fail {
   int code;
@@ -68,8 +71,8 @@ struct Temp {
 
 double dev_dot(const double* a, const double* b, int64_t n, double* part, double* out, cudaStream_t st) {
   const int nb = cqp::grid_for(n, cqp::kSetupThreads, 1024);
-  cqp::k_dot_partial<<<nb, cqp::kSetupThreads, 0, st>>>(n, a, b, part);
-  cqp::k_sum_partials<<<1, 32, 0, st>>>(nb, part, out);
+  count_launch(); cqp::k_dot_partial<<<nb, cqp::kSetupThreads, 0, st>>>(n, a, b, part);
+  count_launch(); cqp::k_sum_partials<<<1, 32, 0, st>>>(nb, part, out);
   double h = 0.0;
   CK(cudaMemcpyAsync(&h, out, sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -81,9 +84,9 @@ void dev_scan(const int32_t* in, int32_t* out, int64_t n, Temp& tmp, cudaStream_
   const int64_t per = 1 << 16;
   const int nb = (int)std::max<int64_t>(1, (n + per - 1) / per);
   int64_t* tot = tmp.alloc<int64_t>(nb + 1);
-  cqp::k_scan_block_totals<<<nb, cqp::kSetupThreads, 0, st>>>(n, in, per, tot);
-  cqp::k_scan_totals<<<1, 32, 0, st>>>(nb, tot);
-  cqp::k_scan_apply<<<nb, cqp::kSetupThreads, 0, st>>>(n, in, per, tot, out);
+  count_launch(); cqp::k_scan_block_totals<<<nb, cqp::kSetupThreads, 0, st>>>(n, in, per, tot);
+  count_launch(); cqp::k_scan_totals<<<1, 32, 0, st>>>(nb, tot);
+  count_launch(); cqp::k_scan_apply<<<nb, cqp::kSetupThreads, 0, st>>>(n, in, per, tot, out);
   CK(cudaGetLastError());
 }
 
@@ -174,6 +177,7 @@ struct Handle : HandleBase {
   T* tmp_x = nullptr;
   T* tmp_y = nullptr;
   double eta = 0, normA = 0, omega0 = 1, setup_ms = 0;
+  long long setup_launches = 0;
   bool grid = false;
   int blocks = 1, threads = 512;
 
@@ -194,6 +198,7 @@ struct Handle : HandleBase {
   void setup(const cqp_csr* A, const cqp_qop* Q, const double* c_in, const double* b_in, const cqp_cones* K,
              const cqp_options& o) {
     auto t0 = std::chrono::steady_clock::now();
+    const long long launches0 = g_launches;
     opt = o;
     st = (cudaStream_t)o.stream;
     int dev = 0;
@@ -286,12 +291,12 @@ struct Handle : HandleBase {
     if (!c_d || (m > 0 && !b_d)) fail(CQP_ERR_INVALID, "c and b are required");
     int* bad = tmp.alloc<int>(1);
     CK(cudaMemsetAsync(bad, 0, sizeof(int), st));
-    cqp::k_validate_csr<<<cqp::grid_for(nnz + m), cqp::kSetupThreads, 0, st>>>(m, n, a_rp64, a_ci_in, a_v_in, bad);
-    cqp::k_validate_vec<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, c_d, bad);
-    if (m > 0) cqp::k_validate_vec<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, b_d, bad);
-    if (qd_in) cqp::k_validate_vec<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, qd_in, bad);
-    if (R_in) cqp::k_validate_vec<<<cqp::grid_for(k * n), cqp::kSetupThreads, 0, st>>>(k * n, R_in, bad);
-    if (has_p) cqp::k_validate_csr<<<cqp::grid_for(pnnz + n), cqp::kSetupThreads, 0, st>>>(n, n, p_rp64, p_ci_in, p_v_in, bad);
+    count_launch(); cqp::k_validate_csr<<<cqp::grid_for(nnz + m), cqp::kSetupThreads, 0, st>>>(m, n, a_rp64, a_ci_in, a_v_in, bad);
+    count_launch(); cqp::k_validate_vec<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, c_d, bad);
+    if (m > 0) { count_launch(); cqp::k_validate_vec<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, b_d, bad); }
+    if (qd_in) { count_launch(); cqp::k_validate_vec<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, qd_in, bad); }
+    if (R_in) { count_launch(); cqp::k_validate_vec<<<cqp::grid_for(k * n), cqp::kSetupThreads, 0, st>>>(k * n, R_in, bad); }
+    if (has_p) { count_launch(); cqp::k_validate_csr<<<cqp::grid_for(pnnz + n), cqp::kSetupThreads, 0, st>>>(n, n, p_rp64, p_ci_in, p_v_in, bad); }
     int hbad = 0;
     CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
     int64_t last_rp = 0;
@@ -311,26 +316,26 @@ struct Handle : HandleBase {
       int64_t* so = tmp.alloc<int64_t>(seg_old.size());
       CK(cudaMemcpyAsync(sn, seg_new.data(), seg_new.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
       CK(cudaMemcpyAsync(so, seg_old.data(), seg_old.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-      k_build_perm<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, (int64_t)seg_new.size(), sn, so, perm, iperm);
+      count_launch(); k_build_perm<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, (int64_t)seg_new.size(), sn, so, perm, iperm);
     }
     // A with remapped columns, FP64 working values
     int32_t* a_rp = mem.alloc<int32_t>(m + 1);
     int32_t* a_ci = mem.alloc<int32_t>(nnz);
     double* av = tmp.alloc<double>(nnz);
-    cqp::k_copy_rowptr32<<<cqp::grid_for(m + 1), cqp::kSetupThreads, 0, st>>>(m + 1, a_rp64, a_rp);
-    cqp::k_remap_cols<<<cqp::grid_for(nnz), cqp::kSetupThreads, 0, st>>>(nnz, iperm, a_ci_in, a_ci);
+    count_launch(); cqp::k_copy_rowptr32<<<cqp::grid_for(m + 1), cqp::kSetupThreads, 0, st>>>(m + 1, a_rp64, a_rp);
+    count_launch(); cqp::k_remap_cols<<<cqp::grid_for(nnz), cqp::kSetupThreads, 0, st>>>(nnz, iperm, a_ci_in, a_ci);
     CK(cudaMemcpyAsync(av, a_v_in, nnz * sizeof(double), cudaMemcpyDeviceToDevice, st));
     double* cv = tmp.alloc<double>(n);
     double* qv = tmp.alloc<double>(n);
     double* bv = tmp.alloc<double>(std::max<int64_t>(m, 1));
-    cqp::k_gather<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, perm, c_d, cv, 0.0);
-    cqp::k_gather<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, perm, qd_in, qv, 0.0);
+    count_launch(); cqp::k_gather<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, perm, c_d, cv, 0.0);
+    count_launch(); cqp::k_gather<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, perm, qd_in, qv, 0.0);
     if (m > 0) CK(cudaMemcpyAsync(bv, b_d, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
     double* Rv = nullptr;
     double* Dv = nullptr;
     if (k > 0) {
       Rv = tmp.alloc<double>(k * n);
-      cqp::k_gather_cols<<<cqp::grid_for(k * n), cqp::kSetupThreads, 0, st>>>(k, n, perm, R_in, Rv);
+      count_launch(); cqp::k_gather_cols<<<cqp::grid_for(k * n), cqp::kSetupThreads, 0, st>>>(k, n, perm, R_in, Rv);
       Dv = mem.alloc<double>(k * k);
       CK(cudaMemcpyAsync(Dv, D_in, k * k * sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
@@ -342,9 +347,9 @@ struct Handle : HandleBase {
       p_rp = mem.alloc<int32_t>(n + 1);
       p_ci = mem.alloc<int32_t>(pnnz);
       pv = tmp.alloc<double>(pnnz);
-      cqp::k_row_lengths_perm<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, perm, p_rp64, len);
+      count_launch(); cqp::k_row_lengths_perm<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, perm, p_rp64, len);
       dev_scan(len, p_rp, n, tmp, st);
-      cqp::k_copy_rows_perm<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, perm, iperm, p_rp64, p_ci_in, p_v_in,
+      count_launch(); cqp::k_copy_rows_perm<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, perm, iperm, p_rp64, p_ci_in, p_v_in,
                                                                                 p_rp, p_ci, pv);
     }
     // ---- transpose of A (deterministic: every row of A' sorted by row of A) ------------
@@ -354,12 +359,12 @@ struct Handle : HandleBase {
     {
       int32_t* cntc = tmp.alloc<int32_t>(n);
       CK(cudaMemsetAsync(cntc, 0, n * sizeof(int32_t), st));
-      cqp::k_count_cols<<<cqp::grid_for(nnz), cqp::kSetupThreads, 0, st>>>(nnz, a_ci, cntc);
+      count_launch(); cqp::k_count_cols<<<cqp::grid_for(nnz), cqp::kSetupThreads, 0, st>>>(nnz, a_ci, cntc);
       dev_scan(cntc, t_rp, n, tmp, st);
       int32_t* cursor = tmp.alloc<int32_t>(n);
       CK(cudaMemcpyAsync(cursor, t_rp, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
-      cqp::k_scatter_transpose<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp, a_ci, cursor, t_ci, tmap);
-      cqp::k_sort_segments<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, t_rp, t_ci, tmap);
+      count_launch(); cqp::k_scatter_transpose<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp, a_ci, cursor, t_ci, tmap);
+      count_launch(); cqp::k_sort_segments<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, t_rp, t_ci, tmap);
     }
     // ---- rescaling (Table practical-defaults: Ruiz x10, Pock-Chambolle alpha = 1,
     // cone-preserving aggregation, bound-objective) -------------------------------------
@@ -367,8 +372,8 @@ struct Handle : HandleBase {
     double* row = mem.alloc<double>(std::max<int64_t>(m, 1));
     double* colf = tmp.alloc<double>(n);
     double* rowf = tmp.alloc<double>(std::max<int64_t>(m, 1));
-    cqp::k_fill<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, col, 1.0);
-    if (m > 0) cqp::k_fill<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, row, 1.0);
+    count_launch(); cqp::k_fill<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, col, 1.0);
+    if (m > 0) { count_launch(); cqp::k_fill<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, row, 1.0); }
     int64_t* d_soc = mem.alloc<int64_t>(soc_off.size());
     int64_t* d_rsoc = mem.alloc<int64_t>(rsoc_off.size());
     CK(cudaMemcpyAsync(d_soc, soc_off.data(), soc_off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
@@ -376,73 +381,73 @@ struct Handle : HandleBase {
     const int64_t n_soc = (int64_t)soc_off.size() - 1, n_rsoc = (int64_t)rsoc_off.size() - 1;
     const int64_t n_exp = cnt[4] / 3, n_pow = cnt[5] / 3;
     auto aggregate = [&](int mode) {
-      if (n_soc) cqp::k_aggregate_blocks<<<cqp::grid_for(n_soc), cqp::kSetupThreads, 0, st>>>(n_soc, d_soc, 0, 0, mode, colf);
-      if (n_rsoc) cqp::k_aggregate_blocks<<<cqp::grid_for(n_rsoc), cqp::kSetupThreads, 0, st>>>(n_rsoc, d_rsoc, 0, 0, mode, colf);
-      if (n_exp) cqp::k_aggregate_blocks<<<cqp::grid_for(n_exp), cqp::kSetupThreads, 0, st>>>(n_exp, nullptr, base[4], 3, mode, colf);
-      if (n_pow) cqp::k_aggregate_blocks<<<cqp::grid_for(n_pow), cqp::kSetupThreads, 0, st>>>(n_pow, nullptr, base[5], 3, mode, colf);
+      if (n_soc) { count_launch(); cqp::k_aggregate_blocks<<<cqp::grid_for(n_soc), cqp::kSetupThreads, 0, st>>>(n_soc, d_soc, 0, 0, mode, colf); }
+      if (n_rsoc) { count_launch(); cqp::k_aggregate_blocks<<<cqp::grid_for(n_rsoc), cqp::kSetupThreads, 0, st>>>(n_rsoc, d_rsoc, 0, 0, mode, colf); }
+      if (n_exp) { count_launch(); cqp::k_aggregate_blocks<<<cqp::grid_for(n_exp), cqp::kSetupThreads, 0, st>>>(n_exp, nullptr, base[4], 3, mode, colf); }
+      if (n_pow) { count_launch(); cqp::k_aggregate_blocks<<<cqp::grid_for(n_pow), cqp::kSetupThreads, 0, st>>>(n_pow, nullptr, base[5], 3, mode, colf); }
     };
     auto scale_step = [&]() {
-      cqp::k_scale_matrix<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp, a_ci, av, rowf, colf);
-      cqp::k_mul<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, col, colf);
-      if (m > 0) cqp::k_mul<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, row, rowf);
+      count_launch(); cqp::k_scale_matrix<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp, a_ci, av, rowf, colf);
+      count_launch(); cqp::k_mul<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, col, colf);
+      if (m > 0) { count_launch(); cqp::k_mul<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, row, rowf); }
     };
     for (int it = 0; it < o.ruiz_iters; ++it) {
-      cqp::k_col_stat<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, t_rp, tmap, av, 0, 0.0, colf);
-      if (m > 0) cqp::k_row_stat<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp, av, 0, 0.0, rowf);
-      cqp::k_sqrt_or_one<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, colf);
-      if (m > 0) cqp::k_sqrt_or_one<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, rowf);
+      count_launch(); cqp::k_col_stat<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, t_rp, tmap, av, 0, 0.0, colf);
+      if (m > 0) { count_launch(); cqp::k_row_stat<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp, av, 0, 0.0, rowf); }
+      count_launch(); cqp::k_sqrt_or_one<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, colf);
+      if (m > 0) { count_launch(); cqp::k_sqrt_or_one<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, rowf); }
       aggregate(0);
       scale_step();
     }
     if (o.pc_alpha >= 0.0) {
       const double al = o.pc_alpha;
-      cqp::k_col_stat<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, t_rp, tmap, av, 1, 2.0 - al, colf);
-      if (m > 0) cqp::k_row_stat<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp, av, 1, al, rowf);
-      cqp::k_sqrt_or_one<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, colf);
-      if (m > 0) cqp::k_sqrt_or_one<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, rowf);
+      count_launch(); cqp::k_col_stat<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, t_rp, tmap, av, 1, 2.0 - al, colf);
+      if (m > 0) { count_launch(); cqp::k_row_stat<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp, av, 1, al, rowf); }
+      count_launch(); cqp::k_sqrt_or_one<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, colf);
+      if (m > 0) { count_launch(); cqp::k_sqrt_or_one<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, rowf); }
       aggregate(1);
       scale_step();
     }
-    cqp::k_div<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, cv, col);
-    if (m > 0) cqp::k_div<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, bv, row);
-    cqp::k_div2<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, qv, col);
-    if (has_p) cqp::k_scale_sym<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, p_rp, p_ci, pv, col);
-    if (k > 0) cqp::k_scale_cols<<<cqp::grid_for(k * n), cqp::kSetupThreads, 0, st>>>(k, n, Rv, col);
+    count_launch(); cqp::k_div<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, cv, col);
+    if (m > 0) { count_launch(); cqp::k_div<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, bv, row); }
+    count_launch(); cqp::k_div2<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, qv, col);
+    if (has_p) { count_launch(); cqp::k_scale_sym<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, p_rp, p_ci, pv, col); }
+    if (k > 0) { count_launch(); cqp::k_scale_cols<<<cqp::grid_for(k * n), cqp::kSetupThreads, 0, st>>>(k, n, Rv, col); }
     double beta_b = 1.0, beta_c = 1.0;
     if (o.bound_obj) {
       beta_b = (m > 0 ? std::sqrt(dev_dot(bv, nullptr, m, part, one, st)) : 0.0) + 1.0;
       beta_c = std::sqrt(dev_dot(cv, nullptr, n, part, one, st)) + 1.0;
-      if (m > 0) cqp::k_scal<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, bv, 1.0 / beta_b);
-      cqp::k_scal<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, cv, 1.0 / beta_c);
+      if (m > 0) { count_launch(); cqp::k_scal<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, bv, 1.0 / beta_b); }
+      count_launch(); cqp::k_scal<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, cv, 1.0 / beta_c);
       const double qs = beta_b / beta_c;
-      cqp::k_scal<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, qv, qs);
-      if (has_p) cqp::k_scal<<<cqp::grid_for(pnnz), cqp::kSetupThreads, 0, st>>>(pnnz, pv, qs);
-      if (k > 0) cqp::k_scal<<<1, 64, 0, st>>>(k * k, Dv, qs);
+      count_launch(); cqp::k_scal<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, qv, qs);
+      if (has_p) { count_launch(); cqp::k_scal<<<cqp::grid_for(pnnz), cqp::kSetupThreads, 0, st>>>(pnnz, pv, qs); }
+      if (k > 0) { count_launch(); cqp::k_scal<<<1, 64, 0, st>>>(k * k, Dv, qs); }
     }
     // full diagonal of Q~ (Jacobi metric) and conversion to the iterate precision
     double* jdv = tmp.alloc<double>(n);
-    cqp::k_full_diag<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, qv, p_rp, p_ci, pv, k, Rv, Dv, jdv);
+    count_launch(); cqp::k_full_diag<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, qv, p_rp, p_ci, pv, k, Rv, Dv, jdv);
     T* a_v = mem.alloc<T>(nnz);
     T* t_v = mem.alloc<T>(nnz);
-    cqp::k_convert<T><<<cqp::grid_for(nnz), cqp::kSetupThreads, 0, st>>>(nnz, av, a_v);
-    cqp::k_gather_convert<T><<<cqp::grid_for(nnz), cqp::kSetupThreads, 0, st>>>(nnz, tmap, av, t_v);
+    count_launch(); cqp::k_convert<T><<<cqp::grid_for(nnz), cqp::kSetupThreads, 0, st>>>(nnz, av, a_v);
+    count_launch(); cqp::k_gather_convert<T><<<cqp::grid_for(nnz), cqp::kSetupThreads, 0, st>>>(nnz, tmap, av, t_v);
     T* cT = mem.alloc<T>(n);
     T* bT = mem.alloc<T>(std::max<int64_t>(m, 1));
     T* qT = mem.alloc<T>(n);
     T* jT = mem.alloc<T>(n);
-    cqp::k_convert<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, cv, cT);
-    if (m > 0) cqp::k_convert<T><<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, bv, bT);
-    cqp::k_convert<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, qv, qT);
-    cqp::k_convert<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, jdv, jT);
+    count_launch(); cqp::k_convert<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, cv, cT);
+    if (m > 0) { count_launch(); cqp::k_convert<T><<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, bv, bT); }
+    count_launch(); cqp::k_convert<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, qv, qT);
+    count_launch(); cqp::k_convert<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, jdv, jT);
     T* RT = nullptr;
     if (k > 0) {
       RT = mem.alloc<T>(k * n);
-      cqp::k_convert<T><<<cqp::grid_for(k * n), cqp::kSetupThreads, 0, st>>>(k * n, Rv, RT);
+      count_launch(); cqp::k_convert<T><<<cqp::grid_for(k * n), cqp::kSetupThreads, 0, st>>>(k * n, Rv, RT);
     }
     T* pT = nullptr;
     if (has_p) {
       pT = mem.alloc<T>(pnnz);
-      cqp::k_convert<T><<<cqp::grid_for(pnnz), cqp::kSetupThreads, 0, st>>>(pnnz, pv, pT);
+      count_launch(); cqp::k_convert<T><<<cqp::grid_for(pnnz), cqp::kSetupThreads, 0, st>>>(pnnz, pv, pT);
     }
     double* palpha = nullptr;
     if (!pow_al.empty()) {
@@ -454,7 +459,7 @@ struct Handle : HandleBase {
     {
       double* acc = tmp.alloc<double>(1);
       CK(cudaMemsetAsync(acc, 0, sizeof(double), st));
-      k_sumsq_range<<<cqp::grid_for(n - base[2]), cqp::kSetupThreads, 0, st>>>(base[2], n, qv, acc);
+      count_launch(); k_sumsq_range<<<cqp::grid_for(n - base[2]), cqp::kSetupThreads, 0, st>>>(base[2], n, qv, acc);
       CK(cudaMemcpyAsync(&qcone, acc, sizeof(double), cudaMemcpyDeviceToHost, st));
     }
     // ---- ||A~||_2 by power iteration on A~'A~ (reading: all-ones start, Rayleigh
@@ -463,15 +468,15 @@ struct Handle : HandleBase {
       double* v = tmp.alloc<double>(n);
       double* w = tmp.alloc<double>(std::max<int64_t>(m, 1));
       double* z = tmp.alloc<double>(n);
-      cqp::k_fill<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, v, 1.0 / std::sqrt((double)n));
+      count_launch(); cqp::k_fill<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, v, 1.0 / std::sqrt((double)n));
       double sig = 0.0;
       for (int it = 0; it < o.power_iters && m > 0; ++it) {
-        cqp::k_spmv_simple<T><<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp, a_ci, a_v, v, w);
+        count_launch(); cqp::k_spmv_simple<T><<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp, a_ci, a_v, v, w);
         const double s_new = std::sqrt(dev_dot(w, nullptr, m, part, one, st));
-        cqp::k_spmv_simple<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, t_rp, t_ci, t_v, w, z);
+        count_launch(); cqp::k_spmv_simple<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, t_rp, t_ci, t_v, w, z);
         const double zn = std::sqrt(dev_dot(z, nullptr, n, part, one, st));
         if (zn == 0.0) { sig = s_new; break; }
-        cqp::k_scal<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, z, 1.0 / zn);
+        count_launch(); cqp::k_scal<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, z, 1.0 / zn);
         CK(cudaMemcpyAsync(v, z, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
         const bool done = it > 0 && std::fabs(s_new - sig) <= o.power_tol * s_new;
         sig = s_new;
@@ -539,6 +544,7 @@ struct Handle : HandleBase {
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
     setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    setup_launches = g_launches - launches0;
   }
 
   int solve(const double* x0, const double* y0, double* xo, double* yo, int on_dev, cqp_result* res) override {
@@ -552,15 +558,15 @@ struct Handle : HandleBase {
       if (y0 && m > 0) { double* d = tmp.alloc<double>(m); CK(cudaMemcpyAsync(d, y0, m * 8, cudaMemcpyHostToDevice, st)); dy0 = d; }
     }
     // scaled start: x~ = col x / beta_b (permuted), y~ = row y / beta_c
-    k_perm_scale<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, perm, dx0, P.col, P.beta_b, W.hx[0]);
-    if (m > 0) k_perm_scale<T><<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, nullptr, dy0, P.row, P.beta_c, W.hy[0]);
-    k_copy_vec<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, W.hx[0], W.ax);
-    k_copy_vec<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, W.hx[0], W.wx[0]);
-    k_copy_vec<T><<<cqp::grid_for(mm), cqp::kSetupThreads, 0, st>>>(mm, W.hy[0], W.ay);
-    k_copy_vec<T><<<cqp::grid_for(mm), cqp::kSetupThreads, 0, st>>>(mm, W.hy[0], W.wy);
+    count_launch(); k_perm_scale<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, perm, dx0, P.col, P.beta_b, W.hx[0]);
+    if (m > 0) { count_launch(); k_perm_scale<T><<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, nullptr, dy0, P.row, P.beta_c, W.hy[0]); }
+    count_launch(); k_copy_vec<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, W.hx[0], W.ax);
+    count_launch(); k_copy_vec<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, W.hx[0], W.wx[0]);
+    count_launch(); k_copy_vec<T><<<cqp::grid_for(mm), cqp::kSetupThreads, 0, st>>>(mm, W.hy[0], W.ay);
+    count_launch(); k_copy_vec<T><<<cqp::grid_for(mm), cqp::kSetupThreads, 0, st>>>(mm, W.hy[0], W.wy);
     if (W.avx) {
-      k_zero<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, W.avx);
-      k_zero<T><<<cqp::grid_for(mm), cqp::kSetupThreads, 0, st>>>(mm, W.avy);
+      count_launch(); k_zero<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, W.avx);
+      count_launch(); k_zero<T><<<cqp::grid_for(mm), cqp::kSetupThreads, 0, st>>>(mm, W.avy);
     }
     cqp::State hs;
     memset(&hs, 0, sizeof(hs));
@@ -573,20 +579,32 @@ struct Handle : HandleBase {
     if (k > 0 && x0) {
       double* t = tmp.alloc<double>(k);
       CK(cudaMemsetAsync(t, 0, k * sizeof(double), st));
-      k_rx_partial<T><<<dim3(cqp::grid_for(n, 256, 256), (unsigned)k), 256, 0, st>>>(k, n, P.R, W.hx[0], t);
-      k_state_set_th<<<1, 32, 0, st>>>(S, t, (int)k);
+      count_launch(); k_rx_partial<T><<<dim3(cqp::grid_for(n, 256, 256), (unsigned)k), 256, 0, st>>>(k, n, P.R, W.hx[0], t);
+      count_launch(); k_state_set_th<<<1, 32, 0, st>>>(S, t, (int)k);
     }
     CK(cudaMemsetAsync(dev_err, 0, sizeof(int), st));
     long long per_launch = opt.launch_iters > 0 ? opt.launch_iters : (long long)O.check_every * (grid ? 4 : 16);
     int launches = 0;
     int status = CQP_ITER_LIMIT;
+    double kernel_ms = 0.0;
+    cudaEvent_t ev0, ev1;
+    CK(cudaEventCreate(&ev0));
+    CK(cudaEventCreate(&ev1));
     cqp::State back;
     for (;;) {
       CK(cudaMemsetAsync(bar_count, 0, sizeof(unsigned), st));
+      CK(cudaEventRecord(ev0, st));
+      count_launch();
       CK(cqp::launch_pdhg<T>(args(per_launch), grid, blocks, threads, st));
+      CK(cudaEventRecord(ev1, st));
       ++launches;
       CK(cudaMemcpyAsync(&back, S, sizeof(back), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
+      {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ev0, ev1));
+        kernel_ms += ms;
+      }
       if (back.err == cqp::kErrBarrier) { status = CQP_ERR_WAIT; break; }
       if (back.err == cqp::kErrNumeric) { status = CQP_ERR_NUMERICAL; break; }
       if (back.status == 1) { status = CQP_OK; break; }
@@ -595,12 +613,14 @@ struct Handle : HandleBase {
       if (opt.time_limit_s > 0 && el > opt.time_limit_s) { status = CQP_TIME_LIMIT; break; }
     }
     // final candidate (average for the averaged variant), unscaled and un-permuted
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
     const T* fx = opt.update == 1 ? W.avx : W.wx[back.wb];
     const T* fy = opt.update == 1 ? W.avy : W.wy;
     double* ox = tmp.alloc<double>(n);
     double* oy = tmp.alloc<double>(mm);
-    k_unscale_unperm<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, perm, fx, P.col, P.beta_b, ox);
-    if (m > 0) k_unscale_unperm<T><<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, nullptr, fy, P.row, P.beta_c, oy);
+    count_launch(); k_unscale_unperm<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, perm, fx, P.col, P.beta_b, ox);
+    if (m > 0) { count_launch(); k_unscale_unperm<T><<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, nullptr, fy, P.row, P.beta_c, oy); }
     if (xo) CK(cudaMemcpyAsync(xo, ox, n * 8, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
     if (yo && m > 0) CK(cudaMemcpyAsync(yo, oy, m * 8, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -620,6 +640,8 @@ struct Handle : HandleBase {
       res->setup_ms = setup_ms;
       res->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
       for (int i = 0; i < 8; ++i) res->phase_ms[i] = back.prof[i] * 1e-6;
+      res->kernel_ms = kernel_ms;
+      res->setup_launches = setup_launches;
     }
     return status;
   }
@@ -637,10 +659,11 @@ struct Handle : HandleBase {
       if (m > 0) CK(cudaMemcpyAsync(e, y, m * 8, cudaMemcpyHostToDevice, st));
       dy = e;
     }
-    k_perm_scale<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, perm, dx, P.col, P.beta_b, tmp_x);
-    if (m > 0) k_perm_scale<T><<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, nullptr, dy, P.row, P.beta_c, tmp_y);
+    count_launch(); k_perm_scale<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, perm, dx, P.col, P.beta_b, tmp_x);
+    if (m > 0) { count_launch(); k_perm_scale<T><<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, nullptr, dy, P.row, P.beta_c, tmp_y); }
     CK(cudaMemsetAsync(bar_count, 0, sizeof(unsigned), st));
     CK(cudaMemsetAsync(dev_err, 0, sizeof(int), st));
+    count_launch();
     CK(cqp::launch_kkt<T>(args(0), tmp_x, tmp_y, kkt_out, grid, blocks, threads, st));
     double h[8];
     CK(cudaMemcpyAsync(h, kkt_out, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -768,6 +791,8 @@ const char* cqp_status_string(int s) {
 
 const char* cqp_last_error(void) { return g_last_error.c_str(); }
 
+long long cqp_kernel_launches(void) { return g_launches; }
+
 int cqp_spmv(int32_t precision, int64_t nrows, int64_t ncols, const int32_t* rowptr, const int32_t* colind,
              const void* val, const void* x, void* y, int32_t threads_per_row, void* stream) {
   if (nrows < 0 || ncols < 0 || !rowptr || (nrows > 0 && (!colind || !val || !x || !y))) return CQP_ERR_INVALID;
@@ -781,6 +806,7 @@ int cqp_spmv(int32_t precision, int64_t nrows, int64_t ncols, const int32_t* row
     }
     cudaStream_t st = (cudaStream_t)stream;
     if (nrows == 0) return CQP_OK;
+    count_launch();
     if (precision == 1)
       CK(cqp::launch_spmv<double>(nrows, rowptr, colind, (const double*)val, (const double*)x, (double*)y, tpr, st));
     else
@@ -795,6 +821,7 @@ int cqp_project(int32_t precision, int64_t n, const cqp_cones* K, const void* r,
   return guarded([&]() {
     cudaStream_t st = (cudaStream_t)stream;
     if (K->nblocks == 0) return CQP_OK;
+    count_launch();
     if (precision == 1)
       CK(cqp::launch_project<double>(K->nblocks, K->type, K->start, K->dim, K->alpha, (const double*)r,
                                      (const double*)m, (double*)out, n, st));

@@ -101,6 +101,7 @@ struct Ctl {
   State s;
   double red[kMaxSlots];           // gathered sums of the last phase
   double w[kMaxRank];              // D~ t for the gradient of the current inner step
+  float wf[kMaxRank];              // the same in FP32 (iterate precision of the mixed mode)
   double tcur[kMaxRank];           // R~ u^j of the current inner iterate
   double alpha, sJs;
   double pid_dx, pid_dy;           // ||w_x - a_x||, ||w_y - a_y|| of the last check
@@ -230,18 +231,24 @@ struct Solver {
     for (int i = threadIdx.x; i < nwarps() * P.k; i += blockDim.x) wacc[i] = 0.0;
     __syncthreads();
   }
-  // add sum over the warp of R[l, i] * val for every l (warp-uniform call; lanes with
-  // valid == false contribute zero)
-  __device__ __forceinline__ void wacc_add(int64_t i, double val, bool valid) {
+  // add the warp's sum of R[l, i] * val for every l (warp-uniform call; lanes with
+  // valid == false contribute zero).  Products and the warp tree in T, the running
+  // per-warp total in FP64.
+  __device__ __forceinline__ void wacc_add(int64_t i, T val, bool valid) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int l = 0; l < P.k; ++l) {
-      double p = valid ? (double)P.R[(int64_t)l * P.n + i] * val : 0.0;
+      T p = valid ? P.R[(int64_t)l * P.n + i] * val : T(0);
       p = warp_sum(p);
-      if (lane == 0) wacc[warp * P.k + l] += p;
+      if (lane == 0) wacc[warp * P.k + l] += (double)p;
     }
   }
-  // (R' w)_i with w in shared memory (k entries)
-  __device__ __forceinline__ double rtw(int64_t i, const double* w) const {
+  // (R' w)_i with w in shared memory (k entries, iterate precision)
+  __device__ __forceinline__ T rtw(int64_t i, const T* w) const {
+    T s = T(0);
+    for (int l = 0; l < P.k; ++l) s += P.R[(int64_t)l * P.n + i] * w[l];
+    return s;
+  }
+  __device__ __forceinline__ double rtw_d(int64_t i, const double* w) const {
     double s = 0.0;
     for (int l = 0; l < P.k; ++l) s += (double)P.R[(int64_t)l * P.n + i] * w[l];
     return s;
@@ -348,20 +355,27 @@ struct Solver {
   // u_next = Pi^J(u_cur - alpha J^{-1} g(u_cur)),   g = Q u + c + (u - v)/tau,
   // with Q u = qd u + R' D t (t = R u_cur, D t in C.w); in sparse-P mode the
   // whole gradient is taken from gs (computed by grad_pass).
-  // Accumulates s = u_next - u_cur: v3 = {||s||^2, <s, J s>, sum (qd + 1/tau) s^2} and,
-  // with R, the warp partials of R u_next.
-  __device__ void inner_step(const T* ucur, T* unext, const T* gs, double alpha, double tau, double (&v3)[4]) {
-    const double itau = 1.0 / tau;
+  // Accumulates s = u_next - u_cur: v3 = {||s||^2, <s, J s>, sum (qd + 1/tau) s^2,
+  // ||u_next||^2} and, with R, the warp partials of R u_next.  Per-element work and
+  // per-thread partial sums are in the iterate precision T.
+  __device__ __forceinline__ const T* wvec() const {
+    if constexpr (sizeof(T) == 4) return reinterpret_cast<const T*>(C.wf);
+    else return reinterpret_cast<const T*>(C.w);
+  }
+  __device__ void inner_step(const T* ucur, T* unext, const T* gs, double alpha_d, double tau, double (&v3)[4]) {
+    const T itau = T(1.0 / tau);
+    const T alpha = T(alpha_d);
     const bool lowr = P.k > 0;
     const bool jac = O.jacobi != 0;
-    auto grad = [&](int64_t i, double u) {
-      if (gs) return (double)gs[i];
-      double g = (double)P.qd[i] * u + (double)P.c[i] + (u - (double)W.v[i]) * itau;
-      if (lowr) g += rtw(i, C.w);
+    const T* w = wvec();
+    auto grad = [&](int64_t i, T u) -> T {
+      if (gs) return gs[i];
+      T g = P.qd[i] * u + P.c[i] + (u - W.v[i]) * itau;
+      if (lowr) g += rtw(i, w);
       return g;
     };
-    auto jm = [&](int64_t i) { return jac ? (double)P.jd[i] + itau : 1.0; };
-    v3[0] = v3[1] = v3[2] = v3[3] = 0.0;
+    auto jm = [&](int64_t i) -> T { return jac ? P.jd[i] + itau : T(1); };
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
     if (lowr) wacc_zero();
     // elementwise segments (free, nonneg): whole warps iterate together
     const int lane = threadIdx.x & 31;
@@ -370,18 +384,18 @@ struct Solver {
       for (int64_t base = a + (threadIdx.x - lane); base < b; base += blockDim.x) {
         const int64_t i = base + lane;
         const bool ok = i < b;
-        double un = 0.0;
+        T un = T(0);
         if (ok) {
-          const double u = (double)ucur[i];
-          const double J = jm(i);
-          const double z = u - alpha * grad(i, u) / J;
-          un = (double)proj_elem(i, T(z));
-          unext[i] = T(un);
-          const double s = un - u;
-          v3[0] += s * s;
-          v3[1] += J * s * s;
-          v3[2] += ((double)P.qd[i] + itau) * s * s;
-          v3[3] += un * un;
+          const T u = ucur[i];
+          const T J = jm(i);
+          const T z = u - alpha * grad(i, u) / J;
+          un = proj_elem(i, z);
+          unext[i] = un;
+          const T sd = un - u;
+          a0 += sd * sd;
+          a1 += J * sd * sd;
+          a2 += (P.qd[i] + itau) * sd * sd;
+          a3 += un * un;
         }
         if (lowr) wacc_add(i, un, ok);
       }
@@ -389,8 +403,8 @@ struct Solver {
     // cone segments: gradient step into unext, then block-local metric projection
     for (int seg = 2; seg < 6; ++seg)
       for (int64_t i = own.x0[seg] + threadIdx.x; i < own.x1[seg]; i += blockDim.x) {
-        const double u = (double)ucur[i];
-        unext[i] = T(u - alpha * grad(i, u) / jm(i));
+        const T u = ucur[i];
+        unext[i] = u - alpha * grad(i, u) / jm(i);
       }
     __syncthreads();
     project_owned_cones(unext, jac ? kJacobi : kEuclid, tau);
@@ -399,18 +413,22 @@ struct Solver {
       for (int64_t base = a + (threadIdx.x - lane); base < b; base += blockDim.x) {
         const int64_t i = base + lane;
         const bool ok = i < b;
-        double un = 0.0;
+        T un = T(0);
         if (ok) {
-          un = (double)unext[i];
-          const double s = un - (double)ucur[i];
-          v3[0] += s * s;
-          v3[1] += jm(i) * s * s;
-          v3[2] += ((double)P.qd[i] + itau) * s * s;
-          v3[3] += un * un;
+          un = unext[i];
+          const T sd = un - ucur[i];
+          a0 += sd * sd;
+          a1 += jm(i) * sd * sd;
+          a2 += (P.qd[i] + itau) * sd * sd;
+          a3 += un * un;
         }
         if (lowr) wacc_add(i, un, ok);
       }
     }
+    v3[0] = (double)a0;
+    v3[1] = (double)a1;
+    v3[2] = (double)a2;
+    v3[3] = (double)a3;
     __syncthreads();
   }
 
@@ -418,23 +436,22 @@ struct Solver {
   // writes g(u) to gout; v2 = {<s, dg>} with s = u - uprev, dg = g(u) - gprev
   __device__ void grad_pass(const T* u, const T* uprev, const T* gprev, T* gout, double tau, double (&v2)[2],
                             bool first) {
-    const double itau = 1.0 / tau;
-    v2[0] = v2[1] = 0.0;
+    const T itau = T(1.0 / tau);
+    const T* w = wvec();
+    T acc = T(0);
     for (int seg = 0; seg < 6; ++seg) {
-      rows_loop_tpr<double>(
-          P.tpr_t, P.p_rp, P.p_ci, P.p_v, own.x0[seg], own.x1[seg], [&](int j) { return u[j]; },
-          [&](int64_t i, int gl, double pu) {
-            if (gl == 0) {
-              double g = pu + (double)P.qd[i] * (double)u[i] + (double)P.c[i] + ((double)u[i] - (double)W.v[i]) * itau;
-              if (P.k > 0) g += rtw(i, C.w);
-              gout[i] = T(g);
-              if (!first) {
-                const double s = (double)u[i] - (double)uprev[i];
-                v2[0] += s * (g - (double)gprev[i]);
-              }
-            }
-          });
+      rows_loop_tpr<T>(P.tpr_t, P.p_rp, P.p_ci, P.p_v, own.x0[seg], own.x1[seg], [&](int j) { return u[j]; },
+                       [&](int64_t i, int gl, T pu) {
+                         if (gl == 0) {
+                           T g = pu + P.qd[i] * u[i] + P.c[i] + (u[i] - W.v[i]) * itau;
+                           if (P.k > 0) g += rtw(i, w);
+                           gout[i] = g;
+                           if (!first) acc += (u[i] - uprev[i]) * (g - gprev[i]);
+                         }
+                       });
     }
+    v2[0] = (double)acc;
+    v2[1] = 0.0;
     __syncthreads();
   }
 

@@ -43,14 +43,15 @@ __device__ __forceinline__ void rows_loop2_tpr(int tpr, const int* rp, const int
   }
 }
 
-// C.w = D~ t (k entries), threads l < k
+// w = D~ t (k entries), threads l < k; wf (optional) receives an FP32 copy
 template <typename T>
-__device__ __forceinline__ void apply_D(const Prob<T>& P, const double* t, double* w) {
+__device__ __forceinline__ void apply_D(const Prob<T>& P, const double* t, double* w, float* wf = nullptr) {
   __syncthreads();
   for (int l = threadIdx.x; l < P.k; l += blockDim.x) {
     double s = 0.0;
     for (int l2 = 0; l2 < P.k; ++l2) s += P.D[l * P.k + l2] * t[l2];
     w[l] = s;
+    if (wf) wf[l] = (float)s;
   }
   __syncthreads();
 }
@@ -67,10 +68,10 @@ __device__ bool Solver<T, Team>::prox_diag(const T* hx) {
   phase_aty(hx, W.hy[C.s.hb], tau);
   tick(0);
   T* u = W.u[0];
+  const T tt = T(tau);
   for (int seg = 0; seg < 6; ++seg)
     for (int64_t i = own.x0[seg] + threadIdx.x; i < own.x1[seg]; i += blockDim.x) {
-      const double mi = 1.0 + tau * (double)P.qd[i];
-      const T z = T(((double)W.v[i] - tau * (double)P.c[i]) / mi);
+      const T z = (W.v[i] - tt * P.c[i]) / (T(1) + tt * P.qd[i]);
       u[i] = seg < 2 ? proj_elem(i, z) : z;
     }
   __syncthreads();
@@ -96,7 +97,7 @@ __device__ bool Solver<T, Team>::prox_bb(const T* hx, int& ub) {
   tick(0);
   // t = R h_x from the state; w = D t
   for (int l = threadIdx.x; l < k; l += blockDim.x) C.tcur[l] = C.s.t_h[l];
-  apply_D(P, C.tcur, C.w);
+  apply_D(P, C.tcur, C.w, C.wf);
   double v3[4];
   int gb = 0;
   // ||u^{j+1} - u^j|| cannot fall below the rounding level of u: the stop test compares it
@@ -138,10 +139,10 @@ __device__ bool Solver<T, Team>::prox_bb(const T* hx, int& ub) {
       __syncthreads();
       sdg = C.alpha;
       for (int l = threadIdx.x; l < k; l += blockDim.x) C.tcur[l] = C.red[4 + l];
-      apply_D(P, C.tcur, C.w);
+      apply_D(P, C.tcur, C.w, C.wf);
     } else {
       for (int l = threadIdx.x; l < k; l += blockDim.x) C.tcur[l] = C.red[4 + l];
-      apply_D(P, C.tcur, C.w);
+      apply_D(P, C.tcur, C.w, C.wf);
       double v2[2];
       grad_pass(W.u[cur], uprev, W.g[gb], W.g[gb ^ 1], tau, v2, false);
       publish<2>(v2, 0, false);
@@ -206,11 +207,11 @@ __device__ bool Solver<T, Team>::kkt(const T* x, const T* y, bool have_rx) {
     for (int64_t base = a + (threadIdx.x - lane); base < b; base += blockDim.x) {
       const int64_t i = base + lane;
       const bool ok = i < b;
-      double xi = 0.0;
+      T xi = T(0);
       if (ok) {
-        xi = (double)x[i];
-        v4[2] += (double)P.c[i] * xi;
-        v4[3] += (double)P.qd[i] * xi * xi;
+        xi = x[i];
+        v4[2] += (double)P.c[i] * (double)xi;
+        v4[3] += (double)P.qd[i] * (double)xi * (double)xi;
       }
       if (need_r) wacc_add(i, xi, ok);
     }
@@ -242,7 +243,7 @@ __device__ bool Solver<T, Team>::kkt(const T* x, const T* y, bool have_rx) {
         [&](int64_t i, int gl, double aty) {
           if (gl == 0) {
             double qx = (double)P.qd[i] * (double)x[i];
-            if (k > 0) qx += rtw(i, wk);
+            if (k > 0) qx += rtw_d(i, wk);
             if (sparse) qx += W.sd[i];
             const double ss = P.beta_c * P.col[i] * (qx + (double)P.c[i] - aty);
             if (seg == 0) v2[0] += ss * ss;
@@ -334,29 +335,33 @@ __device__ void Solver<T, Team>::run(long long budget) {
     const double tau = C.s.tau, sigma = C.s.sigma;
     const double kk = (double)C.s.k;
     const double c1 = (kk + 1.0) / (kk + 2.0), c2 = 1.0 / (kk + 2.0), r2 = 2.0 * O.rho, r1 = 1.0 - 2.0 * O.rho;
-    // ---- P5: dual step on the owned rows, candidate bookkeeping on the owned coordinates
+    // ---- P5: dual step on the owned rows, candidate bookkeeping on the owned coordinates.
+    // Every-iteration work in the iterate precision T; the check-time quantities
+    // (E^2 parts, PID movements) in FP64.
     double v6[6] = {0, 0, 0, 0, 0, 0};
+    T mov_acc = T(0);
     T* hyn = W.hy[hb ^ 1];
+    const T sg = T(sigma), tc1 = T(c1), tc2 = T(c2), tr1 = T(r1), tr2 = T(r2), tkk = T(kk);
     rows_loop2_tpr<T>(
         P.tpr_a, P.a_rp, P.a_ci, P.a_v, own.row0, own.row1,
         [&](int j) { return T(2) * wxn[j] - hx[j]; }, [&](int j) { return needE ? hx[j] - wxn[j] : T(0); },
         [&](int64_t r, int gl, T s1, T s2) {
           if (gl != 0) return;
-          const double h = (double)hy[r];
-          const double wy = h + sigma * ((double)P.b[r] - (double)s1);   // eq. stored-pdhg-candidate
-          W.wy[r] = T(wy);
-          if (halpern_now) hyn[r] = T(c1 * (r2 * wy + r1 * h) + c2 * (double)W.ay[r]);   // eq. rh-update
+          const T h = hy[r];
+          const T wy = h + sg * (P.b[r] - s1);   // eq. stored-pdhg-candidate
+          W.wy[r] = wy;
+          if (halpern_now) hyn[r] = tc1 * (tr2 * wy + tr1 * h) + tc2 * W.ay[r];   // eq. rh-update
           if (avg) {
-            hyn[r] = T(wy);
-            W.avy[r] = T((kk * (double)W.avy[r] + wy) / (kk + 1.0));
+            hyn[r] = wy;
+            W.avy[r] = (tkk * W.avy[r] + wy) / (tkk + T(1));
           }
           if (needE) {
-            const double dy = h - wy;
+            const double dy = (double)h - (double)wy;
             v6[2] += dy * dy;
             v6[3] += (double)s2 * dy;
           }
           if (check) {
-            const double e = wy - (double)W.ay[r];
+            const double e = (double)wy - (double)W.ay[r];
             v6[5] += e * e;
           }
         });
@@ -369,26 +374,27 @@ __device__ void Solver<T, Team>::run(long long budget) {
       for (int64_t base = a + (threadIdx.x - lane); base < b; base += blockDim.x) {
         const int64_t i = base + lane;
         const bool okc = i < b;
-        double hn = 0.0;
+        T hn = T(0);
         if (okc) {
-          const double w = (double)wxn[i], h = (double)hx[i];
-          const double mv = w - (double)wxp[i];
-          v6[0] += mv * mv;
-          wxs[i] = T(w);
-          if (needE) v6[1] += (h - w) * (h - w);
-          if (check) { const double e = w - (double)W.ax[i]; v6[4] += e * e; }
+          const T w = wxn[i], h = hx[i];
+          const T mv = w - wxp[i];
+          mov_acc += mv * mv;
+          wxs[i] = w;
+          if (needE) { const double d = (double)h - (double)w; v6[1] += d * d; }
+          if (check) { const double e = (double)w - (double)W.ax[i]; v6[4] += e * e; }
           if (halpern_now) {
-            hn = c1 * (r2 * w + r1 * h) + c2 * (double)W.ax[i];
-            hxn[i] = T(hn);
+            hn = tc1 * (tr2 * w + tr1 * h) + tc2 * W.ax[i];
+            hxn[i] = hn;
           }
           if (avg) {
-            hxn[i] = T(w);
-            W.avx[i] = T((kk * (double)W.avx[i] + w) / (kk + 1.0));
+            hxn[i] = w;
+            W.avx[i] = (tkk * W.avx[i] + w) / (tkk + T(1));
           }
         }
         if (halpern_now && k > 0) wacc_add(i, hn, okc);
       }
     }
+    v6[0] = (double)mov_acc;
     __syncthreads();
     publish<6>(v6, 0, halpern_now && k > 0);
     if (!sync_gather(6 + ((halpern_now && k > 0) ? k : 0), 3, 4)) return;
@@ -444,8 +450,8 @@ __device__ void Solver<T, Team>::run(long long budget) {
           for (int64_t base = a + (threadIdx.x - lane); base < b; base += blockDim.x) {
             const int64_t i = base + lane;
             const bool okc = i < b;
-            double av = 0.0;
-            if (okc) { av = (double)W.avx[i]; W.hx[hb2][i] = T(av); }
+            T av = T(0);
+            if (okc) { av = W.avx[i]; W.hx[hb2][i] = av; }
             if (k > 0) wacc_add(i, av, okc);
           }
         }
@@ -522,16 +528,16 @@ __device__ void Solver<T, Team>::run(long long budget) {
         for (int64_t base = a + (threadIdx.x - lane); base < b; base += blockDim.x) {
           const int64_t i = base + lane;
           const bool okc = i < b;
-          double hn = 0.0;
+          T hn = T(0);
           if (okc) {
-            hn = c1 * (r2 * (double)wx[i] + r1 * (double)hx[i]) + c2 * (double)W.ax[i];
-            W.hx[hbn][i] = T(hn);
+            hn = T(c1) * (T(r2) * wx[i] + T(r1) * hx[i]) + T(c2) * W.ax[i];
+            W.hx[hbn][i] = hn;
           }
           if (k > 0) wacc_add(i, hn, okc);
         }
       }
       for (int64_t r = own.row0 + threadIdx.x; r < own.row1; r += blockDim.x)
-        W.hy[hbn][r] = T(c1 * (r2 * (double)W.wy[r] + r1 * (double)hy[r]) + c2 * (double)W.ay[r]);
+        W.hy[hbn][r] = T(c1) * (T(r2) * W.wy[r] + T(r1) * hy[r]) + T(c2) * W.ay[r];
       __syncthreads();
       double z1[1] = {0.0};
       publish<1>(z1, 0, k > 0);
