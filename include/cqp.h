@@ -91,7 +91,7 @@ typedef struct {
 
 typedef struct {
   /* arithmetic */
-  int32_t precision;        /* 0: FP32 iterates and matrices, FP64 reductions and cone roots; 1: all FP64 */
+  int32_t precision;        /* 0: FP32 iterates, matrices and SOC roots; FP64 reductions and RSOC/exp/pow roots; 1: all FP64 */
   int32_t update;           /* 0: reflected Halpern (eq. "rh-update"); 1: Cesaro averaged (Alg. "pdhcq1") */
   double rho;               /* reflection coefficient, default 1.0 */
   /* rescaling (Table "practical-defaults") */
@@ -142,8 +142,9 @@ typedef struct {
   double setup_ms, solve_ms;
   /* with opt.profile: device time (block 0) per phase of the iteration: A'y product,
    * prox work, prox barriers, dual step, its barrier, KKT checks, restart/Halpern at
-   * checks, whole loop */
-  double phase_ms[8];
+   * checks, whole loop; then the inner BB step split into its elementwise part, cone
+   * gradient, cone projection and cone bookkeeping */
+  double phase_ms[12];
   double kernel_ms;                /* CUDA-event time of the solver kernel launches of this solve */
   int64_t setup_launches;          /* kernels launched by cqp_setup for this handle */
 } cqp_result;

@@ -178,6 +178,7 @@ struct Handle : HandleBase {
   T* tmp_y = nullptr;
   double eta = 0, normA = 0, omega0 = 1, setup_ms = 0;
   long long setup_launches = 0;
+  int64_t n_roots = 0;
   bool grid = false;
   int blocks = 1, threads = 512;
 
@@ -493,6 +494,18 @@ struct Handle : HandleBase {
     P.a_rp = a_rp; P.a_ci = a_ci; P.a_v = a_v;
     P.t_rp = t_rp; P.t_ci = t_ci; P.t_v = t_v;
     P.qd = qT; P.jd = jT; P.k = (int)k; P.R = RT; P.D = Dv;
+    // D = d I (the common case) lets the kernel skip the k x k products
+    P.d_scale = 0.0;
+    if (k > 0) {
+      std::vector<double> hD(k * k);
+      CK(cudaMemcpyAsync(hD.data(), Dv, k * k * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      bool ident = hD[0] > 0.0;
+      for (int64_t a = 0; a < k && ident; ++a)
+        for (int64_t b2 = 0; b2 < k && ident; ++b2)
+          if ((a == b2 && hD[a * k + b2] != hD[0]) || (a != b2 && hD[a * k + b2] != 0.0)) ident = false;
+      if (ident) P.d_scale = hD[0];
+    }
     P.p_rp = p_rp; P.p_ci = p_ci; P.p_v = pT;
     P.c = cT; P.b = bT; P.col = col; P.row = row; P.beta_b = beta_b; P.beta_c = beta_c;
     P.n_free = cnt[0]; P.n_nonneg = cnt[1];
@@ -502,8 +515,43 @@ struct Handle : HandleBase {
     else if (k > 0 || o.force_inner) P.qmode = cqp::kQLowRank;
     else P.qmode = cqp::kQDiag;
     P.euclid_cones = (P.qmode == cqp::kQDiag && qcone == 0.0) ? 1 : 0;
-    P.tpr_a = o.tpr_a > 0 ? o.tpr_a : pow2_tpr(m > 0 ? (double)nnz / (double)m : 1.0);
-    P.tpr_t = o.tpr_at > 0 ? o.tpr_at : pow2_tpr((double)std::max(nnz, pnnz) / (double)n);
+    // threads per CSR row: user choice, else the fastest of 1..32 lanes measured on this
+    // matrix with the solver's row kernel (CUDA events, best of 3 after one warm-up)
+    {
+      T* xs = tmp.alloc<T>(n);
+      T* ys = tmp.alloc<T>(std::max<int64_t>(std::max(m, n), 1));
+      count_launch(); cqp::k_convert<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, jdv, xs);
+      auto tune = [&](int64_t rows, const int32_t* rp, const int32_t* ci, const T* v) {
+        if (rows == 0) return 1;
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        int best = 8;
+        float best_ms = 1e30f;
+        for (int t = 1; t <= 32; t <<= 1) {
+          count_launch();
+          CK(cqp::launch_spmv<T>(rows, rp, ci, v, xs, ys, t, st));
+          float tot = 1e30f;
+          for (int r = 0; r < 3; ++r) {
+            CK(cudaEventRecord(e0, st));
+            count_launch();
+            CK(cqp::launch_spmv<T>(rows, rp, ci, v, xs, ys, t, st));
+            CK(cudaEventRecord(e1, st));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            tot = std::min(tot, ms);
+          }
+          if (tot < best_ms) { best_ms = tot; best = t; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return best;
+      };
+      P.tpr_a = o.tpr_a > 0 ? o.tpr_a : tune(m, a_rp, a_ci, a_v);
+      P.tpr_t = o.tpr_at > 0 ? o.tpr_at : tune(n, t_rp, t_ci, t_v);
+      P.tpr_p = has_p ? tune(n, p_rp, p_ci, pT) : 1;
+    }
     // ---- work buffers and state -------------------------------------------------------------
     const int64_t mm = std::max<int64_t>(m, 1);
     for (int i = 0; i < 2; ++i) {
@@ -516,10 +564,12 @@ struct Handle : HandleBase {
     W.avy = o.update == 1 ? mem.alloc<T>(mm) : nullptr;
     W.mbuf = mem.alloc<T>(n);
     W.sd = mem.alloc<double>(n);
+    n_roots = n_soc + n_rsoc + n_exp + n_pow;
+    W.root = mem.alloc<float>(std::max<int64_t>(n_roots, 1));
     // team
     threads = o.threads > 0 ? o.threads : 512;
     const int64_t size = n + m;
-    grid = o.team == 1 || (o.team == 0 && size > 40000);
+    grid = o.team == 1 || (o.team == 0 && size > 4096);
     if (grid) {
       const int per = cqp::pdhg_blocks_per_sm<T>(threads);
       if (per < 1) fail(CQP_ERR_UNSUPPORTED, "solver kernel does not fit on an SM with this block size");
@@ -564,6 +614,8 @@ struct Handle : HandleBase {
     count_launch(); k_copy_vec<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, W.hx[0], W.wx[0]);
     count_launch(); k_copy_vec<T><<<cqp::grid_for(mm), cqp::kSetupThreads, 0, st>>>(mm, W.hy[0], W.ay);
     count_launch(); k_copy_vec<T><<<cqp::grid_for(mm), cqp::kSetupThreads, 0, st>>>(mm, W.hy[0], W.wy);
+    // no warm start for the cone roots of a new solve (NaN = none)
+    CK(cudaMemsetAsync(W.root, 0xff, std::max<int64_t>(n_roots, 1) * sizeof(float), st));
     if (W.avx) {
       count_launch(); k_zero<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, W.avx);
       count_launch(); k_zero<T><<<cqp::grid_for(mm), cqp::kSetupThreads, 0, st>>>(mm, W.avy);
@@ -639,7 +691,7 @@ struct Handle : HandleBase {
       res->omega = back.omega;
       res->setup_ms = setup_ms;
       res->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-      for (int i = 0; i < 8; ++i) res->phase_ms[i] = back.prof[i] * 1e-6;
+      for (int i = 0; i < 12; ++i) res->phase_ms[i] = back.prof[i] * 1e-6;
       res->kernel_ms = kernel_ms;
       res->setup_launches = setup_launches;
     }

@@ -63,6 +63,27 @@ __device__ __forceinline__ void block_sum(double (&v)[NS], double* scratch, doub
   __syncthreads();
 }
 
+// Same as block_sum but the per-thread values and the warp trees are in R (the
+// iterate precision for per-iteration sums); warp totals are combined in FP64.
+template <typename R, int NS>
+__device__ __forceinline__ void block_sum_r(R (&v)[NS], double* scratch, double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    R t = v[s];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) scratch[s * nw + warp] = (double)t;
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < NS; s += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += scratch[s * nw + w];
+    out[s] = t;
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // Teams.  A solver phase is written once against this interface:
 //   nb(), bid()            number of blocks in the team and this block's rank

@@ -18,8 +18,14 @@
 namespace cqp {
 
 template <typename T> struct Tol;
-template <> struct Tol<float> { static constexpr double rel = 2e-7; };
+template <> struct Tol<float> { static constexpr double rel = 4e-7; };
 template <> struct Tol<double> { static constexpr double rel = 4e-16; };
+
+// FP64 on this GPU runs at about 1/57 of the FP32 rate, so the warp-level
+// projections keep element work and warp trees in the iterate precision T and
+// run the FP64 scalar iteration on lane 0 only, broadcasting its result.
+
+__device__ __forceinline__ double bcast(double v) { return __shfl_sync(0xffffffffu, v, 0); }
 
 // --------------------------------------------------------------------------
 // Second-order cone, Euclidean (App. A.2, eq. soc-euclidean-projection).
@@ -27,97 +33,114 @@ template <> struct Tol<double> { static constexpr double rel = 4e-16; };
 // --------------------------------------------------------------------------
 template <typename T>
 __device__ __noinline__ void warp_soc_euclid(T* x, int d, int lane) {
-  double s = 0.0;
-  for (int i = lane; i < d - 1; i += 32) s += (double)x[i] * (double)x[i];
-  const double t = (double)x[d - 1];
+  T s = T(0);
+  for (int i = lane; i < d - 1; i += 32) s += x[i] * x[i];
+  const T t = x[d - 1];
   s = warp_sum(s);
-  const double a = sqrt(s);
+  const T a = sqrt(s);
   if (a <= t) return;
   if (a <= -t) {
     for (int i = lane; i < d; i += 32) x[i] = T(0);
     __syncwarp();
     return;
   }
-  const double coef = (a + t) / (2.0 * a);
-  for (int i = lane; i < d - 1; i += 32) x[i] = T(coef * (double)x[i]);
-  if (lane == 0) x[d - 1] = T(0.5 * (a + t));
+  const T coef = (a + t) / (T(2) * a);
+  for (int i = lane; i < d - 1; i += 32) x[i] = coef * x[i];
+  if (lane == 0) x[d - 1] = T(0.5) * (a + t);
   __syncwarp();
 }
 
 // --------------------------------------------------------------------------
 // Second-order cone in the metric M = diag(m) (App. A.2, eq.
-// soc-metric-projection): v_i(l) = m_i z_i/(m_i + l), t(l) = m_t z_t/(m_t - l),
-// root of f(l) = ||v(l)||^2 - t(l)^2.  Bracket: (0, m_t) when z_t > 0; (m_t, l_U]
-// when z_t < 0 with l_U = (A m_t + B m_max)/(A - B), A = ||M_v z_v||,
-// B = m_t |z_t| (f(l_U) >= 0 follows from ||v||^2 >= A^2/(m_max + l)^2).
-// Singular z_t = 0: l = m_t, t = ||v||.  Newton steps kept inside the bracket.
+// soc-metric-projection): v_i(l) = m_i z_i/(m_i + l), t(l) = m_t z_t/(m_t - l).
+// The admissible root solves psi(l) = 1/t(l) - 1/||v(l)|| = 0 (the same root as
+// ||v||^2 - t^2, nearly linear in l so Newton needs few steps), with
+// psi' = -1/(m_t z_t) - S3/S^{3/2}, S = sum a_i/(m_i+l)^2, S3 = sum a_i/(m_i+l)^3,
+// a_i = (m_i z_i)^2.  Bracket: (0, m_t) when z_t > 0 (psi > 0 at 0, < 0 at m_t);
+// (m_t, l_U] when z_t < 0 with l_U = (A m_t + B m_max)/(A - B), A = ||M_v z_v||,
+// B = m_t |z_t| (||v||^2 >= A^2/(m_max + l)^2 gives psi(l_U) >= 0).  Singular
+// z_t = 0: l = m_t, t = ||v||.
 // --------------------------------------------------------------------------
 template <typename T>
-__device__ __noinline__ void warp_soc_metric(T* x, const T* m, int d, int lane) {
+__device__ __noinline__ void warp_soc_metric(T* x, const T* m, int d, int lane, float* guess = nullptr) {
   const int nv = d - 1;
-  double v2 = 0.0, A2 = 0.0, mmax = 0.0;
+  T v2 = T(0), A2 = T(0), mmax = T(0);
   for (int i = lane; i < nv; i += 32) {
-    const double xi = (double)x[i], mi = (double)m[i];
+    const T xi = x[i], mi = m[i];
     v2 += xi * xi;
     A2 += (mi * xi) * (mi * xi);
-    mmax = fmax(mmax, mi);
+    mmax = mi > mmax ? mi : mmax;
   }
-  const double zt = (double)x[nv], mt = (double)m[nv];
+  const T zt = x[nv], mt = m[nv];
   v2 = warp_sum(v2);
   A2 = warp_sum(A2);
-  mmax = warp_max(mmax);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) { const T q = __shfl_xor_sync(0xffffffffu, mmax, o); mmax = q > mmax ? q : mmax; }
   if (sqrt(v2) <= zt) return;                          // z in K
-  const double A = sqrt(A2), B = mt * fabs(zt);
-  if (zt <= 0.0 && A <= B) {                           // -Mz in K* = K
+  const T A = sqrt(A2), B = mt * (zt < T(0) ? -zt : zt);
+  if (zt <= T(0) && A <= B) {                          // -Mz in K* = K
     for (int i = lane; i < d; i += 32) x[i] = T(0);
     __syncwarp();
     return;
   }
-  double lam;
-  if (zt == 0.0) {
-    lam = mt;
-  } else {
-    double lo, hi;
-    if (zt > 0.0) { lo = 0.0; hi = mt; }
-    else { lo = mt; hi = (A * mt + B * mmax) / (A - B) * (1.0 + 1e-12) + 1e-300; }
-    const double bt = (mt * zt) * (mt * zt);
-    // Newton iteration started at the bracket midpoint
-    lam = 0.5 * (lo + hi);
-    for (int it = 0; it < 200; ++it) {
-      // f and f' (the element sums in T precision, accumulated in FP64)
-      double s2 = 0.0, s3 = 0.0;
+  T lam = mt;
+  if (zt != T(0)) {
+    // lane 0 holds the bracket and the Newton state (scalars in the iterate precision T)
+    T lo, hi;
+    if (zt > T(0)) { lo = T(0); hi = mt; }
+    else { lo = mt; hi = (A * mt + B * mmax) / (A - B) * T(1.000001) + T(1e-30); }
+    const bool lo_pos = zt > T(0);
+    const T inv_mtzt = T(1) / (mt * zt);
+    lam = T(0.5) * (lo + hi);
+    // warm start from the previous root of this block when it lies in the bracket
+    if (guess) {
+      const T g0 = T(*guess);
+      if (g0 > lo && g0 < hi) lam = g0;
+    }
+    for (int it = 0; it < 100; ++it) {
+      T s2t = T(0), s3t = T(0);
       for (int i = lane; i < nv; i += 32) {
         const T mi = m[i], xi = x[i];
         const T ai = (mi * xi) * (mi * xi);
-        const T den = mi + T(lam);
+        const T den = mi + lam;
         const T q = ai / (den * den);
-        s2 += (double)q;
-        s3 += (double)(q / den);
+        s2t += q;
+        s3t += q / den;
       }
-      s2 = warp_sum(s2);
-      s3 = warp_sum(s3);
-      const double dm = mt - lam;
-      const double f = s2 - bt / (dm * dm);
-      const double fp = -2.0 * s3 - 2.0 * bt / (dm * dm * dm);
-      if (f == 0.0) break;                               // exact root: keep lam
-      // z_t > 0: f(lo) > 0 > f(hi);  z_t < 0: f(lo) < 0 < f(hi)
-      if ((f > 0.0) == (zt > 0.0)) lo = lam; else hi = lam;
-      double nx = (fp != 0.0) ? lam - f / fp : 0.5 * (lo + hi);
-      if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
-      const double step = fabs(nx - lam);
-      lam = nx;
-      if (step <= Tol<T>::rel * fmax(lam, 1e-300) || (hi - lo) <= Tol<T>::rel * fmax(lam, 1e-300)) break;
+      s2t = warp_sum(s2t);
+      s3t = warp_sum(s3t);
+      int done = 0;
+      if (lane == 0) {
+        const T nrm = sqrt(s2t);
+        const T psi = (mt - lam) * inv_mtzt - T(1) / nrm;
+        const T dpsi = -inv_mtzt - s3t / (s2t * nrm);
+        if (psi == T(0)) {
+          done = 1;
+        } else {
+          if ((psi > T(0)) == lo_pos) lo = lam; else hi = lam;
+          T nx = (dpsi != T(0)) ? lam - psi / dpsi : T(0.5) * (lo + hi);
+          if (!(nx > lo && nx < hi)) nx = T(0.5) * (lo + hi);
+          const T step = nx > lam ? nx - lam : lam - nx;
+          lam = nx;
+          const T tol = T(Tol<T>::rel) * (lam > T(1e-30) ? lam : T(1e-30));
+          done = (step <= tol || (hi - lo) <= tol) ? 1 : 0;
+        }
+      }
+      lam = __shfl_sync(0xffffffffu, lam, 0);
+      if (__shfl_sync(0xffffffffu, done, 0)) break;
     }
   }
-  double vv = 0.0;
+  if (guess && lane == 0 && zt != T(0)) *guess = (float)lam;
+  const T lt = lam;
+  T vv = T(0);
   for (int i = lane; i < nv; i += 32) {
-    const double mi = (double)m[i];
-    const double vi = mi * (double)x[i] / (mi + lam);
-    x[i] = T(vi);
+    const T mi = m[i];
+    const T vi = mi * x[i] / (mi + lt);
+    x[i] = vi;
     vv += vi * vi;
   }
   vv = warp_sum(vv);
-  if (lane == 0) x[nv] = T(sqrt(vv));
+  if (lane == 0) x[nv] = sqrt(vv);
   __syncwarp();
 }
 
@@ -128,25 +151,25 @@ __device__ __noinline__ void warp_soc_metric(T* x, const T* m, int d, int lane) 
 template <typename T>
 __device__ __noinline__ void warp_rsoc_euclid(T* x, int d, int lane) {
   const int nv = d - 2;
-  const double h = 0.70710678118654752440;
-  double s = 0.0;
-  for (int i = lane; i < nv; i += 32) s += (double)x[i] * (double)x[i];
-  const double zs = (double)x[nv], zt = (double)x[nv + 1];
+  const T h = T(0.70710678118654752440);
+  T s = T(0);
+  for (int i = lane; i < nv; i += 32) s += x[i] * x[i];
+  const T zs = x[nv], zt = x[nv + 1];
   s = warp_sum(s);
-  const double w = (zs - zt) * h, tt = (zs + zt) * h;
-  const double a = sqrt(s + w * w);
+  const T w = (zs - zt) * h, tt = (zs + zt) * h;
+  const T a = sqrt(s + w * w);
   if (a <= tt) return;
   if (a <= -tt) {
     for (int i = lane; i < d; i += 32) x[i] = T(0);
     __syncwarp();
     return;
   }
-  const double coef = (a + tt) / (2.0 * a);
-  for (int i = lane; i < nv; i += 32) x[i] = T(coef * (double)x[i]);
+  const T coef = (a + tt) / (T(2) * a);
+  for (int i = lane; i < nv; i += 32) x[i] = coef * x[i];
   if (lane == 0) {
-    const double wp = coef * w, tp = 0.5 * (a + tt);
-    x[nv] = T((wp + tp) * h);
-    x[nv + 1] = T((tp - wp) * h);
+    const T wp = coef * w, tp = T(0.5) * (a + tt);
+    x[nv] = (wp + tp) * h;
+    x[nv + 1] = (tp - wp) * h;
   }
   __syncwarp();
 }
@@ -159,14 +182,14 @@ __device__ __noinline__ void warp_rsoc_euclid(T* x, int d, int lane) {
 // kappa = sqrt(m_s) z_s + sqrt(m_t) z_t the admissible root (s, t >= 0) lies in
 // (l, q/2) when kappa > 0 and in (q/2, u) when kappa < 0, where l, u are the
 // points at which s or t changes sign; f > 0 at l (or u, or infinity) and
-// f -> -inf at the pole.
+// f -> -inf at the pole.  Safeguarded Newton on f inside that bracket.
 // --------------------------------------------------------------------------
 template <typename T>
-__device__ __noinline__ void warp_rsoc_metric(T* x, const T* m, int d, int lane) {
+__device__ __noinline__ void warp_rsoc_metric(T* x, const T* m, int d, int lane, float* guess = nullptr) {
   const int nv = d - 2;
-  double v2 = 0.0, mv2 = 0.0;
+  T v2 = T(0), mv2 = T(0);
   for (int i = lane; i < nv; i += 32) {
-    const double xi = (double)x[i], mi = (double)m[i];
+    const T xi = x[i], mi = m[i];
     v2 += xi * xi;
     mv2 += (mi * xi) * (mi * xi);
   }
@@ -174,13 +197,13 @@ __device__ __noinline__ void warp_rsoc_metric(T* x, const T* m, int d, int lane)
   const double ms = (double)m[nv], mt = (double)m[nv + 1];
   v2 = warp_sum(v2);
   mv2 = warp_sum(mv2);
-  if (zs >= 0.0 && zt >= 0.0 && v2 <= 2.0 * zs * zt) return;
-  if (zs <= 0.0 && zt <= 0.0 && mv2 <= 2.0 * (ms * zs) * (mt * zt)) {
+  if (zs >= 0.0 && zt >= 0.0 && (double)v2 <= 2.0 * zs * zt) return;
+  if (zs <= 0.0 && zt <= 0.0 && (double)mv2 <= 2.0 * (ms * zs) * (mt * zt)) {
     for (int i = lane; i < d; i += 32) x[i] = T(0);
     __syncwarp();
     return;
   }
-  if (v2 == 0.0) {  // cone reduces to the quadrant s, t >= 0
+  if (v2 == T(0)) {  // cone reduces to the quadrant s, t >= 0
     __syncwarp();
     if (lane == 0) {
       x[nv] = T(fmax(zs, 0.0));
@@ -192,17 +215,38 @@ __device__ __noinline__ void warp_rsoc_metric(T* x, const T* m, int d, int lane)
   const double sms = sqrt(ms), smt = sqrt(mt), q = sms * smt;
   const double kappa = sms * zs + smt * zt;
   const double kscale = sms * fabs(zs) + smt * fabs(zt);
-  double s_out, t_out, xi;
-  if (fabs(kappa) <= 64.0 * Tol<T>::rel * kscale) {
-    xi = 0.5 * q;
-    double vv = 0.0;
+  double s_out = 0.0, t_out = 0.0, xi = 0.5 * q;
+  // sums of the element terms at xi (warp-wide, in T); every lane gets them
+  auto sums = [&](double xx, T& sv, T& sv3) {
+    const T tx = T(2.0 * xx);
+    sv = T(0);
+    sv3 = T(0);
     for (int i = lane; i < nv; i += 32) {
-      const double mi = (double)m[i], vi = mi * (double)x[i] / (mi + q);
-      vv += vi * vi;
+      const T mi = m[i], zi = x[i];
+      const T a = (mi * zi) * (mi * zi);
+      const T den = mi + tx;
+      const T qq = a / (den * den);
+      sv += qq;
+      sv3 += qq / den;
     }
-    vv = warp_sum(vv);
+    sv = warp_sum(sv);
+    sv3 = warp_sum(sv3);
+  };
+  // f and f' from the sums (lane 0)
+  auto fval = [&](double xx, double sv, double sv3, double* df) {
+    const double det = ms * mt - 4.0 * xx * xx;
+    const double ns = ms * zs + 2.0 * xx * zt, nt = mt * zt + 2.0 * xx * zs;
+    const double s = mt * ns / det, t = ms * nt / det;
+    const double ds = mt * (2.0 * zt * det + 8.0 * xx * ns) / (det * det);
+    const double dt = ms * (2.0 * zs * det + 8.0 * xx * nt) / (det * det);
+    *df = -4.0 * sv3 - 2.0 * (ds * t + s * dt);
+    return sv - 2.0 * s * t;
+  };
+  if (fabs(kappa) <= 64.0 * Tol<T>::rel * kscale) {
+    T sv, sv3;
+    sums(0.5 * q, sv, sv3);   // sum of v_i^2 at 2 xi = q
     const double delta = sms * zs;
-    const double chi = sqrt(delta * delta + 2.0 * q * vv);
+    const double chi = sqrt(delta * delta + 2.0 * q * (double)sv);
     s_out = (delta + chi) / (2.0 * sms);
     t_out = (-delta + chi) / (2.0 * smt);
   } else {
@@ -219,40 +263,61 @@ __device__ __noinline__ void warp_rsoc_metric(T* x, const T* m, int d, int lane)
       for (int j = 0; j < 2; ++j)
         if (be[j] > 0.0) hi = fmin(hi, -al[j] / (2.0 * be[j]));
     }
-    auto fval = [&](double xx) {
-      double sv = 0.0;
-      for (int i = lane; i < nv; i += 32) {
-        const T mi = m[i], zi = x[i];
-        const T a = (mi * zi) * (mi * zi);
-        const T den = mi + T(2.0 * xx);
-        sv += (double)(a / (den * den));
-      }
-      sv = warp_sum(sv);
-      const double det = ms * mt - 4.0 * xx * xx;
-      const double s = mt * (ms * zs + 2.0 * xx * zt) / det;
-      const double t = ms * (mt * zt + 2.0 * xx * zs) / det;
-      return sv - 2.0 * s * t;
-    };
+    double dfv;
     if (!isfinite(hi)) {
+      // f xi^2 tends to (||M z_v||^2 - 2 m_s m_t z_s z_t)/4 > 0; when rounding hides that
+      // margin the input lies within rounding of -K* and the projection is the origin
       hi = q;
-      for (int it = 0; it < 2000 && fval(hi) <= 0.0; ++it) hi *= 2.0;
+      int it = 0, pos = 0;
+      for (; it < 128; ++it) {
+        T sv, sv3;
+        sums(hi, sv, sv3);
+        if (lane == 0) pos = fval(hi, (double)sv, (double)sv3, &dfv) > 0.0 ? 1 : 0;
+        if (__shfl_sync(0xffffffffu, pos, 0)) break;
+        hi *= 2.0;
+      }
+      if (it == 128) {
+        for (int i = lane; i < d; i += 32) x[i] = T(0);
+        __syncwarp();
+        return;
+      }
     }
-    // bisection: f(lo) > 0 > f(hi) when kappa > 0, f(lo) < 0 < f(hi) when kappa < 0
     const bool lo_pos = kappa > 0.0;
-    for (int it = 0; it < 200; ++it) {
-      const double mid = 0.5 * (lo + hi);
-      if (mid <= lo || mid >= hi || (hi - lo) <= Tol<T>::rel * mid) break;
-      const double f = fval(mid);
-      if ((f > 0.0) == lo_pos) lo = mid; else hi = mid;
+    double xx = 0.5 * (lo + hi);
+    if (guess) {
+      const double g0 = (double)*guess;
+      if (g0 > lo && g0 < hi) xx = g0;
     }
-    xi = 0.5 * (lo + hi);
+    for (int it = 0; it < 200; ++it) {
+      T sv, sv3;
+      sums(xx, sv, sv3);
+      int done = 0;
+      if (lane == 0) {
+        const double f = fval(xx, (double)sv, (double)sv3, &dfv);
+        if (f == 0.0) {
+          done = 1;
+        } else {
+          if ((f > 0.0) == lo_pos) lo = xx; else hi = xx;
+          double nx = (dfv != 0.0 && isfinite(dfv)) ? xx - f / dfv : 0.5 * (lo + hi);
+          if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
+          const double step = fabs(nx - xx);
+          xx = nx;
+          done = (step <= Tol<T>::rel * xx || (hi - lo) <= Tol<T>::rel * xx) ? 1 : 0;
+        }
+      }
+      xx = bcast(xx);
+      if (__shfl_sync(0xffffffffu, done, 0)) break;
+    }
+    xi = xx;
+    if (guess && lane == 0) *guess = (float)xi;
     const double det = ms * mt - 4.0 * xi * xi;
     s_out = fmax(mt * (ms * zs + 2.0 * xi * zt) / det, 0.0);
     t_out = fmax(ms * (mt * zt + 2.0 * xi * zs) / det, 0.0);
   }
+  const T tx = T(2.0 * xi);
   for (int i = lane; i < nv; i += 32) {
-    const double mi = (double)m[i];
-    x[i] = T(mi * (double)x[i] / (mi + 2.0 * xi));
+    const T mi = m[i];
+    x[i] = mi * x[i] / (mi + tx);
   }
   __syncwarp();
   if (lane == 0) {
@@ -310,8 +375,8 @@ __device__ __forceinline__ double exp_g2(const ExpData& c, double rho) {  // > 0
 }
 
 // safeguarded Newton on G over [lo, hi] with G(lo) < 0 < G(hi)
-static __device__ __noinline__ double exp_root(const ExpData& c, double lo, double hi) {
-  double rho = 0.5 * (lo + hi);
+static __device__ __noinline__ double exp_root(const ExpData& c, double lo, double hi, double start) {
+  double rho = (start > lo && start < hi) ? start : 0.5 * (lo + hi);
   for (int it = 0; it < 300; ++it) {
     double dG;
     const double G = exp_G(c, rho, &dG);
@@ -367,7 +432,8 @@ static __device__ bool exp_trivial(const ExpData& c, double* out) {
 // mu = (r0 - rho s0)/(rho^2-rho+1), so {eta > 0, mu > 0} is an interval cut out
 // by two linear inequalities in rho, with G < 0 at its left end and G > 0 at
 // its right end.
-static __device__ __noinline__ void exp_proj_euclid(double r0, double s0, double t0, double* out) {
+static __device__ __noinline__ void exp_proj_euclid(double r0, double s0, double t0, double* out,
+                                                    float* guess = nullptr) {
   const ExpData c{r0, s0, t0, 1.0, 1.0, 1.0};
   if (exp_trivial(c, out)) return;
   double lo = -INFINITY, hi = INFINITY;
@@ -376,6 +442,13 @@ static __device__ __noinline__ void exp_proj_euclid(double r0, double s0, double
   if (s0 > 0.0) hi = fmin(hi, r0 / s0);
   if (s0 < 0.0) lo = fmax(lo, r0 / s0);
   double dG;
+  // a warm start inside the admissible interval tightens one end of the bracket
+  double g0 = guess ? (double)*guess : NAN;
+  if (isfinite(g0) && g0 > lo && g0 < hi) {
+    if (exp_G(c, g0, &dG) < 0.0) lo = g0; else hi = g0;
+  } else {
+    g0 = NAN;
+  }
   if (!isfinite(lo)) {
     double step = 1.0;
     lo = hi - step;
@@ -386,7 +459,9 @@ static __device__ __noinline__ void exp_proj_euclid(double r0, double s0, double
     hi = lo + step;
     while (exp_G(c, hi, &dG) <= 0.0 && step < 1e8) { step *= 2.0; hi = lo + step; }
   }
-  exp_finish(c, exp_root(c, lo, hi), out);
+  const double rho = exp_root(c, lo, hi, g0);
+  if (guess) *guess = (float)rho;
+  exp_finish(c, rho, out);
 }
 
 // zeros of a function that is convex or concave with stationary point rc (NaN:
@@ -459,7 +534,7 @@ static __device__ __noinline__ void exp_proj_metric(double r0, double s0, double
       if (isfinite(a)) { if (exp_G(c, a, &dG) < 0.0) lo = a; }
       else for (double st = 1.0; st < 1e8; st *= 2.0) if (exp_G(c, p - st, &dG) < 0.0) { lo = p - st; break; }
     }
-    if (!isnan(lo) && !isnan(hi)) rho = exp_root(c, lo, hi);
+    if (!isnan(lo) && !isnan(hi)) rho = exp_root(c, lo, hi, NAN);
   }
   if (isnan(rho)) {          // not expected: fall back to the Euclidean direction
     double e[3];
@@ -481,7 +556,8 @@ __device__ __forceinline__ double pow_qroot(double s, double c) {
   return s >= 0.0 ? 0.5 * (s + d) : 2.0 * c / (d - s);
 }
 
-static __device__ __noinline__ void pow_proj(double rx, double ry, double rz, double al, double mx, double my, double mz, double* out) {
+static __device__ __noinline__ void pow_proj(double rx, double ry, double rz, double al, double mx, double my, double mz,
+                                            double* out, float* guess = nullptr) {
   auto geo = [&](double xx, double yy) { return (xx <= 0.0 || yy <= 0.0) ? 0.0 : exp(al * log(xx) + (1.0 - al) * log(yy)); };
   if (rx >= 0.0 && ry >= 0.0 && geo(rx, ry) >= fabs(rz)) { out[0] = rx; out[1] = ry; out[2] = rz; return; }
   {
@@ -491,6 +567,7 @@ static __device__ __noinline__ void pow_proj(double rx, double ry, double rz, do
   if (rz == 0.0) { out[0] = fmax(rx, 0.0); out[1] = fmax(ry, 0.0); out[2] = 0.0; return; }
   const double R = fabs(rz), kx = al * mz / mx, ky = (1.0 - al) * mz / my;
   double lo = 0.0, hi = R, rho = 0.5 * R;
+  if (guess && *guess > 0.0f && *guess < 1.0f) rho = (double)*guess * R;   // warm start: previous rho/R
   for (int it = 0; it < 300; ++it) {
     const double w = rho * (R - rho), dw = R - 2.0 * rho;
     const double cx = kx * w, cy = ky * w;
@@ -509,6 +586,7 @@ static __device__ __noinline__ void pow_proj(double rx, double ry, double rz, do
     rho = nx;
     if (step <= 4e-16 * fmax(rho, 1e-300) || (hi - lo) <= 4e-16 * fmax(1.0, R)) break;
   }
+  if (guess) *guess = (float)(rho / R);
   const double w = rho * (R - rho);
   out[0] = pow_qroot(rx, kx * w);
   out[1] = pow_qroot(ry, ky * w);

@@ -45,6 +45,7 @@ struct Prob {
   const T* qd;                                        // explicit diagonal part of scaled Q (n)
   const T* jd;                                        // full diagonal of scaled Q (n)
   int k; const T* R; const double* D;                 // scaled low-rank factor (k x n), D (k x k)
+  double d_scale;                                     // D = d_scale * I when > 0 (else general D)
   const int* p_rp; const int* p_ci; const T* p_v;     // scaled sparse P (n rows) or null
   const T* c; const T* b;                             // scaled c, b
   const double* col; const double* row;               // x = beta_b x~/col, y = beta_c y~/row
@@ -56,7 +57,7 @@ struct Prob {
   int64_t n_pow, pow_base; const double* pow_alpha;
   int qmode;
   int euclid_cones;                                   // diagonal mode with zero q on cone coordinates
-  int tpr_a, tpr_t;                                   // threads per row of A and of A'
+  int tpr_a, tpr_t, tpr_p;                            // threads per row of A, A' and P
 };
 
 template <typename T>
@@ -69,6 +70,7 @@ struct Work {
   T* g[2];              // gradients (sparse-P mode)
   T* avx; T* avy;       // running averages (averaged variant)
   T* mbuf;              // metric of cone blocks too large for shared staging
+  float* root;          // last scalar root per cone block (warm starts): SOC, RSOC, exp, pow
   double* sd;           // FP64 dual slack of cone coordinates (KKT)
   double* part;         // block partials [kMaxSlots][nb]
 };
@@ -88,8 +90,9 @@ struct State {
   double t_h[kMaxRank];            // R~ h_x of the current Halpern state
   double kkt[8];                   // eps_p, eps_d, eps_g, rel_kkt, pobj, dobj, ||r_p||, ||r_d||
   double lastE;
-  double prof[8];                  // ns per phase: A'y, prox work, prox barriers, dual step, its barrier,
-                                   // KKT, restart/Halpern at checks, whole loop
+  double prof[12];                 // ns per phase: A'y, prox work, prox barriers, dual step, its barrier,
+                                   // KKT, restart/Halpern at checks, whole loop; inner-step split:
+                                   // elementwise, cone gradient, cone projection, cone bookkeeping
   long long k, ktot, restarts, inner_total;
   int hb, wb;                      // current Halpern / candidate buffer
   int status;                      // 0 running, 1 converged, 2 iteration limit
@@ -102,6 +105,7 @@ struct Ctl {
   double red[kMaxSlots];           // gathered sums of the last phase
   double w[kMaxRank];              // D~ t for the gradient of the current inner step
   float wf[kMaxRank];              // the same in FP32 (iterate precision of the mixed mode)
+  double rblk[kMaxRank];           // this block's R x partials, ready to publish
   double tcur[kMaxRank];           // R~ u^j of the current inner iterate
   double alpha, sJs;
   double pid_dx, pid_dy;           // ||w_x - a_x||, ||w_y - a_y|| of the last check
@@ -225,23 +229,15 @@ struct Solver {
       C.t_last = t;
     }
   }
-
-  // zero the per-warp R accumulators
-  __device__ void wacc_zero() {
-    for (int i = threadIdx.x; i < nwarps() * P.k; i += blockDim.x) wacc[i] = 0.0;
-    __syncthreads();
-  }
-  // add the warp's sum of R[l, i] * val for every l (warp-uniform call; lanes with
-  // valid == false contribute zero).  Products and the warp tree in T, the running
-  // per-warp total in FP64.
-  __device__ __forceinline__ void wacc_add(int64_t i, T val, bool valid) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int l = 0; l < P.k; ++l) {
-      T p = valid ? P.R[(int64_t)l * P.n + i] * val : T(0);
-      p = warp_sum(p);
-      if (lane == 0) wacc[warp * P.k + l] += (double)p;
+  // sub-phase clock (does not move the main tick clock)
+  __device__ __forceinline__ void subtick(int slot, unsigned long long& t0) {
+    if (O.profile && team.bid() == 0 && threadIdx.x == 0) {
+      const unsigned long long t = now_ns();
+      C.s.prof[slot] += (double)(t - t0);
+      t0 = t;
     }
   }
+
   // (R' w)_i with w in shared memory (k entries, iterate precision)
   __device__ __forceinline__ T rtw(int64_t i, const T* w) const {
     T s = T(0);
@@ -255,21 +251,53 @@ struct Solver {
   }
 
   // publish NS block totals in slots [slot0, slot0+NS) plus, if with_r, the k R sums
+  // (block totals in C.rblk, filled by the caller)
   template <int NS>
   __device__ void publish(double (&v)[NS], int slot0, bool with_r) {
     block_sum<NS>(v, scratch, C.red);   // C.red used as temporary block totals
     if (threadIdx.x == 0)
       for (int s = 0; s < NS; ++s) team.publish(slot0 + s, C.red[s]);
-    if (with_r) {
-      const int nw = nwarps();
-      for (int l = threadIdx.x; l < P.k; l += blockDim.x) {
-        double t = 0.0;
-        for (int w = 0; w < nw; ++w) t += wacc[w * P.k + l];
-        team.publish(slot0 + NS + l, t);
-      }
+    if (with_r)
+      for (int l = threadIdx.x; l < P.k; l += blockDim.x) team.publish(slot0 + NS + l, C.rblk[l]);
+    __syncthreads();
+  }
+  // same with per-thread values in T (warp trees in T)
+  template <int NS>
+  __device__ void publish_t(T (&v)[NS], int slot0, bool with_r) {
+    block_sum_r<T, NS>(v, scratch, C.red);
+    if (threadIdx.x == 0)
+      for (int s = 0; s < NS; ++s) team.publish(slot0 + s, C.red[s]);
+    if (with_r)
+      for (int l = threadIdx.x; l < P.k; l += blockDim.x) team.publish(slot0 + NS + l, C.rblk[l]);
+    __syncthreads();
+  }
+  // wacc (per-warp R partials) -> C.rblk
+  __device__ void rblk_from_wacc() {
+    __syncthreads();
+    const int nw = nwarps();
+    for (int l = threadIdx.x; l < P.k; l += blockDim.x) {
+      double t = 0.0;
+      for (int w = 0; w < nw; ++w) t += wacc[w * P.k + l];
+      C.rblk[l] = t;
     }
     __syncthreads();
   }
+  // C.rblk[l] = sum over the owned coordinates of R[l, i] x_i: one warp per l, lanes
+  // stream R's row l (contiguous) and x; x must be visible to the block
+  __device__ void rx_lmajor(const T* x) {
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = nwarps();
+    for (int l = warp; l < P.k; l += nw) {
+      const T* Rl = P.R + (int64_t)l * P.n;
+      T acc = T(0);
+      for (int seg = 0; seg < 6; ++seg)
+        for (int64_t i = own.x0[seg] + lane; i < own.x1[seg]; i += 32) acc += Rl[i] * x[i];
+      acc = warp_sum(acc);
+      if (lane == 0) C.rblk[l] = (double)acc;
+    }
+    __syncthreads();
+  }
+
   __device__ bool sync_gather(int nslots, int prof_work = -1, int prof_wait = -1) {
     if (prof_work >= 0) tick(prof_work);
     if (!team.sync()) return false;
@@ -284,12 +312,13 @@ struct Solver {
   //   kDiagQ: m_i = 1 + tau q_i (eq. diagonal-q-metric).
   // Ends with __syncthreads.
   enum MetricKind : int { kEuclid = 0, kJacobi = 1, kDiagQ = 2 };
-  __device__ __forceinline__ double metric(int kind, int64_t i, double tau) const {
-    return kind == kJacobi ? (double)P.jd[i] + 1.0 / tau : (kind == kDiagQ ? 1.0 + tau * (double)P.qd[i] : 1.0);
+  __device__ __forceinline__ T metric(int kind, int64_t i, T tau, T itau) const {
+    return kind == kJacobi ? P.jd[i] + itau : (kind == kDiagQ ? T(1) + tau * P.qd[i] : T(1));
   }
-  __device__ __noinline__ void project_owned_cones(T* x, int kind, double tau) {
+  __device__ __noinline__ void project_owned_cones(T* x, int kind, double tau_d) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = nwarps();
     const bool euclid = kind == kEuclid;
+    const T tau = T(tau_d), itau = T(1.0 / tau_d);
     T* zs = cbuf + warp * 2 * kConeStage;
     T* ms = zs + kConeStage;
     for (int pass = 0; pass < 2; ++pass) {
@@ -303,15 +332,16 @@ struct Solver {
         T* mm = staged ? ms : W.mbuf + s;
         for (int i = lane; i < d; i += 32) {
           if (staged) zs[i] = x[s + i];
-          if (!euclid) mm[i] = T(metric(kind, s + i, tau));
+          if (!euclid) mm[i] = metric(kind, s + i, tau, itau);
         }
         __syncwarp();
+        float* gs = W.root + (pass == 0 ? blk : P.n_soc + blk);
         if (pass == 0) {
           if (euclid) warp_soc_euclid<T>(z, d, lane);
-          else warp_soc_metric<T>(z, mm, d, lane);
+          else warp_soc_metric<T>(z, mm, d, lane, gs);
         } else {
           if (euclid) warp_rsoc_euclid<T>(z, d, lane);
-          else warp_rsoc_metric<T>(z, mm, d, lane);
+          else warp_rsoc_metric<T>(z, mm, d, lane, gs);
         }
         if (staged) {
           for (int i = lane; i < d; i += 32) x[s + i] = zs[i];
@@ -322,16 +352,18 @@ struct Solver {
     for (int64_t e = own.e0 + threadIdx.x; e < own.e1; e += blockDim.x) {
       const int64_t s = P.exp_base + 3 * e;
       double o[3];
-      if (euclid) exp_proj_euclid((double)x[s], (double)x[s + 1], (double)x[s + 2], o);
-      else exp_proj_metric((double)x[s], (double)x[s + 1], (double)x[s + 2], metric(kind, s, tau),
-                           metric(kind, s + 1, tau), metric(kind, s + 2, tau), o);
+      float* gs = W.root + P.n_soc + P.n_rsoc + e;
+      if (euclid) exp_proj_euclid((double)x[s], (double)x[s + 1], (double)x[s + 2], o, gs);
+      else exp_proj_metric((double)x[s], (double)x[s + 1], (double)x[s + 2], (double)metric(kind, s, tau, itau),
+                           (double)metric(kind, s + 1, tau, itau), (double)metric(kind, s + 2, tau, itau), o);
       x[s] = T(o[0]); x[s + 1] = T(o[1]); x[s + 2] = T(o[2]);
     }
     for (int64_t e = own.p0 + threadIdx.x; e < own.p1; e += blockDim.x) {
       const int64_t s = P.pow_base + 3 * e;
       double o[3];
-      pow_proj((double)x[s], (double)x[s + 1], (double)x[s + 2], P.pow_alpha[e], metric(kind, s, tau),
-               metric(kind, s + 1, tau), metric(kind, s + 2, tau), o);
+      pow_proj((double)x[s], (double)x[s + 1], (double)x[s + 2], P.pow_alpha[e], (double)metric(kind, s, tau, itau),
+               (double)metric(kind, s + 1, tau, itau), (double)metric(kind, s + 2, tau, itau), o,
+               W.root + P.n_soc + P.n_rsoc + P.n_exp + e);
       x[s] = T(o[0]); x[s + 1] = T(o[1]); x[s + 2] = T(o[2]);
     }
     __syncthreads();
@@ -356,51 +388,136 @@ struct Solver {
   // with Q u = qd u + R' D t (t = R u_cur, D t in C.w); in sparse-P mode the
   // whole gradient is taken from gs (computed by grad_pass).
   // Accumulates s = u_next - u_cur: v3 = {||s||^2, <s, J s>, sum (qd + 1/tau) s^2,
-  // ||u_next||^2} and, with R, the warp partials of R u_next.  Per-element work and
+  // ||u_next||^2} and the block's R u_next in C.rblk.  Per-element work and
   // per-thread partial sums are in the iterate precision T.
   __device__ __forceinline__ const T* wvec() const {
     if constexpr (sizeof(T) == 4) return reinterpret_cast<const T*>(C.wf);
     else return reinterpret_cast<const T*>(C.w);
   }
-  __device__ void inner_step(const T* ucur, T* unext, const T* gs, double alpha_d, double tau, double (&v3)[4]) {
+  __device__ void inner_step(const T* ucur, T* unext, const T* gs, double alpha_d, double tau, T (&v3)[4]) {
+    if (P.k == 0) inner_step_reg<0>(ucur, unext, gs, alpha_d, tau, v3);
+    else if (P.k <= 32) inner_step_reg<32>(ucur, unext, gs, alpha_d, tau, v3);
+    else inner_step_wide(ucur, unext, gs, alpha_d, tau, v3);
+  }
+
+  // k <= KM: column i of R is loaded once into registers and serves both the gradient
+  // (R' w)_i and the per-thread partials of R u_next (one warp tree per l per pass).
+  template <int KM>
+  __device__ __noinline__ void inner_step_reg(const T* ucur, T* unext, const T* gs, double alpha_d, double tau,
+                                              T (&v3)[4]) {
+    const int k = P.k;
+    const int64_t n = P.n;
     const T itau = T(1.0 / tau);
     const T alpha = T(alpha_d);
-    const bool lowr = P.k > 0;
+    const bool jac = O.jacobi != 0;
+    const T* wr = wvec();            // D t in shared memory (broadcast reads)
+    const T* __restrict__ Rm = P.R;
+    const T* __restrict__ uc = ucur;
+    const T* __restrict__ vv = W.v;
+    const T* __restrict__ qd = P.qd;
+    const T* __restrict__ cc = P.c;
+    const T* __restrict__ jd = P.jd;
+    T* __restrict__ un_out = unext;
+    T racc[KM > 0 ? KM : 1];
+#pragma unroll
+    for (int l = 0; l < (KM > 0 ? KM : 1); ++l) racc[l] = T(0);
+    auto jm = [&](int64_t i) -> T { return jac ? jd[i] + itau : T(1); };
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+    unsigned long long tsub = (O.profile && team.bid() == 0 && threadIdx.x == 0) ? now_ns() : 0ull;
+    // elementwise segments (free, nonneg)
+    for (int seg = 0; seg < 2; ++seg)
+      for (int64_t i = own.x0[seg] + threadIdx.x; i < own.x1[seg]; i += blockDim.x) {
+        T rr[KM > 0 ? KM : 1];
+        T rw = T(0);
+#pragma unroll
+        for (int l = 0; l < KM; ++l) {
+          rr[l] = (l < k) ? __ldg(Rm + (int64_t)l * n + i) : T(0);
+          rw += (l < k) ? rr[l] * wr[l] : T(0);
+        }
+        const T u = uc[i];
+        const T qi = qd[i];
+        const T g = gs ? gs[i] : qi * u + cc[i] + (u - vv[i]) * itau + rw;
+        const T J = jm(i);
+        const T un = proj_elem(i, u - alpha * g / J);
+        un_out[i] = un;
+        const T sd = un - u;
+        a0 += sd * sd;
+        a1 += J * sd * sd;
+        a2 += (qi + itau) * sd * sd;
+        a3 += un * un;
+#pragma unroll
+        for (int l = 0; l < KM; ++l) racc[l] += rr[l] * un;
+      }
+    __syncthreads();
+    subtick(8, tsub);
+    // cone segments: gradient step into unext, then block-local metric projection
+    for (int seg = 2; seg < 6; ++seg)
+      for (int64_t i = own.x0[seg] + threadIdx.x; i < own.x1[seg]; i += blockDim.x) {
+        T rw = T(0);
+#pragma unroll
+        for (int l = 0; l < KM; ++l) rw += (l < k) ? P.R[(int64_t)l * n + i] * wr[l] : T(0);
+        const T u = ucur[i];
+        const T g = gs ? gs[i] : P.qd[i] * u + P.c[i] + (u - W.v[i]) * itau + rw;
+        unext[i] = u - alpha * g / jm(i);
+      }
+    __syncthreads();
+    subtick(9, tsub);
+    project_owned_cones(unext, jac ? kJacobi : kEuclid, tau);
+    subtick(10, tsub);
+    for (int seg = 2; seg < 6; ++seg)
+      for (int64_t i = own.x0[seg] + threadIdx.x; i < own.x1[seg]; i += blockDim.x) {
+        const T un = unext[i];
+        const T sd = un - ucur[i];
+        a0 += sd * sd;
+        a1 += jm(i) * sd * sd;
+        a2 += (P.qd[i] + itau) * sd * sd;
+        a3 += un * un;
+#pragma unroll
+        for (int l = 0; l < KM; ++l) racc[l] += ((l < k) ? P.R[(int64_t)l * n + i] : T(0)) * un;
+      }
+    if (KM > 0) {
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+      for (int l = 0; l < KM; ++l) {
+        if (l < k) {
+          const T t = warp_sum(racc[l]);
+          if (lane == 0) wacc[warp * k + l] = (double)t;
+        }
+      }
+      rblk_from_wacc();
+    }
+    v3[0] = a0;
+    v3[1] = a1;
+    v3[2] = a2;
+    v3[3] = a3;
+    __syncthreads();
+    subtick(11, tsub);
+  }
+
+  // k > 32: gradient from R row by row, R u_next by the l-major block pass
+  __device__ void inner_step_wide(const T* ucur, T* unext, const T* gs, double alpha_d, double tau, T (&v3)[4]) {
+    const T itau = T(1.0 / tau);
+    const T alpha = T(alpha_d);
     const bool jac = O.jacobi != 0;
     const T* w = wvec();
     auto grad = [&](int64_t i, T u) -> T {
       if (gs) return gs[i];
-      T g = P.qd[i] * u + P.c[i] + (u - W.v[i]) * itau;
-      if (lowr) g += rtw(i, w);
-      return g;
+      return P.qd[i] * u + P.c[i] + (u - W.v[i]) * itau + rtw(i, w);
     };
     auto jm = [&](int64_t i) -> T { return jac ? P.jd[i] + itau : T(1); };
     T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-    if (lowr) wacc_zero();
-    // elementwise segments (free, nonneg): whole warps iterate together
-    const int lane = threadIdx.x & 31;
-    for (int seg = 0; seg < 2; ++seg) {
-      const int64_t a = own.x0[seg], b = own.x1[seg];
-      for (int64_t base = a + (threadIdx.x - lane); base < b; base += blockDim.x) {
-        const int64_t i = base + lane;
-        const bool ok = i < b;
-        T un = T(0);
-        if (ok) {
-          const T u = ucur[i];
-          const T J = jm(i);
-          const T z = u - alpha * grad(i, u) / J;
-          un = proj_elem(i, z);
-          unext[i] = un;
-          const T sd = un - u;
-          a0 += sd * sd;
-          a1 += J * sd * sd;
-          a2 += (P.qd[i] + itau) * sd * sd;
-          a3 += un * un;
-        }
-        if (lowr) wacc_add(i, un, ok);
+    for (int seg = 0; seg < 2; ++seg)
+      for (int64_t i = own.x0[seg] + threadIdx.x; i < own.x1[seg]; i += blockDim.x) {
+        const T u = ucur[i];
+        const T J = jm(i);
+        const T un = proj_elem(i, u - alpha * grad(i, u) / J);
+        unext[i] = un;
+        const T sd = un - u;
+        a0 += sd * sd;
+        a1 += J * sd * sd;
+        a2 += (P.qd[i] + itau) * sd * sd;
+        a3 += un * un;
       }
-    }
-    // cone segments: gradient step into unext, then block-local metric projection
     for (int seg = 2; seg < 6; ++seg)
       for (int64_t i = own.x0[seg] + threadIdx.x; i < own.x1[seg]; i += blockDim.x) {
         const T u = ucur[i];
@@ -408,28 +525,20 @@ struct Solver {
       }
     __syncthreads();
     project_owned_cones(unext, jac ? kJacobi : kEuclid, tau);
-    for (int seg = 2; seg < 6; ++seg) {
-      const int64_t a = own.x0[seg], b = own.x1[seg];
-      for (int64_t base = a + (threadIdx.x - lane); base < b; base += blockDim.x) {
-        const int64_t i = base + lane;
-        const bool ok = i < b;
-        T un = T(0);
-        if (ok) {
-          un = unext[i];
-          const T sd = un - ucur[i];
-          a0 += sd * sd;
-          a1 += jm(i) * sd * sd;
-          a2 += (P.qd[i] + itau) * sd * sd;
-          a3 += un * un;
-        }
-        if (lowr) wacc_add(i, un, ok);
+    for (int seg = 2; seg < 6; ++seg)
+      for (int64_t i = own.x0[seg] + threadIdx.x; i < own.x1[seg]; i += blockDim.x) {
+        const T un = unext[i];
+        const T sd = un - ucur[i];
+        a0 += sd * sd;
+        a1 += jm(i) * sd * sd;
+        a2 += (P.qd[i] + itau) * sd * sd;
+        a3 += un * un;
       }
-    }
-    v3[0] = (double)a0;
-    v3[1] = (double)a1;
-    v3[2] = (double)a2;
-    v3[3] = (double)a3;
-    __syncthreads();
+    rx_lmajor(unext);
+    v3[0] = a0;
+    v3[1] = a1;
+    v3[2] = a2;
+    v3[3] = a3;
   }
 
   // ---- sparse-P mode: gradient at u (P u by the owned rows of P), dots -------
@@ -440,7 +549,7 @@ struct Solver {
     const T* w = wvec();
     T acc = T(0);
     for (int seg = 0; seg < 6; ++seg) {
-      rows_loop_tpr<T>(P.tpr_t, P.p_rp, P.p_ci, P.p_v, own.x0[seg], own.x1[seg], [&](int j) { return u[j]; },
+      rows_loop_tpr<T>(P.tpr_p, P.p_rp, P.p_ci, P.p_v, own.x0[seg], own.x1[seg], [&](int j) { return u[j]; },
                        [&](int64_t i, int gl, T pu) {
                          if (gl == 0) {
                            T g = pu + P.qd[i] * u[i] + P.c[i] + (u[i] - W.v[i]) * itau;

@@ -49,7 +49,11 @@ __device__ __forceinline__ void apply_D(const Prob<T>& P, const double* t, doubl
   __syncthreads();
   for (int l = threadIdx.x; l < P.k; l += blockDim.x) {
     double s = 0.0;
-    for (int l2 = 0; l2 < P.k; ++l2) s += P.D[l * P.k + l2] * t[l2];
+    if (P.d_scale > 0.0) {
+      s = P.d_scale * t[l];
+    } else {
+      for (int l2 = 0; l2 < P.k; ++l2) s += P.D[l * P.k + l2] * t[l2];
+    }
     w[l] = s;
     if (wf) wf[l] = (float)s;
   }
@@ -98,7 +102,7 @@ __device__ bool Solver<T, Team>::prox_bb(const T* hx, int& ub) {
   // t = R h_x from the state; w = D t
   for (int l = threadIdx.x; l < k; l += blockDim.x) C.tcur[l] = C.s.t_h[l];
   apply_D(P, C.tcur, C.w, C.wf);
-  double v3[4];
+  T v3[4];
   int gb = 0;
   // ||u^{j+1} - u^j|| cannot fall below the rounding level of u: the stop test compares it
   // with max(eps_in, 4 eps_T ||u||) (precision floor; eps_T = 2^-24 or 2^-53)
@@ -110,7 +114,7 @@ __device__ bool Solver<T, Team>::prox_bb(const T* hx, int& ub) {
   } else {
     inner_step(hx, W.u[0], nullptr, 1.0, tau, v3);
   }
-  publish<4>(v3, 0, k > 0);
+  publish_t<4>(v3, 0, k > 0);
   if (!sync_gather(4 + k, 1, 2)) return false;
   int cur = 0;
   long long j = 1;
@@ -126,15 +130,22 @@ __device__ bool Solver<T, Team>::prox_bb(const T* hx, int& ub) {
     if (threadIdx.x == 0) C.sJs = sJs;
     // t_{j} = R u^{j} from the reduction; dt = t_j - t_{j-1}
     if (!sparse) {
-      if (threadIdx.x == 0) {
-        double q = C.red[2];
-        // (R s)' D (R s) with R s = t_new - t_old
-        for (int l = 0; l < k; ++l) {
-          double dl = 0.0;
-          for (int l2 = 0; l2 < k; ++l2) dl += P.D[l * k + l2] * (C.red[4 + l2] - C.tcur[l2]);
-          q += (C.red[4 + l] - C.tcur[l]) * dl;
+      // <s, dg> = sum (qd + 1/tau) s^2 + (R s)' D (R s), R s = t_new - t_old (warp 0)
+      if (threadIdx.x < 32) {
+        double part = 0.0;
+        for (int l = threadIdx.x; l < k; l += 32) {
+          const double dl = C.red[4 + l] - C.tcur[l];
+          double ddl;
+          if (P.d_scale > 0.0) {
+            ddl = P.d_scale * dl;
+          } else {
+            ddl = 0.0;
+            for (int l2 = 0; l2 < k; ++l2) ddl += P.D[l * k + l2] * (C.red[4 + l2] - C.tcur[l2]);
+          }
+          part += dl * ddl;
         }
-        C.alpha = q;   // <s, dg>
+        part = warp_sum(part);
+        if (threadIdx.x == 0) C.alpha = C.red[2] + part;
       }
       __syncthreads();
       sdg = C.alpha;
@@ -163,7 +174,7 @@ __device__ bool Solver<T, Team>::prox_bb(const T* hx, int& ub) {
     __syncthreads();
     const double alpha = C.alpha;
     inner_step(W.u[cur], W.u[cur ^ 1], sparse ? W.g[gb] : nullptr, alpha, tau, v3);
-    publish<4>(v3, 0, k > 0);
+    publish_t<4>(v3, 0, k > 0);
     if (!sync_gather(4 + k, 1, 2)) return false;
     uprev = W.u[cur];
     cur ^= 1;
@@ -200,7 +211,6 @@ __device__ bool Solver<T, Team>::kkt(const T* x, const T* y, bool have_rx) {
                           }
                         });
   const bool need_r = k > 0 && !have_rx;
-  if (need_r) wacc_zero();
   const int lane = threadIdx.x & 31;
   for (int seg = 0; seg < 6; ++seg) {
     const int64_t a = own.x0[seg], b = own.x1[seg];
@@ -213,14 +223,14 @@ __device__ bool Solver<T, Team>::kkt(const T* x, const T* y, bool have_rx) {
         v4[2] += (double)P.c[i] * (double)xi;
         v4[3] += (double)P.qd[i] * (double)xi * (double)xi;
       }
-      if (need_r) wacc_add(i, xi, ok);
     }
   }
+  if (need_r) rx_lmajor(x);
   double v5[5] = {v4[0], v4[1], v4[2], v4[3], 0.0};
   if (sparse) {
     // (P~ x)_i on the owned coordinates, kept in W.sd until K2 reads it
     for (int seg = 0; seg < 6; ++seg)
-      rows_loop_tpr<double>(P.tpr_t, P.p_rp, P.p_ci, P.p_v, own.x0[seg], own.x1[seg], [&](int j) { return x[j]; },
+      rows_loop_tpr<double>(P.tpr_p, P.p_rp, P.p_ci, P.p_v, own.x0[seg], own.x1[seg], [&](int j) { return x[j]; },
                             [&](int64_t i, int gl, double px) {
                               if (gl == 0) {
                                 W.sd[i] = px;
@@ -365,7 +375,6 @@ __device__ void Solver<T, Team>::run(long long budget) {
             v6[5] += e * e;
           }
         });
-    if (halpern_now && k > 0) wacc_zero();
     T* hxn = W.hx[hb ^ 1];
     T* wxs = W.wx[wb ^ 1];
     const T* wxp = W.wx[wb];
@@ -391,12 +400,17 @@ __device__ void Solver<T, Team>::run(long long budget) {
             W.avx[i] = (tkk * W.avx[i] + w) / (tkk + T(1));
           }
         }
-        if (halpern_now && k > 0) wacc_add(i, hn, okc);
       }
     }
+    if (halpern_now && k > 0) rx_lmajor(hxn);
     v6[0] = (double)mov_acc;
     __syncthreads();
-    publish<6>(v6, 0, halpern_now && k > 0);
+    if (needE || check) {
+      publish<6>(v6, 0, halpern_now && k > 0);
+    } else {
+      T v6t[6] = {mov_acc, T(0), T(0), T(0), T(0), T(0)};
+      publish_t<6>(v6t, 0, halpern_now && k > 0);
+    }
     if (!sync_gather(6 + ((halpern_now && k > 0) ? k : 0), 3, 4)) return;
     // ---- control after the dual step
     if (threadIdx.x == 0) {
@@ -444,17 +458,9 @@ __device__ void Solver<T, Team>::run(long long budget) {
       if (C.s.k >= O.avg_epoch) {
         // restart from the epoch average (Alg. "pdhcq1", averaged branch)
         const int hb2 = C.s.hb;   // after the swap: hx[hb2] holds w; overwrite with the average
-        if (k > 0) wacc_zero();
-        for (int seg = 0; seg < 6; ++seg) {
-          const int64_t a = own.x0[seg], b = own.x1[seg];
-          for (int64_t base = a + (threadIdx.x - lane); base < b; base += blockDim.x) {
-            const int64_t i = base + lane;
-            const bool okc = i < b;
-            T av = T(0);
-            if (okc) { av = W.avx[i]; W.hx[hb2][i] = av; }
-            if (k > 0) wacc_add(i, av, okc);
-          }
-        }
+        for (int seg = 0; seg < 6; ++seg)
+          for (int64_t i = own.x0[seg] + threadIdx.x; i < own.x1[seg]; i += blockDim.x) W.hx[hb2][i] = W.avx[i];
+        if (k > 0) rx_lmajor(W.hx[hb2]);
         for (int64_t r = own.row0 + threadIdx.x; r < own.row1; r += blockDim.x) W.hy[hb2][r] = W.avy[r];
         __syncthreads();
         double z1[1] = {0.0};
@@ -522,20 +528,10 @@ __device__ void Solver<T, Team>::run(long long budget) {
       tick(6);
     } else {
       // deferred reflected-Halpern step of a check iteration
-      if (k > 0) wacc_zero();
-      for (int seg = 0; seg < 6; ++seg) {
-        const int64_t a = own.x0[seg], b = own.x1[seg];
-        for (int64_t base = a + (threadIdx.x - lane); base < b; base += blockDim.x) {
-          const int64_t i = base + lane;
-          const bool okc = i < b;
-          T hn = T(0);
-          if (okc) {
-            hn = T(c1) * (T(r2) * wx[i] + T(r1) * hx[i]) + T(c2) * W.ax[i];
-            W.hx[hbn][i] = hn;
-          }
-          if (k > 0) wacc_add(i, hn, okc);
-        }
-      }
+      for (int seg = 0; seg < 6; ++seg)
+        for (int64_t i = own.x0[seg] + threadIdx.x; i < own.x1[seg]; i += blockDim.x)
+          W.hx[hbn][i] = T(c1) * (T(r2) * wx[i] + T(r1) * hx[i]) + T(c2) * W.ax[i];
+      if (k > 0) rx_lmajor(W.hx[hbn]);
       for (int64_t r = own.row0 + threadIdx.x; r < own.row1; r += blockDim.x)
         W.hy[hbn][r] = T(c1) * (T(r2) * W.wy[r] + T(r1) * hy[r]) + T(c2) * W.ay[r];
       __syncthreads();
