@@ -6,7 +6,7 @@
 //
 // SOC / RSOC blocks are projected by one warp: the block's coordinates are
 // strided over the lanes, norms and root-function sums are warp reductions,
-// and the scalar root iteration runs redundantly (identically) on every lane.
+// and the scalar root iteration runs on lane 0, which broadcasts each iterate.
 // EXP / POW blocks are projected by one thread in FP64.
 #pragma once
 
