@@ -209,6 +209,32 @@ int cqp_spmv(int32_t precision, int64_t nrows, int64_t ncols, const int32_t* row
 int cqp_project(int32_t precision, int64_t n, const cqp_cones* K_device, const void* r, const void* m, void* out,
                 void* stream);
 
+/* ---- allocation-free KKT check (the paper has no counterpart: this is a
+ * library convenience) ----
+ * Same report as cqp_kkt, but from the caller's own unscaled problem data and
+ * without a handle, and without allocating any device memory: it is meant for
+ * callers that must not call cudaMalloc, such as code running inside a
+ * framework that already owns the device memory pool, or code that has to
+ * keep a fixed device footprint.  Its working memory is a static device array
+ * of the library, sized for n <= CQP_KKT_STATIC_MAX_N (about 4.1 MiB, held on
+ * every GPU that loads the library until the process exits).
+ *   A, Q, K: as in cqp_setup, but every array they point to is a device
+ *   array (A->rowptr int64, A->colind int32, A->val double).  c (n), b (m),
+ *   x (n), y (m): device arrays.  rep: host struct, filled on success.
+ *   stream: cudaStream_t or NULL; the call synchronises it before returning.
+ * Errors: CQP_ERR_INVALID for NULL arguments, n < 1, n > CQP_KKT_STATIC_MAX_N,
+ * rank > 64, or malformed A, P or cone blocks (the indices and block layout
+ * are checked on the device; nothing is read out of bounds); CQP_ERR_CUDA;
+ * CQP_ERR_NUMERICAL for a non-finite report.
+ * The first call on each device looks up the array's device address, so make
+ * it before any stream capture.  All calls on one device share the array:
+ * calls that overlap on the GPU (two streams, two threads) race, so serialise
+ * them.  Ax - b, A'y, Qx and the cone projections are recomputed every call;
+ * A'y is accumulated with atomics, so the last bits may differ between calls. */
+#define CQP_KKT_STATIC_MAX_N 524288
+int cqp_kkt_static(const cqp_csr* A_device, const cqp_qop* Q_device, const double* c, const double* b,
+                   const cqp_cones* K_device, const double* x, const double* y, cqp_kkt_report* rep, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

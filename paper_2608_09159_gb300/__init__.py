@@ -105,7 +105,9 @@ def lib():
         L.cqp_project.argtypes = [i32, i64, vp, vp, vp, vp, vp]
         L.cqp_kernel_launches.argtypes = []
         L.cqp_kernel_launches.restype = C.c_longlong
-        for f in ("cqp_default_options", "cqp_setup", "cqp_solve", "cqp_kkt", "cqp_spmv", "cqp_project"):
+        L.cqp_kkt_static.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        for f in ("cqp_default_options", "cqp_setup", "cqp_solve", "cqp_kkt", "cqp_spmv", "cqp_project",
+                  "cqp_kkt_static"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -163,6 +165,12 @@ def cqp_spmv(precision, nrows, ncols, rowptr, colind, val, x, y, threads_per_row
 
 def cqp_project(precision, n, K_device: Cones, r, m, out, stream=None) -> int:
     return _check(lib().cqp_project(precision, n, C.byref(K_device), r, m, out, stream))
+
+
+def cqp_kkt_static(A_device: CSR, Q_device, c, b, K_device: Cones, x, y, rep: KKTReport, stream=None) -> int:
+    """Allocation-free KKT report from device arrays (for callers that must not cudaMalloc)."""
+    return _check(lib().cqp_kkt_static(C.byref(A_device), None if Q_device is None else C.byref(Q_device), c, b,
+                                       C.byref(K_device), x, y, C.byref(rep), stream))
 
 
 # ---------------------------------------------------------------------------

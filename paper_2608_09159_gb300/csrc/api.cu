@@ -746,6 +746,13 @@ int guarded(F f) {
 
 }  // namespace
 
+namespace cqp {
+// error text and launch count for entry points defined in other translation
+// units of this library (they share this thread's cqp_last_error and counter)
+void record_error(const std::string& msg) { g_last_error = msg; }
+void record_launches(long long k) { g_launches += k; }
+}  // namespace cqp
+
 struct cqp_handle {
   HandleBase* impl;
 };
