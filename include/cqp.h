@@ -125,6 +125,7 @@ typedef struct {
   int32_t tpr_a, tpr_at;    /* threads per CSR row for A and A', 0 = autotuned */
   int32_t launch_iters;     /* outer iterations per kernel launch, 0 = auto */
   int32_t profile;          /* 1: record per-phase device time in cqp_result.phase_ms */
+  int32_t warm_roots;       /* 1: start each cone block's root-finding from its previous root (default 1) */
   void* stream;             /* cudaStream_t, NULL = default stream */
 } cqp_options;
 

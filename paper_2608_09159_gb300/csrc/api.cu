@@ -440,9 +440,13 @@ struct Handle : HandleBase {
     if (m > 0) { count_launch(); cqp::k_convert<T><<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, bv, bT); }
     count_launch(); cqp::k_convert<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, qv, qT);
     count_launch(); cqp::k_convert<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, jdv, jT);
+    // R is stored with its row count padded to a multiple of 8 (zero rows), so the
+    // inner step's register loop over a fixed width needs no per-row predicate
     T* RT = nullptr;
+    const int64_t kpad = k > 0 ? (k + 7) / 8 * 8 : 0;
     if (k > 0) {
-      RT = mem.alloc<T>(k * n);
+      RT = mem.alloc<T>(kpad * n);
+      if (kpad > k) CK(cudaMemsetAsync(RT + k * n, 0, (size_t)(kpad - k) * n * sizeof(T), st));
       count_launch(); cqp::k_convert<T><<<cqp::grid_for(k * n), cqp::kSetupThreads, 0, st>>>(k * n, Rv, RT);
     }
     T* pT = nullptr;
@@ -493,7 +497,7 @@ struct Handle : HandleBase {
     P.n = n; P.m = m;
     P.a_rp = a_rp; P.a_ci = a_ci; P.a_v = a_v;
     P.t_rp = t_rp; P.t_ci = t_ci; P.t_v = t_v;
-    P.qd = qT; P.jd = jT; P.k = (int)k; P.R = RT; P.D = Dv;
+    P.qd = qT; P.jd = jT; P.k = (int)k; P.kpad = (int)kpad; P.R = RT; P.D = Dv;
     // D = d I (the common case) lets the kernel skip the k x k products
     P.d_scale = 0.0;
     if (k > 0) {
@@ -591,6 +595,7 @@ struct Handle : HandleBase {
     O.max_iter = o.max_iter; O.check_every = std::max(1, o.check_every); O.max_inner = std::max(1, o.max_inner);
     O.jacobi = o.jacobi; O.pid = o.pid; O.update = o.update; O.avg_epoch = std::max(1, o.avg_epoch);
     O.profile = o.profile;
+    O.warm_roots = o.warm_roots;
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
     setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -790,6 +795,7 @@ int cqp_default_options(cqp_options* o) {
   o->power_iters = 200;
   o->power_tol = 1e-6;
   o->step_factor = 0.998;
+  o->warm_roots = 1;
   return CQP_OK;
 }
 

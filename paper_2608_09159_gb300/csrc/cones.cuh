@@ -235,10 +235,11 @@ __device__ __noinline__ void warp_rsoc_metric(T* x, const T* m, int d, int lane,
   // f and f' from the sums (lane 0)
   auto fval = [&](double xx, double sv, double sv3, double* df) {
     const double det = ms * mt - 4.0 * xx * xx;
+    const double id = 1.0 / det;   // the only FP64 division of the iteration
     const double ns = ms * zs + 2.0 * xx * zt, nt = mt * zt + 2.0 * xx * zs;
-    const double s = mt * ns / det, t = ms * nt / det;
-    const double ds = mt * (2.0 * zt * det + 8.0 * xx * ns) / (det * det);
-    const double dt = ms * (2.0 * zs * det + 8.0 * xx * nt) / (det * det);
+    const double s = mt * ns * id, t = ms * nt * id;
+    const double ds = mt * (2.0 * zt + 8.0 * xx * ns * id) * id;
+    const double dt = ms * (2.0 * zs + 8.0 * xx * nt * id) * id;
     *df = -4.0 * sv3 - 2.0 * (ds * t + s * dt);
     return sv - 2.0 * s * t;
   };
@@ -310,9 +311,9 @@ __device__ __noinline__ void warp_rsoc_metric(T* x, const T* m, int d, int lane,
     }
     xi = xx;
     if (guess && lane == 0) *guess = (float)xi;
-    const double det = ms * mt - 4.0 * xi * xi;
-    s_out = fmax(mt * (ms * zs + 2.0 * xi * zt) / det, 0.0);
-    t_out = fmax(ms * (mt * zt + 2.0 * xi * zs) / det, 0.0);
+    const double id = 1.0 / (ms * mt - 4.0 * xi * xi);
+    s_out = fmax(mt * (ms * zs + 2.0 * xi * zt) * id, 0.0);
+    t_out = fmax(ms * (mt * zt + 2.0 * xi * zs) * id, 0.0);
   }
   const T tx = T(2.0 * xi);
   for (int i = lane; i < nv; i += 32) {

@@ -45,6 +45,7 @@ struct Prob {
   const T* qd;                                        // explicit diagonal part of scaled Q (n)
   const T* jd;                                        // full diagonal of scaled Q (n)
   int k; const T* R; const double* D;                 // scaled low-rank factor (k x n), D (k x k)
+  int kpad;                                            // rows of R as stored: k rounded up to 8, rows >= k zero
   double d_scale;                                     // D = d_scale * I when > 0 (else general D)
   const int* p_rp; const int* p_ci; const T* p_v;     // scaled sparse P (n rows) or null
   const T* c; const T* b;                             // scaled c, b
@@ -81,6 +82,7 @@ struct Opts {
   long long max_iter;
   int check_every, max_inner, jacobi, pid, update, avg_epoch;
   int profile;                     // accumulate per-phase wall time (block 0) into State::prof
+  int warm_roots;                  // start cone root-finding from the block's previous root
 };
 
 // Control state of one solve (device memory, FP64 scalars).
@@ -144,12 +146,40 @@ __device__ void make_own(const Prob<T>& P, int b, int nb, Own& o) {
 // CSR row products by groups of G lanes; every lane of the group gets the sum.
 // X(j) returns the operand for column j.
 // ---------------------------------------------------------------------------
+// Entries of one row handled by lane gl of a G-lane group, kUnroll at a time:
+// the column indices and values of a batch are loaded first and the operand
+// gathers of the batch are issued together, so each lane keeps several
+// independent loads in flight (the persistent kernel runs only 16 warps per SM).
+// ci and v are read-only for the whole kernel, hence the non-coherent loads;
+// the gathered operands are written by other phases and use plain loads.
+constexpr int kUnroll = 4;
+
+template <int G, typename Acc, typename T, typename X>
+__device__ __forceinline__ Acc seg_dot(const int* __restrict__ ci, const T* __restrict__ v, int beg, int end, int gl,
+                                       X xf) {
+  Acc s = Acc(0);
+  int k = beg + gl;
+  for (; k + (kUnroll - 1) * G < end; k += kUnroll * G) {
+    int j[kUnroll];
+    T a[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      j[u] = __ldg(ci + k + u * G);
+      a[u] = __ldg(v + k + u * G);
+    }
+    Acc g[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) g[u] = (Acc)xf(j[u]);
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) s += (Acc)a[u] * g[u];
+  }
+  for (; k < end; k += G) s += (Acc)__ldg(v + k) * (Acc)xf(__ldg(ci + k));
+  return s;
+}
+
 template <int G, typename Acc, typename T, typename X>
 __device__ __forceinline__ Acc row_dot(const int* rp, const int* ci, const T* v, int64_t row, int gl, X xf) {
-  Acc s = Acc(0);
-  const int beg = rp[row], end = rp[row + 1];
-  for (int k = beg + gl; k < end; k += G) s += (Acc)v[k] * (Acc)xf(ci[k]);
-  return group_sum<G>(s);
+  return group_sum<G>(seg_dot<G, Acc>(ci, v, rp[row], rp[row + 1], gl, xf));
 }
 
 // Iterate the rows [r0, r1) of a CSR matrix with groups of G lanes; f(row, gl, sum)
@@ -168,10 +198,7 @@ __device__ __forceinline__ void rows_loop(const int* rp, const int* ci, const T*
     const int64_t r = r0 + base + (lane / G);
     const bool ok = r < r1;
     Acc s = Acc(0);
-    if (ok) {
-      const int beg = rp[r], end = rp[r + 1];
-      for (int k = beg + gl; k < end; k += G) s += (Acc)v[k] * (Acc)xf(ci[k]);
-    }
+    if (ok) s = seg_dot<G, Acc>(ci, v, rp[r], rp[r + 1], gl, xf);
     s = group_sum<G>(s);
     if (ok) f(r, gl, s);
   }
@@ -321,49 +348,57 @@ struct Solver {
     const T tau = T(tau_d), itau = T(1.0 / tau_d);
     T* zs = cbuf + warp * 2 * kConeStage;
     T* ms = zs + kConeStage;
-    for (int pass = 0; pass < 2; ++pass) {
-      const int64_t b0 = pass == 0 ? own.s0 : own.r0, b1 = pass == 0 ? own.s1 : own.r1;
+    // SOC and RSOC blocks form one list dealt round-robin to the warps, so a warp
+    // takes an RSOC block only after every warp has had a SOC block
+    const int64_t nsoc = own.s1 - own.s0, nall = nsoc + (own.r1 - own.r0);
+    for (int64_t item = warp; item < nall; item += nw) {
+      const int pass = item < nsoc ? 0 : 1;
+      const int64_t blk = pass == 0 ? own.s0 + item : own.r0 + (item - nsoc);
       const int64_t* off = pass == 0 ? P.soc_off : P.rsoc_off;
-      for (int64_t blk = b0 + warp; blk < b1; blk += nw) {
-        const int64_t s = off[blk];
-        const int d = (int)(off[blk + 1] - s);
-        const bool staged = d <= kConeStage;
-        T* z = staged ? zs : x + s;
-        T* mm = staged ? ms : W.mbuf + s;
-        for (int i = lane; i < d; i += 32) {
-          if (staged) zs[i] = x[s + i];
-          if (!euclid) mm[i] = metric(kind, s + i, tau, itau);
-        }
+      const int64_t s = off[blk];
+      const int d = (int)(off[blk + 1] - s);
+      const bool staged = d <= kConeStage;
+      T* z = staged ? zs : x + s;
+      T* mm = staged ? ms : W.mbuf + s;
+      for (int i = lane; i < d; i += 32) {
+        if (staged) zs[i] = x[s + i];
+        if (!euclid) mm[i] = metric(kind, s + i, tau, itau);
+      }
+      __syncwarp();
+      float* gs = O.warm_roots ? W.root + (pass == 0 ? blk : P.n_soc + blk) : nullptr;
+      if (pass == 0) {
+        if (euclid) warp_soc_euclid<T>(z, d, lane);
+        else warp_soc_metric<T>(z, mm, d, lane, gs);
+      } else {
+        if (euclid) warp_rsoc_euclid<T>(z, d, lane);
+        else warp_rsoc_metric<T>(z, mm, d, lane, gs);
+      }
+      if (staged) {
+        for (int i = lane; i < d; i += 32) x[s + i] = zs[i];
         __syncwarp();
-        float* gs = W.root + (pass == 0 ? blk : P.n_soc + blk);
-        if (pass == 0) {
-          if (euclid) warp_soc_euclid<T>(z, d, lane);
-          else warp_soc_metric<T>(z, mm, d, lane, gs);
-        } else {
-          if (euclid) warp_rsoc_euclid<T>(z, d, lane);
-          else warp_rsoc_metric<T>(z, mm, d, lane, gs);
-        }
-        if (staged) {
-          for (int i = lane; i < d; i += 32) x[s + i] = zs[i];
-          __syncwarp();
-        }
       }
     }
-    for (int64_t e = own.e0 + threadIdx.x; e < own.e1; e += blockDim.x) {
-      const int64_t s = P.exp_base + 3 * e;
-      double o[3];
-      float* gs = W.root + P.n_soc + P.n_rsoc + e;
-      if (euclid) exp_proj_euclid((double)x[s], (double)x[s + 1], (double)x[s + 2], o, gs);
-      else exp_proj_metric((double)x[s], (double)x[s + 1], (double)x[s + 2], (double)metric(kind, s, tau, itau),
-                           (double)metric(kind, s + 1, tau, itau), (double)metric(kind, s + 2, tau, itau), o);
-      x[s] = T(o[0]); x[s + 1] = T(o[1]); x[s + 2] = T(o[2]);
-    }
-    for (int64_t e = own.p0 + threadIdx.x; e < own.p1; e += blockDim.x) {
+    // exponential and power blocks: one list, one thread per block, so no thread
+    // runs an exp and a pow root-finding back to back while others idle
+    const int64_t nexp = own.e1 - own.e0, n3 = nexp + (own.p1 - own.p0);
+    for (int64_t item = threadIdx.x; item < n3; item += blockDim.x) {
+      if (item < nexp) {
+        const int64_t e = own.e0 + item;
+        const int64_t s = P.exp_base + 3 * e;
+        double o[3];
+        float* gs = O.warm_roots ? W.root + P.n_soc + P.n_rsoc + e : nullptr;
+        if (euclid) exp_proj_euclid((double)x[s], (double)x[s + 1], (double)x[s + 2], o, gs);
+        else exp_proj_metric((double)x[s], (double)x[s + 1], (double)x[s + 2], (double)metric(kind, s, tau, itau),
+                             (double)metric(kind, s + 1, tau, itau), (double)metric(kind, s + 2, tau, itau), o);
+        x[s] = T(o[0]); x[s + 1] = T(o[1]); x[s + 2] = T(o[2]);
+        continue;
+      }
+      const int64_t e = own.p0 + (item - nexp);
       const int64_t s = P.pow_base + 3 * e;
       double o[3];
       pow_proj((double)x[s], (double)x[s + 1], (double)x[s + 2], P.pow_alpha[e], (double)metric(kind, s, tau, itau),
                (double)metric(kind, s + 1, tau, itau), (double)metric(kind, s + 2, tau, itau), o,
-               W.root + P.n_soc + P.n_rsoc + P.n_exp + e);
+               O.warm_roots ? W.root + P.n_soc + P.n_rsoc + P.n_exp + e : nullptr);
       x[s] = T(o[0]); x[s + 1] = T(o[1]); x[s + 2] = T(o[2]);
     }
     __syncthreads();
@@ -395,8 +430,12 @@ struct Solver {
     else return reinterpret_cast<const T*>(C.w);
   }
   __device__ void inner_step(const T* ucur, T* unext, const T* gs, double alpha_d, double tau, T (&v3)[4]) {
+    // register width KM = kpad (R is zero-padded to it and D t is zero beyond k)
     if (P.k == 0) inner_step_reg<0>(ucur, unext, gs, alpha_d, tau, v3);
-    else if (P.k <= 32) inner_step_reg<32>(ucur, unext, gs, alpha_d, tau, v3);
+    else if (P.kpad == 8) inner_step_reg<8>(ucur, unext, gs, alpha_d, tau, v3);
+    else if (P.kpad == 16) inner_step_reg<16>(ucur, unext, gs, alpha_d, tau, v3);
+    else if (P.kpad == 24) inner_step_reg<24>(ucur, unext, gs, alpha_d, tau, v3);
+    else if (P.kpad == 32) inner_step_reg<32>(ucur, unext, gs, alpha_d, tau, v3);
     else inner_step_wide(ucur, unext, gs, alpha_d, tau, v3);
   }
 
@@ -431,8 +470,8 @@ struct Solver {
         T rw = T(0);
 #pragma unroll
         for (int l = 0; l < KM; ++l) {
-          rr[l] = (l < k) ? __ldg(Rm + (int64_t)l * n + i) : T(0);
-          rw += (l < k) ? rr[l] * wr[l] : T(0);
+          rr[l] = __ldg(Rm + (int64_t)l * n + i);
+          rw += rr[l] * wr[l];
         }
         const T u = uc[i];
         const T qi = qd[i];
@@ -455,7 +494,7 @@ struct Solver {
       for (int64_t i = own.x0[seg] + threadIdx.x; i < own.x1[seg]; i += blockDim.x) {
         T rw = T(0);
 #pragma unroll
-        for (int l = 0; l < KM; ++l) rw += (l < k) ? P.R[(int64_t)l * n + i] * wr[l] : T(0);
+        for (int l = 0; l < KM; ++l) rw += __ldg(Rm + (int64_t)l * n + i) * wr[l];
         const T u = ucur[i];
         const T g = gs ? gs[i] : P.qd[i] * u + P.c[i] + (u - W.v[i]) * itau + rw;
         unext[i] = u - alpha * g / jm(i);
@@ -473,7 +512,7 @@ struct Solver {
         a2 += (P.qd[i] + itau) * sd * sd;
         a3 += un * un;
 #pragma unroll
-        for (int l = 0; l < KM; ++l) racc[l] += ((l < k) ? P.R[(int64_t)l * n + i] : T(0)) * un;
+        for (int l = 0; l < KM; ++l) racc[l] += __ldg(Rm + (int64_t)l * n + i) * un;
       }
     if (KM > 0) {
       const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

@@ -17,9 +17,30 @@ __device__ __forceinline__ void rows_loop2(const int* rp, const int* ci, const T
     Acc s1 = Acc(0), s2 = Acc(0);
     if (ok) {
       const int beg = rp[r], end = rp[r + 1];
-      for (int k = beg + gl; k < end; k += G) {
-        const int j = ci[k];
-        const Acc a = (Acc)v[k];
+      int k = beg + gl;
+      for (; k + (kUnroll - 1) * G < end; k += kUnroll * G) {
+        int j[kUnroll];
+        T a[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          j[u] = __ldg(ci + k + u * G);
+          a[u] = __ldg(v + k + u * G);
+        }
+        Acc g1[kUnroll], g2[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          g1[u] = (Acc)x1(j[u]);
+          g2[u] = (Acc)x2(j[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          s1 += (Acc)a[u] * g1[u];
+          s2 += (Acc)a[u] * g2[u];
+        }
+      }
+      for (; k < end; k += G) {
+        const int j = __ldg(ci + k);
+        const Acc a = (Acc)__ldg(v + k);
         s1 += a * (Acc)x1(j);
         s2 += a * (Acc)x2(j);
       }
@@ -56,6 +77,10 @@ __device__ __forceinline__ void apply_D(const Prob<T>& P, const double* t, doubl
     }
     w[l] = s;
     if (wf) wf[l] = (float)s;
+  }
+  for (int l = P.k + threadIdx.x; l < P.kpad; l += blockDim.x) {   // zero padding read by the inner step
+    w[l] = 0.0;
+    if (wf) wf[l] = 0.0f;
   }
   __syncthreads();
 }
