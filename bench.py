@@ -290,7 +290,7 @@ def run_ours(args, rank, world):
     line = {
         "metric": METRIC, "value": step_s, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": step_s * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 (FP64 reductions, KKT and cone roots)", "data": "synthetic (Philox-seeded)",
+        "dtype": "f32", "precision": "FP32 iterates, matrices and SOC roots; FP64 reductions, KKT, restart control and RSOC/exp/pow roots", "data": "synthetic (Philox-seeded)",
         "config": {"workload": WORKLOAD, "n": n, "m": m, "nnz": nnz, "tol": 1e-4, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed before every step (256 MB write)", "inputs": "device-resident FP64 (HBM)"},
         "e2e": {"value": statistics.mean(e2e_times), "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

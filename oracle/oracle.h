@@ -9,6 +9,17 @@
  *
  * Everything here is written for clarity, not speed: single thread, FP64,
  * straightforward loops, bisection for every scalar root.
+ *
+ * Pins (tests/test_oracle_*.py): products against dense / exact integer
+ * results, every projection against its KKT certificate, brute force and
+ * closed forms, the PDHG step against the resolvent identity and Fejer /
+ * Halpern bounds, and whole solves against closed-form optima.
+ * Parity unpinned: the control heuristics inside orc_solve -- the adaptive
+ * restart rule (eq. practical-restart-rule), the PID primal-weight update
+ * (eqs. pid-error / pid-weight) and the adaptive inner tolerance (eq.
+ * monotone-primal-inner-tol).  They change the path, not the fixed point, so
+ * the closed-form solves cannot tell a deviation in them from the paper's
+ * rule; they follow the paper's formulas as written.
  */
 #ifndef CQP_ORACLE_H
 #define CQP_ORACLE_H

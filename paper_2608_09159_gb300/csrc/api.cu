@@ -177,6 +177,7 @@ struct Handle : HandleBase {
   T* tmp_x = nullptr;
   T* tmp_y = nullptr;
   double eta = 0, normA = 0, omega0 = 1, setup_ms = 0;
+  int power_its = 0;                 // power iterations taken by setup
   long long setup_launches = 0;
   int64_t n_roots = 0;
   bool grid = false;
@@ -470,22 +471,35 @@ struct Handle : HandleBase {
     // ---- ||A~||_2 by power iteration on A~'A~ (reading: all-ones start, Rayleigh
     // quotient, stop at power_tol relative change or power_iters) ---------------------------
     {
-      double* v = tmp.alloc<double>(n);
-      double* w = tmp.alloc<double>(std::max<int64_t>(m, 1));
       double* z = tmp.alloc<double>(n);
-      count_launch(); cqp::k_fill<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, v, 1.0 / std::sqrt((double)n));
+      double* w = tmp.alloc<double>(std::max<int64_t>(m, 1));
+      double* ppart = tmp.alloc<double>(2 * (int64_t)nsm);
+      unsigned* pcount = tmp.alloc<unsigned>(1);
+      int* perr = tmp.alloc<int>(1);
+      double* pout = tmp.alloc<double>(2);
+      CK(cudaMemsetAsync(pcount, 0, sizeof(unsigned), st));
+      CK(cudaMemsetAsync(perr, 0, sizeof(int), st));
+      CK(cudaMemsetAsync(pout, 0, 2 * sizeof(double), st));
+      count_launch(); cqp::k_fill<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, z, 1.0 / std::sqrt((double)n));
       double sig = 0.0;
-      for (int it = 0; it < o.power_iters && m > 0; ++it) {
-        count_launch(); cqp::k_spmv_simple<T><<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp, a_ci, a_v, v, w);
-        const double s_new = std::sqrt(dev_dot(w, nullptr, m, part, one, st));
-        count_launch(); cqp::k_spmv_simple<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, t_rp, t_ci, t_v, w, z);
-        const double zn = std::sqrt(dev_dot(z, nullptr, n, part, one, st));
-        if (zn == 0.0) { sig = s_new; break; }
-        count_launch(); cqp::k_scal<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, z, 1.0 / zn);
-        CK(cudaMemcpyAsync(v, z, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        const bool done = it > 0 && std::fabs(s_new - sig) <= o.power_tol * s_new;
-        sig = s_new;
-        if (done) break;
+      if (m > 0) {
+        cqp::GridBarrier pbar{pcount, perr};
+        int iters = o.power_iters;
+        double ptol = o.power_tol;
+        const int32_t* arp = a_rp; const int32_t* aci = a_ci; const T* av = a_v;
+        const int32_t* trp = t_rp; const int32_t* tci = t_ci; const T* tv = t_v;
+        int64_t mm = m, nn = n;
+        void* pargs[] = {&mm, &nn, &arp, &aci, &av, &trp, &tci, &tv, &z, &w, &ppart, &pbar, &iters, &ptol, &pout};
+        count_launch();
+        CK(cudaLaunchCooperativeKernel((void*)cqp::k_power<T>, dim3(nsm), dim3(cqp::kPowerThreads), pargs, 0, st));
+        double hp[2];
+        int herr = 0;
+        CK(cudaMemcpyAsync(hp, pout, sizeof(hp), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(&herr, perr, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (herr != 0) fail(CQP_ERR_WAIT, "power iteration: grid barrier wait expired");
+        sig = hp[0];
+        power_its = (int)hp[1];
       }
       normA = sig;
       eta = o.step_factor / (sig > 0.0 ? sig : 1.0);

@@ -262,4 +262,72 @@ __global__ void k_spmv_simple(int64_t m, const int32_t* rp, const int32_t* ci, c
   }
 }
 
+// ---- ||A~||_2 by power iteration on A~'A~, all iterations in one cooperative launch
+// (eq. practical-stepsizes; reading: all-ones start, Rayleigh quotient ||A v|| with
+// ||v|| = 1, stop at `tol` relative change or `iters` iterations).  v is kept as
+// z / ||z||: each iteration computes w = A z / ||z|| (slot 0: ||w||^2) and z = A' w
+// (slot 1: ||z||^2), so two grid barriers per iteration and no host round trip.
+// Every block combines the partials in the same fixed order, so all blocks take the
+// same stop decision.  out[0] = ||A~||_2 estimate, out[1] = iterations.
+constexpr int kPowerThreads = 512;
+
+template <typename T>
+__global__ void __launch_bounds__(kPowerThreads, 1)
+    k_power(int64_t m, int64_t n, const int32_t* __restrict__ a_rp, const int32_t* __restrict__ a_ci,
+            const T* __restrict__ a_v, const int32_t* __restrict__ t_rp, const int32_t* __restrict__ t_ci,
+            const T* __restrict__ t_v, double* z, double* w, double* part, GridBarrier bar, int iters, double tol,
+            double* out) {
+  GridTeam team;
+  team.init(bar, part);
+  __shared__ double red[kPowerThreads / 32];
+  __shared__ double tot[2];
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+  double sig = 0.0, zscale = 1.0;
+  int it = 0;
+  for (; it < iters; ++it) {
+    double acc[1] = {0.0};
+    for (int64_t r = tid; r < m; r += nt) {
+      double s = 0.0;
+      for (int k = a_rp[r]; k < a_rp[r + 1]; ++k) s += (double)a_v[k] * z[a_ci[k]];
+      s *= zscale;
+      w[r] = s;
+      acc[0] += s * s;
+    }
+    block_sum<1>(acc, red, tot);
+    if (threadIdx.x == 0) team.publish(0, tot[0]);
+    if (!team.sync()) break;
+    team.gather(1, tot);
+    const double s_new = sqrt(tot[0]);
+    acc[0] = 0.0;
+    for (int64_t j = tid; j < n; j += nt) {
+      double s = 0.0;
+      for (int k = t_rp[j]; k < t_rp[j + 1]; ++k) s += (double)t_v[k] * w[t_ci[k]];
+      z[j] = s;
+      acc[0] += s * s;
+    }
+    block_sum<1>(acc, red, tot);
+    if (threadIdx.x == 0) team.publish(1, tot[0]);
+    if (!team.sync()) break;
+    team.gather(2, tot);
+    const double zn = sqrt(tot[1]);
+    if (zn == 0.0) {
+      sig = s_new;
+      ++it;
+      break;
+    }
+    zscale = 1.0 / zn;
+    const bool done = it > 0 && fabs(s_new - sig) <= tol * s_new;
+    sig = s_new;
+    if (done) {
+      ++it;
+      break;
+    }
+  }
+  if (tid == 0) {
+    out[0] = sig;
+    out[1] = (double)it;
+  }
+}
+
 }  // namespace cqp
