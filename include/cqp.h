@@ -195,6 +195,48 @@ const char* cqp_last_error(void);
  * (setup, solver, KKT and kernel-level entry points). */
 long long cqp_kernel_launches(void);
 
+/* ---- batched solve of many independent problems (one persistent launch) ----
+ * Thousands of small, uneven problems are passed as ONE block-diagonal problem:
+ * instance i owns the coordinates [x_off[i], x_off[i+1]) and the rows
+ * [row_off[i], row_off[i+1]).  Every entry of A and of P must join a row and a
+ * column of the same instance, and every cone block must lie inside one
+ * instance's coordinates (checked; CQP_ERR_INVALID otherwise).  The low-rank part
+ * R'DR acts per instance: instance i's R u sums only over its own columns, so R
+ * holds the instances' factors side by side (rows beyond an instance's rank are
+ * zero on its columns) and D is shared.
+ * Each instance is rescaled, gets its own ||A_i||_2, step sizes, primal weight,
+ * restarts, inner tolerance and stop test (rel-KKT of the instance, normalised
+ * by its own ||b_i||, ||c_i||), i.e. it follows the method of cqp_solve as if it
+ * were solved alone (Alg. pdhcq1, Sec. 4).  The solve is one launch: one thread
+ * block per SM takes instances from a work queue, largest first, and solves each
+ * with block-level barriers only. */
+typedef struct {
+  int64_t count;             /* number of instances (>= 1) */
+  const int64_t* x_off;      /* host array, count+1 entries, x_off[0] = 0, x_off[count] = n, increasing */
+  const int64_t* row_off;    /* host array, count+1 entries, row_off[0] = 0, row_off[count] = m, non-decreasing */
+} cqp_batch;
+
+typedef struct {
+  int32_t status;            /* CQP_OK, CQP_ITER_LIMIT, CQP_TIME_LIMIT or CQP_ERR_NUMERICAL */
+  int64_t iters, restarts, inner_total;
+  cqp_kkt_report kkt;        /* of the instance's returned point, relative to its own ||b_i||, ||c_i|| */
+} cqp_instance_result;
+
+/* As cqp_setup, for a batch.  opt->team, blocks_per_sm and launch_iters are
+ * ignored (the batch always runs one block per instance at a time). */
+int cqp_setup_batch(const cqp_csr* A, const cqp_qop* Q, const double* c, const double* b, const cqp_cones* K,
+                    const cqp_batch* B, const cqp_options* opt, cqp_handle** out);
+
+/* Solves every instance of a handle made by cqp_setup_batch.  x0, y0, x_out,
+ * y_out as in cqp_solve (whole block-diagonal vectors).  per_instance: optional
+ * caller-owned array of B->count results.  res: optional summary (status = the
+ * worst instance status, iters = max over instances, restarts and inner_total =
+ * sums, kkt = the instance with the largest rel_kkt, kernel_ms of the launch).
+ * time_limit_s bounds the whole launch: instances still running when it expires
+ * stop with CQP_TIME_LIMIT. */
+int cqp_solve_batch(cqp_handle* h, const double* x0, const double* y0, double* x_out, double* y_out,
+                    int32_t on_device, cqp_instance_result* per_instance, cqp_result* res);
+
 /* ---- kernel-level entry points (device pointers, used for parity and
  * bandwidth measurements).  `precision` selects FP32 (0) or FP64 (1) data:
  * val/x/y are float* or double* accordingly.  rowptr/colind are int32. ---- */

@@ -336,10 +336,110 @@ def fisher_market(n_buyers=10_000, n_goods=1000, density=0.05, seed=1003, pow_fr
                                      is_pow=is_pow, alpha=alpha, z_idx=z_idx, t_idx=t_idx, s_idx=s_idx))
 
 
+
+def portfolio_instance(n, k, stream):
+    """One long-only factor-model portfolio QP (config 4 building block).
+
+    Variables, in order: weights x (n, nonnegative), then one second-order cone
+    block (w_F (k), w_D (n), t) with t last.  Rows: 1'x = 1; F'x - w_F = 0 (k);
+    D^(1/2) x - w_D = 0 (n); t = sigma_bar.  Objective 1/2 x'(F F' + D) x - mu'x,
+    given as Q = diag(D on x) + R' R with R = F' on the x coordinates.  F ~ N(0,
+    0.1^2) (n x k), D ~ U[0.01, 0.1], mu ~ N(0.05, 0.02^2); sigma_bar is the risk
+    ||(F'x_eq, D^(1/2) x_eq)|| of the equal-weight portfolio, which is therefore
+    feasible.  Returns a dict of per-instance arrays (local indices).
+    """
+    F = stream.normal(n * k, 0.0, 0.1).reshape(n, k)
+    Dg = stream.uniform(n, 0.01, 0.1)
+    mu = stream.normal(n, 0.05, 0.02)
+    xeq = np.full(n, 1.0 / n)
+    sigma_bar = float(np.sqrt(np.sum((F.T @ xeq) ** 2) + np.sum(Dg * xeq ** 2)))
+    nv = 2 * n + k + 1
+    m = n + k + 2
+    # CSR rows built directly: budget, k factor rows, n idiosyncratic rows, risk bound
+    lens = np.concatenate([[n], np.full(k, n + 1), np.full(n, 2), [1]]).astype(np.int64)
+    rowptr = np.zeros(m + 1, np.int64)
+    np.cumsum(lens, out=rowptr[1:])
+    xs = np.arange(n, dtype=np.int64)
+    fac_cols = np.concatenate([np.concatenate([xs, [n + l]]) for l in range(k)]) if k else np.zeros(0, np.int64)
+    fac_vals = np.concatenate([np.concatenate([F[:, l], [-1.0]]) for l in range(k)]) if k else np.zeros(0)
+    idio_cols = np.stack([xs, n + k + xs], axis=1).ravel()
+    idio_vals = np.stack([np.sqrt(Dg), -np.ones(n)], axis=1).ravel()
+    colind = np.concatenate([xs, fac_cols, idio_cols, [2 * n + k]]).astype(np.int64)
+    val = np.concatenate([np.ones(n), fac_vals, idio_vals, [1.0]])
+    b = np.concatenate([[1.0], np.zeros(k + n), [sigma_bar]])
+    c = np.concatenate([-mu, np.zeros(k + n + 1)])
+    q = np.concatenate([Dg, np.zeros(k + n + 1)])
+    return dict(n=nv, m=m, n_assets=n, k=k, rowptr=rowptr, colind=colind, val=val, b=b, c=c, q=q, F=F,
+                blocks=[(CONE_NONNEG, n, 0.0), (CONE_SOC, k + n + 1, 0.0)])
+
+
+def portfolio_batch(count=4096, n_range=(50, 2000), k_range=(10, 50), seed=1004):
+    """Config 4: a batch of uneven portfolio QPs as one block-diagonal problem.
+
+    Instance i has n_i ~ U[n_range] assets and k_i ~ U[k_range] factors (see
+    portfolio_instance).  The instances are concatenated: coordinates and rows
+    of instance i occupy [x_off[i], x_off[i+1]) and [row_off[i], row_off[i+1]);
+    the low-rank factor R is max_i k_i rows by n columns, instance i filling
+    rows 0..k_i-1 of its own x columns, with D = I.
+    """
+    st = Stream(seed, 0)
+    ns = st.integers(count, n_range[0], n_range[1] + 1)
+    ks = st.integers(count, k_range[0], k_range[1] + 1)
+    parts = [portfolio_instance(int(ns[i]), int(ks[i]), Stream(seed, 1 + i)) for i in range(count)]
+    x_off = np.zeros(count + 1, np.int64)
+    row_off = np.zeros(count + 1, np.int64)
+    x_off[1:] = np.cumsum([p["n"] for p in parts])
+    row_off[1:] = np.cumsum([p["m"] for p in parts])
+    n, m = int(x_off[-1]), int(row_off[-1])
+    nnz_off = np.zeros(count + 1, np.int64)
+    nnz_off[1:] = np.cumsum([p["rowptr"][-1] for p in parts])
+    a_rowptr = np.zeros(m + 1, np.int64)
+    a_colind = np.empty(int(nnz_off[-1]), np.int64)
+    a_val = np.empty(int(nnz_off[-1]))
+    c = np.empty(n)
+    b = np.empty(m)
+    q = np.empty(n)
+    K = int(ks.max()) if count else 0
+    R = np.zeros((K, n))
+    blist = []
+    for i, p in enumerate(parts):
+        r0, x0, z0 = row_off[i], x_off[i], nnz_off[i]
+        a_rowptr[r0 + 1:row_off[i + 1] + 1] = p["rowptr"][1:] + z0
+        a_colind[z0:nnz_off[i + 1]] = p["colind"] + x0
+        a_val[z0:nnz_off[i + 1]] = p["val"]
+        c[x0:x_off[i + 1]] = p["c"]
+        b[r0:row_off[i + 1]] = p["b"]
+        q[x0:x_off[i + 1]] = p["q"]
+        R[:p["k"], x0:x0 + p["n_assets"]] = p["F"].T
+        blist.extend(p["blocks"])
+    btype, bstart, bdim, balpha = blocks_from_list(blist)
+    inst = make_instance("portfolio_batch_%d" % count, m, n, a_rowptr, a_colind, a_val, c, b, btype, bstart,
+                         bdim, balpha, q_diag=q, q_R=R, q_D=np.eye(K))
+    inst.update(batch_count=count, x_off=x_off, row_off=row_off, n_assets=ns.astype(np.int64),
+                n_factors=ks.astype(np.int64))
+    return inst
+
+
+def batch_member(inst, i):
+    """Instance i of a block-diagonal batch as a stand-alone instance dict."""
+    x0, x1 = int(inst["x_off"][i]), int(inst["x_off"][i + 1])
+    r0, r1 = int(inst["row_off"][i]), int(inst["row_off"][i + 1])
+    rp = inst["a_rowptr"]
+    z0, z1 = int(rp[r0]), int(rp[r1])
+    sel = (inst["blk_start"] >= x0) & (inst["blk_start"] < x1)
+    R = None if inst.get("q_R") is None else inst["q_R"][:, x0:x1]
+    return make_instance("%s[%d]" % (inst["name"], i), r1 - r0, x1 - x0, rp[r0:r1 + 1] - z0,
+                         inst["a_colind"][z0:z1] - x0, inst["a_val"][z0:z1], inst["c"][x0:x1], inst["b"][r0:r1],
+                         inst["blk_type"][sel], inst["blk_start"][sel] - x0, inst["blk_dim"][sel],
+                         inst["blk_alpha"][sel],
+                         q_diag=None if inst.get("q_diag") is None else inst["q_diag"][x0:x1],
+                         q_R=R, q_D=inst.get("q_D"))
+
 CONFIGS = {
     1: lambda: sparse_qp_nonneg(),
     2: lambda: socp_mix(),
     3: lambda: fisher_market(),
+    4: lambda: portfolio_batch(),
 }
 
 
@@ -351,4 +451,6 @@ def small_config(k: int):
         return socp_mix(n=3000, n_nonneg=1500, n_soc=30, n_rsoc=10, m=1500, seed=2002)
     if k == 3:
         return fisher_market(n_buyers=200, n_goods=40, density=0.1, seed=2003)
+    if k == 4:
+        return portfolio_batch(count=12, n_range=(20, 60), k_range=(3, 8), seed=2004)
     raise KeyError(k)

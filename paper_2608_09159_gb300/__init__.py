@@ -68,6 +68,15 @@ class KKTReport(C.Structure):
                 ("pobj", C.c_double), ("dobj", C.c_double), ("norm_res_p", C.c_double), ("norm_res_d", C.c_double)]
 
 
+class Batch(C.Structure):
+    _fields_ = [("count", C.c_int64), ("x_off", C.c_void_p), ("row_off", C.c_void_p)]
+
+
+class InstanceResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iters", C.c_int64), ("restarts", C.c_int64), ("inner_total", C.c_int64),
+                ("kkt", KKTReport)]
+
+
 class Result(C.Structure):
     _fields_ = [("status", C.c_int32), ("iters", C.c_int64), ("restarts", C.c_int64), ("inner_total", C.c_int64),
                 ("kernel_launches", C.c_int64), ("kkt", KKTReport), ("eta", C.c_double), ("norm_A", C.c_double),
@@ -106,8 +115,10 @@ def lib():
         L.cqp_kernel_launches.argtypes = []
         L.cqp_kernel_launches.restype = C.c_longlong
         L.cqp_kkt_static.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.cqp_setup_batch.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+        L.cqp_solve_batch.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp]
         for f in ("cqp_default_options", "cqp_setup", "cqp_solve", "cqp_kkt", "cqp_spmv", "cqp_project",
-                  "cqp_kkt_static"):
+                  "cqp_kkt_static", "cqp_setup_batch", "cqp_solve_batch"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -153,6 +164,17 @@ def cqp_solve(h, x0, y0, x_out, y_out, on_device: int, res: Result) -> int:
 
 def cqp_kkt(h, x, y, on_device: int, rep: KKTReport) -> int:
     return _check(lib().cqp_kkt(h, x, y, on_device, C.byref(rep)))
+
+
+def cqp_setup_batch(A: CSR, Q, c, b, K: Cones, B: Batch, opt: Options):
+    h = C.c_void_p()
+    _check(lib().cqp_setup_batch(C.byref(A), None if Q is None else C.byref(Q), c, b, C.byref(K), C.byref(B),
+                                 C.byref(opt), C.byref(h)))
+    return h
+
+
+def cqp_solve_batch(h, x0, y0, x_out, y_out, on_device: int, per_instance, res: Result) -> int:
+    return _check(lib().cqp_solve_batch(h, x0, y0, x_out, y_out, on_device, per_instance, C.byref(res)))
 
 
 def cqp_free(h) -> None:
@@ -231,7 +253,10 @@ class Solver:
         self.K = Cones(int(len(inst["blk_type"])), p(arrs["blk_type"]), p(arrs["blk_start"]), p(arrs["blk_dim"]),
                        p(arrs["blk_alpha"]))
         self.opt = cqp_default_options(**opts)
-        self.h = cqp_setup(self.A, self.Q, p(arrs["c"]), p(arrs["b"]), self.K, self.opt)
+        self.h = self._setup(arrs)
+
+    def _setup(self, arrs):
+        return cqp_setup(self.A, self.Q, _ptr(arrs["c"]), _ptr(arrs["b"]), self.K, self.opt)
 
     def solve(self, x0=None, y0=None, out_device=False):
         """Returns (x, y, result dict).  With out_device the outputs are torch CUDA tensors."""
@@ -269,6 +294,40 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+class BatchSolver(Solver):
+    """Owns a batch handle (cqp_setup_batch) built from a block-diagonal batch
+    instance dict (keys of an instance plus batch_count, x_off, row_off)."""
+
+    def _setup(self, arrs):
+        inst = self.inst
+        self.count = int(inst["batch_count"])
+        self._xo = np.ascontiguousarray(inst["x_off"], dtype=np.int64)
+        self._ro = np.ascontiguousarray(inst["row_off"], dtype=np.int64)
+        self.B = Batch(self.count, self._xo.ctypes.data, self._ro.ctypes.data)
+        return cqp_setup_batch(self.A, self.Q, _ptr(arrs["c"]), _ptr(arrs["b"]), self.K, self.B, self.opt)
+
+    def solve(self, x0=None, y0=None, out_device=False):
+        """Returns (x, y, per-instance list of dicts, summary result dict)."""
+        res = Result()
+        per = (InstanceResult * self.count)()
+        if out_device:
+            import torch
+            x = torch.empty(self.n, dtype=torch.float64, device="cuda")
+            y = torch.empty(max(self.m, 1), dtype=torch.float64, device="cuda")
+            rc = cqp_solve_batch(self.h, None if x0 is None else x0.data_ptr(), None if y0 is None else y0.data_ptr(),
+                                 x.data_ptr(), y.data_ptr(), 1, per, res)
+            y = y[:self.m]
+        else:
+            x = np.zeros(self.n)
+            y = np.zeros(self.m)
+            x0 = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
+            y0 = None if y0 is None else np.ascontiguousarray(y0, dtype=np.float64)
+            rc = cqp_solve_batch(self.h, _ptr(x0), _ptr(y0), _ptr(x), _ptr(y), 0, per, res)
+        plist = [{"rc": r.status, "iters": r.iters, "restarts": r.restarts, "inner_total": r.inner_total,
+                  "kkt": {f: getattr(r.kkt, f) for f, _ in KKTReport._fields_}} for r in per]
+        return x, y, plist, result_dict(res, rc)
 
 
 def result_dict(res: Result, rc: int):

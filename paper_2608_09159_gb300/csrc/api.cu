@@ -17,6 +17,7 @@
 #include "launch.h"
 #include "setup.cuh"
 #include "solver_impl.cuh"
+#include "batch_setup.cuh"
 
 namespace {
 
@@ -94,6 +95,8 @@ struct HandleBase {
   virtual ~HandleBase() {}
   virtual int solve(const double* x0, const double* y0, double* xo, double* yo, int on_dev, cqp_result* res) = 0;
   virtual int kkt(const double* x, const double* y, int on_dev, cqp_kkt_report* rep) = 0;
+  virtual int solve_batch(const double* x0, const double* y0, double* xo, double* yo, int on_dev,
+                          cqp_instance_result* per, cqp_result* res) = 0;
 };
 
 // unscale + un-permute: out[perm[i]] = scale * v[i] / f[i]
@@ -182,6 +185,14 @@ struct Handle : HandleBase {
   int64_t n_roots = 0;
   bool grid = false;
   int blocks = 1, threads = 512;
+  // batched mode (cqp_setup_batch): per-instance ranges, factors and step sizes
+  bool batched = false;
+  int64_t bcount = 0;
+  cqp::Own* d_own = nullptr;
+  double *d_bb = nullptr, *d_bc = nullptr, *d_nb = nullptr, *d_nc = nullptr;
+  int* d_order = nullptr;
+  unsigned* d_queue = nullptr;
+  std::vector<double> h_eta, h_om;
 
   ~Handle() override { mem.release(); }
 
@@ -198,7 +209,7 @@ struct Handle : HandleBase {
   }
 
   void setup(const cqp_csr* A, const cqp_qop* Q, const double* c_in, const double* b_in, const cqp_cones* K,
-             const cqp_options& o) {
+             const cqp_options& o, const cqp_batch* B = nullptr) {
     auto t0 = std::chrono::steady_clock::now();
     const long long launches0 = g_launches;
     opt = o;
@@ -269,6 +280,63 @@ struct Handle : HandleBase {
       }
     soc_off[0] = base[2];
     rsoc_off[0] = base[3];
+    // ---- batched mode: instance of every block and each instance's permuted ranges -----
+    std::vector<cqp::Own> hown;
+    std::vector<int32_t> inst_col, inst_row;
+    if (B) {
+      batched = true;
+      bcount = B->count;
+      if (bcount < 1 || !B->x_off || !B->row_off) fail(CQP_ERR_INVALID, "batch: count >= 1 and offsets required");
+      const int64_t* xo = B->x_off;
+      const int64_t* ro = B->row_off;
+      if (xo[0] != 0 || xo[bcount] != n || ro[0] != 0 || ro[bcount] != m)
+        fail(CQP_ERR_INVALID, "batch: offsets must start at 0 and end at n (x_off) and m (row_off)");
+      for (int64_t i = 0; i < bcount; ++i)
+        if (xo[i + 1] <= xo[i] || ro[i + 1] < ro[i]) fail(CQP_ERR_INVALID, "batch: offsets must increase");
+      std::vector<int64_t> ib(nb);
+      int64_t cur = 0;
+      for (int64_t j = 0; j < nb; ++j) {
+        while (bs[j] >= xo[cur + 1]) ++cur;
+        if (bs[j] + bd[j] > xo[cur + 1]) fail(CQP_ERR_INVALID, "batch: a cone block straddles two instances");
+        ib[j] = cur;
+      }
+      hown.assign(bcount, cqp::Own{});
+      std::vector<int64_t> bidx0(6 * bcount, -1), bidx1(6 * bcount, -1);
+      for (auto& ow : hown)
+        for (int t = 0; t < 6; ++t) { ow.x0[t] = -1; ow.x1[t] = -1; }
+      int64_t f2[6];
+      for (int t = 0; t < 6; ++t) f2[t] = base[t];
+      int64_t tidx[6] = {0, 0, 0, 0, 0, 0};
+      for (int t = 0; t < 6; ++t)
+        for (int64_t j = 0; j < nb; ++j) {
+          if (bt[j] != t) continue;
+          cqp::Own& ow = hown[ib[j]];
+          if (ow.x0[t] < 0) { ow.x0[t] = f2[t]; bidx0[6 * ib[j] + t] = tidx[t]; }
+          f2[t] += bd[j];
+          ow.x1[t] = f2[t];
+          ++tidx[t];
+          bidx1[6 * ib[j] + t] = tidx[t];
+        }
+      for (int64_t i = 0; i < bcount; ++i) {
+        cqp::Own& ow = hown[i];
+        for (int t = 0; t < 6; ++t)
+          if (ow.x0[t] < 0) { ow.x0[t] = ow.x1[t] = base[t]; bidx0[6 * i + t] = bidx1[6 * i + t] = 0; }
+        ow.f0 = ow.x0[0]; ow.f1 = ow.x1[0];
+        ow.nn0 = ow.x0[1]; ow.nn1 = ow.x1[1];
+        ow.s0 = bidx0[6 * i + 2]; ow.s1 = bidx1[6 * i + 2];
+        ow.r0 = bidx0[6 * i + 3]; ow.r1 = bidx1[6 * i + 3];
+        // exp / pow blocks are indexed by their position in the segment (3 coordinates each)
+        ow.e0 = (ow.x0[4] - base[4]) / 3; ow.e1 = (ow.x1[4] - base[4]) / 3;
+        ow.p0 = (ow.x0[5] - base[5]) / 3; ow.p1 = (ow.x1[5] - base[5]) / 3;
+        ow.row0 = ro[i]; ow.row1 = ro[i + 1];
+      }
+      inst_col.resize(n);
+      inst_row.resize(std::max<int64_t>(m, 1));
+      for (int64_t i = 0; i < bcount; ++i) {
+        for (int64_t j = xo[i]; j < xo[i + 1]; ++j) inst_col[j] = (int32_t)i;
+        for (int64_t r = ro[i]; r < ro[i + 1]; ++r) inst_row[r] = (int32_t)i;
+      }
+    }
     // ---- sizes and options --------------------------------------------------------
     if (m < 0 || n < 1 || nnz < 0 || nnz >= (int64_t(1) << 31)) fail(CQP_ERR_INVALID, "bad matrix sizes");
     k = Q ? Q->rank : 0;
@@ -310,6 +378,27 @@ struct Handle : HandleBase {
     double* one = tmp.alloc<double>(1);
     P.norm_b = m > 0 ? std::sqrt(dev_dot(b_d, nullptr, m, part, one, st)) : 0.0;
     P.norm_c = std::sqrt(dev_dot(c_d, nullptr, n, part, one, st));
+    if (batched) {
+      d_own = mem.alloc<cqp::Own>(bcount);
+      CK(cudaMemcpyAsync(d_own, hown.data(), bcount * sizeof(cqp::Own), cudaMemcpyHostToDevice, st));
+      int32_t* d_ic = tmp.alloc<int32_t>(n);
+      int32_t* d_ir = tmp.alloc<int32_t>(std::max<int64_t>(m, 1));
+      CK(cudaMemcpyAsync(d_ic, inst_col.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(d_ir, inst_row.data(), inst_row.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+      CK(cudaMemsetAsync(bad, 0, sizeof(int), st));
+      if (m > 0) { count_launch(); cqp::k_check_blockdiag<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp64, a_ci_in, d_ir, d_ic, bad); }
+      if (has_p) { count_launch(); cqp::k_check_blockdiag<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, p_rp64, p_ci_in, d_ic, d_ic, bad); }
+      int64_t* d_xo = tmp.alloc<int64_t>(bcount + 1);
+      int64_t* d_ro = tmp.alloc<int64_t>(bcount + 1);
+      CK(cudaMemcpyAsync(d_xo, B->x_off, (bcount + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(d_ro, B->row_off, (bcount + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+      d_nb = mem.alloc<double>(bcount);
+      d_nc = mem.alloc<double>(bcount);
+      count_launch(); cqp::k_inst_norms<<<(int)std::min<int64_t>(bcount, 8 * nsm), cqp::kBatchSetupThreads, 0, st>>>(bcount, d_xo, d_ro, c_d, b_d, d_nb, d_nc);
+      CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (hbad) fail(CQP_ERR_INVALID, "batch: an entry of A or P joins two instances");
+    }
     // ---- permutation ------------------------------------------------------------------
     perm = mem.alloc<int64_t>(n);
     iperm = mem.alloc<int64_t>(n);
@@ -416,7 +505,13 @@ struct Handle : HandleBase {
     if (has_p) { count_launch(); cqp::k_scale_sym<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, p_rp, p_ci, pv, col); }
     if (k > 0) { count_launch(); cqp::k_scale_cols<<<cqp::grid_for(k * n), cqp::kSetupThreads, 0, st>>>(k, n, Rv, col); }
     double beta_b = 1.0, beta_c = 1.0;
-    if (o.bound_obj) {
+    if (batched) {
+      d_bb = mem.alloc<double>(bcount);
+      d_bc = mem.alloc<double>(bcount);
+      count_launch();
+      cqp::k_inst_bound_obj<<<(int)std::min<int64_t>(bcount, 8 * nsm), cqp::kBatchSetupThreads, 0, st>>>(
+          bcount, d_own, n, o.bound_obj, cv, bv, qv, k, Rv, p_rp, pv, d_bb, d_bc);
+    } else if (o.bound_obj) {
       beta_b = (m > 0 ? std::sqrt(dev_dot(bv, nullptr, m, part, one, st)) : 0.0) + 1.0;
       beta_c = std::sqrt(dev_dot(cv, nullptr, n, part, one, st)) + 1.0;
       if (m > 0) { count_launch(); cqp::k_scal<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, bv, 1.0 / beta_b); }
@@ -482,7 +577,23 @@ struct Handle : HandleBase {
       CK(cudaMemsetAsync(pout, 0, 2 * sizeof(double), st));
       count_launch(); cqp::k_fill<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, z, 1.0 / std::sqrt((double)n));
       double sig = 0.0;
-      if (m > 0) {
+      if (batched) {
+        double* d_eta = tmp.alloc<double>(bcount);
+        double* d_om = tmp.alloc<double>(bcount);
+        double* d_na = tmp.alloc<double>(bcount);
+        count_launch();
+        cqp::k_inst_power<T><<<(int)std::min<int64_t>(bcount, 8 * nsm), cqp::kBatchSetupThreads, 0, st>>>(
+            bcount, d_own, a_rp, a_ci, a_v, t_rp, t_ci, t_v, cv, bv, z, w, o.power_iters, o.power_tol,
+            o.step_factor, d_eta, d_om, d_na);
+        h_eta.resize(bcount);
+        h_om.resize(bcount);
+        std::vector<double> h_na(bcount);
+        CK(cudaMemcpyAsync(h_eta.data(), d_eta, bcount * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(h_om.data(), d_om, bcount * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(h_na.data(), d_na, bcount * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (double v : h_na) sig = std::max(sig, v);
+      } else if (m > 0) {
         cqp::GridBarrier pbar{pcount, perr};
         int iters = o.power_iters;
         double ptol = o.power_tol;
@@ -502,10 +613,15 @@ struct Handle : HandleBase {
         power_its = (int)hp[1];
       }
       normA = sig;
-      eta = o.step_factor / (sig > 0.0 ? sig : 1.0);
-      const double cn = std::sqrt(dev_dot(cv, nullptr, n, part, one, st));
-      const double bn = m > 0 ? std::sqrt(dev_dot(bv, nullptr, m, part, one, st)) : 0.0;
-      omega0 = (cn > 1e-10 && bn > 1e-10) ? cn / bn : 1.0;   // reading: ||c~||/||b~||
+      if (batched) {
+        eta = h_eta[0];
+        omega0 = h_om[0];
+      } else {
+        eta = o.step_factor / (sig > 0.0 ? sig : 1.0);
+        const double cn = std::sqrt(dev_dot(cv, nullptr, n, part, one, st));
+        const double bn = m > 0 ? std::sqrt(dev_dot(bv, nullptr, m, part, one, st)) : 0.0;
+        omega0 = (cn > 1e-10 && bn > 1e-10) ? cn / bn : 1.0;   // reading: ||c~||/||b~||
+      }
     }
     // ---- problem descriptor ----------------------------------------------------------------
     P.n = n; P.m = m;
@@ -587,8 +703,12 @@ struct Handle : HandleBase {
     // team
     threads = o.threads > 0 ? o.threads : 512;
     const int64_t size = n + m;
-    grid = o.team == 1 || (o.team == 0 && size > 4096);
-    if (grid) {
+    grid = !batched && (o.team == 1 || (o.team == 0 && size > 4096));
+    if (batched) {
+      const int per = cqp::pdhg_blocks_per_sm<T>(threads);
+      if (per < 1) fail(CQP_ERR_UNSUPPORTED, "solver kernel does not fit on an SM with this block size");
+      blocks = (int)std::min<int64_t>((int64_t)nsm * per, bcount);
+    } else if (grid) {
       const int per = cqp::pdhg_blocks_per_sm<T>(threads);
       if (per < 1) fail(CQP_ERR_UNSUPPORTED, "solver kernel does not fit on an SM with this block size");
       const int want = o.blocks_per_sm > 0 ? std::min(o.blocks_per_sm, per) : 1;
@@ -597,7 +717,20 @@ struct Handle : HandleBase {
       blocks = 1;
     }
     W.part = mem.alloc<double>((int64_t)cqp::kMaxSlots * blocks);
-    S = mem.alloc<cqp::State>(1);
+    S = mem.alloc<cqp::State>(batched ? bcount : 1);
+    if (batched) {
+      // largest instances first (coordinates + rows), so the tail of the queue is short
+      std::vector<int> ord(bcount);
+      for (int64_t i = 0; i < bcount; ++i) ord[i] = (int)i;
+      const int64_t* xo = B->x_off;
+      const int64_t* ro = B->row_off;
+      std::stable_sort(ord.begin(), ord.end(), [&](int a2, int b3) {
+        return (xo[a2 + 1] - xo[a2]) + (ro[a2 + 1] - ro[a2]) > (xo[b3 + 1] - xo[b3]) + (ro[b3 + 1] - ro[b3]);
+      });
+      d_order = mem.alloc<int>(bcount);
+      CK(cudaMemcpyAsync(d_order, ord.data(), bcount * sizeof(int), cudaMemcpyHostToDevice, st));
+      d_queue = mem.alloc<unsigned>(1);
+    }
     bar_count = mem.alloc<unsigned>(1);
     dev_err = mem.alloc<int>(1);
     kkt_out = mem.alloc<double>(8);
@@ -617,6 +750,7 @@ struct Handle : HandleBase {
   }
 
   int solve(const double* x0, const double* y0, double* xo, double* yo, int on_dev, cqp_result* res) override {
+    if (batched) fail(CQP_ERR_UNSUPPORTED, "handle was made by cqp_setup_batch: use cqp_solve_batch");
     auto t0 = std::chrono::steady_clock::now();
     const int64_t mm = std::max<int64_t>(m, 1);
     Temp tmp;
@@ -717,7 +851,109 @@ struct Handle : HandleBase {
     return status;
   }
 
+  int solve_batch(const double* x0, const double* y0, double* xo, double* yo, int on_dev, cqp_instance_result* per,
+                  cqp_result* res) override {
+    if (!batched) fail(CQP_ERR_UNSUPPORTED, "handle was made by cqp_setup: use cqp_solve");
+    auto t0 = std::chrono::steady_clock::now();
+    const int64_t mm = std::max<int64_t>(m, 1);
+    Temp tmp;
+    const double* dx0 = x0;
+    const double* dy0 = y0;
+    if (!on_dev) {
+      if (x0) { double* d = tmp.alloc<double>(n); CK(cudaMemcpyAsync(d, x0, n * 8, cudaMemcpyHostToDevice, st)); dx0 = d; }
+      if (y0 && m > 0) { double* d = tmp.alloc<double>(m); CK(cudaMemcpyAsync(d, y0, m * 8, cudaMemcpyHostToDevice, st)); dy0 = d; }
+    }
+    if (m == 0) dy0 = nullptr;
+    double* ox = tmp.alloc<double>(n);
+    double* oy = tmp.alloc<double>(mm);
+    CK(cudaMemsetAsync(W.root, 0xff, std::max<int64_t>(n_roots, 1) * sizeof(float), st));
+    CK(cudaMemsetAsync(d_queue, 0, sizeof(unsigned), st));
+    std::vector<cqp::State> hs(bcount);
+    for (int64_t i = 0; i < bcount; ++i) {
+      cqp::State& z = hs[i];
+      memset(&z, 0, sizeof(z));
+      z.omega = h_om[i];
+      z.eta = h_eta[i];
+      z.tau = h_eta[i] / h_om[i];
+      z.sigma = h_eta[i] * h_om[i];
+      z.eps_in = opt.eps0_in;
+    }
+    CK(cudaMemcpyAsync(S, hs.data(), bcount * sizeof(cqp::State), cudaMemcpyHostToDevice, st));
+    cqp::BatchArgs ba{};
+    ba.count = bcount;
+    ba.order = d_order;
+    ba.queue = d_queue;
+    ba.own = d_own;
+    ba.beta_b = d_bb; ba.beta_c = d_bc; ba.norm_b = d_nb; ba.norm_c = d_nc;
+    ba.S = S;
+    ba.perm = perm;
+    ba.x0 = dx0; ba.y0 = dy0;
+    ba.x_out = ox; ba.y_out = oy;
+    ba.chunk = (long long)O.check_every * 16;
+    ba.time_limit_ns = opt.time_limit_s > 0 ? (unsigned long long)(opt.time_limit_s * 1e9) : 0ull;
+    cudaEvent_t ev0, ev1;
+    CK(cudaEventCreate(&ev0));
+    CK(cudaEventCreate(&ev1));
+    CK(cudaEventRecord(ev0, st));
+    count_launch();
+    CK(cqp::launch_pdhg_batch<T>(args(O.max_iter), ba, blocks, threads, st));
+    CK(cudaEventRecord(ev1, st));
+    std::vector<cqp::State> back(bcount);
+    CK(cudaMemcpyAsync(back.data(), S, bcount * sizeof(cqp::State), cudaMemcpyDeviceToHost, st));
+    if (xo) CK(cudaMemcpyAsync(xo, ox, n * 8, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    if (yo && m > 0) CK(cudaMemcpyAsync(yo, oy, m * 8, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ev0, ev1));
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    auto rank = [](int stt) { return stt == CQP_OK ? 0 : stt == CQP_ITER_LIMIT ? 1 : stt == CQP_TIME_LIMIT ? 2 : 3; };
+    int worst = CQP_OK;
+    int64_t max_it = 0, rs = 0, inn = 0, worst_i = 0;
+    for (int64_t i = 0; i < bcount; ++i) {
+      const cqp::State& b2 = back[i];
+      int stt = CQP_ITER_LIMIT;
+      if (b2.err == cqp::kErrNumeric) stt = CQP_ERR_NUMERICAL;
+      else if (b2.status == 1) stt = CQP_OK;
+      else if (b2.status == 3) stt = CQP_TIME_LIMIT;
+      if (rank(stt) > rank(worst)) worst = stt;
+      max_it = std::max<int64_t>(max_it, b2.ktot);
+      rs += b2.restarts;
+      inn += b2.inner_total;
+      if (b2.kkt[3] > back[worst_i].kkt[3]) worst_i = i;
+      if (per) {
+        cqp_instance_result& r = per[i];
+        r.status = stt;
+        r.iters = b2.ktot;
+        r.restarts = b2.restarts;
+        r.inner_total = b2.inner_total;
+        r.kkt.eps_p = b2.kkt[0]; r.kkt.eps_d = b2.kkt[1]; r.kkt.eps_g = b2.kkt[2]; r.kkt.rel_kkt = b2.kkt[3];
+        r.kkt.pobj = b2.kkt[4]; r.kkt.dobj = b2.kkt[5]; r.kkt.norm_res_p = b2.kkt[6]; r.kkt.norm_res_d = b2.kkt[7];
+      }
+    }
+    if (res) {
+      memset(res, 0, sizeof(*res));
+      const cqp::State& b2 = back[worst_i];
+      res->status = worst;
+      res->iters = max_it;
+      res->restarts = rs;
+      res->inner_total = inn;
+      res->kernel_launches = 1;
+      res->kkt.eps_p = b2.kkt[0]; res->kkt.eps_d = b2.kkt[1]; res->kkt.eps_g = b2.kkt[2]; res->kkt.rel_kkt = b2.kkt[3];
+      res->kkt.pobj = b2.kkt[4]; res->kkt.dobj = b2.kkt[5]; res->kkt.norm_res_p = b2.kkt[6]; res->kkt.norm_res_d = b2.kkt[7];
+      res->eta = eta;
+      res->norm_A = normA;
+      res->omega = b2.omega;
+      res->setup_ms = setup_ms;
+      res->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      res->kernel_ms = ms;
+      res->setup_launches = setup_launches;
+    }
+    return worst;
+  }
+
   int kkt(const double* x, const double* y, int on_dev, cqp_kkt_report* rep) override {
+    if (batched) fail(CQP_ERR_UNSUPPORTED, "cqp_kkt on a batch handle: each instance reports its KKT in cqp_solve_batch");
     const int64_t mm = std::max<int64_t>(m, 1);
     Temp tmp;
     const double* dx = x;
@@ -834,6 +1070,35 @@ int cqp_setup(const cqp_csr* A, const cqp_qop* Q, const double* c, const double*
     *out = new cqp_handle{h};
     return CQP_OK;
   });
+}
+
+int cqp_setup_batch(const cqp_csr* A, const cqp_qop* Q, const double* c, const double* b, const cqp_cones* K,
+                    const cqp_batch* B, const cqp_options* opt, cqp_handle** out) {
+  if (!out) return CQP_ERR_INVALID;
+  *out = nullptr;
+  if (!A || !K || !c || !B) return CQP_ERR_INVALID;
+  cqp_options o;
+  if (opt) o = *opt; else cqp_default_options(&o);
+  return guarded([&]() {
+    HandleBase* h = nullptr;
+    if (o.precision == 1) {
+      auto* hh = new Handle<double>();
+      try { hh->setup(A, Q, c, b, K, o, B); } catch (...) { delete hh; throw; }
+      h = hh;
+    } else {
+      auto* hh = new Handle<float>();
+      try { hh->setup(A, Q, c, b, K, o, B); } catch (...) { delete hh; throw; }
+      h = hh;
+    }
+    *out = new cqp_handle{h};
+    return CQP_OK;
+  });
+}
+
+int cqp_solve_batch(cqp_handle* h, const double* x0, const double* y0, double* x_out, double* y_out, int32_t on_device,
+                    cqp_instance_result* per_instance, cqp_result* res) {
+  if (!h || !h->impl) return CQP_ERR_INVALID;
+  return guarded([&]() { return h->impl->solve_batch(x0, y0, x_out, y_out, on_device, per_instance, res); });
 }
 
 int cqp_solve(cqp_handle* h, const double* x0, const double* y0, double* x_out, double* y_out, int32_t on_device,

@@ -20,6 +20,10 @@ template <typename T>
 cudaError_t launch_kkt(const KernelArgs<T>& a, const T* x, const T* y, double* out, bool grid, int blocks, int threads,
                        cudaStream_t st);
 
+// Batched persistent solve (one block per instance at a time, work queue).
+template <typename T>
+cudaError_t launch_pdhg_batch(const KernelArgs<T>& a, const BatchArgs& b, int blocks, int threads, cudaStream_t st);
+
 // Blocks per SM that can be co-resident for the cooperative solver kernel.
 template <typename T>
 int pdhg_blocks_per_sm(int threads);

@@ -124,6 +124,23 @@ struct Own {
   int64_t row0, row1;
 };
 
+// Batched mode: independent instances of one block-diagonal problem, each solved by
+// one thread block (CtaTeam) with its own scaling, step sizes, restarts and stop.
+struct BatchArgs {
+  int64_t count;
+  const int* order;                 // processing order (largest instances first)
+  unsigned* queue;                  // next position in `order` (zeroed by the host)
+  const Own* own;                   // per instance: its ranges in the permuted layout
+  const double* beta_b; const double* beta_c;   // per-instance bound-objective factors
+  const double* norm_b; const double* norm_c;   // per-instance ||b||, ||c|| (unscaled)
+  State* S;                         // per-instance control state
+  const int64_t* perm;              // permuted -> original coordinate
+  const double* x0; const double* y0;           // unscaled starts, original order (or null)
+  double* x_out; double* y_out;     // unscaled final candidates, original order
+  long long chunk;                  // outer iterations between time-limit checks
+  unsigned long long time_limit_ns; // 0: none
+};
+
 template <typename T>
 __device__ void make_own(const Prob<T>& P, int b, int nb, Own& o) {
   split_range(P.n_free, b, nb, o.f0, o.f1);

@@ -52,3 +52,26 @@ def test_fisher_rows():
     assert inst["n"] == f["edges"] + 4 * nb
     # every supply row and utility row is non-empty
     assert np.all(np.diff(inst["a_rowptr"]) > 0)
+
+
+def test_portfolio_batch_structure():
+    # members cut out of the batch reproduce the batch; every row and entry stays inside
+    # its instance; the equal-weight portfolio is feasible and on the risk bound
+    b = I.portfolio_batch(count=5, n_range=(6, 12), k_range=(2, 4), seed=77)
+    assert b["x_off"][-1] == b["n"] and b["row_off"][-1] == b["m"]
+    rp, ci = b["a_rowptr"], b["a_colind"]
+    for i in range(b["batch_count"]):
+        x0, x1 = b["x_off"][i], b["x_off"][i + 1]
+        for r in range(b["row_off"][i], b["row_off"][i + 1]):
+            cols = ci[rp[r]:rp[r + 1]]
+            assert cols.min() >= x0 and cols.max() < x1
+        m = I.batch_member(b, i)
+        n_as, k = int(b["n_assets"][i]), int(b["n_factors"][i])
+        assert m["n"] == 2 * n_as + k + 1 and m["m"] == n_as + k + 2
+        F = m["q_R"][:k, :n_as].T
+        D = m["q_diag"][:n_as]
+        xe = np.full(n_as, 1.0 / n_as)
+        z = np.concatenate([xe, F.T @ xe, np.sqrt(D) * xe, [m["b"][-1]]])
+        assert np.allclose(I.csr_matvec(m["a_rowptr"], m["a_colind"], m["a_val"], z), m["b"], atol=1e-12)
+        assert abs(np.linalg.norm(z[n_as:-1]) - z[-1]) <= 1e-12
+        assert list(m["blk_type"]) == [I.CONE_NONNEG, I.CONE_SOC]
