@@ -191,6 +191,7 @@ struct Handle : HandleBase {
   cqp::Own* d_own = nullptr;
   double *d_bb = nullptr, *d_bc = nullptr, *d_nb = nullptr, *d_nc = nullptr;
   int* d_order = nullptr;
+  int* d_rank = nullptr;
   unsigned* d_queue = nullptr;
   std::vector<double> h_eta, h_om;
 
@@ -511,6 +512,11 @@ struct Handle : HandleBase {
       count_launch();
       cqp::k_inst_bound_obj<<<(int)std::min<int64_t>(bcount, 8 * nsm), cqp::kBatchSetupThreads, 0, st>>>(
           bcount, d_own, n, o.bound_obj, cv, bv, qv, k, Rv, p_rp, pv, d_bb, d_bc);
+      if (k > 0) {
+        d_rank = mem.alloc<int>(bcount);
+        count_launch();
+        cqp::k_inst_rank<<<(int)std::min<int64_t>(bcount, 8 * nsm), cqp::kBatchSetupThreads, 0, st>>>(bcount, d_own, n, k, Rv, d_rank);
+      }
     } else if (o.bound_obj) {
       beta_b = (m > 0 ? std::sqrt(dev_dot(bv, nullptr, m, part, one, st)) : 0.0) + 1.0;
       beta_c = std::sqrt(dev_dot(cv, nullptr, n, part, one, st)) + 1.0;
@@ -701,7 +707,9 @@ struct Handle : HandleBase {
     n_roots = n_soc + n_rsoc + n_exp + n_pow;
     W.root = mem.alloc<float>(std::max<int64_t>(n_roots, 1));
     // team
-    threads = o.threads > 0 ? o.threads : 512;
+    // batched instances are small: 128 threads per instance lets four instances share an SM,
+    // which hides more latency than one wide block per instance (measured on GB300)
+    threads = o.threads > 0 ? o.threads : (batched ? 128 : 512);
     const int64_t size = n + m;
     grid = !batched && (o.team == 1 || (o.team == 0 && size > 4096));
     if (batched) {
@@ -885,6 +893,7 @@ struct Handle : HandleBase {
     ba.queue = d_queue;
     ba.own = d_own;
     ba.beta_b = d_bb; ba.beta_c = d_bc; ba.norm_b = d_nb; ba.norm_c = d_nc;
+    ba.rank = P.d_scale > 0.0 ? d_rank : nullptr;   // per-instance width needs D = d I (D's stride is the full rank)
     ba.S = S;
     ba.perm = perm;
     ba.x0 = dx0; ba.y0 = dy0;

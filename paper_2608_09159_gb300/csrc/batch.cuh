@@ -44,6 +44,10 @@ __global__ void __launch_bounds__(512, 1) pdhg_batch_kernel(KernelArgs<T> a, Bat
       Pi.beta_c = b.beta_c[i];
       Pi.norm_b = b.norm_b[i];
       Pi.norm_c = b.norm_c[i];
+      if (b.rank) {   // rows of R beyond the instance's rank are zero on its columns
+        Pi.k = b.rank[i];
+        Pi.kpad = (Pi.k + 7) / 8 * 8;
+      }
     }
     load_state(C, b.S + i);
     Solver<T, CtaTeam> s(Pi, W, a.O, team, C, scratch, wacc, cbuf);

@@ -149,4 +149,23 @@ __global__ void __launch_bounds__(kBatchSetupThreads) k_inst_power(
   }
 }
 
+// rows of R that are nonzero on the instance's columns: its rank (R rows are
+// stored instance by instance side by side, zero beyond each instance's rank)
+__global__ void __launch_bounds__(kBatchSetupThreads) k_inst_rank(int64_t count, const Own* own, int64_t n, int64_t k,
+                                                                  const double* Rv, int* rank) {
+  for (int64_t i = blockIdx.x; i < count; i += gridDim.x) {
+    const Own o = own[i];
+    int r = 0;
+    for (int64_t l = k - 1; l >= 0; --l) {
+      int nz = 0;
+      for (int seg = 0; seg < 6 && !nz; ++seg)
+        for (int64_t j = o.x0[seg] + threadIdx.x; j < o.x1[seg]; j += blockDim.x)
+          if (Rv[l * n + j] != 0.0) { nz = 1; break; }
+      if (__syncthreads_or(nz)) { r = (int)l + 1; break; }
+    }
+    if (threadIdx.x == 0) rank[i] = r;
+    __syncthreads();
+  }
+}
+
 }  // namespace cqp

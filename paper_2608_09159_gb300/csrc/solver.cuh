@@ -133,6 +133,7 @@ struct BatchArgs {
   const Own* own;                   // per instance: its ranges in the permuted layout
   const double* beta_b; const double* beta_c;   // per-instance bound-objective factors
   const double* norm_b; const double* norm_c;   // per-instance ||b||, ||c|| (unscaled)
+  const int* rank;                  // per-instance rows of R in use (null: all)
   State* S;                         // per-instance control state
   const int64_t* perm;              // permuted -> original coordinate
   const double* x0; const double* y0;           // unscaled starts, original order (or null)
