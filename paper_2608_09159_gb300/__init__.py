@@ -117,8 +117,19 @@ def lib():
         L.cqp_kkt_static.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.cqp_setup_batch.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
         L.cqp_solve_batch.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp]
+        f32 = C.c_float
+        L.cqp_ws_features.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, i64, vp, vp, vp]
+        L.cqp_gemm_bf16.argtypes = [i32, i32, i64, i64, i64, vp, i64, vp, i64, vp, i64, vp, i32, i32, vp]
+        L.cqp_ws_head_forward.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.cqp_ws_loss.argtypes = [i64, vp, vp, vp, vp, vp, f32, f32, vp, vp, vp, vp]
+        L.cqp_ws_head_backward.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.cqp_relu_backward_bf16.argtypes = [i64, i64, vp, vp, vp, vp]
+        L.cqp_adam_step.argtypes = [i64, vp, vp, vp, vp, f32, f32, f32, f32, i64, vp, vp]
+        L.cqp_ws_start.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, i64, vp, vp, vp, f32, vp, vp, vp]
         for f in ("cqp_default_options", "cqp_setup", "cqp_solve", "cqp_kkt", "cqp_spmv", "cqp_project",
-                  "cqp_kkt_static", "cqp_setup_batch", "cqp_solve_batch"):
+                  "cqp_kkt_static", "cqp_setup_batch", "cqp_solve_batch", "cqp_ws_features", "cqp_gemm_bf16",
+                  "cqp_ws_head_forward", "cqp_ws_loss", "cqp_ws_head_backward", "cqp_relu_backward_bf16",
+                  "cqp_adam_step", "cqp_ws_start"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -175,6 +186,44 @@ def cqp_setup_batch(A: CSR, Q, c, b, K: Cones, B: Batch, opt: Options):
 
 def cqp_solve_batch(h, x0, y0, x_out, y_out, on_device: int, per_instance, res: Result) -> int:
     return _check(lib().cqp_solve_batch(h, x0, y0, x_out, y_out, on_device, per_instance, C.byref(res)))
+
+
+def cqp_ws_features(count, x_off, n_assets, asset_off, row_off, rank, c, q, R, ldr, b, X, stream=None) -> int:
+    return _check(lib().cqp_ws_features(count, x_off, n_assets, asset_off, row_off, rank, c, q, R, ldr, b, X, stream))
+
+
+def cqp_gemm_bf16(trans_a, trans_b, M, N, K, A, lda, B, ldb, Cm, ldc, bias, epilogue, split_k=1, stream=None) -> int:
+    return _check(lib().cqp_gemm_bf16(trans_a, trans_b, M, N, K, A, lda, B, ldb, Cm, ldc, bias, epilogue, split_k,
+                                      stream))
+
+
+def cqp_ws_head_forward(count, asset_off, H2, w3, b3, Wd, bd, score, x0, pooled, ydual, stream=None) -> int:
+    return _check(lib().cqp_ws_head_forward(count, asset_off, H2, w3, b3, Wd, bd, score, x0, pooled, ydual, stream))
+
+
+def cqp_ws_loss(count, asset_off, x0, xstar, ydual, ystar, lam, scale, dscore, dydual, loss, stream=None) -> int:
+    return _check(lib().cqp_ws_loss(count, asset_off, x0, xstar, ydual, ystar, lam, scale, dscore, dydual, loss,
+                                    stream))
+
+
+def cqp_ws_head_backward(count, asset_off, H2, w3, Wd, dscore, dydual, pooled, dZ2, gw3, gb3, gWd, gbd,
+                         stream=None) -> int:
+    return _check(lib().cqp_ws_head_backward(count, asset_off, H2, w3, Wd, dscore, dydual, pooled, dZ2, gw3, gb3,
+                                             gWd, gbd, stream))
+
+
+def cqp_relu_backward_bf16(rows, cols, H, dH, gbias, stream=None) -> int:
+    return _check(lib().cqp_relu_backward_bf16(rows, cols, H, dH, gbias, stream))
+
+
+def cqp_adam_step(n, w, g, m, v, lr, beta1, beta2, eps, step, w_bf16, stream=None) -> int:
+    return _check(lib().cqp_adam_step(n, w, g, m, v, lr, beta1, beta2, eps, step, w_bf16, stream))
+
+
+def cqp_ws_start(count, x_off, row_off, n_assets, asset_off, rank, q, R, ldr, b, xw, ydual, yb_scale, x0, y0,
+                 stream=None) -> int:
+    return _check(lib().cqp_ws_start(count, x_off, row_off, n_assets, asset_off, rank, q, R, ldr, b, xw, ydual,
+                                     yb_scale, x0, y0, stream))
 
 
 def cqp_free(h) -> None:

@@ -29,7 +29,7 @@ def _nvcc() -> str:
 def _inputs():
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     deps = srcs + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
-        glob.glob(os.path.join(CSRC, "*.inc")) + [os.path.join(INCLUDE, "cqp.h"), os.path.abspath(__file__)]
+        glob.glob(os.path.join(CSRC, "*.inc")) + glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)]
     return srcs, deps
 
 
