@@ -33,8 +33,9 @@ extern "C" {
 /* Per-asset features X (rows = asset_off[count], CQP_WS_FEATURES BF16 columns) from the
  * batch data: mu = -c, D = q (diagonal of Q), the factor loadings R[0..rank_i-1, x]
  * (R row-major with leading dimension ldr), sigma_bar = last entry of b of each instance.
- * Features: 20 mu, 20 D, 100 |F_j|^2, 0.1 mu/(D + |F_j|^2), 50 (mu - mean mu),
- * log(n_i)/8, k_i/50, 10 sigma_bar. */
+ * Features: 20 mu, 20 D, 100 |F_j|^2, 0.1 rr with rr = mu/(D + |F_j|^2), 50 (mu - mean mu),
+ * log(n_i)/8, k_i/50, 10 sigma_bar, (mu - mean mu)/std mu, D/mean D, |F_j|^2/mean |F|^2,
+ * rr/max rr (means, std and max over the instance's assets). */
 int cqp_ws_features(int64_t count, const int64_t* x_off, const int64_t* n_assets, const int64_t* asset_off,
                     const int64_t* row_off, const int32_t* rank, const double* c, const double* q, const double* R,
                     int64_t ldr, const double* b, uint16_t* X, void* stream);
@@ -79,11 +80,13 @@ int cqp_adam_step(int64_t n, float* w, const float* g, float* m, float* v, float
 
 /* The batch start from the head outputs: x = xw (softmax weights), w_F = F'x, w_D =
  * D^(1/2) x, t = sigma_bar; y = (ydual_0 / yb_scale, lambda w_F, lambda w_D, ydual_1)
- * with lambda = ydual_1 / sigma_bar.  x0 (n) and y0 (m) in the batch layout (FP64). */
+ * with lambda = ydual_1 / sigma_bar.  dual_mode 0 keeps y0 = 0 (primal start only), 1 sets
+ * the budget and risk rows only, 2 the whole dual above.  x0 (n) and y0 (m) in the batch
+ * layout (FP64, y0 fully written). */
 int cqp_ws_start(int64_t count, const int64_t* x_off, const int64_t* row_off, const int64_t* n_assets,
                  const int64_t* asset_off, const int32_t* rank, const double* q, const double* R, int64_t ldr,
-                 const double* b, const float* xw, const float* ydual, float yb_scale, double* x0, double* y0,
-                 void* stream);
+                 const double* b, const float* xw, const float* ydual, float yb_scale, int32_t dual_mode, double* x0,
+                 double* y0, void* stream);
 
 #ifdef __cplusplus
 }

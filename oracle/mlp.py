@@ -38,6 +38,11 @@ def features(batch, rank):
         f[:, 5] = np.log(na) / 8.0
         f[:, 6] = k / 50.0
         f[:, 7] = 10.0 * sig
+        rr = mu / (d + f2)
+        f[:, 8] = (mu - mu.mean()) / (mu.std() + 1e-12)
+        f[:, 9] = d / d.mean()
+        f[:, 10] = f2 / f2.mean()
+        f[:, 11] = rr / rr.max() if rr.max() > 0 else 0.0
         out.append(f)
     return np.concatenate(out, axis=0)
 

@@ -125,7 +125,7 @@ def lib():
         L.cqp_ws_head_backward.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.cqp_relu_backward_bf16.argtypes = [i64, i64, vp, vp, vp, vp]
         L.cqp_adam_step.argtypes = [i64, vp, vp, vp, vp, f32, f32, f32, f32, i64, vp, vp]
-        L.cqp_ws_start.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, i64, vp, vp, vp, f32, vp, vp, vp]
+        L.cqp_ws_start.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, i64, vp, vp, vp, f32, i32, vp, vp, vp]
         for f in ("cqp_default_options", "cqp_setup", "cqp_solve", "cqp_kkt", "cqp_spmv", "cqp_project",
                   "cqp_kkt_static", "cqp_setup_batch", "cqp_solve_batch", "cqp_ws_features", "cqp_gemm_bf16",
                   "cqp_ws_head_forward", "cqp_ws_loss", "cqp_ws_head_backward", "cqp_relu_backward_bf16",
@@ -220,10 +220,10 @@ def cqp_adam_step(n, w, g, m, v, lr, beta1, beta2, eps, step, w_bf16, stream=Non
     return _check(lib().cqp_adam_step(n, w, g, m, v, lr, beta1, beta2, eps, step, w_bf16, stream))
 
 
-def cqp_ws_start(count, x_off, row_off, n_assets, asset_off, rank, q, R, ldr, b, xw, ydual, yb_scale, x0, y0,
-                 stream=None) -> int:
+def cqp_ws_start(count, x_off, row_off, n_assets, asset_off, rank, q, R, ldr, b, xw, ydual, yb_scale, dual_mode, x0,
+                 y0, stream=None) -> int:
     return _check(lib().cqp_ws_start(count, x_off, row_off, n_assets, asset_off, rank, q, R, ldr, b, xw, ydual,
-                                     yb_scale, x0, y0, stream))
+                                     yb_scale, dual_mode, x0, y0, stream))
 
 
 def cqp_free(h) -> None:

@@ -53,20 +53,45 @@ __global__ void __launch_bounds__(256) k_ws_features(int64_t count, const int64_
                                                       const int64_t* asset_off, const int64_t* row_off,
                                                       const int32_t* rank, const double* c, const double* q,
                                                       const double* R, int64_t ldr, const double* b, bf16* X) {
-  __shared__ double red[8];
-  __shared__ double mean_mu;
+  // per-instance statistics: mean and second moment of mu, mean of D, mean of |F_j|^2,
+  // max of the return-to-risk ratio mu / (D + |F_j|^2)
+  __shared__ double red[8][5];
+  __shared__ double st[5];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int64_t i = blockIdx.x; i < count; i += gridDim.x) {
     const int64_t x0 = x_off[i], na = n_assets[i], a0 = asset_off[i];
     const int k = rank[i];
-    double s = 0.0;
-    for (int64_t j = threadIdx.x; j < na; j += blockDim.x) s += -c[x0 + j];
-    s = cqp::warp_sum(s);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    double v[5] = {0.0, 0.0, 0.0, 0.0, -1e300};
+    for (int64_t j = threadIdx.x; j < na; j += blockDim.x) {
+      const double mu = -c[x0 + j], d = q[x0 + j];
+      double f2 = 0.0;
+      for (int l = 0; l < k; ++l) {
+        const double r = R[(int64_t)l * ldr + x0 + j];
+        f2 += r * r;
+      }
+      v[0] += mu;
+      v[1] += mu * mu;
+      v[2] += d;
+      v[3] += f2;
+      v[4] = fmax(v[4], mu / (d + f2));
+    }
+    for (int t = 0; t < 4; ++t) v[t] = cqp::warp_sum(v[t]);
+    for (int o = 16; o; o >>= 1) v[4] = fmax(v[4], __shfl_xor_sync(0xffffffffu, v[4], o));
+    if (lane == 0)
+      for (int t = 0; t < 5; ++t) red[warp][t] = v[t];
     __syncthreads();
     if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-      mean_mu = na > 0 ? t / (double)na : 0.0;
+      double a[5] = {0.0, 0.0, 0.0, 0.0, -1e300};
+      for (int w = 0; w < nw; ++w) {
+        for (int t = 0; t < 4; ++t) a[t] += red[w][t];
+        a[4] = fmax(a[4], red[w][4]);
+      }
+      const double inv = na > 0 ? 1.0 / (double)na : 0.0;
+      st[0] = a[0] * inv;
+      st[1] = sqrt(fmax(a[1] * inv - st[0] * st[0], 0.0)) + 1e-12;
+      st[2] = a[2] * inv + 1e-300;
+      st[3] = a[3] * inv + 1e-300;
+      st[4] = a[4];
     }
     __syncthreads();
     const double sig = b[row_off[i + 1] - 1];
@@ -77,16 +102,21 @@ __global__ void __launch_bounds__(256) k_ws_features(int64_t count, const int64_
         const double r = R[(int64_t)l * ldr + x0 + j];
         f2 += r * r;
       }
+      const double rr = mu / (d + f2);
       float f[kFeat];
       f[0] = (float)(20.0 * mu);
       f[1] = (float)(20.0 * d);
       f[2] = (float)(100.0 * f2);
-      f[3] = (float)(0.1 * mu / (d + f2));
-      f[4] = (float)(50.0 * (mu - mean_mu));
+      f[3] = (float)(0.1 * rr);
+      f[4] = (float)(50.0 * (mu - st[0]));
       f[5] = (float)(log((double)na) / 8.0);
       f[6] = (float)(k / 50.0);
       f[7] = (float)(10.0 * sig);
-      for (int t = 8; t < kFeat; ++t) f[t] = 0.f;
+      f[8] = (float)((mu - st[0]) / st[1]);
+      f[9] = (float)(d / st[2]);
+      f[10] = (float)(f2 / st[3]);
+      f[11] = (float)(st[4] > 0.0 ? rr / st[4] : 0.0);
+      for (int t = 12; t < kFeat; ++t) f[t] = 0.f;
       bf16* xr = X + (a0 + j) * kFeat;
       for (int t = 0; t < kFeat; ++t) xr[t] = __float2bfloat16(f[t]);
     }
@@ -373,13 +403,14 @@ __global__ void __launch_bounds__(256) k_ws_start(int64_t count, const int64_t* 
                                                   const int64_t* n_assets, const int64_t* asset_off,
                                                   const int32_t* rank, const double* q, const double* R, int64_t ldr,
                                                   const double* b, const float* xw, const float* ydual,
-                                                  float yb_scale, double* x0, double* y0) {
+                                                  float yb_scale, int dual_mode, double* x0, double* y0) {
   for (int64_t i = blockIdx.x; i < count; i += gridDim.x) {
     const int64_t xo = x_off[i], ro = row_off[i], na = n_assets[i], a0 = asset_off[i];
     const int k = rank[i];
     const double sig = b[row_off[i + 1] - 1];
-    const double yb = (double)ydual[i * 2] / yb_scale, yt = (double)ydual[i * 2 + 1];
-    const double lam = sig > 0.0 ? yt / sig : 0.0;
+    const double yb = dual_mode >= 1 ? (double)ydual[i * 2] / yb_scale : 0.0;
+    const double yt = dual_mode >= 1 ? (double)ydual[i * 2 + 1] : 0.0;
+    const double lam = (dual_mode >= 2 && sig > 0.0) ? yt / sig : 0.0;
     for (int64_t j = threadIdx.x; j < na; j += blockDim.x) {
       const double xv = (double)xw[a0 + j];
       x0[xo + j] = xv;
@@ -518,13 +549,13 @@ int cqp_adam_step(int64_t n, float* w, const float* g, float* m, float* v, float
 
 int cqp_ws_start(int64_t count, const int64_t* x_off, const int64_t* row_off, const int64_t* n_assets,
                  const int64_t* asset_off, const int32_t* rank, const double* q, const double* R, int64_t ldr,
-                 const double* b, const float* xw, const float* ydual, float yb_scale, double* x0, double* y0,
-                 void* stream) {
+                 const double* b, const float* xw, const float* ydual, float yb_scale, int32_t dual_mode, double* x0,
+                 double* y0, void* stream) {
   if (count < 1 || !x_off || !row_off || !n_assets || !asset_off || !rank || !q || !b || !xw || !ydual || !x0 || !y0 ||
-      (ldr > 0 && !R) || !(yb_scale > 0.f))
+      (ldr > 0 && !R) || !(yb_scale > 0.f) || dual_mode < 0 || dual_mode > 2)
     return fail_with(CQP_ERR_INVALID, "cqp_ws_start: bad arguments");
   k_ws_start<<<(int)std::min<int64_t>(count, 152 * 8), 256, 0, (cudaStream_t)stream>>>(
-      count, x_off, row_off, n_assets, asset_off, rank, q, R, ldr, b, xw, ydual, yb_scale, x0, y0);
+      count, x_off, row_off, n_assets, asset_off, rank, q, R, ldr, b, xw, ydual, yb_scale, dual_mode, x0, y0);
   cqp::record_launches(1);
   MLP_CK(cudaGetLastError());
   return CQP_OK;

@@ -4,7 +4,8 @@ A 3-layer MLP (features -> 512 -> 512 -> 1 per asset, ReLU, BF16 weights and
 activations, FP32 accumulation and master weights) proposes the start (x0, y0)
 of cqp_solve_batch: x0 is the softmax of the asset scores within each instance
 (so 1'x0 = 1, x0 >= 0) completed by w_F = F'x0, w_D = D^(1/2) x0, t = sigma_bar;
-y0 comes from two predicted duals per instance (budget row, risk row).  The
+a dual head predicts the budget-row and risk-row duals, which seed those two rows
+of y0 (the other duals start at zero, which measured best).  The
 network is trained on solutions of the batched solver.  Device memory is held
 in torch tensors; every computation is one of the library's kernels, called
 through the C ABI.  The solver is unchanged and a cold start stays available.
@@ -133,15 +134,17 @@ class WarmStartNet:
             cqp_adam_step(self.p[k].numel(), _p(self.p[k]), _p(self.g[k]), _p(self.m[k]), _p(self.v[k]), lr, beta1,
                           beta2, eps, self.step, _p(self.bf.get(k)))
 
-    def start(self, dev: BatchDevice, X=None):
-        """(x0, y0) of the batch (FP64 device tensors) from the network."""
+    def start(self, dev: BatchDevice, X=None, dual_mode: int = 1):
+        """(x0, y0) of the batch (FP64 device tensors) from the network.  dual_mode: 0 primal
+        start only (y0 = 0), 1 budget and risk duals, 2 the whole dual from lambda = y_t / t."""
         torch = self.torch
         X = dev.features() if X is None else X
         f = self.forward(X, dev.asset_off, dev.count)
         x0 = torch.zeros(dev.n, dtype=torch.float64, device="cuda")
         y0 = torch.zeros(dev.m, dtype=torch.float64, device="cuda")
         cqp_ws_start(dev.count, _p(dev.x_off), _p(dev.row_off), _p(dev.n_assets), _p(dev.asset_off), _p(dev.rank),
-                     _p(dev.q), _p(dev.R), dev.ldr, _p(dev.b), _p(f["x0"]), _p(f["ydual"]), YB_SCALE, _p(x0), _p(y0))
+                     _p(dev.q), _p(dev.R), dev.ldr, _p(dev.b), _p(f["x0"]), _p(f["ydual"]), YB_SCALE, dual_mode,
+                     _p(x0), _p(y0))
         return x0, y0
 
 
@@ -183,14 +186,14 @@ def train(net: WarmStartNet, data: TrainingSet, steps: int, instances: int = 256
     return hist
 
 
-def solve_batch(batch, net: WarmStartNet | None = None, **opts):
+def solve_batch(batch, net: WarmStartNet | None = None, dual_mode: int = 1, **opts):
     """Batched solve of a portfolio batch, from the network's start when `net` is given,
     else from zero.  Returns (x, y, per-instance results, summary)."""
     s = BatchSolver(batch, device=True, **opts)
     try:
         if net is None:
             return s.solve(out_device=True)
-        x0, y0 = net.start(BatchDevice(batch))
+        x0, y0 = net.start(BatchDevice(batch), dual_mode=dual_mode)
         return s.solve(x0=x0, y0=y0, out_device=True)
     finally:
         s.close()
