@@ -435,12 +435,105 @@ def batch_member(inst, i):
                          q_diag=None if inst.get("q_diag") is None else inst["q_diag"][x0:x1],
                          q_R=R, q_D=inst.get("q_D"))
 
+
+# ---------------------------------------------------------------------------
+# index-addressed draws (random access, for instances generated on the device)
+# ---------------------------------------------------------------------------
+
+def philox_at(seed, stream, idx):
+    """Philox-4x32-10 block of counter (idx_lo, idx_hi, 0, 0) under key (seed, stream)."""
+    idx = np.asarray(idx, dtype=np.uint64).reshape(-1)
+    ctr = np.zeros((idx.size, 4), dtype=np.uint32)
+    ctr[:, 0] = (idx & _MASK32).astype(np.uint32)
+    ctr[:, 1] = (idx >> np.uint64(32)).astype(np.uint32)
+    key = np.array([seed & 0xFFFFFFFF, stream & 0xFFFFFFFF], dtype=np.uint32)
+    return philox4x32_10(ctr, key)
+
+
+def _u53(w_hi, w_lo):
+    m = ((w_hi.astype(np.uint64) >> np.uint64(5)) << np.uint64(26)) | (w_lo.astype(np.uint64) >> np.uint64(6))
+    return m.astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def uniform_at(seed, stream, idx):
+    """U[0,1) with 53 bits from words 0 and 1 of the block of index idx."""
+    w = philox_at(seed, stream, idx)
+    return _u53(w[:, 0], w[:, 1])
+
+
+def normal_at(seed, stream, idx):
+    """N(0,1) by Box-Muller from the block of index idx (words 0,1 -> u1, words 2,3 -> u2)."""
+    w = philox_at(seed, stream, idx)
+    u1 = _u53(w[:, 0], w[:, 1])
+    u2 = _u53(w[:, 2], w[:, 3])
+    return np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * np.pi * u2)
+
+
+LARGE_NNZ_PER_ROW = 20
+
+
+def large_qp(n=200_000_000, m=50_000_000, seed=1005):
+    """Config 5 (any size): large sparse QP over the nonnegative orthant.
+
+    A (m x n): row r has 20 entries, slot e drawing column floor(U * n) from stream 1
+    and value N(0,1) from stream 2 at index 20 r + e; a row's entries are sorted by
+    column (ties by slot) and a repeated column keeps the sum of its values in its
+    first entry and an explicit 0 in the others, so every row keeps 20 stored entries
+    (about 5 per column on average).  Q = diag(q) + S: q_j ~ U[0,1] (stream 5) and S
+    the Laplacian of a perfect matching j <-> j + d (j even, indices mod n, d odd from
+    stream 7) with pair weight |N(0,1)| (stream 6, at the even endpoint), given as P
+    with rows {j: w, partner: -w} in column order.  c_j ~ N(0,1) (stream 3),
+    b = A x0 with x0_j = |N(0,1)| (stream 4), summed in stored order.  n must be even.
+    Generated identically by instances.gpu.large_qp_device on the GPU.
+    """
+    assert n % 2 == 0
+    k = LARGE_NNZ_PER_ROW
+    idx = np.arange(m * k, dtype=np.uint64)
+    cols = np.minimum((uniform_at(seed, 1, idx) * n).astype(np.int64), n - 1).reshape(m, k)
+    vals = normal_at(seed, 2, idx).reshape(m, k)
+    order = np.argsort(cols, axis=1, kind="stable")
+    cols = np.take_along_axis(cols, order, axis=1)
+    vals = np.take_along_axis(vals, order, axis=1)
+    for e in range(1, k):                 # repeated columns: running sum into the first entry
+        dup = cols[:, e] == cols[:, e - 1]
+        if dup.any():
+            r = np.nonzero(dup)[0]
+            first = e - 1
+            while True:
+                back = (first > 0) & (cols[r, np.maximum(first - 1, 0)] == cols[r, e])
+                if not np.any(back):
+                    break
+                first = np.where(back, first - 1, first)
+            vals[r, first] += vals[r, e]
+            vals[r, e] = 0.0
+    a_rowptr = np.arange(0, m * k + 1, k, dtype=np.int64)
+    x0 = np.abs(normal_at(seed, 4, np.arange(n, dtype=np.uint64)))
+    b = np.zeros(m)
+    for e in range(k):
+        b += vals[:, e] * x0[cols[:, e]]
+    c = normal_at(seed, 3, np.arange(n, dtype=np.uint64))
+    q = uniform_at(seed, 5, np.arange(n, dtype=np.uint64))
+    d = 2 * int(uniform_at(seed, 7, np.zeros(1, dtype=np.uint64))[0] * (n // 2)) + 1
+    j = np.arange(n, dtype=np.int64)
+    even = (j % 2) == 0
+    partner = np.where(even, (j + d) % n, (j - d) % n)
+    anchor = np.where(even, j, partner)
+    w = np.abs(normal_at(seed, 6, anchor.astype(np.uint64)))
+    lo_first = j < partner
+    p_colind = np.stack([np.where(lo_first, j, partner), np.where(lo_first, partner, j)], axis=1).ravel()
+    p_val = np.stack([np.where(lo_first, w, -w), np.where(lo_first, -w, w)], axis=1).ravel()
+    p_rowptr = np.arange(0, 2 * n + 1, 2, dtype=np.int64)
+    btype, bstart, bdim, balpha = blocks_from_list([(CONE_NONNEG, n, 0.0)])
+    return make_instance("large_qp_n%d_m%d" % (n, m), m, n, a_rowptr, cols.ravel(), vals.ravel(), c, b,
+                         btype, bstart, bdim, balpha, q_diag=q, p_csr=(p_rowptr, p_colind, p_val), x_feasible=x0)
+
 CONFIGS = {
     1: lambda: sparse_qp_nonneg(),
     2: lambda: socp_mix(),
     3: lambda: fisher_market(),
     4: lambda: portfolio_batch(),
 }
+# config 5 (n = 2e8, m = 5e7, 1e9 nonzeros) is generated on the device: instances.gpu.large_qp_device
 
 
 def small_config(k: int):
@@ -453,4 +546,6 @@ def small_config(k: int):
         return fisher_market(n_buyers=200, n_goods=40, density=0.1, seed=2003)
     if k == 4:
         return portfolio_batch(count=12, n_range=(20, 60), k_range=(3, 8), seed=2004)
+    if k == 5:
+        return large_qp(n=20_000, m=5_000, seed=2005)
     raise KeyError(k)
