@@ -699,7 +699,7 @@ struct Handle : HandleBase {
       W.u[i] = mem.alloc<T>(n);
       W.g[i] = P.qmode == cqp::kQSparse ? mem.alloc<T>(n) : nullptr;
     }
-    W.ax = mem.alloc<T>(n); W.ay = mem.alloc<T>(mm); W.wy = mem.alloc<T>(mm); W.v = mem.alloc<T>(n);
+    W.ax = mem.alloc<T>(n); W.ay = mem.alloc<T>(mm); W.wy = mem.alloc<T>(mm); W.v = mem.alloc<T>(n); W.z = mem.alloc<T>(n);
     W.avx = o.update == 1 ? mem.alloc<T>(n) : nullptr;
     W.avy = o.update == 1 ? mem.alloc<T>(mm) : nullptr;
     W.mbuf = mem.alloc<T>(n);

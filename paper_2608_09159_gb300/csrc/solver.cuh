@@ -67,6 +67,7 @@ struct Work {
   T* ax; T* ay;         // anchors
   T* wx[2]; T* wy;      // stored candidates (x double-buffered for the movement)
   T* v;                 // x + tau A'y
+  T* z;                 // 2 w_x - h_x, the operand of the dual step's row products
   T* u[2];              // inner iterates
   T* g[2];              // gradients (sparse-P mode)
   T* avx; T* avy;       // running averages (averaged variant)
@@ -164,34 +165,37 @@ __device__ void make_own(const Prob<T>& P, int b, int nb, Own& o) {
 // CSR row products by groups of G lanes; every lane of the group gets the sum.
 // X(j) returns the operand for column j.
 // ---------------------------------------------------------------------------
-// Entries of one row handled by lane gl of a G-lane group, kUnroll at a time:
-// the column indices and values of a batch are loaded first and the operand
-// gathers of the batch are issued together, so each lane keeps several
-// independent loads in flight (the persistent kernel runs only 16 warps per SM).
+// Entries of one row handled by lane gl of a G-lane group, kBatch<G> at a time:
+// the column indices and values of a batch are loaded first (the last, partial
+// batch under a predicate) and the operand gathers of the batch are issued
+// together, so each lane keeps several independent loads in flight (the
+// persistent kernel runs only 16 warps per SM).  Narrow groups get wider batches.
 // ci and v are read-only for the whole kernel, hence the non-coherent loads;
 // the gathered operands are written by other phases and use plain loads.
 constexpr int kUnroll = 4;
+template <int G> struct RowBatch { static constexpr int value = G <= 2 ? 8 : 4; };
 
 template <int G, typename Acc, typename T, typename X>
 __device__ __forceinline__ Acc seg_dot(const int* __restrict__ ci, const T* __restrict__ v, int beg, int end, int gl,
                                        X xf) {
+  constexpr int U = RowBatch<G>::value;
   Acc s = Acc(0);
-  int k = beg + gl;
-  for (; k + (kUnroll - 1) * G < end; k += kUnroll * G) {
-    int j[kUnroll];
-    T a[kUnroll];
+  for (int k = beg + gl; k < end; k += U * G) {
+    int j[U];
+    T a[U];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      j[u] = __ldg(ci + k + u * G);
-      a[u] = __ldg(v + k + u * G);
+    for (int u = 0; u < U; ++u) {
+      const int kk = k + u * G;
+      const bool ok = kk < end;
+      j[u] = ok ? __ldg(ci + kk) : -1;
+      a[u] = ok ? __ldg(v + kk) : T(0);
     }
-    Acc g[kUnroll];
+    Acc g[U];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) g[u] = (Acc)xf(j[u]);
+    for (int u = 0; u < U; ++u) g[u] = j[u] >= 0 ? (Acc)xf(j[u]) : Acc(0);
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) s += (Acc)a[u] * g[u];
+    for (int u = 0; u < U; ++u) s += (Acc)a[u] * g[u];
   }
-  for (; k < end; k += G) s += (Acc)__ldg(v + k) * (Acc)xf(__ldg(ci + k));
   return s;
 }
 

@@ -17,32 +17,28 @@ __device__ __forceinline__ void rows_loop2(const int* rp, const int* ci, const T
     Acc s1 = Acc(0), s2 = Acc(0);
     if (ok) {
       const int beg = rp[r], end = rp[r + 1];
-      int k = beg + gl;
-      for (; k + (kUnroll - 1) * G < end; k += kUnroll * G) {
-        int j[kUnroll];
-        T a[kUnroll];
+      constexpr int U = RowBatch<G>::value;
+      for (int k = beg + gl; k < end; k += U * G) {
+        int j[U];
+        T a[U];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-          j[u] = __ldg(ci + k + u * G);
-          a[u] = __ldg(v + k + u * G);
+        for (int u = 0; u < U; ++u) {
+          const int kk = k + u * G;
+          const bool okk = kk < end;
+          j[u] = okk ? __ldg(ci + kk) : -1;
+          a[u] = okk ? __ldg(v + kk) : T(0);
         }
-        Acc g1[kUnroll], g2[kUnroll];
+        Acc g1[U], g2[U];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-          g1[u] = (Acc)x1(j[u]);
-          g2[u] = (Acc)x2(j[u]);
+        for (int u = 0; u < U; ++u) {
+          g1[u] = j[u] >= 0 ? (Acc)x1(j[u]) : Acc(0);
+          g2[u] = j[u] >= 0 ? (Acc)x2(j[u]) : Acc(0);
         }
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
+        for (int u = 0; u < U; ++u) {
           s1 += (Acc)a[u] * g1[u];
           s2 += (Acc)a[u] * g2[u];
         }
-      }
-      for (; k < end; k += G) {
-        const int j = __ldg(ci + k);
-        const Acc a = (Acc)__ldg(v + k);
-        s1 += a * (Acc)x1(j);
-        s2 += a * (Acc)x2(j);
       }
     }
     s1 = group_sum<G>(s1);
@@ -377,29 +373,40 @@ __device__ void Solver<T, Team>::run(long long budget) {
     T mov_acc = T(0);
     T* hyn = W.hy[hb ^ 1];
     const T sg = T(sigma), tc1 = T(c1), tc2 = T(c2), tr1 = T(r1), tr2 = T(r2), tkk = T(kk);
-    rows_loop2_tpr<T>(
-        P.tpr_a, P.a_rp, P.a_ci, P.a_v, own.row0, own.row1,
-        [&](int j) { return T(2) * wxn[j] - hx[j]; }, [&](int j) { return needE ? hx[j] - wxn[j] : T(0); },
-        [&](int64_t r, int gl, T s1, T s2) {
-          if (gl != 0) return;
-          const T h = hy[r];
-          const T wy = h + sg * (P.b[r] - s1);   // eq. stored-pdhg-candidate
-          W.wy[r] = wy;
-          if (halpern_now) hyn[r] = tc1 * (tr2 * wy + tr1 * h) + tc2 * W.ay[r];   // eq. rh-update
-          if (avg) {
-            hyn[r] = wy;
-            W.avy[r] = (tkk * W.avy[r] + wy) / (tkk + T(1));
-          }
-          if (needE) {
-            const double dy = (double)h - (double)wy;
-            v6[2] += dy * dy;
-            v6[3] += (double)s2 * dy;
-          }
-          if (check) {
-            const double e = (double)wy - (double)W.ay[r];
-            v6[5] += e * e;
-          }
-        });
+    auto dual_row = [&](int64_t r, int gl, T s1, T s2) {
+      if (gl != 0) return;
+      const T h = hy[r];
+      const T wy = h + sg * (P.b[r] - s1);   // eq. stored-pdhg-candidate
+      W.wy[r] = wy;
+      if (halpern_now) hyn[r] = tc1 * (tr2 * wy + tr1 * h) + tc2 * W.ay[r];   // eq. rh-update
+      if (avg) {
+        hyn[r] = wy;
+        W.avy[r] = (tkk * W.avy[r] + wy) / (tkk + T(1));
+      }
+      if (needE) {
+        const double dy = (double)h - (double)wy;
+        v6[2] += dy * dy;
+        v6[3] += (double)s2 * dy;
+      }
+      if (check) {
+        const double e = (double)wy - (double)W.ay[r];
+        v6[5] += e * e;
+      }
+    };
+    if (needE) {
+      rows_loop2_tpr<T>(P.tpr_a, P.a_rp, P.a_ci, P.a_v, own.row0, own.row1,
+                        [&](int j) { return T(2) * wxn[j] - hx[j]; }, [&](int j) { return hx[j] - wxn[j]; },
+                        dual_row);
+    } else {
+      // between checks the row products need only 2 w_x - h_x: written once for the owned
+      // coordinates, it is gathered as one operand instead of two
+      T* zv = W.z;
+      for (int seg = 0; seg < 6; ++seg)
+        for (int64_t i = own.x0[seg] + threadIdx.x; i < own.x1[seg]; i += blockDim.x) zv[i] = T(2) * wxn[i] - hx[i];
+      if (!team.sync()) return;
+      rows_loop_tpr<T>(P.tpr_a, P.a_rp, P.a_ci, P.a_v, own.row0, own.row1, [&](int j) { return zv[j]; },
+                       [&](int64_t r, int gl, T s1) { dual_row(r, gl, s1, T(0)); });
+    }
     T* hxn = W.hx[hb ^ 1];
     T* wxs = W.wx[wb ^ 1];
     const T* wxp = W.wx[wb];
