@@ -25,7 +25,12 @@
  *    point states which it expects.
  *  - A stream argument (cudaStream_t passed as void*) may be NULL for the
  *    default stream.  Entry points that return results to the host
- *    synchronise that stream before returning.
+ *    synchronise that stream before returning.  A handle allocates and frees
+ *    its device memory in order on its stream (opt->stream), so that stream
+ *    must outlive the handle.
+ *  - Device memory comes from a memory pool the library keeps per device;
+ *    memory freed by the library stays reserved for its later allocations
+ *    until the process exits (repeated set-ups then cost no driver calls).
  *  - The library needs a GB300 (sm_103a); on any CUDA error the call returns
  *    CQP_ERR_CUDA and cqp_last_error() describes it.
  */
@@ -122,7 +127,7 @@ typedef struct {
   int32_t team;             /* 0 auto, 1 whole-GPU cooperative kernel, 2 one thread block */
   int32_t threads;          /* threads per block, 0 = auto */
   int32_t blocks_per_sm;    /* 0 = auto (cooperative team only) */
-  int32_t tpr_a, tpr_at;    /* threads per CSR row for A and A', 0 = autotuned */
+  int32_t tpr_a, tpr_at;    /* threads per CSR row for A and A', 0 = autotuned (timed per matrix shape, cached) */
   int32_t launch_iters;     /* outer iterations per kernel launch, 0 = auto */
   int32_t profile;          /* 1: record per-phase device time in cqp_result.phase_ms */
   int32_t warm_roots;       /* 1: start each cone block's root-finding from its previous root (default 1) */

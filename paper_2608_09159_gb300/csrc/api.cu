@@ -9,6 +9,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -44,28 +47,57 @@ void fail(int code, const std::string& msg) {
     }                                                                                                         \
   } while (0)
 
-// device allocations owned by a handle
+// The library's device memory comes from its own stream-ordered pool, one per device,
+// which keeps freed blocks for reuse (release threshold at its maximum): repeated set-ups
+// and solves then allocate without driver calls or device-wide synchronisation.  Memory
+// freed by the library stays reserved for it until the process exits.
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64] = {};
+
+cudaMemPool_t lib_pool() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) fail(CQP_ERR_CUDA, "no current device");
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) fail(CQP_ERR_CUDA, "cudaMemPoolCreate failed");
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &thr);
+    g_pool[dev] = p;
+  }
+  return g_pool[dev];
+}
+
+// device allocations owned by a handle (stream-ordered on the handle's stream, which
+// must outlive the handle)
 struct Arena {
   std::vector<void*> ptrs;
+  cudaStream_t st = nullptr;
   template <typename U>
   U* alloc(int64_t n) {
     void* p = nullptr;
     const size_t bytes = (size_t)std::max<int64_t>(n, 1) * sizeof(U);
-    cudaError_t e = cudaMalloc(&p, bytes);
-    if (e != cudaSuccess) fail(e == cudaErrorMemoryAllocation ? CQP_ERR_OOM : CQP_ERR_CUDA, "cudaMalloc failed");
+    cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, lib_pool(), st);
+    if (e != cudaSuccess) fail(e == cudaErrorMemoryAllocation ? CQP_ERR_OOM : CQP_ERR_CUDA, "device allocation failed");
     ptrs.push_back(p);
     return (U*)p;
   }
   void release() {
-    for (void* p : ptrs) cudaFree(p);
+    for (void* p : ptrs) cudaFreeAsync(p, st);
     ptrs.clear();
   }
   ~Arena() { release(); }
 };
 
-// scoped temporary allocations (setup only)
+// scoped temporary allocations (set-up, solve and KKT helpers)
 struct Temp {
   Arena a;
+  explicit Temp(cudaStream_t s) { a.st = s; }
   template <typename U>
   U* alloc(int64_t n) { return a.alloc<U>(n); }
 };
@@ -155,6 +187,11 @@ __global__ void k_state_set_th(cqp::State* S, const double* t, int k) {
     for (int l = 0; l < k; ++l) S->t_h[l] = t[l];
 }
 
+// threads-per-row decisions of the timing autotuner, per device and matrix shape
+// (rows, nonzeros, value size), so later set-ups of same-shaped problems skip the sweep
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int64_t, int64_t, int>, int> g_tune_cache;
+
 int pow2_tpr(double mean) {
   int t = 1;
   while (t < 32 && t < mean) t <<= 1;
@@ -215,6 +252,7 @@ struct Handle : HandleBase {
     const long long launches0 = g_launches;
     opt = o;
     st = (cudaStream_t)o.stream;
+    mem.st = st;
     int dev = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -222,7 +260,7 @@ struct Handle : HandleBase {
     n = A->ncols;
     nnz = A->nnz;
     const bool on_dev = o.input_on_device != 0;
-    Temp tmp;
+    Temp tmp(st);
     auto upload = [&](const void* src, size_t bytes) -> const void* {
       if (!src) return nullptr;
       if (on_dev) return src;
@@ -655,24 +693,33 @@ struct Handle : HandleBase {
     else if (k > 0 || o.force_inner) P.qmode = cqp::kQLowRank;
     else P.qmode = cqp::kQDiag;
     P.euclid_cones = (P.qmode == cqp::kQDiag && qcone == 0.0) ? 1 : 0;
-    // threads per CSR row: user choice, else the fastest of 1..32 lanes measured on this
-    // matrix with the solver's row kernel (CUDA events, best of 3 after one warm-up)
+    // threads per CSR row: user choice, else the fastest of 1..16 lanes measured on this
+    // matrix shape with the solver's row kernel (CUDA events, best of 2 after one warm-up),
+    // remembered per device and shape for the rest of the process
     {
       T* xs = tmp.alloc<T>(n);
       T* ys = tmp.alloc<T>(std::max<int64_t>(std::max(m, n), 1));
       count_launch(); cqp::k_convert<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, jdv, xs);
-      auto tune = [&](int64_t rows, const int32_t* rp, const int32_t* ci, const T* v) {
+      auto tune = [&](int64_t rows, int64_t nz, const int32_t* rp, const int32_t* ci, const T* v) {
         if (rows == 0) return 1;
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        const auto key = std::make_tuple(dev, rows, nz, (int)sizeof(T));
+        {
+          std::lock_guard<std::mutex> lock(g_tune_mu);
+          auto it = g_tune_cache.find(key);
+          if (it != g_tune_cache.end()) return it->second;
+        }
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
         int best = 8;
         float best_ms = 1e30f;
-        for (int t = 1; t <= 32; t <<= 1) {
+        for (int t = 1; t <= 16; t <<= 1) {   // 32 lanes per row never won on these matrices
           count_launch();
           CK(cqp::launch_spmv<T>(rows, rp, ci, v, xs, ys, t, st));
           float tot = 1e30f;
-          for (int r = 0; r < 3; ++r) {
+          for (int r = 0; r < 2; ++r) {
             CK(cudaEventRecord(e0, st));
             count_launch();
             CK(cqp::launch_spmv<T>(rows, rp, ci, v, xs, ys, t, st));
@@ -686,11 +733,13 @@ struct Handle : HandleBase {
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = best;
         return best;
       };
-      P.tpr_a = o.tpr_a > 0 ? o.tpr_a : tune(m, a_rp, a_ci, a_v);
-      P.tpr_t = o.tpr_at > 0 ? o.tpr_at : tune(n, t_rp, t_ci, t_v);
-      P.tpr_p = has_p ? tune(n, p_rp, p_ci, pT) : 1;
+      P.tpr_a = o.tpr_a > 0 ? o.tpr_a : tune(m, nnz, a_rp, a_ci, a_v);
+      P.tpr_t = o.tpr_at > 0 ? o.tpr_at : tune(n, nnz, t_rp, t_ci, t_v);
+      P.tpr_p = has_p ? tune(n, pnnz, p_rp, p_ci, pT) : 1;
     }
     // ---- work buffers and state -------------------------------------------------------------
     const int64_t mm = std::max<int64_t>(m, 1);
@@ -761,7 +810,7 @@ struct Handle : HandleBase {
     if (batched) fail(CQP_ERR_UNSUPPORTED, "handle was made by cqp_setup_batch: use cqp_solve_batch");
     auto t0 = std::chrono::steady_clock::now();
     const int64_t mm = std::max<int64_t>(m, 1);
-    Temp tmp;
+    Temp tmp(st);
     const double* dx0 = x0;
     const double* dy0 = y0;
     if (!on_dev) {
@@ -864,7 +913,7 @@ struct Handle : HandleBase {
     if (!batched) fail(CQP_ERR_UNSUPPORTED, "handle was made by cqp_setup: use cqp_solve");
     auto t0 = std::chrono::steady_clock::now();
     const int64_t mm = std::max<int64_t>(m, 1);
-    Temp tmp;
+    Temp tmp(st);
     const double* dx0 = x0;
     const double* dy0 = y0;
     if (!on_dev) {
@@ -964,7 +1013,7 @@ struct Handle : HandleBase {
   int kkt(const double* x, const double* y, int on_dev, cqp_kkt_report* rep) override {
     if (batched) fail(CQP_ERR_UNSUPPORTED, "cqp_kkt on a batch handle: each instance reports its KKT in cqp_solve_batch");
     const int64_t mm = std::max<int64_t>(m, 1);
-    Temp tmp;
+    Temp tmp(st);
     const double* dx = x;
     const double* dy = y;
     if (!on_dev) {
