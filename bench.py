@@ -20,6 +20,14 @@ cold start) is timed once as the comparison the metric names.
 With --gpus N under torchrun each rank solves its own instance (seed + rank):
 replicas, no collectives; rank 0 prints the max-over-ranks time.
 --impl reference times the FP64 CPU oracle on the host cores instead.
+
+Other workloads (not the default line):
+  --workload portfolio  4,096 uneven portfolio QPs solved in one batched launch
+                        (setup + solve of the whole batch per step); with
+                        --ws-train N a warm-start network is first trained on N
+                        solved instances and the warm-started step is timed too.
+  --workload large      the large sparse QP (n = --large-n, m = n/4, 20 nnz per
+                        row), generated in device memory; setup + solve per step.
 """
 from __future__ import annotations
 
@@ -119,10 +127,14 @@ def algorithmic_bytes(inst, res, esize=4, isize=4):
     return res["iters"] * (aty + dual) + res["inner_total"] * inner + checks * kkt
 
 
+SOLVER_SOURCES = ("common.cuh", "cones.cuh", "solver.cuh", "solver_impl.cuh", "kernels.inc", "solver_f32.cu")
+
+
 def _source_hash():
+    """Hash of the sources that make up pdhg_grid_kernel<float>."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2608_09159_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in SOLVER_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -309,6 +321,128 @@ def run_ours(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def _timed(fn, steps, warmup, flush):
+    import torch
+    for _ in range(warmup):
+        flush.fill_(1.0)
+        fn()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    times, out = [], None
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    return times, out
+
+
+def run_portfolio(args):
+    import numpy as np
+    import torch
+
+    import instances
+    import paper_2608_09159_gb300 as g
+    from paper_2608_09159_gb300 import warmstart as W
+    g.build()
+    g.lib()
+    batch = instances.portfolio_batch()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    opts = dict(precision=0, tol=1e-4, max_iter=100000, time_limit_s=600.0)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    launches0 = g.cqp_kernel_launches()
+    times, (x, y, per, res) = _timed(lambda: W.solve_batch(batch, None, **opts), args.steps, args.warmup, flush)
+    launches = (g.cqp_kernel_launches() - launches0) // max(args.steps + args.warmup, 1)
+    its = np.array([r["iters"] for r in per])
+    line = {"metric": "time to 1e-4 rel KKT on every instance of the batch", "value": statistics.mean(times),
+            "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": statistics.mean(times) * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (Philox-seeded)",
+            "config": {"workload": "portfolio_batch: 4096 instances, n_i ~ U[50,2000] assets, k_i ~ U[10,50] "
+                                   "factors, seed 1004", "n": batch["n"], "m": batch["m"],
+                       "nnz": int(batch["a_rowptr"][-1]), "l2": "flushed before every step (256 MB write)",
+                       "inputs": "host arrays copied to the device inside the step"},
+            "batch": {"converged": int(sum(r["rc"] == 0 for r in per)), "count": len(per),
+                      "iters_mean": float(its.mean()), "iters_max": int(its.max()),
+                      "inner_total": res["inner_total"], "kernel_ms": res["kernel_ms"], "setup_ms": res["setup_ms"],
+                      "max_rel_kkt": max(r["kkt"]["rel_kkt"] for r in per)},
+            "gpu_launches": launches}
+    if args.ws_train > 0:
+        data = W.TrainingSet()
+        per_batch = min(4096, args.ws_train)
+        nb = (args.ws_train + per_batch - 1) // per_batch
+        for k in range(nb):
+            tb = instances.portfolio_batch(count=per_batch, seed=11001 + k)
+            xt, yt, pt, rt = W.solve_batch(tb, None, **opts)
+            data.add(tb, xt.cpu().numpy(), yt.cpu().numpy())
+        net = W.WarmStartNet(seed=1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        W.train(net, data, steps=args.ws_steps, instances=256, lr=1e-3)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        del data
+        wt, (xw, yw, pw, rw) = _timed(lambda: W.solve_batch(batch, net, **opts), args.steps, args.warmup, flush)
+        iw = np.array([r["iters"] for r in pw])
+        line["warm_start"] = {"value": statistics.mean(wt), "unit": "s", "trained_on": nb * per_batch,
+                              "train_steps": args.ws_steps, "train_s": t_train, "iters_mean": float(iw.mean()),
+                              "kernel_ms": rw["kernel_ms"], "converged": int(sum(r["rc"] == 0 for r in pw)),
+                              "max_rel_kkt": max(r["kkt"]["rel_kkt"] for r in pw)}
+    line["clocks"] = clocks.stop()
+    print(json.dumps(line), flush=True)
+
+
+def run_large(args):
+    import torch
+
+    import paper_2608_09159_gb300 as g
+    from instances import gpu as G
+    g.build()
+    g.lib()
+    n = int(args.large_n)
+    n -= n % 2
+    m = n // 4
+    inst = G.large_qp_device(n=n, m=m, seed=1005)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def step():
+        s = g.Solver(inst, device=True, precision=0, tol=1e-4, max_iter=1000000, time_limit_s=900.0)
+        out = s.solve(out_device=True)
+        s.close()
+        return out
+
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    times, (x, y, res) = _timed(step, args.steps, args.warmup, flush)
+    nnz, pnnz = m * 20, 2 * n
+    # algorithmic bytes (FP32 values, int32 indices): A' and A passes with their vectors
+    # per outer iteration, P and 9 n-vectors per inner step
+    per_it = 2 * (nnz * 8 + (n + m) * 4) + 8 * n * 4 + 6 * m * 4
+    per_inner = pnnz * 8 + n * 4 + 8 * n * 4
+    alg = res["iters"] * per_it + res["inner_total"] * per_inner
+    peaks, src = _peaks()
+    achieved = alg / (res["kernel_ms"] / 1e3) / 1e9
+    line = {"metric": "time to 1e-4 rel KKT", "value": statistics.mean(times), "unit": "s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(times) * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (Philox-seeded, generated in device memory)",
+            "config": {"workload": "large_qp: n=%d nonneg, m=%d, 20 nnz per row, Q = diag(U[0,1]) + matching "
+                                   "Laplacian, seed 1005" % (n, m), "n": n, "m": m, "nnz": nnz, "pnnz": pnnz,
+                       "inputs": "device-resident FP64"},
+            "solve": {"rc": res["rc"], "iters": res["iters"], "inner_total": res["inner_total"],
+                      "rel_kkt": res["kkt"]["rel_kkt"], "setup_ms": res["setup_ms"], "kernel_ms": res["kernel_ms"]},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
+                         "kernel": "pdhg_grid_kernel<float>", "algorithmic_bytes_per_solve": alg},
+            "clocks": clocks.stop()}
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(inst, iters_to_tol, args):
     """The FP64 oracle (single thread) on a bounded sample of the same workload: setup plus
     `sample_iters` outer iterations, extrapolated to the iteration count the FP64 method needs
@@ -363,7 +497,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle", action="store_true")
     ap.add_argument("--small", action="store_true", help="10x smaller instance (quick checks)")
+    ap.add_argument("--workload", default="socp", choices=["socp", "portfolio", "large"])
+    ap.add_argument("--ws-train", type=int, default=0, help="portfolio: instances to train the warm start on")
+    ap.add_argument("--ws-steps", type=int, default=3000, help="portfolio: warm-start training steps")
+    ap.add_argument("--large-n", type=float, default=2e8, help="large: number of variables")
     args = ap.parse_args()
+    if args.workload != "socp" and args.impl == "ours":
+        (run_portfolio if args.workload == "portfolio" else run_large)(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1 and args.impl == "ours":

@@ -29,12 +29,34 @@ def _p(t):
     return None if t is None else t.data_ptr()
 
 
+_DEVICE_KEYS = {"a_rowptr": np.int64, "a_colind": np.int32, "a_val": np.float64, "c": np.float64, "b": np.float64,
+                "q_diag": np.float64, "q_R": np.float64, "q_D": np.float64, "blk_type": np.int32,
+                "blk_start": np.int64, "blk_dim": np.int64, "blk_alpha": np.float64}
+
+
+def _cuda(a, dt):
+    import torch
+    if hasattr(a, "data_ptr"):
+        return a
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).cuda()
+
+
+def to_device(batch):
+    """The batch with its problem arrays copied to the device once (shared by the solver
+    and the warm start)."""
+    out = dict(batch)
+    for k, dt in _DEVICE_KEYS.items():
+        if batch.get(k) is not None:
+            out[k] = _cuda(batch[k], dt)
+    return out
+
+
 class BatchDevice:
-    """Device copies of the arrays of a portfolio batch that the warm start reads."""
+    """Device copies of the arrays of a portfolio batch that the warm start reads
+    (arrays that are already CUDA tensors are used in place)."""
 
     def __init__(self, batch):
-        import torch
-        cuda = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).cuda()
+        cuda = _cuda
         self.count = int(batch["batch_count"])
         self.n, self.m = int(batch["n"]), int(batch["m"])
         na = np.asarray(batch["n_assets"], dtype=np.int64)
@@ -189,11 +211,12 @@ def train(net: WarmStartNet, data: TrainingSet, steps: int, instances: int = 256
 def solve_batch(batch, net: WarmStartNet | None = None, dual_mode: int = 1, **opts):
     """Batched solve of a portfolio batch, from the network's start when `net` is given,
     else from zero.  Returns (x, y, per-instance results, summary)."""
-    s = BatchSolver(batch, device=True, **opts)
+    dbatch = to_device(batch)
+    s = BatchSolver(dbatch, device=True, **opts)
     try:
         if net is None:
             return s.solve(out_device=True)
-        x0, y0 = net.start(BatchDevice(batch), dual_mode=dual_mode)
+        x0, y0 = net.start(BatchDevice(dbatch), dual_mode=dual_mode)
         return s.solve(x0=x0, y0=y0, out_device=True)
     finally:
         s.close()
