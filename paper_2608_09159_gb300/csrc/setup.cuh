@@ -271,6 +271,30 @@ __global__ void k_spmv_simple(int64_t m, const int32_t* rp, const int32_t* ci, c
 // same stop decision.  out[0] = ||A~||_2 estimate, out[1] = iterations.
 constexpr int kPowerThreads = 512;
 
+// one CSR row product in FP64, eight entries at a time (indices and values first, then
+// the gathers together) so each thread keeps several loads in flight
+template <typename T>
+__device__ __forceinline__ double power_row(int beg, int end, const int32_t* __restrict__ ci,
+                                            const T* __restrict__ v, const double* x) {
+  double s = 0.0;
+  for (int k = beg; k < end; k += 8) {
+    int j[8];
+    double a[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const bool ok = k + u < end;
+      j[u] = ok ? __ldg(ci + k + u) : -1;
+      a[u] = ok ? (double)__ldg(v + k + u) : 0.0;
+    }
+    double g[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) g[u] = j[u] >= 0 ? x[j[u]] : 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += a[u] * g[u];
+  }
+  return s;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kPowerThreads, 1)
     k_power(int64_t m, int64_t n, const int32_t* __restrict__ a_rp, const int32_t* __restrict__ a_ci,
@@ -288,9 +312,7 @@ __global__ void __launch_bounds__(kPowerThreads, 1)
   for (; it < iters; ++it) {
     double acc[1] = {0.0};
     for (int64_t r = tid; r < m; r += nt) {
-      double s = 0.0;
-      for (int k = a_rp[r]; k < a_rp[r + 1]; ++k) s += (double)a_v[k] * z[a_ci[k]];
-      s *= zscale;
+      const double s = power_row(a_rp[r], a_rp[r + 1], a_ci, a_v, z) * zscale;
       w[r] = s;
       acc[0] += s * s;
     }
@@ -301,8 +323,7 @@ __global__ void __launch_bounds__(kPowerThreads, 1)
     const double s_new = sqrt(tot[0]);
     acc[0] = 0.0;
     for (int64_t j = tid; j < n; j += nt) {
-      double s = 0.0;
-      for (int k = t_rp[j]; k < t_rp[j + 1]; ++k) s += (double)t_v[k] * w[t_ci[k]];
+      const double s = power_row(t_rp[j], t_rp[j + 1], t_ci, t_v, w);
       z[j] = s;
       acc[0] += s * s;
     }
