@@ -28,6 +28,7 @@ Other workloads (not the default line):
                         solved instances and the warm-started step is timed too.
   --workload large      the large sparse QP (n = --large-n, m = n/4, 20 nnz per
                         row), generated in device memory; setup + solve per step.
+  --workload gemm       the warm-start network's BF16 GEMMs at the training shape.
 """
 from __future__ import annotations
 
@@ -443,6 +444,54 @@ def run_large(args):
     print(json.dumps(line), flush=True)
 
 
+def run_gemm(args):
+    """The warm-start network's GEMMs at the training shape (262,144 asset rows, width 512)."""
+    import torch
+
+    import paper_2608_09159_gb300 as g
+    g.build()
+    g.lib()
+    rows, H = 262144, 512
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    H1 = torch.randn(rows, H, device="cuda", generator=gen).to(torch.bfloat16)
+    Wt = torch.randn(H, H, device="cuda", generator=gen).to(torch.bfloat16)
+    out = torch.empty(rows, H, dtype=torch.bfloat16, device="cuda")
+    gw = torch.zeros(H, H, dtype=torch.float32, device="cuda")
+    bias = torch.zeros(H, device="cuda")
+    cases = {
+        "forward Z2 = H1 W2 (+bias, ReLU, BF16 out)":
+            lambda: g.cqp_gemm_bf16(0, 0, rows, H, H, H1.data_ptr(), H, Wt.data_ptr(), H, out.data_ptr(), H,
+                                    bias.data_ptr(), 2),
+        "backward dH1 = dZ2 W2' (BF16 out)":
+            lambda: g.cqp_gemm_bf16(0, 1, rows, H, H, H1.data_ptr(), H, Wt.data_ptr(), H, out.data_ptr(), H, None, 4),
+        "backward dW2 += H1' dZ2 (split-K, FP32 atomics)":
+            lambda: g.cqp_gemm_bf16(1, 0, H, H, rows, H1.data_ptr(), H, out.data_ptr(), H, gw.data_ptr(), H, None, 3,
+                                    128)}
+    peaks, src = _peaks()
+    res = {}
+    for name, fn in cases.items():
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        res[name] = {"ms": ms, "tflops": 2.0 * rows * H * H / ms / 1e9}
+    best = max(v["tflops"] for v in res.values())
+    line = {"metric": "warm-start GEMM throughput", "value": statistics.mean(v["tflops"] for v in res.values()),
+            "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "dtype": "bf16 (FP32 accumulation)", "data": "synthetic",
+            "config": {"workload": "MLP layer 2: 262144 x 512 x 512"}, "gemms": res,
+            "roofline": {"bound": "tensor", "achieved": best, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                         "frac": best / peaks["bf16_tflops"], "peak_source": src, "kernel": "k_gemm_bf16_v"}}
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(inst, iters_to_tol, args):
     """The FP64 oracle (single thread) on a bounded sample of the same workload: setup plus
     `sample_iters` outer iterations, extrapolated to the iteration count the FP64 method needs
@@ -497,13 +546,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle", action="store_true")
     ap.add_argument("--small", action="store_true", help="10x smaller instance (quick checks)")
-    ap.add_argument("--workload", default="socp", choices=["socp", "portfolio", "large"])
+    ap.add_argument("--workload", default="socp", choices=["socp", "portfolio", "large", "gemm"])
     ap.add_argument("--ws-train", type=int, default=0, help="portfolio: instances to train the warm start on")
     ap.add_argument("--ws-steps", type=int, default=3000, help="portfolio: warm-start training steps")
     ap.add_argument("--large-n", type=float, default=2e8, help="large: number of variables")
     args = ap.parse_args()
     if args.workload != "socp" and args.impl == "ours":
-        (run_portfolio if args.workload == "portfolio" else run_large)(args)
+        {"portfolio": run_portfolio, "large": run_large, "gemm": run_gemm}[args.workload](args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstdint>
 #include <string>
+#include <type_traits>
 
 #include "cqp.h"
 #include "cqp_mlp.h"
@@ -186,6 +187,140 @@ __global__ void __launch_bounds__(256) k_gemm_bf16(int64_t M, int64_t N, int64_t
     __syncthreads();
   }
   // epilogue through a per-warp 16 x 16 staging tile
+  float* cs = Cs[warp];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      wmma::store_matrix_sync(cs, acc[i][j], 16, wmma::mem_row_major);
+      __syncwarp();
+      for (int e = lane; e < 256; e += 32) {
+        const int r = e >> 4, cc = e & 15;
+        const int64_t gm = m0 + wm * 32 + i * 16 + r, gn = n0 + wn * 64 + j * 16 + cc;
+        if (gm < M && gn < N) {
+          float v = cs[e];
+          if (epi == 3) {
+            atomicAdd(reinterpret_cast<float*>(C) + gm * ldc + gn, v);
+          } else {
+            if (bias && (epi == 1 || epi == 2)) v += bias[gn];
+            if (epi == 2) reinterpret_cast<bf16*>(C)[gm * ldc + gn] = __float2bfloat16(v > 0.f ? v : 0.f);
+            else if (epi == 4) reinterpret_cast<bf16*>(C)[gm * ldc + gn] = __float2bfloat16(v);
+            else reinterpret_cast<float*>(C)[gm * ldc + gn] = v;
+          }
+        }
+      }
+      __syncwarp();
+    }
+}
+
+// Vectorised variant for 16-byte aligned operands (leading dimensions multiples of 8):
+// each operand tile is staged in its stored layout with 16-byte loads (a transposed
+// operand is read by column-major fragments, so nothing is transposed through shared
+// memory), and the next K tile is loaded into registers while the current one is
+// multiplied.  Same tiles, epilogues and results as k_gemm_bf16.
+union Pack8 {
+  uint4 v;
+  bf16 h[8];
+};
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) k_gemm_bf16_v(int64_t M, int64_t N, int64_t K, const bf16* __restrict__ A,
+                                                     int64_t lda, const bf16* __restrict__ B, int64_t ldb, void* C,
+                                                     int64_t ldc, const float* __restrict__ bias, int epi,
+                                                     int64_t k_chunk) {
+  // A tile: [TM][TK + APAD] (row-major op(A)) or [TK][TM + APAD] (stored A' layout)
+  // B tile: [TK][TN + BPAD] (row-major op(B)) or [TN][TK + BPAD] (stored B' layout)
+  constexpr int A_ROWS = TA ? TK : TM, A_COLS = (TA ? TM : TK) + APAD;
+  constexpr int B_ROWS = TB ? TN : TK, B_COLS = (TB ? TK : TN) + BPAD;
+  __shared__ __align__(128) bf16 As[A_ROWS][A_COLS];
+  __shared__ __align__(128) bf16 Bs[B_ROWS][B_COLS];
+  __shared__ __align__(32) float Cs[8][16 * 16];
+  using LA = typename std::conditional<TA, wmma::col_major, wmma::row_major>::type;
+  using LB = typename std::conditional<TB, wmma::col_major, wmma::row_major>::type;
+  const int64_t m0 = blockIdx.y * (int64_t)TM, n0 = blockIdx.x * (int64_t)TN;
+  const int64_t kb = blockIdx.z * k_chunk, ke = min(K, kb + k_chunk);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wm = warp >> 1, wn = warp & 1;
+  // each thread moves two 8-element vectors of each tile: vector e covers stored row
+  // e / (cols/8), columns 8 * (e % (cols/8)) .. +7
+  constexpr int AV = (TA ? TM : TK) / 8, BV = (TB ? TK : TN) / 8;
+  Pack8 ra[2], rb[2];
+  auto load_a = [&](int64_t k0) {
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int e = threadIdx.x + t * 256;
+      const int r = e / AV, c = (e % AV) * 8;
+      // stored element (row, col): !TA: (m, k) = A[m * lda + k]; TA: (k, m) = A[k * lda + m]
+      const int64_t grow = TA ? k0 + r : m0 + r, gcol = TA ? m0 + c : k0 + c;
+      const int64_t rlim = TA ? ke : M, clim = TA ? M : ke;
+      const bf16* src = A + grow * lda + gcol;
+      if (grow < rlim && gcol + 7 < clim) {
+        ra[t].v = __ldg(reinterpret_cast<const uint4*>(src));
+      } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) ra[t].h[u] = (grow < rlim && gcol + u < clim) ? src[u] : __float2bfloat16(0.f);
+      }
+    }
+  };
+  auto load_b = [&](int64_t k0) {
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int e = threadIdx.x + t * 256;
+      const int r = e / BV, c = (e % BV) * 8;
+      // stored element: !TB: (k, n) = B[k * ldb + n]; TB: (n, k) = B[n * ldb + k]
+      const int64_t grow = TB ? n0 + r : k0 + r, gcol = TB ? k0 + c : n0 + c;
+      const int64_t rlim = TB ? N : ke, clim = TB ? ke : N;
+      const bf16* src = B + grow * ldb + gcol;
+      if (grow < rlim && gcol + 7 < clim) {
+        rb[t].v = __ldg(reinterpret_cast<const uint4*>(src));
+      } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) rb[t].h[u] = (grow < rlim && gcol + u < clim) ? src[u] : __float2bfloat16(0.f);
+      }
+    }
+  };
+  wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc[2][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) wmma::fill_fragment(acc[i][j], 0.0f);
+  if (kb < ke) {
+    load_a(kb);
+    load_b(kb);
+  }
+  for (int64_t k0 = kb; k0 < ke; k0 += TK) {
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int ea = threadIdx.x + t * 256, eb = threadIdx.x + t * 256;
+      *reinterpret_cast<uint4*>(&As[ea / AV][(ea % AV) * 8]) = ra[t].v;
+      *reinterpret_cast<uint4*>(&Bs[eb / BV][(eb % BV) * 8]) = rb[t].v;
+    }
+    __syncthreads();
+    if (k0 + TK < ke) {   // next tile in flight during the multiply
+      load_a(k0 + TK);
+      load_b(k0 + TK);
+    }
+#pragma unroll
+    for (int kk = 0; kk < TK; kk += 16) {
+      wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, LA> fa[2];
+      wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, LB> fb[4];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const bf16* pa = TA ? &As[kk][wm * 32 + i * 16] : &As[wm * 32 + i * 16][kk];
+        wmma::load_matrix_sync(fa[i], pa, A_COLS);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const bf16* pb = TB ? &Bs[wn * 64 + j * 16][kk] : &Bs[kk][wn * 64 + j * 16];
+        wmma::load_matrix_sync(fb[j], pb, B_COLS);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) wmma::mma_sync(acc[i][j], fa[i], fb[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
   float* cs = Cs[warp];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
@@ -473,10 +608,19 @@ int cqp_gemm_bf16(int32_t trans_a, int32_t trans_b, int64_t M, int64_t N, int64_
   cudaStream_t st = (cudaStream_t)stream;
   const bf16* a = reinterpret_cast<const bf16*>(A);
   const bf16* bb = reinterpret_cast<const bf16*>(B);
-  if (!trans_a && !trans_b) k_gemm_bf16<false, false><<<grid, 256, 0, st>>>(M, N, K, a, lda, bb, ldb, C, ldc, bias, epilogue, kc);
-  else if (!trans_a && trans_b) k_gemm_bf16<false, true><<<grid, 256, 0, st>>>(M, N, K, a, lda, bb, ldb, C, ldc, bias, epilogue, kc);
-  else if (trans_a && !trans_b) k_gemm_bf16<true, false><<<grid, 256, 0, st>>>(M, N, K, a, lda, bb, ldb, C, ldc, bias, epilogue, kc);
-  else k_gemm_bf16<true, true><<<grid, 256, 0, st>>>(M, N, K, a, lda, bb, ldb, C, ldc, bias, epilogue, kc);
+  const bool vec = lda % 8 == 0 && ldb % 8 == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0 &&
+                   (reinterpret_cast<uintptr_t>(B) & 15) == 0;
+  if (vec) {
+    if (!trans_a && !trans_b) k_gemm_bf16_v<false, false><<<grid, 256, 0, st>>>(M, N, K, a, lda, bb, ldb, C, ldc, bias, epilogue, kc);
+    else if (!trans_a && trans_b) k_gemm_bf16_v<false, true><<<grid, 256, 0, st>>>(M, N, K, a, lda, bb, ldb, C, ldc, bias, epilogue, kc);
+    else if (trans_a && !trans_b) k_gemm_bf16_v<true, false><<<grid, 256, 0, st>>>(M, N, K, a, lda, bb, ldb, C, ldc, bias, epilogue, kc);
+    else k_gemm_bf16_v<true, true><<<grid, 256, 0, st>>>(M, N, K, a, lda, bb, ldb, C, ldc, bias, epilogue, kc);
+  } else {
+    if (!trans_a && !trans_b) k_gemm_bf16<false, false><<<grid, 256, 0, st>>>(M, N, K, a, lda, bb, ldb, C, ldc, bias, epilogue, kc);
+    else if (!trans_a && trans_b) k_gemm_bf16<false, true><<<grid, 256, 0, st>>>(M, N, K, a, lda, bb, ldb, C, ldc, bias, epilogue, kc);
+    else if (trans_a && !trans_b) k_gemm_bf16<true, false><<<grid, 256, 0, st>>>(M, N, K, a, lda, bb, ldb, C, ldc, bias, epilogue, kc);
+    else k_gemm_bf16<true, true><<<grid, 256, 0, st>>>(M, N, K, a, lda, bb, ldb, C, ldc, bias, epilogue, kc);
+  }
   cqp::record_launches(1);
   MLP_CK(cudaGetLastError());
   return CQP_OK;
