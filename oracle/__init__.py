@@ -41,7 +41,8 @@ class Problem(C.Structure):
                 ("c", C.c_void_p), ("b", C.c_void_p),
                 ("nblocks", C.c_int64),
                 ("blk_type", C.c_void_p), ("blk_start", C.c_void_p), ("blk_dim", C.c_void_p),
-                ("blk_alpha", C.c_void_p)]
+                ("blk_alpha", C.c_void_p),
+                ("row_lo", C.c_void_p), ("row_hi", C.c_void_p), ("x_lo", C.c_void_p), ("x_hi", C.c_void_p)]
 
 
 class Options(C.Structure):
@@ -140,7 +141,9 @@ class _Prob:
             c=_p(arr("c", np.float64)), b=_p(arr("b", np.float64)),
             nblocks=int(len(inst["blk_type"])),
             blk_type=_p(arr("blk_type", np.int32)), blk_start=_p(arr("blk_start", np.int64)),
-            blk_dim=_p(arr("blk_dim", np.int64)), blk_alpha=_p(arr("blk_alpha", np.float64)))
+            blk_dim=_p(arr("blk_dim", np.int64)), blk_alpha=_p(arr("blk_alpha", np.float64)),
+            row_lo=_p(arr("row_lo", np.float64)), row_hi=_p(arr("row_hi", np.float64)),
+            x_lo=_p(arr("x_lo", np.float64)), x_hi=_p(arr("x_hi", np.float64)))
 
     @property
     def ptr(self):

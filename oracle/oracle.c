@@ -573,8 +573,32 @@ int orc_proj_block(int type, int64_t d, double alpha, const double* r, const dou
 void orc_proj_product(const orc_problem* p, const double* r, const double* m, double* out) {
   for (int64_t j = 0; j < p->nblocks; ++j) {
     int64_t s = p->blk_start[j], d = p->blk_dim[j];
+    if (p->blk_type[j] == ORC_BOX) {   /* coordinatewise clip: metric-independent (App. A.1) */
+      for (int64_t i = s; i < s + d; ++i) out[i] = fmin(fmax(r[i], p->x_lo[i]), p->x_hi[i]);
+      continue;
+    }
     orc_proj_block(p->blk_type[j], d, p->blk_alpha[j], r + s, m ? m + s : NULL, out + s);
   }
+}
+
+/* bounds of row i: [row_lo, row_hi], or [b, b] for an equality row */
+static void row_bounds(const orc_problem* p, int64_t i, double* lo, double* hi) {
+  if (p->row_lo) { *lo = p->row_lo[i]; *hi = p->row_hi[i]; }
+  else { *lo = p->b[i]; *hi = p->b[i]; }
+}
+
+/* size of the right-hand side used to normalise primal residuals and in the bound
+ * scaling (reading): per row the largest finite bound magnitude (|b_i| for equalities) */
+static double bound_norm(const orc_problem* p) {
+  double s = 0.0;
+  for (int64_t i = 0; i < p->m; ++i) {
+    double lo, hi, a = 0.0;
+    row_bounds(p, i, &lo, &hi);
+    if (isfinite(lo)) a = fmax(a, fabs(lo));
+    if (isfinite(hi)) a = fmax(a, fabs(hi));
+    s += a * a;
+  }
+  return sqrt(s);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -591,18 +615,39 @@ void orc_kkt(const orc_problem* p, const double* x, const double* y, orc_kkt_rep
   orc_spmv(m, p->a_rowptr, p->a_colind, p->a_val, x, ax);
   orc_spmv_t(m, n, p->a_rowptr, p->a_colind, p->a_val, y, aty);
   orc_q_apply(p, x, qx);
-  double rp = 0.0;
-  for (int64_t i = 0; i < m; ++i) rp += sq(ax[i] - p->b[i]);
+  /* primal: distance of Ax to [row_lo, row_hi]; dual objective term min_{z in [lo,hi]} y'z,
+   * whose finiteness (y_i <= 0 when lo_i = -inf, y_i >= 0 when hi_i = +inf) joins the dual
+   * residual; equality rows give |Ax - b| and b'y as before */
+  double rp = 0.0, by = 0.0, rd2 = 0.0;
+  for (int64_t i = 0; i < m; ++i) {
+    double lo, hi;
+    row_bounds(p, i, &lo, &hi);
+    rp += sq(ax[i] - fmin(fmax(ax[i], lo), hi));
+    if (y[i] > 0.0) { if (isfinite(lo)) by += y[i] * lo; else rd2 += sq(y[i]); }
+    else if (y[i] < 0.0) { if (isfinite(hi)) by += y[i] * hi; else rd2 += sq(y[i]); }
+  }
   rp = sqrt(rp);
-  /* s = Qx + c - A'y; dist(s, K*) = ||Pi_K(-s)|| by the Moreau decomposition */
+  /* s = Qx + c - A'y; on cone blocks dist(s, K*) = ||Pi_K(-s)|| by the Moreau decomposition;
+   * on box blocks min_{x_j in [lo,hi]} s_j x_j joins the dual objective and is finite only if
+   * s_j <= 0 when lo_j = -inf and s_j >= 0 when hi_j = +inf */
   for (int64_t i = 0; i < n; ++i) s[i] = -(qx[i] + p->c[i] - aty[i]);
   orc_proj_product(p, s, NULL, ps);
-  double rd = nrm2(n, ps);
-  double xqx = dot(n, x, qx), cx = dot(n, p->c, x), by = dot(m, p->b, y);
-  double pobj = 0.5 * xqx + cx, dobj = by - 0.5 * xqx;
+  double boxterm = 0.0;
+  for (int64_t j = 0; j < p->nblocks; ++j) {
+    if (p->blk_type[j] != ORC_BOX) continue;
+    for (int64_t i = p->blk_start[j]; i < p->blk_start[j] + p->blk_dim[j]; ++i) {
+      double sj = -s[i], lo = p->x_lo[i], hi = p->x_hi[i], r = 0.0;
+      if (sj > 0.0) { if (isfinite(lo)) boxterm += sj * lo; else r = sj; }
+      else if (sj < 0.0) { if (isfinite(hi)) boxterm += sj * hi; else r = sj; }
+      ps[i] = r;
+    }
+  }
+  double rd = sqrt(dot(n, ps, ps) + rd2);
+  double xqx = dot(n, x, qx), cx = dot(n, p->c, x);
+  double pobj = 0.5 * xqx + cx, dobj = by + boxterm - 0.5 * xqx;
   rep->norm_res_p = rp;
   rep->norm_res_d = rd;
-  rep->eps_p = rp / (1.0 + nrm2(m, p->b));
+  rep->eps_p = rp / (1.0 + bound_norm(p));
   rep->eps_d = rd / (1.0 + nrm2(n, p->c));
   rep->eps_g = fabs(pobj - dobj) / (1.0 + fabs(pobj) + fabs(dobj));
   rep->pobj = pobj;
@@ -623,6 +668,8 @@ typedef struct {
   int64_t *pr, *pc; double* pv; int64_t pnnz;   /* sparse P or NULL */
   int64_t k; double *R, *D;          /* low-rank part */
   double *c, *b;
+  double *lo, *hi;                   /* row bounds (NULL: equality rows, b) */
+  double *xlo, *xhi;                 /* box bounds (NULL: no box blocks) */
   orc_problem view;                  /* problem struct pointing at the arrays above */
 } wprob;
 
@@ -682,7 +729,19 @@ static void wprob_init(wprob* w, const orc_problem* p) {
   w->c = dalloc(w->n);
   memcpy(w->c, p->c, (size_t)w->n * sizeof(double));
   w->b = dalloc(w->m);
-  memcpy(w->b, p->b, (size_t)w->m * sizeof(double));
+  if (p->b) memcpy(w->b, p->b, (size_t)w->m * sizeof(double));
+  if (p->row_lo) {
+    w->lo = dalloc(w->m);
+    w->hi = dalloc(w->m);
+    memcpy(w->lo, p->row_lo, (size_t)w->m * sizeof(double));
+    memcpy(w->hi, p->row_hi, (size_t)w->m * sizeof(double));
+  }
+  if (p->x_lo) {
+    w->xlo = dalloc(w->n);
+    w->xhi = dalloc(w->n);
+    memcpy(w->xlo, p->x_lo, (size_t)w->n * sizeof(double));
+    memcpy(w->xhi, p->x_hi, (size_t)w->n * sizeof(double));
+  }
   build_transpose(w);
   w->view = *p;
   w->view.a_rowptr = w->ar; w->view.a_colind = w->ac; w->view.a_val = w->av;
@@ -690,11 +749,13 @@ static void wprob_init(wprob* w, const orc_problem* p) {
   w->view.p_rowptr = w->pr; w->view.p_colind = w->pc; w->view.p_val = w->pv;
   w->view.q_R = w->R; w->view.q_D = w->D;
   w->view.c = w->c; w->view.b = w->b;
+  w->view.row_lo = w->lo; w->view.row_hi = w->hi; w->view.x_lo = w->xlo; w->view.x_hi = w->xhi;
 }
 
 static void wprob_free(wprob* w) {
   free(w->ar); free(w->ac); free(w->av); free(w->tr); free(w->tc); free(w->tv);
   free(w->qd); free(w->pr); free(w->pc); free(w->pv); free(w->R); free(w->D); free(w->c); free(w->b);
+  free(w->lo); free(w->hi); free(w->xlo); free(w->xhi);
 }
 
 static int q_is_diagonal(const wprob* w) { return w->pr == NULL && w->k == 0; }
@@ -715,12 +776,12 @@ typedef struct {
 } scaling;
 
 /* Cone-preserving aggregation of column candidates: max over the block for
- * Ruiz, root-mean-square over the block for Pock-Chambolle; nonnegative and
- * free coordinates stay coordinatewise. */
+ * Ruiz, root-mean-square over the block for Pock-Chambolle; nonnegative, free
+ * and box coordinates stay coordinatewise. */
 static void aggregate_blocks(const orc_problem* p, double* cand, int use_rms) {
   for (int64_t j = 0; j < p->nblocks; ++j) {
     int t = p->blk_type[j];
-    if (t == ORC_FREE || t == ORC_NONNEG) continue;
+    if (t == ORC_FREE || t == ORC_NONNEG || t == ORC_BOX) continue;
     int64_t s = p->blk_start[j], d = p->blk_dim[j];
     double agg = 0.0;
     if (use_rms) {
@@ -787,6 +848,10 @@ static void do_rescale(wprob* w, const orc_problem* p, const orc_options* o, sca
   /* data in the scaled variables: c~ = c/col, b~ = b/row, Q~ = S^-1 Q S^-1 */
   for (int64_t j = 0; j < n; ++j) w->c[j] /= sc->col[j];
   for (int64_t i = 0; i < m; ++i) w->b[i] /= sc->row[i];
+  if (w->lo)   /* bounds scale like b (rows) and like x (boxes); infinities stay */
+    for (int64_t i = 0; i < m; ++i) { w->lo[i] /= sc->row[i]; w->hi[i] /= sc->row[i]; }
+  if (w->xlo)
+    for (int64_t j = 0; j < n; ++j) { w->xlo[j] *= sc->col[j]; w->xhi[j] *= sc->col[j]; }
   for (int64_t j = 0; j < n; ++j) w->qd[j] /= sc->col[j] * sc->col[j];
   if (w->pr)
     for (int64_t i = 0; i < n; ++i)
@@ -798,9 +863,13 @@ static void do_rescale(wprob* w, const orc_problem* p, const orc_options* o, sca
   sc->beta_b = 1.0;
   sc->beta_c = 1.0;
   if (o->bound_obj) {
-    sc->beta_b = nrm2(m, w->b) + 1.0;
+    sc->beta_b = bound_norm(&w->view) + 1.0;
     sc->beta_c = nrm2(n, w->c) + 1.0;
     for (int64_t i = 0; i < m; ++i) w->b[i] /= sc->beta_b;
+    if (w->lo)
+      for (int64_t i = 0; i < m; ++i) { w->lo[i] /= sc->beta_b; w->hi[i] /= sc->beta_b; }
+    if (w->xlo)
+      for (int64_t j = 0; j < n; ++j) { w->xlo[j] /= sc->beta_b; w->xhi[j] /= sc->beta_b; }
     for (int64_t j = 0; j < n; ++j) w->c[j] /= sc->beta_c;
     double qs = sc->beta_b / sc->beta_c;
     for (int64_t j = 0; j < n; ++j) w->qd[j] *= qs;
@@ -951,7 +1020,17 @@ static int pdhg_operator(const wprob* w, double tau, double sigma, const double*
   int inner = do_prox(w, tau, v, x, eps_in, max_inner, jacobi, force_inner, xo);
   for (int64_t i = 0; i < n; ++i) v[i] = 2.0 * xo[i] - x[i];
   orc_spmv(m, w->ar, w->ac, w->av, v, scratch_m);
-  for (int64_t i = 0; i < m; ++i) yo[i] = y[i] + sigma * (w->b[i] - scratch_m[i]);
+  for (int64_t i = 0; i < m; ++i) {
+    double lo, hi;
+    row_bounds(&w->view, i, &lo, &hi);
+    if (lo == hi) {
+      yo[i] = y[i] + sigma * (lo - scratch_m[i]);
+    } else {
+      /* prox of the support function of [lo, hi] (Moreau): y - sigma v + sigma Pi(v - y/sigma) */
+      const double v = scratch_m[i];
+      yo[i] = y[i] - sigma * v + sigma * fmin(fmax(v - y[i] / sigma, lo), hi);
+    }
+  }
   return inner;
 }
 
@@ -1026,7 +1105,7 @@ int orc_solve(const orc_problem* p, const orc_options* o, const double* x0, cons
   double normA = orc_norm_est(m, n, w.ar, w.ac, w.av, o->power_iters, o->power_tol, &pits);
   double eta = o->step_factor / (normA > 0.0 ? normA : 1.0);
   /* initial primal weight (reading): ||c~||/||b~|| when both are positive, else 1 */
-  double cn = nrm2(n, w.c), bn = nrm2(m, w.b);
+  double cn = nrm2(n, w.c), bn = bound_norm(&w.view);
   double omega = (cn > 1e-10 && bn > 1e-10) ? cn / bn : 1.0;
   double tau = eta / omega, sigma = eta * omega;
 

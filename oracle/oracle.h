@@ -30,7 +30,7 @@ extern "C" {
 #endif
 
 /* Cone block types (a block is a contiguous slice of x). */
-enum { ORC_FREE = 0, ORC_NONNEG = 1, ORC_SOC = 2, ORC_RSOC = 3, ORC_EXP = 4, ORC_POW = 5 };
+enum { ORC_FREE = 0, ORC_NONNEG = 1, ORC_SOC = 2, ORC_RSOC = 3, ORC_EXP = 4, ORC_POW = 5, ORC_BOX = 6 };
 
 typedef struct {
   int64_t m, n;
@@ -43,6 +43,10 @@ typedef struct {
   const double* c; const double* b;
   int64_t nblocks;
   const int32_t* blk_type; const int64_t* blk_start; const int64_t* blk_dim; const double* blk_alpha;
+  /* general form (solver-input of Sec. 4): row_lo <= A x <= row_hi (NULL: A x = b) and,
+   * on ORC_BOX blocks, x_lo <= x <= x_hi (n entries, read on box coordinates only);
+   * infinite entries mean no bound */
+  const double* row_lo; const double* row_hi; const double* x_lo; const double* x_hi;
 } orc_problem;
 
 typedef struct {
