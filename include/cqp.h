@@ -61,6 +61,7 @@ extern "C" {
 #define CQP_CONE_RSOC 3    /* {(v, s, t): ||v||^2 <= 2 s t, s, t >= 0}, s, t last, d >= 3 */
 #define CQP_CONE_EXP 4     /* cl{(r, s, t): s > 0, s exp(r/s) <= t}, d = 3 */
 #define CQP_CONE_POW 5     /* {(r, s, t): r, s >= 0, r^a s^(1-a) >= |t|}, d = 3, 0 < a < 1 */
+#define CQP_CONE_BOX 6     /* {x: x_lo <= x <= x_hi} coordinatewise (cqp_setup_general only), d >= 1 */
 
 /* CSR matrix.  rowptr has nrows+1 entries (int64, rowptr[0] = 0), colind and
  * val have nnz entries; colind in [0, ncols).  nnz must be < 2^31. */
@@ -172,6 +173,29 @@ int cqp_default_options(cqp_options* opt);
  * 2^31, non-finite values), CQP_ERR_OOM, CQP_ERR_CUDA; *out is NULL then. */
 int cqp_setup(const cqp_csr* A, const cqp_qop* Q, const double* c, const double* b, const cqp_cones* K,
               const cqp_options* opt, cqp_handle** out);
+
+/* General standard form (Sec. 4, eq. "solver-input"):
+ *     min 1/2 x'Qx + c'x   s.t.  row_lo <= A x <= row_hi,  x in K,
+ * where K may also hold CQP_CONE_BOX blocks x_lo <= x <= x_hi.  Infinite entries mean
+ * no bound; equal finite entries make an equality row.  Arrays follow
+ * opt->input_on_device like the other inputs; row_lo, row_hi have m entries (required
+ * when m > 0); x_lo, x_hi have n entries, read on box coordinates only (required when
+ * a box block exists).  Not available in batched mode. */
+typedef struct {
+  const double* row_lo;
+  const double* row_hi;
+  const double* x_lo;
+  const double* x_hi;
+} cqp_bounds;
+
+/* As cqp_setup for the general form.  The dual step becomes the prox of the support
+ * function of [row_lo, row_hi] (y+ = y - sigma v + sigma Pi_[lo,hi](v - y/sigma),
+ * v = A(2x+ - x)), box coordinates are clipped in every projection, and the KKT report
+ * measures the distance of Ax to [row_lo, row_hi], adds the support terms to the dual
+ * objective and their sign conditions to the dual residual.  Errors as cqp_setup, plus
+ * CQP_ERR_INVALID for NaN bounds or lo > hi. */
+int cqp_setup_general(const cqp_csr* A, const cqp_qop* Q, const double* c, const cqp_bounds* bounds,
+                      const cqp_cones* K, const cqp_options* opt, cqp_handle** out);
 
 /* Runs the restarted PDHG loop on the GPU until rel-KKT <= tol (checked on the
  * unscaled candidate every check_every iterations, Sec. 4.2.2 last paragraph),

@@ -68,6 +68,10 @@ class KKTReport(C.Structure):
                 ("pobj", C.c_double), ("dobj", C.c_double), ("norm_res_p", C.c_double), ("norm_res_d", C.c_double)]
 
 
+class Bounds(C.Structure):
+    _fields_ = [("row_lo", C.c_void_p), ("row_hi", C.c_void_p), ("x_lo", C.c_void_p), ("x_hi", C.c_void_p)]
+
+
 class Batch(C.Structure):
     _fields_ = [("count", C.c_int64), ("x_off", C.c_void_p), ("row_off", C.c_void_p)]
 
@@ -116,6 +120,7 @@ def lib():
         L.cqp_kernel_launches.restype = C.c_longlong
         L.cqp_kkt_static.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.cqp_setup_batch.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+        L.cqp_setup_general.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.cqp_solve_batch.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp]
         f32 = C.c_float
         L.cqp_ws_features.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, i64, vp, vp, vp]
@@ -127,7 +132,8 @@ def lib():
         L.cqp_adam_step.argtypes = [i64, vp, vp, vp, vp, f32, f32, f32, f32, i64, vp, vp]
         L.cqp_ws_start.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, i64, vp, vp, vp, f32, i32, vp, vp, vp]
         for f in ("cqp_default_options", "cqp_setup", "cqp_solve", "cqp_kkt", "cqp_spmv", "cqp_project",
-                  "cqp_kkt_static", "cqp_setup_batch", "cqp_solve_batch", "cqp_ws_features", "cqp_gemm_bf16",
+                  "cqp_kkt_static", "cqp_setup_batch", "cqp_solve_batch", "cqp_setup_general", "cqp_ws_features",
+                  "cqp_gemm_bf16",
                   "cqp_ws_head_forward", "cqp_ws_loss", "cqp_ws_head_backward", "cqp_relu_backward_bf16",
                   "cqp_adam_step", "cqp_ws_start"):
             getattr(L, f).restype = C.c_int
@@ -175,6 +181,13 @@ def cqp_solve(h, x0, y0, x_out, y_out, on_device: int, res: Result) -> int:
 
 def cqp_kkt(h, x, y, on_device: int, rep: KKTReport) -> int:
     return _check(lib().cqp_kkt(h, x, y, on_device, C.byref(rep)))
+
+
+def cqp_setup_general(A: CSR, Q, c, bounds: Bounds, K: Cones, opt: Options):
+    h = C.c_void_p()
+    _check(lib().cqp_setup_general(C.byref(A), None if Q is None else C.byref(Q), c, C.byref(bounds), C.byref(K),
+                                   C.byref(opt), C.byref(h)))
+    return h
 
 
 def cqp_setup_batch(A: CSR, Q, c, b, K: Cones, B: Batch, opt: Options):
@@ -272,7 +285,8 @@ class Solver:
             "a_rowptr": np.int64, "a_colind": np.int32, "a_val": np.float64, "c": np.float64, "b": np.float64,
             "q_diag": np.float64, "q_R": np.float64, "q_D": np.float64, "p_rowptr": np.int64, "p_colind": np.int32,
             "p_val": np.float64, "blk_type": np.int32, "blk_start": np.int64, "blk_dim": np.int64,
-            "blk_alpha": np.float64}
+            "blk_alpha": np.float64, "row_lo": np.float64, "row_hi": np.float64, "x_lo": np.float64,
+            "x_hi": np.float64}
         arrs = {}
         for k, dt in conv.items():
             v = inst.get(k)
@@ -305,6 +319,10 @@ class Solver:
         self.h = self._setup(arrs)
 
     def _setup(self, arrs):
+        if any(arrs.get(k) is not None for k in ("row_lo", "row_hi", "x_lo", "x_hi")):
+            self.G = Bounds(_ptr(arrs.get("row_lo")), _ptr(arrs.get("row_hi")), _ptr(arrs.get("x_lo")),
+                            _ptr(arrs.get("x_hi")))
+            return cqp_setup_general(self.A, self.Q, _ptr(arrs["c"]), self.G, self.K, self.opt)
         return cqp_setup(self.A, self.Q, _ptr(arrs["c"]), _ptr(arrs["b"]), self.K, self.opt)
 
     def solve(self, x0=None, y0=None, out_device=False):

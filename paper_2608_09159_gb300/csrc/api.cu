@@ -247,7 +247,7 @@ struct Handle : HandleBase {
   }
 
   void setup(const cqp_csr* A, const cqp_qop* Q, const double* c_in, const double* b_in, const cqp_cones* K,
-             const cqp_options& o, const cqp_batch* B = nullptr) {
+             const cqp_options& o, const cqp_batch* B = nullptr, const cqp_bounds* G = nullptr) {
     auto t0 = std::chrono::steady_clock::now();
     const long long launches0 = g_launches;
     opt = o;
@@ -288,7 +288,9 @@ struct Handle : HandleBase {
     for (int64_t j = 0; j < nb; ++j) {
       if (bs[j] != pos || bd[j] < 1) fail(CQP_ERR_INVALID, "cone blocks must partition 0..n-1 contiguously in order");
       const int t = bt[j];
-      if (t < 0 || t > 5) fail(CQP_ERR_INVALID, "unknown cone type");
+      if (t < 0 || t > 6) fail(CQP_ERR_INVALID, "unknown cone type");
+      if (t == CQP_CONE_BOX && (!G || !G->x_lo || !G->x_hi)) fail(CQP_ERR_INVALID, "box blocks need x_lo and x_hi");
+      if (t == CQP_CONE_BOX && B) fail(CQP_ERR_UNSUPPORTED, "box blocks in a batch");
       if (t == CQP_CONE_SOC && bd[j] < 2) fail(CQP_ERR_INVALID, "SOC block dimension < 2");
       if (t == CQP_CONE_RSOC && bd[j] < 3) fail(CQP_ERR_INVALID, "RSOC block dimension < 3");
       if ((t == CQP_CONE_EXP || t == CQP_CONE_POW) && bd[j] != 3) fail(CQP_ERR_INVALID, "EXP/POW block dimension != 3");
@@ -301,7 +303,10 @@ struct Handle : HandleBase {
     std::vector<int64_t> soc_off{0}, rsoc_off{0};
     std::vector<double> pow_al;
     int64_t cnt[6] = {0, 0, 0, 0, 0, 0};
-    for (int64_t j = 0; j < nb; ++j) cnt[bt[j]] += bd[j];
+    // box blocks live in the free segment (their bounds are applied coordinatewise)
+    std::vector<int32_t> seg_of(nb);
+    for (int64_t j = 0; j < nb; ++j) seg_of[j] = bt[j] == CQP_CONE_BOX ? 0 : bt[j];
+    for (int64_t j = 0; j < nb; ++j) cnt[seg_of[j]] += bd[j];
     int64_t base[6];
     base[0] = 0;
     for (int t = 1; t < 6; ++t) base[t] = base[t - 1] + cnt[t - 1];
@@ -309,7 +314,7 @@ struct Handle : HandleBase {
     for (int t = 0; t < 6; ++t) fill[t] = base[t];
     for (int t = 0; t < 6; ++t)
       for (int64_t j = 0; j < nb; ++j) {
-        if (bt[j] != t) continue;
+        if (seg_of[j] != t) continue;
         seg_new.push_back(fill[t]);
         seg_old.push_back(bs[j]);
         if (t == CQP_CONE_SOC) soc_off.push_back(fill[t] + bd[j]);
@@ -390,7 +395,12 @@ struct Handle : HandleBase {
     const int32_t* a_ci_in = (const int32_t*)upload(A->colind, nnz * sizeof(int32_t));
     const double* a_v_in = (const double*)upload(A->val, nnz * sizeof(double));
     const double* c_d = (const double*)upload(c_in, n * sizeof(double));
-    const double* b_d = (const double*)upload(b_in, m * sizeof(double));
+    const bool general = G != nullptr;
+    if (general && m > 0 && (!G->row_lo || !G->row_hi)) fail(CQP_ERR_INVALID, "row_lo and row_hi are required");
+    const double* b_d = (const double*)upload(general ? G->row_lo : b_in, m * sizeof(double));
+    const double* bhi_d = general ? (const double*)upload(G->row_hi, m * sizeof(double)) : nullptr;
+    const double* xlo_d = general && G->x_lo ? (const double*)upload(G->x_lo, n * sizeof(double)) : nullptr;
+    const double* xhi_d = general && G->x_hi ? (const double*)upload(G->x_hi, n * sizeof(double)) : nullptr;
     const double* qd_in = Q ? (const double*)upload(Q->diag, n * sizeof(double)) : nullptr;
     const double* R_in = k > 0 ? (const double*)upload(Q->R, k * n * sizeof(double)) : nullptr;
     const double* D_in = k > 0 ? (const double*)upload(Q->D, k * k * sizeof(double)) : nullptr;
@@ -402,7 +412,17 @@ struct Handle : HandleBase {
     CK(cudaMemsetAsync(bad, 0, sizeof(int), st));
     count_launch(); cqp::k_validate_csr<<<cqp::grid_for(nnz + m), cqp::kSetupThreads, 0, st>>>(m, n, a_rp64, a_ci_in, a_v_in, bad);
     count_launch(); cqp::k_validate_vec<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, c_d, bad);
-    if (m > 0) { count_launch(); cqp::k_validate_vec<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, b_d, bad); }
+    if (m > 0 && !general) { count_launch(); cqp::k_validate_vec<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, b_d, bad); }
+    if (m > 0 && general) { count_launch(); cqp::k_validate_bounds<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, b_d, bhi_d, nullptr, bad); }
+    uint8_t* boxmask = nullptr;
+    if (xlo_d) {
+      std::vector<uint8_t> hm(n, 0);
+      for (int64_t j = 0; j < nb; ++j)
+        if (bt[j] == CQP_CONE_BOX) memset(hm.data() + bs[j], 1, (size_t)bd[j]);
+      boxmask = tmp.alloc<uint8_t>(n);
+      CK(cudaMemcpyAsync(boxmask, hm.data(), n, cudaMemcpyHostToDevice, st));
+      count_launch(); cqp::k_validate_bounds<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, xlo_d, xhi_d, boxmask, bad);
+    }
     if (qd_in) { count_launch(); cqp::k_validate_vec<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, qd_in, bad); }
     if (R_in) { count_launch(); cqp::k_validate_vec<<<cqp::grid_for(k * n), cqp::kSetupThreads, 0, st>>>(k * n, R_in, bad); }
     if (has_p) { count_launch(); cqp::k_validate_csr<<<cqp::grid_for(pnnz + n), cqp::kSetupThreads, 0, st>>>(n, n, p_rp64, p_ci_in, p_v_in, bad); }
@@ -415,7 +435,15 @@ struct Handle : HandleBase {
     if (last_rp != nnz) fail(CQP_ERR_INVALID, "A.rowptr[m] != nnz");
     double* part = tmp.alloc<double>(1024);
     double* one = tmp.alloc<double>(1);
-    P.norm_b = m > 0 ? std::sqrt(dev_dot(b_d, nullptr, m, part, one, st)) : 0.0;
+    // size of the right-hand side (reading: per row the largest finite bound magnitude)
+    auto bound_norm = [&](const double* lo, const double* hi) {
+      if (m == 0) return 0.0;
+      if (!hi) return std::sqrt(dev_dot(lo, nullptr, m, part, one, st));
+      double* mag = tmp.alloc<double>(m);
+      count_launch(); cqp::k_bound_mag<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, lo, hi, mag);
+      return std::sqrt(dev_dot(mag, nullptr, m, part, one, st));
+    };
+    P.norm_b = bound_norm(b_d, bhi_d);
     P.norm_c = std::sqrt(dev_dot(c_d, nullptr, n, part, one, st));
     if (batched) {
       d_own = mem.alloc<cqp::Own>(bcount);
@@ -461,6 +489,11 @@ struct Handle : HandleBase {
     count_launch(); cqp::k_gather<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, perm, c_d, cv, 0.0);
     count_launch(); cqp::k_gather<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, perm, qd_in, qv, 0.0);
     if (m > 0) CK(cudaMemcpyAsync(bv, b_d, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    double* bhv = nullptr;   // general form: scaled row upper bounds (FP64 working copy)
+    if (bhi_d && m > 0) {
+      bhv = tmp.alloc<double>(m);
+      CK(cudaMemcpyAsync(bhv, bhi_d, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
     double* Rv = nullptr;
     double* Dv = nullptr;
     if (k > 0) {
@@ -540,6 +573,7 @@ struct Handle : HandleBase {
     }
     count_launch(); cqp::k_div<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, cv, col);
     if (m > 0) { count_launch(); cqp::k_div<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, bv, row); }
+    if (bhv) { count_launch(); cqp::k_div<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, bhv, row); }
     count_launch(); cqp::k_div2<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, qv, col);
     if (has_p) { count_launch(); cqp::k_scale_sym<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, p_rp, p_ci, pv, col); }
     if (k > 0) { count_launch(); cqp::k_scale_cols<<<cqp::grid_for(k * n), cqp::kSetupThreads, 0, st>>>(k, n, Rv, col); }
@@ -556,9 +590,10 @@ struct Handle : HandleBase {
         cqp::k_inst_rank<<<(int)std::min<int64_t>(bcount, 8 * nsm), cqp::kBatchSetupThreads, 0, st>>>(bcount, d_own, n, k, Rv, d_rank);
       }
     } else if (o.bound_obj) {
-      beta_b = (m > 0 ? std::sqrt(dev_dot(bv, nullptr, m, part, one, st)) : 0.0) + 1.0;
+      beta_b = bound_norm(bv, bhv) + 1.0;
       beta_c = std::sqrt(dev_dot(cv, nullptr, n, part, one, st)) + 1.0;
       if (m > 0) { count_launch(); cqp::k_scal<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, bv, 1.0 / beta_b); }
+      if (bhv) { count_launch(); cqp::k_scal<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, bhv, 1.0 / beta_b); }
       count_launch(); cqp::k_scal<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, cv, 1.0 / beta_c);
       const double qs = beta_b / beta_c;
       count_launch(); cqp::k_scal<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, qv, qs);
@@ -578,6 +613,19 @@ struct Handle : HandleBase {
     T* jT = mem.alloc<T>(n);
     count_launch(); cqp::k_convert<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, cv, cT);
     if (m > 0) { count_launch(); cqp::k_convert<T><<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, bv, bT); }
+    T* rhiT = nullptr;
+    if (bhv) {
+      rhiT = mem.alloc<T>(m);
+      count_launch(); cqp::k_convert<T><<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, bhv, rhiT);
+    }
+    // box bounds of the free segment, x~ = col x / beta_b (infinite on free coordinates)
+    T* xloT = nullptr;
+    T* xhiT = nullptr;
+    if (xlo_d && cnt[0] > 0) {
+      xloT = mem.alloc<T>(cnt[0]);
+      xhiT = mem.alloc<T>(cnt[0]);
+      count_launch(); cqp::k_box_bounds<T><<<cqp::grid_for(cnt[0]), cqp::kSetupThreads, 0, st>>>(cnt[0], perm, boxmask, xlo_d, xhi_d, col, beta_b, xloT, xhiT);
+    }
     count_launch(); cqp::k_convert<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, qv, qT);
     count_launch(); cqp::k_convert<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, jdv, jT);
     // R is stored with its row count padded to a multiple of 8 (zero rows), so the
@@ -663,7 +711,7 @@ struct Handle : HandleBase {
       } else {
         eta = o.step_factor / (sig > 0.0 ? sig : 1.0);
         const double cn = std::sqrt(dev_dot(cv, nullptr, n, part, one, st));
-        const double bn = m > 0 ? std::sqrt(dev_dot(bv, nullptr, m, part, one, st)) : 0.0;
+        const double bn = bound_norm(bv, bhv);
         omega0 = (cn > 1e-10 && bn > 1e-10) ? cn / bn : 1.0;   // reading: ||c~||/||b~||
       }
     }
@@ -686,6 +734,7 @@ struct Handle : HandleBase {
     }
     P.p_rp = p_rp; P.p_ci = p_ci; P.p_v = pT;
     P.c = cT; P.b = bT; P.col = col; P.row = row; P.beta_b = beta_b; P.beta_c = beta_c;
+    P.rhi = rhiT; P.xlo = xloT; P.xhi = xhiT;
     P.n_free = cnt[0]; P.n_nonneg = cnt[1];
     P.n_soc = n_soc; P.soc_off = d_soc; P.n_rsoc = n_rsoc; P.rsoc_off = d_rsoc;
     P.n_exp = n_exp; P.exp_base = base[4]; P.n_pow = n_pow; P.pow_base = base[5]; P.pow_alpha = palpha;
@@ -1124,6 +1173,29 @@ int cqp_setup(const cqp_csr* A, const cqp_qop* Q, const double* c, const double*
     } else {
       auto* hh = new Handle<float>();
       try { hh->setup(A, Q, c, b, K, o); } catch (...) { delete hh; throw; }
+      h = hh;
+    }
+    *out = new cqp_handle{h};
+    return CQP_OK;
+  });
+}
+
+int cqp_setup_general(const cqp_csr* A, const cqp_qop* Q, const double* c, const cqp_bounds* bounds,
+                      const cqp_cones* K, const cqp_options* opt, cqp_handle** out) {
+  if (!out) return CQP_ERR_INVALID;
+  *out = nullptr;
+  if (!A || !K || !c || !bounds) return CQP_ERR_INVALID;
+  cqp_options o;
+  if (opt) o = *opt; else cqp_default_options(&o);
+  return guarded([&]() {
+    HandleBase* h = nullptr;
+    if (o.precision == 1) {
+      auto* hh = new Handle<double>();
+      try { hh->setup(A, Q, c, nullptr, K, o, nullptr, bounds); } catch (...) { delete hh; throw; }
+      h = hh;
+    } else {
+      auto* hh = new Handle<float>();
+      try { hh->setup(A, Q, c, nullptr, K, o, nullptr, bounds); } catch (...) { delete hh; throw; }
       h = hh;
     }
     *out = new cqp_handle{h};

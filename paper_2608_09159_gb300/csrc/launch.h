@@ -20,6 +20,13 @@ template <typename T>
 cudaError_t launch_kkt(const KernelArgs<T>& a, const T* x, const T* y, double* out, bool grid, int blocks, int threads,
                        cudaStream_t st);
 
+// General-form variant of launch_pdhg (row bounds, box blocks), built in its own
+// translation unit; launch_pdhg forwards to it when P.rhi or P.xlo is set.
+template <typename T>
+cudaError_t launch_pdhg_general(const KernelArgs<T>& a, bool grid, int blocks, int threads, cudaStream_t st);
+template <typename T>
+int pdhg_general_blocks_per_sm(int threads);
+
 // Batched persistent solve (one block per instance at a time, work queue).
 template <typename T>
 cudaError_t launch_pdhg_batch(const KernelArgs<T>& a, const BatchArgs& b, int blocks, int threads, cudaStream_t st);

@@ -262,6 +262,40 @@ __global__ void k_spmv_simple(int64_t m, const int32_t* rp, const int32_t* ci, c
   }
 }
 
+// ---- general form (rows lo <= Ax <= hi, box blocks) ---------------------------------
+// no NaN and lo <= hi (on masked coordinates when mask is given)
+__global__ void k_validate_bounds(int64_t n, const double* lo, const double* hi, const uint8_t* mask, int* bad) {
+  CQP_GRID_LOOP(i, n) {
+    if (mask && !mask[i]) continue;
+    const double l = lo[i], h = hi[i];
+    if (l != l || h != h || l > h || l == INFINITY || h == -INFINITY) atomicOr(bad, 32);
+  }
+}
+// per-row magnitude of the right-hand side: the largest finite bound magnitude
+__global__ void k_bound_mag(int64_t m, const double* lo, const double* hi, double* mag) {
+  CQP_GRID_LOOP(i, m) {
+    double a = 0.0;
+    if (isfinite(lo[i])) a = fmax(a, fabs(lo[i]));
+    if (isfinite(hi[i])) a = fmax(a, fabs(hi[i]));
+    mag[i] = a;
+  }
+}
+// scaled box bounds of the free segment: x~ = col x / beta_b; free coordinates unbounded
+template <typename T>
+__global__ void k_box_bounds(int64_t nf, const int64_t* perm, const uint8_t* mask, const double* lo, const double* hi,
+                             const double* col, double beta_b, T* olo, T* ohi) {
+  CQP_GRID_LOOP(i, nf) {
+    const int64_t o = perm[i];
+    if (mask[o]) {
+      olo[i] = T(lo[o] * col[i] / beta_b);
+      ohi[i] = T(hi[o] * col[i] / beta_b);
+    } else {
+      olo[i] = T(-INFINITY);
+      ohi[i] = T(INFINITY);
+    }
+  }
+}
+
 // ---- ||A~||_2 by power iteration on A~'A~, all iterations in one cooperative launch
 // (eq. practical-stepsizes; reading: all-ones start, Rayleigh quotient ||A v|| with
 // ||v|| = 1, stop at `tol` relative change or `iters` iterations).  v is kept as

@@ -48,7 +48,7 @@ struct Prob {
   int kpad;                                            // rows of R as stored: k rounded up to 8, rows >= k zero
   double d_scale;                                     // D = d_scale * I when > 0 (else general D)
   const int* p_rp; const int* p_ci; const T* p_v;     // scaled sparse P (n rows) or null
-  const T* c; const T* b;                             // scaled c, b
+  const T* c; const T* b;                             // scaled c, b (general form: b holds the row lower bounds)
   const double* col; const double* row;               // x = beta_b x~/col, y = beta_c y~/row
   double beta_b, beta_c, norm_b, norm_c;              // ||b||, ||c|| of the unscaled data
   int64_t n_free, n_nonneg;                           // [0,n_free) free, then nonneg
@@ -59,6 +59,8 @@ struct Prob {
   int qmode;
   int euclid_cones;                                   // diagonal mode with zero q on cone coordinates
   int tpr_a, tpr_t, tpr_p;                            // threads per row of A, A' and P
+  const T* rhi;                                       // general form: scaled row upper bounds (null: A x = b)
+  const T* xlo; const T* xhi;                         // general form: scaled bounds of the free segment (null: free)
 };
 
 template <typename T>
@@ -244,7 +246,9 @@ __device__ __forceinline__ void rows_loop_tpr(int tpr, const int* rp, const int*
 // ---------------------------------------------------------------------------
 // The solver.  Team is GridTeam (whole GPU) or CtaTeam (one block).
 // ---------------------------------------------------------------------------
-template <typename T, class Team>
+// GEN: general standard form compiled in (row bounds, box blocks; the pointers are still
+// checked at run time).  The equality-form kernels are built with GEN = false.
+template <typename T, class Team, bool GEN = false>
 struct Solver {
   const Prob<T>& P;
   const Work<T>& W;
@@ -427,7 +431,14 @@ struct Solver {
   }
 
   // Elementwise projection onto the free / nonnegative segments (metric-free, App. A.1)
-  __device__ __forceinline__ T proj_elem(int64_t i, T z) const { return (i < P.n_free) ? z : (z > T(0) ? z : T(0)); }
+  __device__ __forceinline__ T proj_elem(int64_t i, T z) const {
+    if (i < P.n_free) {
+      if (!GEN || !P.xlo) return z;
+      const T lo = P.xlo[i], hi = P.xhi[i];   // box bounds (infinite on free coordinates)
+      return z < lo ? lo : (z > hi ? hi : z);
+    }
+    return z > T(0) ? z : T(0);
+  }
 
   // ---- A' products: v = h_x + tau A' h_y on the owned coordinates -----------
   __device__ void phase_aty(const T* hx, const T* hy, double tau) {

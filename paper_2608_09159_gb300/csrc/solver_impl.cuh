@@ -86,9 +86,9 @@ __device__ __forceinline__ void apply_D(const Prob<T>& P, const double* t, doubl
 // diagonal-q-metric-projection, M_sc = I): u = Pi^M((v - tau c)/(1 + tau q)),
 // M = I + tau diag(q).  Result in W.u[0].
 // ---------------------------------------------------------------------------
-template <typename T, class Team>
-__device__ bool Solver<T, Team>::prox_diag(const T* hx) {
-  using S = Solver<T, Team>;
+template <typename T, class Team, bool GEN>
+__device__ bool Solver<T, Team, GEN>::prox_diag(const T* hx) {
+  using S = Solver<T, Team, GEN>;
   const double tau = C.s.tau;
   phase_aty(hx, W.hy[C.s.hb], tau);
   tick(0);
@@ -113,8 +113,8 @@ __device__ bool Solver<T, Team>::prox_diag(const T* hx) {
 // step alpha = 1, stop when ||u^{j+1} - u^j||_2 <= eps_in or max_inner steps.
 // Returns the buffer index of the final iterate in ub.
 // ---------------------------------------------------------------------------
-template <typename T, class Team>
-__device__ bool Solver<T, Team>::prox_bb(const T* hx, int& ub) {
+template <typename T, class Team, bool GEN>
+__device__ bool Solver<T, Team, GEN>::prox_bb(const T* hx, int& ub) {
   const double tau = C.s.tau;
   const int k = P.k;
   const bool sparse = P.qmode == kQSparse;
@@ -216,19 +216,36 @@ __device__ bool Solver<T, Team>::prox_bb(const T* hx, int& ub) {
 // eps_d = ||Pi_K(-s)||/(1+||c||), s = Qx + c - A'y, eps_g = |p-d|/(1+|p|+|d|)).
 // have_rx: C.tcur already holds R~ x.
 // ---------------------------------------------------------------------------
-template <typename T, class Team>
-__device__ bool Solver<T, Team>::kkt(const T* x, const T* y, bool have_rx) {
+template <typename T, class Team, bool GEN>
+__device__ bool Solver<T, Team, GEN>::kkt(const T* x, const T* y, bool have_rx) {
   const int k = P.k;
   const bool sparse = P.qmode == kQSparse;
   __shared__ double tk[kMaxRank], wk[kMaxRank];
-  // K1: rows (primal residual, b'y) and x-part (c'x, sum qd x^2, R x)
+  // K1: rows (primal residual, b'y) and x-part (c'x, sum qd x^2, R x).  General form:
+  // distance of Ax to [lo, hi], the dual objective term min_{z in [lo,hi]} y'z, and the
+  // dual-sign residual of rows with an infinite side (added to the dual residual in K2)
   double v4[4] = {0.0, 0.0, 0.0, 0.0};
+  double rd_rows = 0.0;
   rows_loop_tpr<double>(P.tpr_a, P.a_rp, P.a_ci, P.a_v, own.row0, own.row1, [&](int j) { return x[j]; },
                         [&](int64_t r, int gl, double ax) {
                           if (gl == 0) {
-                            const double res = P.beta_b * P.row[r] * (ax - (double)P.b[r]);
-                            v4[0] += res * res;
-                            v4[1] += (double)P.b[r] * (double)y[r];
+                            if (GEN && P.rhi) {
+                              const double lo = (double)P.b[r], hi = (double)P.rhi[r];
+                              const double res = P.beta_b * P.row[r] * (ax - fmin(fmax(ax, lo), hi));
+                              v4[0] += res * res;
+                              const double yr = (double)y[r];
+                              if (lo == hi) {
+                                v4[1] += lo * yr;
+                              } else if (yr != 0.0) {
+                                const double bd = yr > 0.0 ? lo : hi;
+                                if (isfinite(bd)) v4[1] += bd * yr;
+                                else { const double yu = P.beta_c * yr / P.row[r]; rd_rows += yu * yu; }
+                              }
+                            } else {
+                              const double res = P.beta_b * P.row[r] * (ax - (double)P.b[r]);
+                              v4[0] += res * res;
+                              v4[1] += (double)P.b[r] * (double)y[r];
+                            }
                           }
                         });
   const bool need_r = k > 0 && !have_rx;
@@ -267,7 +284,7 @@ __device__ bool Solver<T, Team>::kkt(const T* x, const T* y, bool have_rx) {
   apply_D(P, tk, wk);
   // K2: s~ = Q~x + c~ - A~'y on the owned coordinates, unscaled s = beta_c col s~,
   // ||Pi_K(-s)||^2 (free: K* = {0}; nonneg: max(-s, 0); cones below)
-  double v2[2] = {0.0, 0.0};
+  double v2[2] = {rd_rows, 0.0};   // dual residual^2, box term of the dual objective (scaled)
   for (int seg = 0; seg < 6; ++seg) {
     rows_loop_tpr<double>(
         P.tpr_t, P.t_rp, P.t_ci, P.t_v, own.x0[seg], own.x1[seg], [&](int j) { return y[j]; },
@@ -276,8 +293,17 @@ __device__ bool Solver<T, Team>::kkt(const T* x, const T* y, bool have_rx) {
             double qx = (double)P.qd[i] * (double)x[i];
             if (k > 0) qx += rtw_d(i, wk);
             if (sparse) qx += W.sd[i];
-            const double ss = P.beta_c * P.col[i] * (qx + (double)P.c[i] - aty);
-            if (seg == 0) v2[0] += ss * ss;
+            const double st = qx + (double)P.c[i] - aty;
+            const double ss = P.beta_c * P.col[i] * st;
+            if (seg == 0 && GEN && P.xlo) {
+              // box coordinate: min_{x in [lo,hi]} s x joins the dual objective; an infinite
+              // side demands the matching sign of s
+              if (st != 0.0) {
+                const double bd = st > 0.0 ? (double)P.xlo[i] : (double)P.xhi[i];
+                if (isfinite(bd)) v2[1] += st * bd;
+                else v2[0] += ss * ss;
+              }
+            } else if (seg == 0) v2[0] += ss * ss;
             else if (seg == 1) { const double t = fmax(-ss, 0.0); v2[0] += t * t; }
             else W.sd[i] = -ss;
           }
@@ -320,7 +346,7 @@ __device__ bool Solver<T, Team>::kkt(const T* x, const T* y, bool have_rx) {
     for (int l = 0; l < k; ++l) rqr += tk[l] * wk[l];
     const double xqx = xqdx + rqr + xpx;
     const double sc = P.beta_b * P.beta_c;
-    const double pobj = sc * (0.5 * xqx + cx), dobj = sc * (by - 0.5 * xqx);
+    const double pobj = sc * (0.5 * xqx + cx), dobj = sc * (by + (GEN ? C.red[1] : 0.0) - 0.5 * xqx);
     const double nrp = sqrt(rp2), nrd = sqrt(C.red[0]);
     double* K = C.s.kkt;
     K[0] = nrp / (1.0 + P.norm_b);
@@ -337,8 +363,8 @@ __device__ bool Solver<T, Team>::kkt(const T* x, const T* y, bool have_rx) {
 // ---------------------------------------------------------------------------
 // main loop: `budget` outer iterations at most (the host relaunches)
 // ---------------------------------------------------------------------------
-template <typename T, class Team>
-__device__ void Solver<T, Team>::run(long long budget) {
+template <typename T, class Team, bool GEN>
+__device__ void Solver<T, Team, GEN>::run(long long budget) {
   const int k = P.k;
   const bool avg = O.update == 1;
   const int lane = threadIdx.x & 31;
@@ -376,7 +402,14 @@ __device__ void Solver<T, Team>::run(long long budget) {
     auto dual_row = [&](int64_t r, int gl, T s1, T s2) {
       if (gl != 0) return;
       const T h = hy[r];
-      const T wy = h + sg * (P.b[r] - s1);   // eq. stored-pdhg-candidate
+      T wy = h + sg * (P.b[r] - s1);   // eq. stored-pdhg-candidate
+      if (GEN && P.rhi) {   // general form: prox of the support function of [lo, hi] (Moreau)
+        const T lo = P.b[r], hi = P.rhi[r];
+        if (lo != hi) {
+          const T z = s1 - h / sg;
+          wy = h - sg * s1 + sg * (z < lo ? lo : (z > hi ? hi : z));
+        }
+      }
       W.wy[r] = wy;
       if (halpern_now) hyn[r] = tc1 * (tr2 * wy + tr1 * h) + tc2 * W.ay[r];   // eq. rh-update
       if (avg) {
@@ -608,7 +641,7 @@ __host__ __device__ constexpr size_t solver_smem_bytes(int threads) {
          sizeof(T) * (size_t)(threads / 32) * 2 * 128 + 64;
 }
 
-template <typename T, class Team>
+template <typename T, class Team, bool GEN>
 __device__ __forceinline__ void solver_entry(const KernelArgs<T>& a, Team& team, char* smem) {
   Ctl& C = *reinterpret_cast<Ctl*>(smem);
   const int nw = blockDim.x >> 5;
@@ -616,7 +649,7 @@ __device__ __forceinline__ void solver_entry(const KernelArgs<T>& a, Team& team,
   double* wacc = scratch + (size_t)kMaxSlots * nw;
   T* cbuf = reinterpret_cast<T*>(wacc + (size_t)nw * kMaxRank);
   load_state(C, a.S);
-  Solver<T, Team> s(a.P, a.W, a.O, team, C, scratch, wacc, cbuf);
+  Solver<T, Team, GEN> s(a.P, a.W, a.O, team, C, scratch, wacc, cbuf);
   s.run(a.budget);
   __syncthreads();
   if (team.bid() == 0 && threadIdx.x == 0) {
@@ -625,21 +658,21 @@ __device__ __forceinline__ void solver_entry(const KernelArgs<T>& a, Team& team,
   }
 }
 
-template <typename T>
+template <typename T, bool GEN>
 __global__ void __launch_bounds__(512, 1) pdhg_grid_kernel(KernelArgs<T> a) {
   extern __shared__ __align__(16) char smem[];
   GridTeam team;
   team.init(a.bar, a.W.part);
-  solver_entry<T, GridTeam>(a, team, smem);
+  solver_entry<T, GridTeam, GEN>(a, team, smem);
 }
 
-template <typename T>
+template <typename T, bool GEN>
 __global__ void __launch_bounds__(512, 1) pdhg_cta_kernel(KernelArgs<T> a) {
   extern __shared__ __align__(16) char smem[];
   __shared__ double part[kMaxSlots];
   CtaTeam team;
   team.init(part);
-  solver_entry<T, CtaTeam>(a, team, smem);
+  solver_entry<T, CtaTeam, GEN>(a, team, smem);
 }
 
 }  // namespace cqp
