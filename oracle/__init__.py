@@ -54,7 +54,7 @@ class Options(C.Structure):
                 ("check_every", C.c_int), ("max_iter", C.c_int64), ("max_inner", C.c_int),
                 ("tol", C.c_double), ("update", C.c_int), ("avg_epoch", C.c_int),
                 ("power_iters", C.c_int), ("power_tol", C.c_double), ("step_factor", C.c_double),
-                ("force_inner", C.c_int), ("pid", C.c_int), ("hist_cap", C.c_int)]
+                ("force_inner", C.c_int), ("pid", C.c_int), ("hist_cap", C.c_int), ("rescaled_cones", C.c_int)]
 
 
 class KKT(C.Structure):
@@ -89,6 +89,9 @@ def lib():
         for fn in ("orc_in_cone", "orc_in_dual_cone"):
             getattr(_lib, fn).argtypes = [C.c_int, C.c_int64, C.c_double, C.c_void_p, C.c_double]
         _lib.orc_proj_block.argtypes = [C.c_int, C.c_int64, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]
+        _lib.orc_proj_block_scaled.restype = C.c_int
+        _lib.orc_proj_block_scaled.argtypes = [C.c_int, C.c_int64, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                                               C.c_void_p]
         _lib.orc_norm_est.argtypes = [C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                       C.c_double, C.c_void_p]
         _lib.orc_pdhg_operator.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
@@ -195,6 +198,17 @@ def proj_block(ctype, r, alpha=0.0, m=None):
     mm = None if m is None else _f64(m)
     out = np.zeros_like(r)
     rc = lib().orc_proj_block(int(ctype), r.size, float(alpha), _p(r), _p(mm), _p(out))
+    if rc != 0:
+        raise ValueError("invalid cone block")
+    return out
+
+
+def proj_block_scaled(ctype, sc, r, alpha=0.0, m=None):
+    """Projection onto the rescaled cone diag(sc) K in the metric m (eq. scaling-induced-metric)."""
+    r, sc = _f64(r), _f64(sc)
+    mm = None if m is None else _f64(m)
+    out = np.zeros_like(r)
+    rc = lib().orc_proj_block_scaled(int(ctype), r.size, float(alpha), _p(sc), _p(r), _p(mm), _p(out))
     if rc != 0:
         raise ValueError("invalid cone block")
     return out

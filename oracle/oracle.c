@@ -670,6 +670,7 @@ typedef struct {
   double *c, *b;
   double *lo, *hi;                   /* row bounds (NULL: equality rows, b) */
   double *xlo, *xhi;                 /* box bounds (NULL: no box blocks) */
+  double* csc;                       /* rescaled-cone mode: S_x on cone coordinates (NULL: blocks are cones) */
   orc_problem view;                  /* problem struct pointing at the arrays above */
 } wprob;
 
@@ -755,7 +756,7 @@ static void wprob_init(wprob* w, const orc_problem* p) {
 static void wprob_free(wprob* w) {
   free(w->ar); free(w->ac); free(w->av); free(w->tr); free(w->tc); free(w->tv);
   free(w->qd); free(w->pr); free(w->pc); free(w->pv); free(w->R); free(w->D); free(w->c); free(w->b);
-  free(w->lo); free(w->hi); free(w->xlo); free(w->xhi);
+  free(w->lo); free(w->hi); free(w->xlo); free(w->xhi); free(w->csc);
 }
 
 static int q_is_diagonal(const wprob* w) { return w->pr == NULL && w->k == 0; }
@@ -822,7 +823,7 @@ static void do_rescale(wprob* w, const orc_problem* p, const orc_options* o, sca
       rowf[i] = mx > 0.0 ? sqrt(mx) : 1.0;
     }
     for (int64_t j = 0; j < n; ++j) colf[j] = colf[j] > 0.0 ? sqrt(colf[j]) : 1.0;
-    aggregate_blocks(p, colf, 0);
+    if (!o->rescaled_cones) aggregate_blocks(p, colf, 0);
     apply_scaling_step(w, colf, rowf, sc->col, sc->row);
   }
   /* Pock-Chambolle: p_i = (sum_l |A_li|^(2-alpha))^(1/2) per column and
@@ -840,7 +841,7 @@ static void do_rescale(wprob* w, const orc_problem* p, const orc_options* o, sca
       rowf[i] = sr > 0.0 ? sqrt(sr) : 1.0;
     }
     for (int64_t j = 0; j < n; ++j) colf[j] = colf[j] > 0.0 ? sqrt(colf[j]) : 1.0;
-    aggregate_blocks(p, colf, 1);
+    if (!o->rescaled_cones) aggregate_blocks(p, colf, 1);
     apply_scaling_step(w, colf, rowf, sc->col, sc->row);
   }
   free(colf);
@@ -877,6 +878,12 @@ static void do_rescale(wprob* w, const orc_problem* p, const orc_options* o, sca
     for (int64_t t = 0; t < w->k * w->k; ++t) w->D[t] *= qs;
   }
   refresh_transpose_values(w);
+  /* rescaled-cone mode: the scaled variable x~ = S_x x / beta_b lies in S_j K_j on each
+   * cone block (beta_b is a positive scalar and drops out of the cone) */
+  if (o->rescaled_cones) {
+    w->csc = dalloc(n);
+    memcpy(w->csc, sc->col, (size_t)n * sizeof(double));
+  }
 }
 
 void orc_rescale(const orc_problem* p, const orc_options* o, double* col_scale, double* row_scale, double* beta_bc,
@@ -927,9 +934,50 @@ double orc_norm_est(int64_t m, int64_t n, const int64_t* rowptr, const int64_t* 
 /* Primal prox (eq. prox-subproblem)                                         */
 /* ------------------------------------------------------------------------- */
 
+int orc_proj_block_scaled(int type, int64_t d, double alpha, const double* sc, const double* r, const double* m,
+                          double* out) {
+  double* rs = dalloc(d);
+  double* ms = dalloc(d);
+  double* os = dalloc(d);
+  for (int64_t i = 0; i < d; ++i) {
+    rs[i] = r[i] / sc[i];
+    ms[i] = (m ? m[i] : 1.0) * sc[i] * sc[i];
+  }
+  int rc = orc_proj_block(type, d, alpha, rs, ms, os);
+  for (int64_t i = 0; i < d; ++i) out[i] = sc[i] * os[i];
+  free(rs); free(ms); free(os);
+  return rc;
+}
+
+/* Projection of the scaled variable onto the product set in the diagonal metric m
+ * (NULL: Euclidean).  In the rescaled-cone mode a cone block is S K with S = diag(csc)
+ * on the block; the change of variables u = S w turns the m-metric projection onto S K
+ * into S Pi_K^{S m S}(S^-1 r), the metric form of eq. scaling-induced-metric (and of
+ * eq. metric-rescaled-cone-equivalence).  Free, nonnegative and box coordinates are
+ * projected coordinatewise as in the cone-preserving mode (S R+ = R+). */
+static void proj_scaled(const wprob* w, const double* r, const double* m, double* out) {
+  if (!w->csc) { orc_proj_product(&w->view, r, m, out); return; }
+  const orc_problem* p = &w->view;
+  for (int64_t j = 0; j < p->nblocks; ++j) {
+    int64_t s = p->blk_start[j], d = p->blk_dim[j];
+    int t = p->blk_type[j];
+    if (t == ORC_FREE || t == ORC_NONNEG || t == ORC_BOX) {
+      orc_problem one = *p;
+      one.nblocks = 1;
+      one.blk_type = p->blk_type + j; one.blk_start = p->blk_start + j; one.blk_dim = p->blk_dim + j;
+      one.blk_alpha = p->blk_alpha + j;
+      orc_proj_product(&one, r, m, out);
+      continue;
+    }
+    orc_proj_block_scaled(t, d, p->blk_alpha[j], w->csc + s, r + s, m ? m + s : NULL, out + s);
+  }
+}
+
 /* Diagonal Q: single metric projection p = Pi^{M}(x~), M = I + tau diag(q),
  * x~ = M^{-1}(v - tau c) with v = x + tau A'y (eqs. diagonal-q-metric,
- * diagonal-q-metric-projection; M_sc = I in cone-preserving mode). */
+ * diagonal-q-metric-projection).  The scaled variable is used directly, so M_sc = I here;
+ * in the rescaled-cone mode the cone scaling enters through proj_scaled, which is the
+ * same projection written in the scaled coordinates. */
 static void prox_diag(const wprob* w, double tau, const double* v, double* out) {
   int64_t n = w->n;
   double* mm = dalloc(n);
@@ -938,7 +986,7 @@ static void prox_diag(const wprob* w, double tau, const double* v, double* out) 
     mm[i] = 1.0 + tau * w->qd[i];
     xt[i] = (v[i] - tau * w->c[i]) / mm[i];
   }
-  orc_proj_product(&w->view, xt, mm, out);
+  proj_scaled(w, xt, mm, out);
   free(mm); free(xt);
 }
 
@@ -978,7 +1026,7 @@ static int prox_bb(const wprob* w, double tau, const double* v, const double* u0
   double du = 0.0;
   for (it = 0; it < max_inner; ++it) {
     for (int64_t i = 0; i < n; ++i) trial[i] = u[i] - alpha * g[i] / J[i];
-    orc_proj_product(&w->view, trial, jacobi ? J : NULL, un);
+    proj_scaled(w, trial, jacobi ? J : NULL, un);
     du = 0.0;
     for (int64_t i = 0; i < n; ++i) du += sq(un[i] - u[i]);
     du = sqrt(du);
@@ -1070,7 +1118,7 @@ void orc_default_options(orc_options* o) {
   o->check_every = 64; o->max_iter = 100000; o->max_inner = 1000; o->tol = 1e-4;
   o->update = 0; o->avg_epoch = 64;
   o->power_iters = 200; o->power_tol = 1e-6; o->step_factor = 0.998;
-  o->force_inner = 0; o->pid = 1; o->hist_cap = 0;
+  o->force_inner = 0; o->pid = 1; o->hist_cap = 0; o->rescaled_cones = 0;
 }
 
 static void unscale(const wprob* w, const scaling* sc, const double* xs, const double* ys, double* x, double* y) {

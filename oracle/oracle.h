@@ -70,6 +70,9 @@ typedef struct {
   int force_inner;       /* 1: always use the BB inner solver even for diagonal Q */
   int pid;               /* 1: primal-weight PID at restarts */
   int hist_cap;          /* capacity of the history arrays in orc_info */
+  int rescaled_cones;    /* 0: cone-preserving block scaling (eq. cone-preserving-scaling);
+                            1: rescaled-cone mode, coordinatewise factors on cone blocks and
+                            projections onto S_j K_j (eq. scaling-induced-metric) */
 } orc_options;
 
 typedef struct {
@@ -101,6 +104,10 @@ void orc_q_apply(const orc_problem* p, const double* x, double* out);
 /* projections: metric m (diagonal, same length as the block) may be NULL for Euclidean */
 int orc_proj_block(int type, int64_t dim, double alpha, const double* r, const double* m, double* out);
 void orc_proj_product(const orc_problem* p, const double* r, const double* m, double* out);
+/* projection onto the rescaled cone S K, S = diag(sc) > 0, in the diagonal metric m
+ * (NULL: Euclidean): S Pi_K^{S m S}(S^-1 r) (eq. scaling-induced-metric) */
+int orc_proj_block_scaled(int type, int64_t dim, double alpha, const double* sc, const double* r, const double* m,
+                          double* out);
 /* 1 if r lies in the block's cone (tol absolute slack), for tests */
 int orc_in_cone(int type, int64_t dim, double alpha, const double* r, double tol);
 int orc_in_dual_cone(int type, int64_t dim, double alpha, const double* r, double tol);
