@@ -104,6 +104,9 @@ typedef struct {
   int32_t ruiz_iters;       /* 10 */
   double pc_alpha;          /* 1.0; < 0 disables Pock-Chambolle */
   int32_t bound_obj;        /* 1 */
+  int32_t rescaled_cones;   /* 0: cone-preserving block scaling (eq. "cone-preserving-scaling", default);
+                               1: rescaled-cone mode, coordinatewise factors on cone blocks, each block
+                               projected onto S_j K_j (eq. "scaling-induced-metric"); not in batched mode */
   /* inner solver */
   double eps0_in, gamma_in, eps_min_in;   /* 1e-3, 5e-4, 1e-9 */
   int32_t jacobi;           /* 1 */

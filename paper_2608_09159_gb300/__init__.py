@@ -50,6 +50,7 @@ class Cones(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("update", C.c_int32), ("rho", C.c_double),
                 ("ruiz_iters", C.c_int32), ("pc_alpha", C.c_double), ("bound_obj", C.c_int32),
+                ("rescaled_cones", C.c_int32),
                 ("eps0_in", C.c_double), ("gamma_in", C.c_double), ("eps_min_in", C.c_double),
                 ("jacobi", C.c_int32), ("max_inner", C.c_int32), ("force_inner", C.c_int32),
                 ("beta_s", C.c_double), ("beta_n", C.c_double), ("beta_a", C.c_double),

@@ -300,6 +300,7 @@ struct Handle : HandleBase {
     if (pos != n) fail(CQP_ERR_INVALID, "cone blocks do not cover 0..n-1");
     // segment table in the new order: free, nonneg, soc, rsoc, exp, pow (stable within a type)
     std::vector<int64_t> seg_new, seg_old;
+    if (B && o.rescaled_cones) fail(CQP_ERR_UNSUPPORTED, "rescaled-cone mode in a batch");
     std::vector<int64_t> soc_off{0}, rsoc_off{0};
     std::vector<double> pow_al;
     int64_t cnt[6] = {0, 0, 0, 0, 0, 0};
@@ -559,7 +560,7 @@ struct Handle : HandleBase {
       if (m > 0) { count_launch(); cqp::k_row_stat<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp, av, 0, 0.0, rowf); }
       count_launch(); cqp::k_sqrt_or_one<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, colf);
       if (m > 0) { count_launch(); cqp::k_sqrt_or_one<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, rowf); }
-      aggregate(0);
+      if (!o.rescaled_cones) aggregate(0);
       scale_step();
     }
     if (o.pc_alpha >= 0.0) {
@@ -568,7 +569,7 @@ struct Handle : HandleBase {
       if (m > 0) { count_launch(); cqp::k_row_stat<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp, av, 1, al, rowf); }
       count_launch(); cqp::k_sqrt_or_one<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, colf);
       if (m > 0) { count_launch(); cqp::k_sqrt_or_one<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, rowf); }
-      aggregate(1);
+      if (!o.rescaled_cones) aggregate(1);
       scale_step();
     }
     count_launch(); cqp::k_div<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, cv, col);
@@ -628,6 +629,13 @@ struct Handle : HandleBase {
     }
     count_launch(); cqp::k_convert<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, qv, qT);
     count_launch(); cqp::k_convert<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, jdv, jT);
+    // rescaled-cone mode: a cone block of the scaled variable x~ = col x / beta_b is S K with
+    // S = diag(col) on the block (the scalar beta_b drops out of a cone)
+    T* cscT = nullptr;
+    if (o.rescaled_cones && n > base[2]) {
+      cscT = mem.alloc<T>(n);
+      count_launch(); cqp::k_convert<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, col, cscT);
+    }
     // R is stored with its row count padded to a multiple of 8 (zero rows), so the
     // inner step's register loop over a fixed width needs no per-row predicate
     T* RT = nullptr;
@@ -734,7 +742,7 @@ struct Handle : HandleBase {
     }
     P.p_rp = p_rp; P.p_ci = p_ci; P.p_v = pT;
     P.c = cT; P.b = bT; P.col = col; P.row = row; P.beta_b = beta_b; P.beta_c = beta_c;
-    P.rhi = rhiT; P.xlo = xloT; P.xhi = xhiT;
+    P.rhi = rhiT; P.xlo = xloT; P.xhi = xhiT; P.csc = cscT;
     P.n_free = cnt[0]; P.n_nonneg = cnt[1];
     P.n_soc = n_soc; P.soc_off = d_soc; P.n_rsoc = n_rsoc; P.rsoc_off = d_rsoc;
     P.n_exp = n_exp; P.exp_base = base[4]; P.n_pow = n_pow; P.pow_base = base[5]; P.pow_alpha = palpha;

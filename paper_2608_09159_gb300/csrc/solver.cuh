@@ -61,6 +61,7 @@ struct Prob {
   int tpr_a, tpr_t, tpr_p;                            // threads per row of A, A' and P
   const T* rhi;                                       // general form: scaled row upper bounds (null: A x = b)
   const T* xlo; const T* xhi;                         // general form: scaled bounds of the free segment (null: free)
+  const T* csc;                                       // rescaled-cone mode: S_x per coordinate (null: blocks are cones)
 };
 
 template <typename T>
@@ -363,6 +364,8 @@ struct Solver {
   // Projects, in place, the owned SOC/RSOC/EXP/POW blocks of x in the metric
   //   kEuclid: M = I;  kJacobi: m_i = diag(Q~)_i + 1/tau (eq. jacobi-inner-metric);
   //   kDiagQ: m_i = 1 + tau q_i (eq. diagonal-q-metric).
+  // Rescaled-cone mode (GEN kernels with P.csc): a block is S K, S = diag(csc), and its
+  // m-metric projection is S Pi_K^{S m S}(S^-1 x) (eq. scaling-induced-metric).
   // Ends with __syncthreads.
   enum MetricKind : int { kEuclid = 0, kJacobi = 1, kDiagQ = 2 };
   __device__ __forceinline__ T metric(int kind, int64_t i, T tau, T itau) const {
@@ -370,7 +373,8 @@ struct Solver {
   }
   __device__ __noinline__ void project_owned_cones(T* x, int kind, double tau_d) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = nwarps();
-    const bool euclid = kind == kEuclid;
+    const T* csc = GEN ? P.csc : nullptr;
+    const bool euclid = kind == kEuclid && !csc;
     const T tau = T(tau_d), itau = T(1.0 / tau_d);
     T* zs = cbuf + warp * 2 * kConeStage;
     T* ms = zs + kConeStage;
@@ -387,8 +391,15 @@ struct Solver {
       T* z = staged ? zs : x + s;
       T* mm = staged ? ms : W.mbuf + s;
       for (int i = lane; i < d; i += 32) {
-        if (staged) zs[i] = x[s + i];
-        if (!euclid) mm[i] = metric(kind, s + i, tau, itau);
+        if (csc) {
+          const T si = csc[s + i];
+          const T zi = x[s + i] / si;
+          if (staged) zs[i] = zi; else x[s + i] = zi;
+          mm[i] = metric(kind, s + i, tau, itau) * si * si;
+        } else {
+          if (staged) zs[i] = x[s + i];
+          if (!euclid) mm[i] = metric(kind, s + i, tau, itau);
+        }
       }
       __syncwarp();
       float* gs = O.warm_roots ? W.root + (pass == 0 ? blk : P.n_soc + blk) : nullptr;
@@ -399,8 +410,8 @@ struct Solver {
         if (euclid) warp_rsoc_euclid<T>(z, d, lane);
         else warp_rsoc_metric<T>(z, mm, d, lane, gs);
       }
-      if (staged) {
-        for (int i = lane; i < d; i += 32) x[s + i] = zs[i];
+      if (staged || csc) {
+        for (int i = lane; i < d; i += 32) x[s + i] = (staged ? zs[i] : x[s + i]) * (csc ? csc[s + i] : T(1));
         __syncwarp();
       }
     }
@@ -413,6 +424,17 @@ struct Solver {
         const int64_t s = P.exp_base + 3 * e;
         double o[3];
         float* gs = O.warm_roots ? W.root + P.n_soc + P.n_rsoc + e : nullptr;
+        if (csc) {
+          double sc3[3], z3[3], m3[3];
+          for (int q = 0; q < 3; ++q) {
+            sc3[q] = (double)csc[s + q];
+            z3[q] = (double)x[s + q] / sc3[q];
+            m3[q] = (double)metric(kind, s + q, tau, itau) * sc3[q] * sc3[q];
+          }
+          exp_proj_metric(z3[0], z3[1], z3[2], m3[0], m3[1], m3[2], o);
+          for (int q = 0; q < 3; ++q) x[s + q] = T(o[q] * sc3[q]);
+          continue;
+        }
         if (euclid) exp_proj_euclid((double)x[s], (double)x[s + 1], (double)x[s + 2], o, gs);
         else exp_proj_metric((double)x[s], (double)x[s + 1], (double)x[s + 2], (double)metric(kind, s, tau, itau),
                              (double)metric(kind, s + 1, tau, itau), (double)metric(kind, s + 2, tau, itau), o);
@@ -422,6 +444,18 @@ struct Solver {
       const int64_t e = own.p0 + (item - nexp);
       const int64_t s = P.pow_base + 3 * e;
       double o[3];
+      if (csc) {
+        double sc3[3], z3[3], m3[3];
+        for (int q = 0; q < 3; ++q) {
+          sc3[q] = (double)csc[s + q];
+          z3[q] = (double)x[s + q] / sc3[q];
+          m3[q] = (double)metric(kind, s + q, tau, itau) * sc3[q] * sc3[q];
+        }
+        pow_proj(z3[0], z3[1], z3[2], P.pow_alpha[e], m3[0], m3[1], m3[2], o,
+                 O.warm_roots ? W.root + P.n_soc + P.n_rsoc + P.n_exp + e : nullptr);
+        for (int q = 0; q < 3; ++q) x[s + q] = T(o[q] * sc3[q]);
+        continue;
+      }
       pow_proj((double)x[s], (double)x[s + 1], (double)x[s + 2], P.pow_alpha[e], (double)metric(kind, s, tau, itau),
                (double)metric(kind, s + 1, tau, itau), (double)metric(kind, s + 2, tau, itau), o,
                O.warm_roots ? W.root + P.n_soc + P.n_rsoc + P.n_exp + e : nullptr);

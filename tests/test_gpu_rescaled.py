@@ -1,0 +1,85 @@
+"""GPU parity of the rescaled-cone mode (option rescaled_cones = 1, Sec. 4.2.2).
+
+* One outer iteration in FP64 with scaling on matches the oracle's first candidate in
+  the same mode. The two differ only in the power-iteration estimate of ||A||_2, so the
+  bound is 1e-6 relative; a wrong cone transform is an O(1) difference.
+* min 1/2||x - p||^2 s.t. a'x = beta over one SOC/RSOC/exp/pow block equals the bisection
+  reference Pi_K(p + lam a), in FP64.
+* Scaled-down benchmark workloads reach rel-KKT <= 1e-4, re-measured by the oracle, in
+  FP32 and FP64. Their objective matches the oracle's solve in the same mode, and x
+  matches the oracle's tight solution where it is unique.
+* The batched mode rejects the option.
+"""
+import numpy as np
+import pytest
+
+import instances as I
+from test_oracle_rescaled import _bisect_reference, _one_cone_row
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2608_09159_gb300 as g
+    g.build()
+    g.lib()
+    return g
+
+
+def _rel(a, b):
+    return abs(a - b) / (1.0 + abs(a) + abs(b))
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_first_iteration_matches_oracle(gpu, orc, k):
+    inst = I.small_config(k)
+    s = gpu.Solver(inst, precision=1, team=2, max_iter=1, eps0_in=1e-13, max_inner=100000, warm_roots=0,
+                   rescaled_cones=1)
+    x, y, res = s.solve()
+    s.close()
+    xr, yr, info = orc.solve(inst, max_iter=1, eps0_in=1e-13, max_inner=100000, rescaled_cones=1)
+    assert abs(res["norm_A"] - info["norm_A"]) <= 1e-5 * info["norm_A"]
+    assert np.abs(x - xr).max() <= 1e-6 * (1 + np.abs(xr).max())
+    assert np.abs(y - yr).max() <= 1e-6 * (1 + np.abs(yr).max())
+
+
+@pytest.mark.parametrize("t,d", [(I.CONE_SOC, 6), (I.CONE_RSOC, 6), (I.CONE_EXP, 3), (I.CONE_POW, 3)])
+def test_one_row_over_one_cone(gpu, orc, t, d):
+    rng = np.random.default_rng(40 + t)
+    al = 0.35 if t == I.CONE_POW else 0.0
+    inst, a, p, beta = _one_cone_row(t, d, al, rng)
+    ref = _bisect_reference(orc, t, al, a, p, beta)
+    s = gpu.Solver(inst, precision=1, tol=1e-10, max_iter=200000, time_limit_s=60.0, rescaled_cones=1)
+    x, y, res = s.solve()
+    s.close()
+    assert res["rc"] == 0, res
+    assert np.abs(x - ref).max() <= 1e-6 * (1 + np.abs(ref).max())
+
+
+@pytest.mark.parametrize("k", [2, 3])
+@pytest.mark.parametrize("precision", [1, 0])
+def test_small_configs_solve(gpu, orc, k, precision):
+    inst = I.small_config(k)
+    s = gpu.Solver(inst, precision=precision, max_iter=200000, tol=1e-4, time_limit_s=120.0, rescaled_cones=1)
+    x, y, res = s.solve()
+    s.close()
+    assert res["rc"] == 0, res
+    rep = orc.kkt(inst, x, y)
+    assert rep["rel_kkt"] <= 1.5e-4, rep
+    assert abs(rep["rel_kkt"] - res["kkt"]["rel_kkt"]) <= 1e-5 + 0.05 * rep["rel_kkt"]
+    xo, yo, info = orc.solve(inst, max_iter=200000, tol=1e-4, rescaled_cones=1)
+    assert _rel(rep["pobj"], info["kkt"]["pobj"]) <= 5e-4
+    if k == 2:                                # Q positive definite: x* unique
+        xs, ys, _ = orc.solve(inst, max_iter=400000, tol=1e-9)
+        assert np.linalg.norm(x - xs) <= 2e-2 * (1 + np.linalg.norm(xs))
+
+
+def test_batch_rejects_rescaled_cones(gpu):
+    batch = I.small_config(4)
+    with pytest.raises(gpu.CQPError) as e:
+        gpu.BatchSolver(batch, rescaled_cones=1)
+    assert e.value.code == -6       # CQP_ERR_UNSUPPORTED
