@@ -527,6 +527,80 @@ def large_qp(n=200_000_000, m=50_000_000, seed=1005):
     return make_instance("large_qp_n%d_m%d" % (n, m), m, n, a_rowptr, cols.ravel(), vals.ravel(), c, b,
                          btype, bstart, bdim, balpha, q_diag=q, p_csr=(p_rowptr, p_colind, p_val), x_feasible=x0)
 
+# ---------------------------------------------------------------------------
+# original-form problems for the modeling front-ends (no reformulation here)
+# ---------------------------------------------------------------------------
+
+def _rows_uniform(stream, m, n, per_row):
+    """CSR with per_row[i] uniform columns in row i (repeats summed) and N(0,1) values."""
+    per_row = np.asarray(per_row, dtype=np.int64)
+    tot = int(per_row.sum())
+    rows = np.repeat(np.arange(m, dtype=np.int64), per_row)
+    cols = stream.integers(tot, 0, n)
+    vals = stream.normal(tot)
+    return _coo_to_csr(m, n, rows, cols, vals)
+
+
+def lasso_problem(m=677_399, n=47_236, density=1.55e-3, seed=1006, support=0.1, noise=0.1):
+    """Synthetic Lasso data min ||Ax - b||^2 + lam ||x||_1 with the shape and density of the
+    rcv1_test instance of the paper's Lasso table (its values are not used: A has a
+    Poisson(n density) number of uniform columns per row with N(0,1)/sqrt(row count)
+    values, b = A x_true + noise with a support-fraction sparse x_true).  lam is the
+    paper's 0.01 ||A'b||_inf."""
+    st = Stream(seed, 0)
+    lam_row = n * density
+    # Poisson counts by inversion of uniforms is slow for large means: use the normal
+    # approximation, rounded and clipped to >= 1 (every sample has a feature)
+    cnt = np.maximum(1, np.rint(lam_row + np.sqrt(lam_row) * st.normal(m))).astype(np.int64)
+    rp, ci, v = _rows_uniform(st, m, n, cnt)
+    v = v / np.sqrt(np.repeat(np.diff(rp), np.diff(rp)).astype(np.float64))
+    xt = np.zeros(n)
+    k = max(1, int(support * n))
+    idx = st.integers(k, 0, n)
+    xt[idx] = st.normal(k)
+    b = csr_matvec(rp, ci, v, xt) + noise * st.normal(m)
+    aty = np.zeros(n)
+    np.add.at(aty, ci, v * np.repeat(b, np.diff(rp)))
+    lam = 0.01 * float(np.abs(aty).max())
+    return dict(m=m, n=n, a_rowptr=rp, a_colind=ci, a_val=v, b=b, lam=lam, x_true=xt)
+
+
+def qcqp_problem(n=2000, m_lin=500, p=5, k=20, k0=10, lin_per_row=10, quad_per_row=20, seed=1007, box=1.0,
+                 c_nnz=None):
+    """Synthetic convex QCQP in the form of eq. qcqp-benchmark-form:
+        min 1/2 x'Q0 x + c0'x  s.t.  lo <= A x <= hi,  -box <= x <= box,
+                                     1/2 ||R_i x||^2 + c_i'x <= d_i  (Q_i = R_i'R_i), i = 1..p
+    Q0 = diag(q0) + R0'R0 (q0 ~ U[0.1, 1], R0 k0 x n N(0, 1/n)); A has lin_per_row
+    N(0,1) entries per row; R_i has k rows with quad_per_row N(0,1) entries each; c_i
+    ~ N(0, 0.1^2) (dense, or c_nnz uniform positions when given).  x0 ~ U(-box/2, box/2) is strictly feasible: the rows get bounds
+    A x0 -/+ U[0.1, 1] (a third one-sided), and d_i = value at x0 + U[0.05, 0.5].
+    c0 ~ N(0,1) pulls the optimum onto the constraints."""
+    st = Stream(seed, 0)
+    x0 = st.uniform(n, -0.5 * box, 0.5 * box)
+    q0 = st.uniform(n, 0.1, 1.0)
+    R0 = st.normal(k0 * n, 0.0, 1.0 / np.sqrt(n)).reshape(k0, n)
+    c0 = st.normal(n)
+    arp, aci, av = _rows_uniform(st, m_lin, n, np.full(m_lin, lin_per_row))
+    ax0 = csr_matvec(arp, aci, av, x0)
+    lo = ax0 - st.uniform(m_lin, 0.1, 1.0)
+    hi = ax0 + st.uniform(m_lin, 0.1, 1.0)
+    third = m_lin // 3
+    lo[:third] = -np.inf
+    quad = []
+    for _ in range(p):
+        rrp, rci, rv = _rows_uniform(st, k, n, np.full(k, quad_per_row))
+        if c_nnz is None:
+            ci = st.normal(n, 0.0, 0.1)
+        else:
+            ci = np.zeros(n)
+            ci[st.integers(c_nnz, 0, n)] = st.normal(c_nnz, 0.0, 0.1)
+        rx = csr_matvec(rrp, rci, rv, x0)
+        d = 0.5 * float(rx @ rx) + float(ci @ x0) + float(st.uniform(1, 0.05, 0.5)[0])
+        quad.append(dict(R=(rrp, rci, rv), k=k, c=ci, d=d))
+    return dict(n=n, c0=c0, q0_diag=q0, q0_R=R0, A=(arp, aci, av), m_lin=m_lin, row_lo=lo, row_hi=hi,
+                x_lo=np.full(n, -box), x_hi=np.full(n, box), quad=quad, x_feasible=x0)
+
+
 CONFIGS = {
     1: lambda: sparse_qp_nonneg(),
     2: lambda: socp_mix(),

@@ -92,6 +92,7 @@ def lib():
         _lib.orc_proj_block_scaled.restype = C.c_int
         _lib.orc_proj_block_scaled.argtypes = [C.c_int, C.c_int64, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                                C.c_void_p]
+        _lib.orc_power_start.argtypes = [C.c_int64, C.c_void_p]
         _lib.orc_norm_est.argtypes = [C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                       C.c_double, C.c_void_p]
         _lib.orc_pdhg_operator.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
@@ -250,6 +251,12 @@ def rescale(inst, **opts):
     c, b = np.zeros(n), np.zeros(m)
     lib().orc_rescale(P.ptr, C.byref(o), _p(col), _p(row), _p(bc), _p(av), _p(c), _p(b))
     return dict(col=col, row=row, beta_b=bc[0], beta_c=bc[1], a_val=av, c=c, b=b)
+
+
+def power_start(n):
+    out = np.zeros(n)
+    lib().orc_power_start(n, _p(out))
+    return out
 
 
 def norm_est(rowptr, colind, val, n, iters=200, tol=1e-6):

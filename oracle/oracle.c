@@ -903,16 +903,37 @@ void orc_rescale(const orc_problem* p, const orc_options* o, double* col_scale, 
   wprob_free(&w);
 }
 
+/* Start vector of the power iteration (reading): entry j is 1/2 + U_j with U_j in [0, 1)
+ * the top 53 bits of output j+1 of SplitMix64 (Steele, Lea and Flood, "Fast splittable
+ * pseudorandom number generators", OOPSLA 2014) from state 0, i.e. the finaliser applied to
+ * (j+1) times the golden-ratio increment.  An all-ones start can be orthogonal to the top
+ * singular subspace (the estimate then converges to a smaller singular value); a positive
+ * perturbation of it keeps all-ones' overlap with the leading direction of scaled matrices. */
+static double power_start(uint64_t j) {
+  uint64_t z = (j + 1) * 0x9e3779b97f4a7c15ULL;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  z = z ^ (z >> 31);
+  return 0.5 + (double)(z >> 11) / 9007199254740992.0;
+}
+
+void orc_power_start(int64_t n, double* out) {
+  for (int64_t j = 0; j < n; ++j) out[j] = power_start((uint64_t)j);
+}
+
 /* ||A||_2 (needed for eta = 0.998/||A||_2, eq. practical-stepsizes).  The paper
  * does not say how it is estimated; reading: power iteration on A'A from the
- * normalised all-ones vector, Rayleigh quotient sigma^2 = ||A v||^2, stop when
+ * normalised SplitMix64 start above, Rayleigh quotient sigma^2 = ||A v||^2, stop when
  * the estimate changes by <= tol relative or after `iters` iterations. */
 double orc_norm_est(int64_t m, int64_t n, const int64_t* rowptr, const int64_t* colind, const double* val,
                     int iters, double tol, int* iters_used) {
   double* v = dalloc(n);
   double* av = dalloc(m);
   double* z = dalloc(n);
-  for (int64_t j = 0; j < n; ++j) v[j] = 1.0 / sqrt((double)n);
+  double vn = 0.0;
+  for (int64_t j = 0; j < n; ++j) { v[j] = power_start((uint64_t)j); vn += v[j] * v[j]; }
+  vn = sqrt(vn);
+  for (int64_t j = 0; j < n; ++j) v[j] = vn > 0.0 ? v[j] / vn : 0.0;
   double sig = 0.0;
   int it;
   for (it = 0; it < iters; ++it) {

@@ -120,6 +120,9 @@ void orc_kkt(const orc_problem* p, const double* x, const double* y, orc_kkt_rep
 void orc_rescale(const orc_problem* p, const orc_options* o,
                  double* col_scale, double* row_scale, double* beta_bc,
                  double* a_val_out, double* c_out, double* b_out);
+/* the unnormalised start vector of orc_norm_est: entry j = 1/2 + (top 53 bits of SplitMix64
+ * output j+1 from state 0) / 2^53 */
+void orc_power_start(int64_t n, double* out);
 double orc_norm_est(int64_t m, int64_t n, const int64_t* rowptr, const int64_t* colind, const double* val,
                     int iters, double tol, int* iters_used);
 

@@ -397,6 +397,7 @@ struct Handle : HandleBase {
     const double* a_v_in = (const double*)upload(A->val, nnz * sizeof(double));
     const double* c_d = (const double*)upload(c_in, n * sizeof(double));
     const bool general = G != nullptr;
+    int64_t* d_xoff_old = nullptr;   // batch: instance x offsets in the caller's coordinates
     if (general && m > 0 && (!G->row_lo || !G->row_hi)) fail(CQP_ERR_INVALID, "row_lo and row_hi are required");
     const double* b_d = (const double*)upload(general ? G->row_lo : b_in, m * sizeof(double));
     const double* bhi_d = general ? (const double*)upload(G->row_hi, m * sizeof(double)) : nullptr;
@@ -457,6 +458,7 @@ struct Handle : HandleBase {
       if (m > 0) { count_launch(); cqp::k_check_blockdiag<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp64, a_ci_in, d_ir, d_ic, bad); }
       if (has_p) { count_launch(); cqp::k_check_blockdiag<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, p_rp64, p_ci_in, d_ic, d_ic, bad); }
       int64_t* d_xo = tmp.alloc<int64_t>(bcount + 1);
+      d_xoff_old = d_xo;
       int64_t* d_ro = tmp.alloc<int64_t>(bcount + 1);
       CK(cudaMemcpyAsync(d_xo, B->x_off, (bcount + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
       CK(cudaMemcpyAsync(d_ro, B->row_off, (bcount + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
@@ -663,8 +665,9 @@ struct Handle : HandleBase {
       count_launch(); k_sumsq_range<<<cqp::grid_for(n - base[2]), cqp::kSetupThreads, 0, st>>>(base[2], n, qv, acc);
       CK(cudaMemcpyAsync(&qcone, acc, sizeof(double), cudaMemcpyDeviceToHost, st));
     }
-    // ---- ||A~||_2 by power iteration on A~'A~ (reading: all-ones start, Rayleigh
-    // quotient, stop at power_tol relative change or power_iters) ---------------------------
+    // ---- ||A~||_2 by power iteration on A~'A~ (reading: SplitMix64 start keyed by the
+    // caller's coordinate index, Rayleigh quotient, stop at power_tol relative change or
+    // power_iters) --------------------------------------------------------------------------
     {
       double* z = tmp.alloc<double>(n);
       double* w = tmp.alloc<double>(std::max<int64_t>(m, 1));
@@ -675,7 +678,11 @@ struct Handle : HandleBase {
       CK(cudaMemsetAsync(pcount, 0, sizeof(unsigned), st));
       CK(cudaMemsetAsync(perr, 0, sizeof(int), st));
       CK(cudaMemsetAsync(pout, 0, 2 * sizeof(double), st));
-      count_launch(); cqp::k_fill<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, z, 1.0 / std::sqrt((double)n));
+      if (!batched) {
+        count_launch(); cqp::k_power_start<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, perm, z);
+        const double zn = std::sqrt(dev_dot(z, nullptr, n, part, one, st));
+        count_launch(); cqp::k_scal<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, z, zn > 0.0 ? 1.0 / zn : 0.0);
+      }
       double sig = 0.0;
       if (batched) {
         double* d_eta = tmp.alloc<double>(bcount);
@@ -684,7 +691,7 @@ struct Handle : HandleBase {
         count_launch();
         cqp::k_inst_power<T><<<(int)std::min<int64_t>(bcount, 8 * nsm), cqp::kBatchSetupThreads, 0, st>>>(
             bcount, d_own, a_rp, a_ci, a_v, t_rp, t_ci, t_v, cv, bv, z, w, o.power_iters, o.power_tol,
-            o.step_factor, d_eta, d_om, d_na);
+            o.step_factor, d_eta, d_om, d_na, perm, d_xoff_old);
         h_eta.resize(bcount);
         h_om.resize(bcount);
         std::vector<double> h_na(bcount);

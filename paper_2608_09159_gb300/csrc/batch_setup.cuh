@@ -10,6 +10,7 @@
 #include <cstdint>
 
 #include "common.cuh"
+#include "setup.cuh"
 #include "solver.cuh"
 
 namespace cqp {
@@ -85,23 +86,30 @@ __global__ void __launch_bounds__(kBatchSetupThreads) k_inst_bound_obj(
 }
 
 // ||A~_i||_2 by power iteration on the instance's block (same reading as k_power:
-// all-ones start, Rayleigh quotient, stop at `tol` relative change or `iters`),
+// SplitMix64 start keyed by the instance-local coordinate index perm[j] - x_off_old[i],
+// Rayleigh quotient, stop at `tol` relative change or `iters`),
 // eta_i = step / ||A~_i||, omega0_i = ||c~_i|| / ||b~_i||.
 template <typename T>
 __global__ void __launch_bounds__(kBatchSetupThreads) k_inst_power(
     int64_t count, const Own* own, const int32_t* __restrict__ a_rp, const int32_t* __restrict__ a_ci,
     const T* __restrict__ a_v, const int32_t* __restrict__ t_rp, const int32_t* __restrict__ t_ci,
     const T* __restrict__ t_v, const double* cv, const double* bv, double* z, double* w, int iters, double tol,
-    double step, double* eta, double* omega0, double* norm_a) {
+    double step, double* eta, double* omega0, double* norm_a, const int64_t* perm, const int64_t* x_off_old) {
   __shared__ double red[2 * (kBatchSetupThreads / 32)];
   __shared__ double tot[2];
   for (int64_t i = blockIdx.x; i < count; i += gridDim.x) {
     const Own o = own[i];
-    int64_t nn = 0;
-    for (int seg = 0; seg < 6; ++seg) nn += o.x1[seg] - o.x0[seg];
-    const double z0 = nn > 0 ? 1.0 / sqrt((double)nn) : 0.0;
+    double z2[1] = {0.0};
     for (int seg = 0; seg < 6; ++seg)
-      for (int64_t j = o.x0[seg] + threadIdx.x; j < o.x1[seg]; j += blockDim.x) z[j] = z0;
+      for (int64_t j = o.x0[seg] + threadIdx.x; j < o.x1[seg]; j += blockDim.x) {
+        const double u = power_start_value((uint64_t)(perm[j] - x_off_old[i]) + 1);
+        z[j] = u;
+        z2[0] += u * u;
+      }
+    block_sum<1>(z2, red, tot);
+    const double zinv = tot[0] > 0.0 ? 1.0 / sqrt(tot[0]) : 0.0;
+    for (int seg = 0; seg < 6; ++seg)
+      for (int64_t j = o.x0[seg] + threadIdx.x; j < o.x1[seg]; j += blockDim.x) z[j] *= zinv;
     __syncthreads();
     double sig = 0.0, zscale = 1.0;
     for (int it = 0; it < iters && o.row1 > o.row0; ++it) {

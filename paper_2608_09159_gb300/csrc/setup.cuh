@@ -296,8 +296,27 @@ __global__ void k_box_bounds(int64_t nf, const int64_t* perm, const uint8_t* mas
   }
 }
 
+// ---- start vector of the power iteration (reading): entry j is 1/2 + U_j, U_j in [0, 1) the
+// top 53 bits of output j+1 of the SplitMix64 generator (Steele, Lea and Flood, OOPSLA 2014)
+// started from state 0.  Entries are keyed by the caller's coordinate index, so the start
+// does not depend on the solver's permutation.  An all-ones start can be exactly orthogonal
+// to the top singular subspace (e.g. the Lasso reformulation with A = I), and the estimate
+// then stalls at a smaller singular value; the positive perturbation keeps all-ones'
+// overlap with the leading direction of rescaled matrices (same iteration count there).
+__device__ __forceinline__ double power_start_value(uint64_t idx) {
+  uint64_t z = idx * 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  z ^= z >> 31;
+  return 0.5 + (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
+// z[i] = start value of the caller's coordinate perm[i] (unnormalised)
+__global__ void k_power_start(int64_t n, const int64_t* perm, double* z) {
+  CQP_GRID_LOOP(i, n) z[i] = power_start_value((uint64_t)perm[i] + 1);
+}
+
 // ---- ||A~||_2 by power iteration on A~'A~, all iterations in one cooperative launch
-// (eq. practical-stepsizes; reading: all-ones start, Rayleigh quotient ||A v|| with
+// (eq. practical-stepsizes; reading: SplitMix64 start, Rayleigh quotient ||A v|| with
 // ||v|| = 1, stop at `tol` relative change or `iters` iterations).  v is kept as
 // z / ||z||: each iteration computes w = A z / ||z|| (slot 0: ||w||^2) and z = A' w
 // (slot 1: ||z||^2), so two grid barriers per iteration and no host round trip.

@@ -7,6 +7,7 @@ identity and Fejer monotonicity of the exact PDHG step (Sec. 2, Lemma
 bound (eq. rh-residual-decay).
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -369,3 +370,34 @@ def test_small_configs_reach_tolerance(orc, k):
     # restarts: KKT at the last check is far below the first (trend of the restarted scheme)
     h = info["hist"]
     assert h["kkt"][-1] < h["kkt"][0]
+
+
+def _golden_splitmix():
+    path = os.path.join(os.path.dirname(__file__), "golden", "splitmix64_state0.txt")
+    with open(path) as f:
+        return [int(l, 16) for l in f if l.strip() and not l.startswith("#")]
+
+
+def test_power_start_is_splitmix64(orc):
+    # entry j of the start vector is 1/2 + (top 53 bits of SplitMix64 output j+1 from state 0) / 2^53
+    vals = _golden_splitmix()
+    ref = np.array([0.5 + (w >> 11) / 2.0 ** 53 for w in vals])
+    assert np.array_equal(orc.power_start(len(vals)), ref)
+
+
+def test_norm_estimate_symmetric_lasso_model(orc):
+    # the Lasso reformulation with A = I after rescaling: its top singular vector is
+    # orthogonal to the all-ones vector, which an all-ones start would never leave
+    from oracle import frontends as OF
+    b = np.random.default_rng(54).normal(size=12)
+    inst = OF.lasso(np.eye(12), b, 0.8)
+    sc = orc.rescale(inst)
+    m, n = inst["m"], inst["n"]
+    A = np.zeros((m, n))
+    for i in range(m):
+        for t in range(inst["a_rowptr"][i], inst["a_rowptr"][i + 1]):
+            A[i, inst["a_colind"][t]] = sc["a_val"][t]
+    top = np.linalg.svd(A, compute_uv=False)[0]
+    assert abs(np.ones(n) @ np.linalg.svd(A)[2][0]) <= 1e-12 * np.sqrt(n)
+    s, it = orc.norm_est(inst["a_rowptr"], inst["a_colind"], sc["a_val"], n)
+    assert abs(s - top) <= 1e-5 * top
