@@ -779,14 +779,16 @@ struct Handle : HandleBase {
         CK(cudaEventCreate(&e1));
         int best = 8;
         float best_ms = 1e30f;
-        for (int t = 1; t <= 16; t <<= 1) {   // 32 lanes per row never won on these matrices
+        // timed on the solver's grid (one 512-thread block per SM), so the choice reflects the
+        // loads in flight the persistent kernel has; 32 lanes per row never won
+        for (int t = 1; t <= 16; t <<= 1) {
           count_launch();
-          CK(cqp::launch_spmv<T>(rows, rp, ci, v, xs, ys, t, st));
+          CK(cqp::launch_spmv<T>(rows, rp, ci, v, xs, ys, t, st, nsm));
           float tot = 1e30f;
           for (int r = 0; r < 2; ++r) {
             CK(cudaEventRecord(e0, st));
             count_launch();
-            CK(cqp::launch_spmv<T>(rows, rp, ci, v, xs, ys, t, st));
+            CK(cqp::launch_spmv<T>(rows, rp, ci, v, xs, ys, t, st, nsm));
             CK(cudaEventRecord(e1, st));
             CK(cudaEventSynchronize(e1));
             float ms = 0.f;

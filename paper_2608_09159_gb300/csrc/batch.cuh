@@ -52,6 +52,7 @@ __global__ void __launch_bounds__(512, 1) pdhg_batch_kernel(KernelArgs<T> a, Bat
     load_state(C, b.S + i);
     Solver<T, CtaTeam> s(Pi, W, a.O, team, C, scratch, wacc, cbuf);
     s.own = b.own[i];
+    s.own.g_a = Pi.tpr_a; s.own.g_t = Pi.tpr_t; s.own.g_p = Pi.tpr_p;
     const Own& o = s.own;
     // scaled start x~ = col x0 / beta_b (permuted), y~ = row y0 / beta_c; anchors and
     // candidates start there, averages at zero

@@ -186,22 +186,43 @@ __device__ __forceinline__ int64_t lower_bound_rows(const int* rowptr, int64_t n
   return lo;
 }
 
-// rows of a CSR matrix shared among nb blocks with (almost) equal nnz + row count
-__device__ __forceinline__ void split_rows_by_nnz(const int* rowptr, int64_t nrows, int b, int nb, int64_t& lo,
-                                                  int64_t& hi) {
-  const int64_t nnz = rowptr[nrows];
-  const int64_t work = nnz + nrows;
-  // balance nnz + rows: search on rowptr[r] + r
+// Work of a CSR row for the block splits: its entries plus kRowWork for the row itself
+// (row pointers, the result, and the per-coordinate vector work of the phases that walk
+// the same range), so a range of very short rows is not handed to one block.
+constexpr int64_t kRowWork = 8;
+
+// [lo, hi) share for block b of nb of the rows [base, base + count) of a CSR matrix,
+// balancing nnz + kRowWork per row (offsets relative to base)
+__device__ __forceinline__ void split_rows_weighted(const int* rowptr, int64_t base, int64_t count, int b, int nb,
+                                                    int64_t& lo, int64_t& hi) {
+  const int64_t r0 = rowptr[base];
+  const int64_t work = (int64_t)rowptr[base + count] - r0 + kRowWork * count;
   auto find = [&](int64_t target) {
-    int64_t l = 0, h = nrows;
+    int64_t l = 0, h = count;
     while (l < h) {
-      int64_t mid = (l + h) >> 1;
-      if ((int64_t)rowptr[mid] + mid < target) l = mid + 1; else h = mid;
+      const int64_t mid = (l + h) >> 1;
+      if ((int64_t)rowptr[base + mid] - r0 + kRowWork * mid < target) l = mid + 1; else h = mid;
     }
     return l;
   };
   lo = b == 0 ? 0 : find((work * b) / nb);
-  hi = b == nb - 1 ? nrows : find((work * (b + 1)) / nb);
+  hi = b == nb - 1 ? count : find((work * (b + 1)) / nb);
+}
+
+// rows of a CSR matrix shared among nb blocks with (almost) equal nnz + kRowWork * rows
+__device__ __forceinline__ void split_rows_by_nnz(const int* rowptr, int64_t nrows, int b, int nb, int64_t& lo,
+                                                  int64_t& hi) {
+  split_rows_weighted(rowptr, 0, nrows, b, nb, lo, hi);
+}
+
+// Lanes per row for one block's rows: the tuned width, unless the block's rows average
+// less than a quarter of it, then the largest power of two not above their mean length
+// (short rows under a wide group leave most lanes idle and serialise the block).
+__device__ __forceinline__ int block_group_width(int tuned, int64_t nnz, int64_t rows) {
+  if (rows <= 0 || 4 * nnz >= (int64_t)tuned * rows) return tuned;
+  int g = 1;
+  while (2 * g * rows <= nnz) g *= 2;
+  return g;
 }
 
 }  // namespace cqp

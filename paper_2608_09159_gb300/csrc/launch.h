@@ -39,9 +39,11 @@ template <typename T>
 size_t pdhg_smem(int threads);
 
 // Kernel-level entry points used by the C ABI.
+// blocks <= 0: four 512-thread blocks per SM; the threads-per-row autotuner passes the
+// solver's own grid (one block per SM) so it times the concurrency the solver runs at.
 template <typename T>
 cudaError_t launch_spmv(int64_t nrows, const int* rp, const int* ci, const T* v, const T* x, T* y, int tpr,
-                        cudaStream_t st);
+                        cudaStream_t st, int blocks = 0);
 template <typename T>
 cudaError_t launch_project(int64_t nblocks, const int32_t* type, const int64_t* start, const int64_t* dim,
                            const double* alpha, const T* r, const T* m, T* out, int64_t n, cudaStream_t st);

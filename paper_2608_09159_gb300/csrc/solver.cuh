@@ -126,6 +126,7 @@ struct Own {
   int64_t x0[6], x1[6];   // owned coordinate ranges: free, nonneg, soc, rsoc, exp, pow
   int64_t f0, f1, nn0, nn1, s0, s1, r0, r1, e0, e1, p0, p1;
   int64_t row0, row1;
+  int g_a, g_t, g_p;      // lanes per row of A, A' and P on this block's rows
 };
 
 // Batched mode: independent instances of one block-diagonal problem, each solved by
@@ -146,10 +147,12 @@ struct BatchArgs {
   unsigned long long time_limit_ns; // 0: none
 };
 
+// Free and nonnegative coordinates are shared by the work of their A' rows (a coordinate's
+// column of A), cone segments by block count; rows of A by nnz (both with kRowWork per row).
 template <typename T>
 __device__ void make_own(const Prob<T>& P, int b, int nb, Own& o) {
-  split_range(P.n_free, b, nb, o.f0, o.f1);
-  split_range(P.n_nonneg, b, nb, o.nn0, o.nn1);
+  split_rows_weighted(P.t_rp, 0, P.n_free, b, nb, o.f0, o.f1);
+  split_rows_weighted(P.t_rp, P.n_free, P.n_nonneg, b, nb, o.nn0, o.nn1);
   o.nn0 += P.n_free; o.nn1 += P.n_free;
   split_range(P.n_soc, b, nb, o.s0, o.s1);
   split_range(P.n_rsoc, b, nb, o.r0, o.r1);
@@ -162,6 +165,15 @@ __device__ void make_own(const Prob<T>& P, int b, int nb, Own& o) {
   o.x0[4] = P.exp_base + 3 * o.e0; o.x1[4] = P.exp_base + 3 * o.e1;
   o.x0[5] = P.pow_base + 3 * o.p0; o.x1[5] = P.pow_base + 3 * o.p1;
   split_rows_by_nnz(P.a_rp, P.m, b, nb, o.row0, o.row1);
+  o.g_a = block_group_width(P.tpr_a, (int64_t)P.a_rp[o.row1] - P.a_rp[o.row0], o.row1 - o.row0);
+  int64_t tn = 0, pn = 0, cnt = 0;
+  for (int s = 0; s < 6; ++s) {
+    cnt += o.x1[s] - o.x0[s];
+    tn += (int64_t)P.t_rp[o.x1[s]] - P.t_rp[o.x0[s]];
+    if (P.p_rp) pn += (int64_t)P.p_rp[o.x1[s]] - P.p_rp[o.x0[s]];
+  }
+  o.g_t = block_group_width(P.tpr_t, tn, cnt);
+  o.g_p = P.p_rp ? block_group_width(P.tpr_p, pn, cnt) : P.tpr_p;
 }
 
 // ---------------------------------------------------------------------------
@@ -477,7 +489,7 @@ struct Solver {
   // ---- A' products: v = h_x + tau A' h_y on the owned coordinates -----------
   __device__ void phase_aty(const T* hx, const T* hy, double tau) {
     for (int seg = 0; seg < 6; ++seg) {
-      rows_loop_tpr<T>(P.tpr_t, P.t_rp, P.t_ci, P.t_v, own.x0[seg], own.x1[seg], [&](int j) { return hy[j]; },
+      rows_loop_tpr<T>(own.g_t, P.t_rp, P.t_ci, P.t_v, own.x0[seg], own.x1[seg], [&](int j) { return hy[j]; },
                        [&](int64_t i, int gl, T s) {
                          if (gl == 0) W.v[i] = hx[i] + T(tau) * s;
                        });
@@ -655,7 +667,7 @@ struct Solver {
     const T* w = wvec();
     T acc = T(0);
     for (int seg = 0; seg < 6; ++seg) {
-      rows_loop_tpr<T>(P.tpr_p, P.p_rp, P.p_ci, P.p_v, own.x0[seg], own.x1[seg], [&](int j) { return u[j]; },
+      rows_loop_tpr<T>(own.g_p, P.p_rp, P.p_ci, P.p_v, own.x0[seg], own.x1[seg], [&](int j) { return u[j]; },
                        [&](int64_t i, int gl, T pu) {
                          if (gl == 0) {
                            T g = pu + P.qd[i] * u[i] + P.c[i] + (u[i] - W.v[i]) * itau;

@@ -226,7 +226,7 @@ __device__ bool Solver<T, Team, GEN>::kkt(const T* x, const T* y, bool have_rx) 
   // dual-sign residual of rows with an infinite side (added to the dual residual in K2)
   double v4[4] = {0.0, 0.0, 0.0, 0.0};
   double rd_rows = 0.0;
-  rows_loop_tpr<double>(P.tpr_a, P.a_rp, P.a_ci, P.a_v, own.row0, own.row1, [&](int j) { return x[j]; },
+  rows_loop_tpr<double>(own.g_a, P.a_rp, P.a_ci, P.a_v, own.row0, own.row1, [&](int j) { return x[j]; },
                         [&](int64_t r, int gl, double ax) {
                           if (gl == 0) {
                             if (GEN && P.rhi) {
@@ -268,7 +268,7 @@ __device__ bool Solver<T, Team, GEN>::kkt(const T* x, const T* y, bool have_rx) 
   if (sparse) {
     // (P~ x)_i on the owned coordinates, kept in W.sd until K2 reads it
     for (int seg = 0; seg < 6; ++seg)
-      rows_loop_tpr<double>(P.tpr_p, P.p_rp, P.p_ci, P.p_v, own.x0[seg], own.x1[seg], [&](int j) { return x[j]; },
+      rows_loop_tpr<double>(own.g_p, P.p_rp, P.p_ci, P.p_v, own.x0[seg], own.x1[seg], [&](int j) { return x[j]; },
                             [&](int64_t i, int gl, double px) {
                               if (gl == 0) {
                                 W.sd[i] = px;
@@ -287,7 +287,7 @@ __device__ bool Solver<T, Team, GEN>::kkt(const T* x, const T* y, bool have_rx) 
   double v2[2] = {rd_rows, 0.0};   // dual residual^2, box term of the dual objective (scaled)
   for (int seg = 0; seg < 6; ++seg) {
     rows_loop_tpr<double>(
-        P.tpr_t, P.t_rp, P.t_ci, P.t_v, own.x0[seg], own.x1[seg], [&](int j) { return y[j]; },
+        own.g_t, P.t_rp, P.t_ci, P.t_v, own.x0[seg], own.x1[seg], [&](int j) { return y[j]; },
         [&](int64_t i, int gl, double aty) {
           if (gl == 0) {
             double qx = (double)P.qd[i] * (double)x[i];
@@ -427,7 +427,7 @@ __device__ void Solver<T, Team, GEN>::run(long long budget) {
       }
     };
     if (needE) {
-      rows_loop2_tpr<T>(P.tpr_a, P.a_rp, P.a_ci, P.a_v, own.row0, own.row1,
+      rows_loop2_tpr<T>(own.g_a, P.a_rp, P.a_ci, P.a_v, own.row0, own.row1,
                         [&](int j) { return T(2) * wxn[j] - hx[j]; }, [&](int j) { return hx[j] - wxn[j]; },
                         dual_row);
     } else {
@@ -437,7 +437,7 @@ __device__ void Solver<T, Team, GEN>::run(long long budget) {
       for (int seg = 0; seg < 6; ++seg)
         for (int64_t i = own.x0[seg] + threadIdx.x; i < own.x1[seg]; i += blockDim.x) zv[i] = T(2) * wxn[i] - hx[i];
       if (!team.sync()) return;
-      rows_loop_tpr<T>(P.tpr_a, P.a_rp, P.a_ci, P.a_v, own.row0, own.row1, [&](int j) { return zv[j]; },
+      rows_loop_tpr<T>(own.g_a, P.a_rp, P.a_ci, P.a_v, own.row0, own.row1, [&](int j) { return zv[j]; },
                        [&](int64_t r, int gl, T s1) { dual_row(r, gl, s1, T(0)); });
     }
     T* hxn = W.hx[hb ^ 1];
