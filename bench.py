@@ -297,7 +297,7 @@ def run_ours(args, rank, world):
     traffic = _ncu_traffic()
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": (achieved / peaks["hbm_gbs"]) if achieved else None, "traffic": traffic,
-            "peak_source": src, "kernel": "pdhg_grid_kernel<float>", "algorithmic_bytes_per_solve": alg,
+            "peak_source": src, "kernel": "pdhg_grid_kernel<float, false>", "algorithmic_bytes_per_solve": alg,
             "kernel_s_per_solve": kern_s}
 
     cpu = None
@@ -443,7 +443,7 @@ def run_large(args):
                       "rel_kkt": res["kkt"]["rel_kkt"], "setup_ms": res["setup_ms"], "kernel_ms": res["kernel_ms"]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
-                         "kernel": "pdhg_grid_kernel<float>", "algorithmic_bytes_per_solve": alg},
+                         "kernel": "pdhg_grid_kernel<float, false>", "algorithmic_bytes_per_solve": alg},
             "clocks": clocks.stop()}
     print(json.dumps(line), flush=True)
 
