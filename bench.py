@@ -188,6 +188,18 @@ def _pinned_inst(inst, torch):
     return out
 
 
+def max_over_ranks(value, world):
+    """The largest of the ranks' values (the job's time is its slowest replica's).  Uses the
+    process group's backend: a CUDA tensor under NCCL, a host tensor under gloo."""
+    if world <= 1:
+        return value
+    import torch
+    dev = "cuda" if torch.distributed.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_instance(args, rank):
     import instances
     if args.small:
@@ -246,10 +258,7 @@ def run_ours(args, rank, world):
     launches = g.cqp_kernel_launches() - launches0
     clk = clocks.stop()
     step_s = statistics.mean(times)
-    if world > 1:
-        t = torch.tensor([step_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_s = float(t.item())
+    step_s = max_over_ranks(step_s, world)
     res = results[-1]
     # parity of the timed solution, measured independently on the host (rank 0, FP64 oracle)
     kkt_check = None
