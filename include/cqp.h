@@ -123,7 +123,7 @@ typedef struct {
   int32_t check_every;      /* KKT / restart check cadence, 64 */
   double time_limit_s;      /* <= 0: none */
   /* step size */
-  int32_t power_iters;      /* 200 */
+  int32_t power_iters;      /* 200: cap on the Lanczos steps of the ||A~||_2 estimate (at most 256 on the GPU) */
   double power_tol;         /* 1e-6 */
   double step_factor;       /* 0.998 */
   /* execution */
@@ -166,7 +166,7 @@ int cqp_default_options(cqp_options* opt);
 
 /* Builds the device-resident, rescaled problem (Sec. 4.2.2 rescaling and
  * eq. "practical-stepsizes": Ruiz, Pock-Chambolle and bound-objective scaling,
- * power-iteration estimate of ||A||_2, eta = step_factor/||A||_2).
+ * Lanczos estimate of ||A||_2, eta = step_factor/||A||_2).
  *   A: m x n equality matrix; Q: objective operator (NULL = 0); c: n; b: m;
  *   K: cone partition of 0..n-1; opt: NULL = defaults.
  * Pointers are host pointers unless opt->input_on_device = 1.  On success

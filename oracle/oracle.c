@@ -903,7 +903,7 @@ void orc_rescale(const orc_problem* p, const orc_options* o, double* col_scale, 
   wprob_free(&w);
 }
 
-/* Start vector of the power iteration (reading): entry j is 1/2 + U_j with U_j in [0, 1)
+/* Start vector of the norm estimate (reading): entry j is 1/2 + U_j with U_j in [0, 1)
  * the top 53 bits of output j+1 of SplitMix64 (Steele, Lea and Flood, "Fast splittable
  * pseudorandom number generators", OOPSLA 2014) from state 0, i.e. the finaliser applied to
  * (j+1) times the golden-ratio increment.  An all-ones start can be orthogonal to the top
@@ -921,33 +921,72 @@ void orc_power_start(int64_t n, double* out) {
   for (int64_t j = 0; j < n; ++j) out[j] = power_start((uint64_t)j);
 }
 
-/* ||A||_2 (needed for eta = 0.998/||A||_2, eq. practical-stepsizes).  The paper
- * does not say how it is estimated; reading: power iteration on A'A from the
- * normalised SplitMix64 start above, Rayleigh quotient sigma^2 = ||A v||^2, stop when
- * the estimate changes by <= tol relative or after `iters` iterations. */
+/* Largest eigenvalue of the symmetric tridiagonal matrix with diagonal a[0..k) and
+ * off-diagonal b[0..k-1), by bisection on the Sturm count (Golub and Van Loan, Matrix
+ * Computations, Sec. 8.4.1): below(x) = number of negative pivots of the LDL' factorisation
+ * of T - x I = number of eigenvalues below x.  The bracket starts at the Gershgorin bound. */
+static double tridiag_max_eig(const double* a, const double* b, int k) {
+  double lo = a[0], hi = a[0];
+  for (int i = 0; i < k; ++i) {
+    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < k - 1 ? fabs(b[i]) : 0.0);
+    if (a[i] - r < lo) lo = a[i] - r;
+    if (a[i] + r > hi) hi = a[i] + r;
+  }
+  for (int step = 0; step < 200 && hi - lo > 1e-15 * fabs(hi); ++step) {
+    const double x = 0.5 * (lo + hi);
+    int below = 0;
+    double d = 1.0;
+    for (int i = 0; i < k; ++i) {
+      d = a[i] - x - (i > 0 ? b[i - 1] * b[i - 1] / d : 0.0);
+      if (d == 0.0) d = -1e-300;      /* an exact zero pivot counts as negative */
+      if (d < 0.0) ++below;
+    }
+    if (below == k) hi = x; else lo = x;
+  }
+  return hi;
+}
+
+/* ||A||_2 (needed for eta = 0.998/||A||_2, eq. practical-stepsizes).  The paper does not
+ * say how it is estimated; reading: the Lanczos process on A'A (Lanczos 1950; Golub and
+ * Van Loan, Sec. 9.1) from the normalised SplitMix64 start above, without
+ * reorthogonalisation.  Step j: alpha_j = ||A v_j||^2 (= v_j'A'A v_j),
+ * w = A'A v_j - alpha_j v_j - beta_{j-1} v_{j-1}, beta_j = ||w||, v_{j+1} = w / beta_j;
+ * sigma_j = sqrt of the largest eigenvalue of the tridiagonal T_j.  Stop when sigma changes
+ * by <= tol relative, when beta_j = 0 (an invariant subspace: sigma is exact), or after
+ * `iters` steps. */
 double orc_norm_est(int64_t m, int64_t n, const int64_t* rowptr, const int64_t* colind, const double* val,
                     int iters, double tol, int* iters_used) {
   double* v = dalloc(n);
+  double* vprev = dalloc(n);
   double* av = dalloc(m);
   double* z = dalloc(n);
+  double* al = dalloc(iters > 0 ? iters : 1);
+  double* be = dalloc(iters > 0 ? iters : 1);
   double vn = 0.0;
   for (int64_t j = 0; j < n; ++j) { v[j] = power_start((uint64_t)j); vn += v[j] * v[j]; }
   vn = sqrt(vn);
   for (int64_t j = 0; j < n; ++j) v[j] = vn > 0.0 ? v[j] / vn : 0.0;
-  double sig = 0.0;
+  double sig = 0.0, beta_prev = 0.0;
   int it;
   for (it = 0; it < iters; ++it) {
     orc_spmv(m, rowptr, colind, val, v, av);
-    double s_new = nrm2(m, av);
+    const double alpha = dot(m, av, av);
     orc_spmv_t(m, n, rowptr, colind, val, av, z);
-    double zn = nrm2(n, z);
-    if (zn == 0.0) { sig = s_new; break; }
-    for (int64_t j = 0; j < n; ++j) v[j] = z[j] / zn;
-    if (it > 0 && fabs(s_new - sig) <= tol * s_new) { sig = s_new; ++it; break; }
+    for (int64_t j = 0; j < n; ++j) z[j] -= alpha * v[j] + beta_prev * vprev[j];
+    const double beta = nrm2(n, z);
+    al[it] = alpha;
+    const double s_new = sqrt(fmax(tridiag_max_eig(al, be, it + 1), 0.0));
+    if ((it > 0 && fabs(s_new - sig) <= tol * s_new) || beta == 0.0) { sig = s_new; ++it; break; }
     sig = s_new;
+    be[it] = beta;
+    for (int64_t j = 0; j < n; ++j) {
+      vprev[j] = v[j];
+      v[j] = z[j] / beta;
+    }
+    beta_prev = beta;
   }
   if (iters_used) *iters_used = it;
-  free(v); free(av); free(z);
+  free(v); free(vprev); free(av); free(z); free(al); free(be);
   return sig;
 }
 

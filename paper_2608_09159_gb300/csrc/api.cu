@@ -217,7 +217,7 @@ struct Handle : HandleBase {
   T* tmp_x = nullptr;
   T* tmp_y = nullptr;
   double eta = 0, normA = 0, omega0 = 1, setup_ms = 0;
-  int power_its = 0;                 // power iterations taken by setup
+  int power_its = 0;                 // Lanczos steps of the norm estimate taken by setup
   long long setup_launches = 0;
   int64_t n_roots = 0;
   bool grid = false;
@@ -665,11 +665,13 @@ struct Handle : HandleBase {
       count_launch(); k_sumsq_range<<<cqp::grid_for(n - base[2]), cqp::kSetupThreads, 0, st>>>(base[2], n, qv, acc);
       CK(cudaMemcpyAsync(&qcone, acc, sizeof(double), cudaMemcpyDeviceToHost, st));
     }
-    // ---- ||A~||_2 by power iteration on A~'A~ (reading: SplitMix64 start keyed by the
+    // ---- ||A~||_2 by the Lanczos process on A~'A~ (reading: SplitMix64 start keyed by the
     // caller's coordinate index, Rayleigh quotient, stop at power_tol relative change or
     // power_iters) --------------------------------------------------------------------------
     {
       double* z = tmp.alloc<double>(n);
+      double* zp = tmp.alloc<double>(n);   // previous Lanczos vector (zero at the start)
+      CK(cudaMemsetAsync(zp, 0, n * sizeof(double), st));
       double* w = tmp.alloc<double>(std::max<int64_t>(m, 1));
       double* ppart = tmp.alloc<double>(2 * (int64_t)nsm);
       unsigned* pcount = tmp.alloc<unsigned>(1);
@@ -690,7 +692,7 @@ struct Handle : HandleBase {
         double* d_na = tmp.alloc<double>(bcount);
         count_launch();
         cqp::k_inst_power<T><<<(int)std::min<int64_t>(bcount, 8 * nsm), cqp::kBatchSetupThreads, 0, st>>>(
-            bcount, d_own, a_rp, a_ci, a_v, t_rp, t_ci, t_v, cv, bv, z, w, o.power_iters, o.power_tol,
+            bcount, d_own, a_rp, a_ci, a_v, t_rp, t_ci, t_v, cv, bv, z, zp, w, o.power_iters, o.power_tol,
             o.step_factor, d_eta, d_om, d_na, perm, d_xoff_old);
         h_eta.resize(bcount);
         h_om.resize(bcount);
@@ -707,7 +709,7 @@ struct Handle : HandleBase {
         const int32_t* arp = a_rp; const int32_t* aci = a_ci; const T* av = a_v;
         const int32_t* trp = t_rp; const int32_t* tci = t_ci; const T* tv = t_v;
         int64_t mm = m, nn = n;
-        void* pargs[] = {&mm, &nn, &arp, &aci, &av, &trp, &tci, &tv, &z, &w, &ppart, &pbar, &iters, &ptol, &pout};
+        void* pargs[] = {&mm, &nn, &arp, &aci, &av, &trp, &tci, &tv, &z, &zp, &w, &ppart, &pbar, &iters, &ptol, &pout};
         count_launch();
         CK(cudaLaunchCooperativeKernel((void*)cqp::k_power<T>, dim3(nsm), dim3(cqp::kPowerThreads), pargs, 0, st));
         double hp[2];
@@ -715,7 +717,7 @@ struct Handle : HandleBase {
         CK(cudaMemcpyAsync(hp, pout, sizeof(hp), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(&herr, perr, sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        if (herr != 0) fail(CQP_ERR_WAIT, "power iteration: grid barrier wait expired");
+        if (herr != 0) fail(CQP_ERR_WAIT, "norm estimate: grid barrier wait expired");
         sig = hp[0];
         power_its = (int)hp[1];
       }

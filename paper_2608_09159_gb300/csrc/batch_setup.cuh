@@ -85,18 +85,22 @@ __global__ void __launch_bounds__(kBatchSetupThreads) k_inst_bound_obj(
   }
 }
 
-// ||A~_i||_2 by power iteration on the instance's block (same reading as k_power:
+// ||A~_i||_2 by the Lanczos process on the instance's block (same reading as k_power:
 // SplitMix64 start keyed by the instance-local coordinate index perm[j] - x_off_old[i],
-// Rayleigh quotient, stop at `tol` relative change or `iters`),
+// stop at `tol` relative change of sigma, at beta = 0 or after `iters` steps),
 // eta_i = step / ||A~_i||, omega0_i = ||c~_i|| / ||b~_i||.
 template <typename T>
 __global__ void __launch_bounds__(kBatchSetupThreads) k_inst_power(
     int64_t count, const Own* own, const int32_t* __restrict__ a_rp, const int32_t* __restrict__ a_ci,
     const T* __restrict__ a_v, const int32_t* __restrict__ t_rp, const int32_t* __restrict__ t_ci,
-    const T* __restrict__ t_v, const double* cv, const double* bv, double* z, double* w, int iters, double tol,
-    double step, double* eta, double* omega0, double* norm_a, const int64_t* perm, const int64_t* x_off_old) {
+    const T* __restrict__ t_v, const double* cv, const double* bv, double* z, double* zp, double* w, int iters,
+    double tol, double step, double* eta, double* omega0, double* norm_a, const int64_t* perm,
+    const int64_t* x_off_old) {
   __shared__ double red[2 * (kBatchSetupThreads / 32)];
   __shared__ double tot[2];
+  __shared__ double al[kMaxLanczos], be[kMaxLanczos];
+  __shared__ double theta;
+  const int nit = iters < kMaxLanczos ? iters : kMaxLanczos;
   for (int64_t i = blockIdx.x; i < count; i += gridDim.x) {
     const Own o = own[i];
     double z2[1] = {0.0};
@@ -104,6 +108,7 @@ __global__ void __launch_bounds__(kBatchSetupThreads) k_inst_power(
       for (int64_t j = o.x0[seg] + threadIdx.x; j < o.x1[seg]; j += blockDim.x) {
         const double u = power_start_value((uint64_t)(perm[j] - x_off_old[i]) + 1);
         z[j] = u;
+        zp[j] = 0.0;
         z2[0] += u * u;
       }
     block_sum<1>(z2, red, tot);
@@ -111,8 +116,8 @@ __global__ void __launch_bounds__(kBatchSetupThreads) k_inst_power(
     for (int seg = 0; seg < 6; ++seg)
       for (int64_t j = o.x0[seg] + threadIdx.x; j < o.x1[seg]; j += blockDim.x) z[j] *= zinv;
     __syncthreads();
-    double sig = 0.0, zscale = 1.0;
-    for (int it = 0; it < iters && o.row1 > o.row0; ++it) {
+    double sig = 0.0, zscale = 1.0, beta_prev = 0.0;
+    for (int it = 0; it < nit && o.row1 > o.row0; ++it) {
       double acc[1] = {0.0};
       for (int64_t r = o.row0 + threadIdx.x; r < o.row1; r += blockDim.x) {
         double s = 0.0;
@@ -122,25 +127,35 @@ __global__ void __launch_bounds__(kBatchSetupThreads) k_inst_power(
         acc[0] += s * s;
       }
       block_sum<1>(acc, red, tot);
-      const double s_new = sqrt(tot[0]);
+      const double alpha = tot[0];
       acc[0] = 0.0;
       for (int seg = 0; seg < 6; ++seg)
         for (int64_t j = o.x0[seg] + threadIdx.x; j < o.x1[seg]; j += blockDim.x) {
           double s = 0.0;
           for (int e = t_rp[j]; e < t_rp[j + 1]; ++e) s += (double)t_v[e] * w[t_ci[e]];
+          const double vj = z[j] * zscale, vp = zp[j];
+          s -= alpha * vj + beta_prev * vp;
+          zp[j] = vj;
           z[j] = s;
           acc[0] += s * s;
         }
       block_sum<1>(acc, red, tot);
-      const double zn = sqrt(tot[0]);
-      if (zn == 0.0) {
-        sig = s_new;
-        break;
+      const double beta = sqrt(tot[0]);
+      if (threadIdx.x == 0) al[it] = alpha;
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        const double th = tridiag_max_eig_warp(al, be, it + 1, threadIdx.x);
+        if (threadIdx.x == 0) theta = th;
       }
-      zscale = 1.0 / zn;
-      const bool done = it > 0 && fabs(s_new - sig) <= tol * s_new;
+      __syncthreads();
+      const double s_new = sqrt(fmax(theta, 0.0));
+      const bool done = (it > 0 && fabs(s_new - sig) <= tol * s_new) || beta == 0.0;
       sig = s_new;
       if (done) break;
+      if (threadIdx.x == 0) be[it] = beta;
+      zscale = 1.0 / beta;
+      beta_prev = beta;
+      __syncthreads();
     }
     double v[2] = {0.0, 0.0};
     for (int seg = 0; seg < 6; ++seg)

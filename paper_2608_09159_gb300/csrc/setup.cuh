@@ -252,7 +252,7 @@ __global__ void k_sum_partials(int nb, const double* part, double* out) {
   }
 }
 
-// ---- power iteration pieces: y = A x (FP64 accumulation over T values) --------------
+// ---- norm-estimate pieces: y = A x (FP64 accumulation over T values) ----------------
 template <typename T>
 __global__ void k_spmv_simple(int64_t m, const int32_t* rp, const int32_t* ci, const T* v, const double* x, double* y) {
   CQP_GRID_LOOP(r, m) {
@@ -296,7 +296,7 @@ __global__ void k_box_bounds(int64_t nf, const int64_t* perm, const uint8_t* mas
   }
 }
 
-// ---- start vector of the power iteration (reading): entry j is 1/2 + U_j, U_j in [0, 1) the
+// ---- start vector of the norm estimate (reading): entry j is 1/2 + U_j, U_j in [0, 1) the
 // top 53 bits of output j+1 of the SplitMix64 generator (Steele, Lea and Flood, OOPSLA 2014)
 // started from state 0.  Entries are keyed by the caller's coordinate index, so the start
 // does not depend on the solver's permutation.  An all-ones start can be exactly orthogonal
@@ -315,14 +315,61 @@ __global__ void k_power_start(int64_t n, const int64_t* perm, double* z) {
   CQP_GRID_LOOP(i, n) z[i] = power_start_value((uint64_t)perm[i] + 1);
 }
 
-// ---- ||A~||_2 by power iteration on A~'A~, all iterations in one cooperative launch
-// (eq. practical-stepsizes; reading: SplitMix64 start, Rayleigh quotient ||A v|| with
-// ||v|| = 1, stop at `tol` relative change or `iters` iterations).  v is kept as
-// z / ||z||: each iteration computes w = A z / ||z|| (slot 0: ||w||^2) and z = A' w
-// (slot 1: ||z||^2), so two grid barriers per iteration and no host round trip.
-// Every block combines the partials in the same fixed order, so all blocks take the
-// same stop decision.  out[0] = ||A~||_2 estimate, out[1] = iterations.
+// ---- largest eigenvalue of a symmetric tridiagonal matrix (diagonal a[0..k), off-diagonal
+// b[0..k-1)) by one warp: 32-point multisection of the Gershgorin bracket on the Sturm count
+// (Golub and Van Loan, Sec. 8.4.1).  Lane l evaluates the count at the (l+1)-th of 32 interior
+// points through the division-free recurrence of the leading principal minors
+// p_i = (a_i - x) p_{i-1} - b_{i-1}^2 p_{i-2} (a sign change = an eigenvalue below x; an exact
+// zero counts as a change), rescaled by 2^-+500 to stay in range; the bracket shrinks 33-fold
+// per step.  Every lane returns the same value.
+__device__ __forceinline__ int sturm_below(const double* a, const double* b, int k, double x) {
+  double pm = 1.0, p = a[0] - x;
+  int below = p <= 0.0 ? 1 : 0;
+  for (int i = 1; i < k; ++i) {
+    const double q = (a[i] - x) * p - b[i - 1] * b[i - 1] * pm;
+    pm = p;
+    p = q;
+    const double ap = fabs(p);
+    if (ap > 0x1p500) { p *= 0x1p-500; pm *= 0x1p-500; }
+    else if (ap < 0x1p-500 && ap > 0.0) { p *= 0x1p500; pm *= 0x1p500; }
+    if (p == 0.0 || (p < 0.0) != (pm < 0.0)) ++below;
+  }
+  return below;
+}
+__device__ double tridiag_max_eig_warp(const double* a, const double* b, int k, int lane) {
+  double lo = a[0], hi = a[0];
+  for (int i = 0; i < k; ++i) {
+    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < k - 1 ? fabs(b[i]) : 0.0);
+    lo = fmin(lo, a[i] - r);
+    hi = fmax(hi, a[i] + r);
+  }
+  for (int step = 0; step < 40 && hi - lo > 1e-15 * fabs(hi); ++step) {
+    const double h = (hi - lo) / 33.0;
+    const double x = lo + h * (double)(lane + 1);
+    const unsigned above = __ballot_sync(0xffffffffu, sturm_below(a, b, k, x) == k);
+    if (above == 0u) {
+      lo = lo + h * 32.0;
+    } else {
+      const int l0 = __ffs((int)above) - 1;
+      const double nhi = lo + h * (double)(l0 + 1);
+      lo = l0 > 0 ? lo + h * (double)l0 : lo;
+      hi = nhi;
+    }
+  }
+  return hi;
+}
+
+// ---- ||A~||_2 by the Lanczos process on A~'A~, all steps in one cooperative launch
+// (eq. practical-stepsizes; reading: SplitMix64 start, no reorthogonalisation, stop at `tol`
+// relative change of sigma = sqrt(theta_max(T_j)), at beta_j = 0, or after `iters` steps,
+// at most kMaxLanczos).  The current vector is v = zscale z, the previous one zp.  Each step:
+// w = A v (slot 0: alpha = ||w||^2 = v'A'A v), then z = A'w - alpha v - beta_prev zp with
+// zp = v (slot 1: beta^2 = ||z||^2), two grid barriers and no host round trip.  Every block
+// combines the partials in the same fixed order and runs the same tridiagonal eigenvalue
+// search (warp 0), so all blocks take the same stop decision.  out[0] = ||A~||_2 estimate,
+// out[1] = steps.
 constexpr int kPowerThreads = 512;
+constexpr int kMaxLanczos = 256;
 
 // one CSR row product in FP64, eight entries at a time (indices and values first, then
 // the gathers together) so each thread keeps several loads in flight
@@ -352,15 +399,18 @@ template <typename T>
 __global__ void __launch_bounds__(kPowerThreads, 1)
     k_power(int64_t m, int64_t n, const int32_t* __restrict__ a_rp, const int32_t* __restrict__ a_ci,
             const T* __restrict__ a_v, const int32_t* __restrict__ t_rp, const int32_t* __restrict__ t_ci,
-            const T* __restrict__ t_v, double* z, double* w, double* part, GridBarrier bar, int iters, double tol,
-            double* out) {
+            const T* __restrict__ t_v, double* z, double* zp, double* w, double* part, GridBarrier bar, int iters,
+            double tol, double* out) {
   GridTeam team;
   team.init(bar, part);
   __shared__ double red[kPowerThreads / 32];
   __shared__ double tot[2];
+  __shared__ double al[kMaxLanczos], be[kMaxLanczos];
+  __shared__ double theta;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nt = (int64_t)gridDim.x * blockDim.x;
-  double sig = 0.0, zscale = 1.0;
+  if (iters > kMaxLanczos) iters = kMaxLanczos;
+  double sig = 0.0, zscale = 1.0, beta_prev = 0.0;
   int it = 0;
   for (; it < iters; ++it) {
     double acc[1] = {0.0};
@@ -373,10 +423,12 @@ __global__ void __launch_bounds__(kPowerThreads, 1)
     if (threadIdx.x == 0) team.publish(0, tot[0]);
     if (!team.sync()) break;
     team.gather(1, tot);
-    const double s_new = sqrt(tot[0]);
+    const double alpha = tot[0];
     acc[0] = 0.0;
     for (int64_t j = tid; j < n; j += nt) {
-      const double s = power_row(t_rp[j], t_rp[j + 1], t_ci, t_v, w);
+      const double vj = z[j] * zscale, vp = zp[j];
+      const double s = power_row(t_rp[j], t_rp[j + 1], t_ci, t_v, w) - alpha * vj - beta_prev * vp;
+      zp[j] = vj;
       z[j] = s;
       acc[0] += s * s;
     }
@@ -384,19 +436,25 @@ __global__ void __launch_bounds__(kPowerThreads, 1)
     if (threadIdx.x == 0) team.publish(1, tot[0]);
     if (!team.sync()) break;
     team.gather(2, tot);
-    const double zn = sqrt(tot[1]);
-    if (zn == 0.0) {
-      sig = s_new;
-      ++it;
-      break;
+    const double beta = sqrt(tot[1]);
+    if (threadIdx.x == 0) al[it] = alpha;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const double th = tridiag_max_eig_warp(al, be, it + 1, threadIdx.x);
+      if (threadIdx.x == 0) theta = th;
     }
-    zscale = 1.0 / zn;
-    const bool done = it > 0 && fabs(s_new - sig) <= tol * s_new;
+    __syncthreads();
+    const double s_new = sqrt(fmax(theta, 0.0));
+    const bool done = (it > 0 && fabs(s_new - sig) <= tol * s_new) || beta == 0.0;
     sig = s_new;
     if (done) {
       ++it;
       break;
     }
+    if (threadIdx.x == 0) be[it] = beta;
+    zscale = 1.0 / beta;
+    beta_prev = beta;
+    __syncthreads();
   }
   if (tid == 0) {
     out[0] = sig;

@@ -1,7 +1,7 @@
 """GPU parity of the rescaled-cone mode (option rescaled_cones = 1, Sec. 4.2.2).
 
 * One outer iteration in FP64 with scaling on matches the oracle's first candidate in
-  the same mode. The two differ only in the power-iteration estimate of ||A||_2, so the
+  the same mode. The two differ only in the rounding of the ||A||_2 estimate, so the
   bound is 1e-6 relative; a wrong cone transform is an O(1) difference.
 * min 1/2||x - p||^2 s.t. a'x = beta over one SOC/RSOC/exp/pow block equals the bisection
   reference Pi_K(p + lam a), in FP64.
