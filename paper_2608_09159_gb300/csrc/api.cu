@@ -530,7 +530,18 @@ struct Handle : HandleBase {
       int32_t* cursor = tmp.alloc<int32_t>(n);
       CK(cudaMemcpyAsync(cursor, t_rp, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
       count_launch(); cqp::k_scatter_transpose<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp, a_ci, cursor, t_ci, tmap);
-      count_launch(); cqp::k_sort_segments<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, t_rp, t_ci, tmap);
+      int32_t* long_list = tmp.alloc<int32_t>(n);
+      unsigned* long_cm = tmp.alloc<unsigned>(2);   // count, longest
+      CK(cudaMemsetAsync(long_cm, 0, 2 * sizeof(unsigned), st));
+      count_launch(); cqp::k_sort_segments<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, t_rp, t_ci, tmap, long_list, long_cm, long_cm + 1);
+      count_launch(); cqp::k_sort_long_segments<<<2 * nsm, cqp::kSegSortThreads, 0, st>>>(t_rp, t_ci, tmap, long_list, long_cm);
+      unsigned hcm[2] = {0u, 0u};
+      CK(cudaMemcpyAsync(hcm, long_cm, sizeof(hcm), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (hcm[1] > (unsigned)cqp::kSegSortCap) {
+        unsigned long long* sbuf = tmp.alloc<unsigned long long>(hcm[1]);
+        count_launch(); cqp::k_sort_huge_segments<<<1, cqp::kSegSortThreads, 0, st>>>(t_rp, t_ci, tmap, long_list, long_cm, sbuf);
+      }
     }
     // ---- rescaling (Table practical-defaults: Ruiz x10, Pock-Chambolle alpha = 1,
     // cone-preserving aggregation, bound-objective) -------------------------------------

@@ -127,10 +127,23 @@ __global__ void k_scatter_transpose(int64_t m, const int32_t* rp, const int32_t*
     }
   }
 }
-// order every transposed row by its column (original row) index: deterministic layout
-__global__ void k_sort_segments(int64_t n, const int32_t* trp, int32_t* tci, int32_t* tmap) {
+// Order every transposed row by (original row, position in A): a deterministic layout.
+// Rows of at most kShortSeg entries are insertion-sorted by one thread (stable, and two
+// entries of one row of A arrive in their CSR order from the same scattering thread); longer
+// ones are listed for k_sort_long_segments (one block, bitonic sort in shared memory) and,
+// beyond kSegSortCap entries, k_sort_huge_segments.
+constexpr int kShortSeg = 32;
+constexpr int kSegSortCap = 4096;
+constexpr int kSegSortThreads = 512;
+__global__ void k_sort_segments(int64_t n, const int32_t* trp, int32_t* tci, int32_t* tmap, int32_t* long_list,
+                                unsigned* long_count, unsigned* long_max) {
   CQP_GRID_LOOP(j, n) {
     const int b = trp[j], e = trp[j + 1];
+    if (e - b > kShortSeg) {
+      long_list[atomicAdd(long_count, 1u)] = (int32_t)j;
+      atomicMax(long_max, (unsigned)(e - b));
+      continue;
+    }
     for (int a = b + 1; a < e; ++a) {
       const int key = tci[a], val = tmap[a];
       int t = a - 1;
@@ -138,6 +151,82 @@ __global__ void k_sort_segments(int64_t n, const int32_t* trp, int32_t* tci, int
       tci[t + 1] = key;
       tmap[t + 1] = val;
     }
+  }
+}
+
+// (row, position) packed so that unsigned order is the layout order
+__device__ __forceinline__ unsigned long long seg_key(const int32_t* tci, const int32_t* tmap, int i) {
+  return ((unsigned long long)(uint32_t)tci[i] << 32) | (uint32_t)tmap[i];
+}
+// sorts entries [b, b + len) of tci/tmap (len <= kSegSortCap) with the calling block: bitonic
+// sort of the packed keys in shared memory, padded to a power of two with the largest key
+__device__ void block_sort_run(int32_t* tci, int32_t* tmap, int b, int len, unsigned long long* s) {
+  int P = 1;
+  while (P < len) P <<= 1;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) s[i] = i < len ? seg_key(tci, tmap, b + i) : ~0ull;
+  __syncthreads();
+  for (int k = 2; k <= P; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const unsigned long long a = s[i], c = s[ixj];
+          if ((a > c) == ((i & k) == 0)) {
+            s[i] = c;
+            s[ixj] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  for (int i = threadIdx.x; i < len; i += blockDim.x) {
+    tci[b + i] = (int32_t)(s[i] >> 32);
+    tmap[b + i] = (int32_t)(s[i] & 0xffffffffull);
+  }
+  __syncthreads();
+}
+__global__ void __launch_bounds__(kSegSortThreads) k_sort_long_segments(const int32_t* trp, int32_t* tci,
+                                                                        int32_t* tmap, const int32_t* list,
+                                                                        const unsigned* count) {
+  __shared__ unsigned long long s[kSegSortCap];
+  const unsigned cnt = *count;
+  for (unsigned i = blockIdx.x; i < cnt; i += gridDim.x) {
+    const int j = list[i];
+    const int b = trp[j], len = trp[j + 1] - b;
+    if (len <= kSegSortCap) block_sort_run(tci, tmap, b, len, s);
+  }
+}
+// rows longer than kSegSortCap (one block): kSegSortCap-entry runs sorted in shared memory,
+// then merged bottom-up by thread 0 through buf (as many entries as the longest row)
+__global__ void __launch_bounds__(kSegSortThreads) k_sort_huge_segments(const int32_t* trp, int32_t* tci,
+                                                                        int32_t* tmap, const int32_t* list,
+                                                                        const unsigned* count, unsigned long long* buf) {
+  __shared__ unsigned long long s[kSegSortCap];
+  const unsigned cnt = *count;
+  for (unsigned i = 0; i < cnt; ++i) {
+    const int j = list[i];
+    const int b = trp[j], L = trp[j + 1] - b;
+    if (L <= kSegSortCap) continue;
+    for (int r = 0; r < L; r += kSegSortCap) block_sort_run(tci, tmap, b + r, min(kSegSortCap, L - r), s);
+    if (threadIdx.x == 0) {
+      for (int w = kSegSortCap; w < L; w <<= 1) {
+        for (int lo = 0; lo < L; lo += 2 * w) {
+          const int mid = min(lo + w, L), hi = min(lo + 2 * w, L);
+          int p = lo, q = mid, o = lo;
+          while (p < mid && q < hi) {
+            const unsigned long long kp = seg_key(tci, tmap, b + p), kq = seg_key(tci, tmap, b + q);
+            if (kp <= kq) { buf[o++] = kp; ++p; } else { buf[o++] = kq; ++q; }
+          }
+          while (p < mid) { buf[o++] = seg_key(tci, tmap, b + p); ++p; }
+          while (q < hi) { buf[o++] = seg_key(tci, tmap, b + q); ++q; }
+        }
+        for (int t = 0; t < L; ++t) {
+          tci[b + t] = (int32_t)(buf[t] >> 32);
+          tmap[b + t] = (int32_t)(buf[t] & 0xffffffffull);
+        }
+      }
+    }
+    __syncthreads();
   }
 }
 
