@@ -335,7 +335,10 @@ def run_ours(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
-def _timed(fn, steps, warmup, flush):
+def _timed(fn, steps, warmup, flush, counter=None):
+    """W untimed warm-up steps, then `steps` steps each bracketed by CUDA events on the current
+    stream with an L2 flush before it.  Returns (step times, last output, library kernel launches
+    inside the timed steps as read from `counter`, or None)."""
     import torch
     for _ in range(warmup):
         flush.fill_(1.0)
@@ -343,6 +346,7 @@ def _timed(fn, steps, warmup, flush):
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     times, out = [], None
+    c0 = counter() if counter else 0
     for _ in range(steps):
         flush.fill_(1.0)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -352,7 +356,7 @@ def _timed(fn, steps, warmup, flush):
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
-    return times, out
+    return times, out, (counter() - c0 if counter else None)
 
 
 def run_portfolio(args):
@@ -369,9 +373,8 @@ def run_portfolio(args):
     opts = dict(precision=0, tol=1e-4, max_iter=100000, time_limit_s=600.0)
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
-    launches0 = g.cqp_kernel_launches()
-    times, (x, y, per, res) = _timed(lambda: W.solve_batch(batch, None, **opts), args.steps, args.warmup, flush)
-    launches = (g.cqp_kernel_launches() - launches0) // max(args.steps + args.warmup, 1)
+    times, (x, y, per, res), launches = _timed(lambda: W.solve_batch(batch, None, **opts), args.steps, args.warmup,
+                                               flush, g.cqp_kernel_launches)
     its = np.array([r["iters"] for r in per])
     line = {"metric": "time to 1e-4 rel KKT on every instance of the batch", "value": statistics.mean(times),
             "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -401,7 +404,7 @@ def run_portfolio(args):
         torch.cuda.synchronize()
         t_train = time.perf_counter() - t0
         del data
-        wt, (xw, yw, pw, rw) = _timed(lambda: W.solve_batch(batch, net, **opts), args.steps, args.warmup, flush)
+        wt, (xw, yw, pw, rw), _ = _timed(lambda: W.solve_batch(batch, net, **opts), args.steps, args.warmup, flush)
         iw = np.array([r["iters"] for r in pw])
         line["warm_start"] = {"value": statistics.mean(wt), "unit": "s", "trained_on": nb * per_batch,
                               "train_steps": args.ws_steps, "train_s": t_train, "iters_mean": float(iw.mean()),
@@ -432,7 +435,7 @@ def run_large(args):
 
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
-    times, (x, y, res) = _timed(step, args.steps, args.warmup, flush)
+    times, (x, y, res), launches = _timed(step, args.steps, args.warmup, flush, g.cqp_kernel_launches)
     nnz, pnnz = m * 20, 2 * n
     # algorithmic bytes (FP32 values, int32 indices): A' and A passes with their vectors
     # per outer iteration, P and 9 n-vectors per inner step
@@ -448,6 +451,7 @@ def run_large(args):
             "config": {"workload": "large_qp: n=%d nonneg, m=%d, 20 nnz per row, Q = diag(U[0,1]) + matching "
                                    "Laplacian, seed 1005" % (n, m), "n": n, "m": m, "nnz": nnz, "pnnz": pnnz,
                        "inputs": "device-resident FP64"},
+            "gpu_launches": launches,
             "solve": {"rc": res["rc"], "iters": res["iters"], "inner_total": res["inner_total"],
                       "rel_kkt": res["kkt"]["rel_kkt"], "setup_ms": res["setup_ms"], "kernel_ms": res["kernel_ms"]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -494,9 +498,7 @@ def run_frontend(args):
 
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
-    launches0 = g.cqp_kernel_launches()
-    times, (x, y, res) = _timed(step, args.steps, args.warmup, flush)
-    launches = (g.cqp_kernel_launches() - launches0) // max(1, args.steps + args.warmup) * args.steps
+    times, (x, y, res), launches = _timed(step, args.steps, args.warmup, flush, g.cqp_kernel_launches)
     alg = algorithmic_bytes(inst, res)
     peaks, src = _peaks()
     achieved = alg / (res["kernel_ms"] / 1e3) / 1e9
@@ -547,16 +549,19 @@ def run_gemm(args):
                                     128)}
     peaks, src = _peaks()
     res = {}
+    launches = 0
     for name, fn in cases.items():
         for _ in range(args.warmup):
             fn()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        c0 = g.cqp_kernel_launches()
         e0.record()
         for _ in range(args.steps):
             fn()
         e1.record()
+        launches += g.cqp_kernel_launches() - c0
         e1.synchronize()
         ms = e0.elapsed_time(e1) / args.steps
         res[name] = {"ms": ms, "tflops": 2.0 * rows * H * H / ms / 1e9}
@@ -564,7 +569,9 @@ def run_gemm(args):
     line = {"metric": "warm-start GEMM throughput", "value": statistics.mean(v["tflops"] for v in res.values()),
             "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "dtype": "bf16 (FP32 accumulation)", "data": "synthetic",
-            "config": {"workload": "MLP layer 2: 262144 x 512 x 512"}, "gemms": res,
+            "config": {"workload": "MLP layer 2: 262144 x 512 x 512",
+                       "l2": "operands larger than L2 (268 MB of BF16 activations per GEMM)"},
+            "gemms": res, "gpu_launches": launches,
             "roofline": {"bound": "tensor", "achieved": best, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                          "frac": best / peaks["bf16_tflops"], "peak_source": src, "kernel": "k_gemm_bf16_v"}}
     print(json.dumps(line), flush=True)
