@@ -93,6 +93,8 @@ def lib():
         _lib.orc_proj_block_scaled.argtypes = [C.c_int, C.c_int64, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                                C.c_void_p]
         _lib.orc_power_start.argtypes = [C.c_int64, C.c_void_p]
+        _lib.orc_tridiag_max_eig.restype = C.c_double
+        _lib.orc_tridiag_max_eig.argtypes = [C.c_void_p, C.c_void_p, C.c_int]
         _lib.orc_norm_est.argtypes = [C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                       C.c_double, C.c_void_p]
         _lib.orc_pdhg_operator.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
@@ -251,6 +253,11 @@ def rescale(inst, **opts):
     c, b = np.zeros(n), np.zeros(m)
     lib().orc_rescale(P.ptr, C.byref(o), _p(col), _p(row), _p(bc), _p(av), _p(c), _p(b))
     return dict(col=col, row=row, beta_b=bc[0], beta_c=bc[1], a_val=av, c=c, b=b)
+
+
+def tridiag_max_eig(a, b):
+    a, b = _f64(a), _f64(b if len(b) else np.zeros(1))
+    return lib().orc_tridiag_max_eig(_p(a), _p(b), a.size)
 
 
 def power_start(n):

@@ -946,6 +946,8 @@ static double tridiag_max_eig(const double* a, const double* b, int k) {
   return hi;
 }
 
+double orc_tridiag_max_eig(const double* a, const double* b, int k) { return tridiag_max_eig(a, b, k); }
+
 /* ||A||_2 (needed for eta = 0.998/||A||_2, eq. practical-stepsizes).  The paper does not
  * say how it is estimated; reading: the Lanczos process on A'A (Lanczos 1950; Golub and
  * Van Loan, Sec. 9.1) from the normalised SplitMix64 start above, without

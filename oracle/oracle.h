@@ -120,6 +120,9 @@ void orc_kkt(const orc_problem* p, const double* x, const double* y, orc_kkt_rep
 void orc_rescale(const orc_problem* p, const orc_options* o,
                  double* col_scale, double* row_scale, double* beta_bc,
                  double* a_val_out, double* c_out, double* b_out);
+/* largest eigenvalue of the symmetric tridiagonal matrix with diagonal a[0..k) and
+ * off-diagonal b[0..k-1) (the Lanczos step of orc_norm_est), by Sturm bisection */
+double orc_tridiag_max_eig(const double* a, const double* b, int k);
 /* the unnormalised start vector of orc_norm_est: entry j = 1/2 + (top 53 bits of SplitMix64
  * output j+1 from state 0) / 2^53 */
 void orc_power_start(int64_t n, double* out);

@@ -401,3 +401,29 @@ def test_norm_estimate_symmetric_lasso_model(orc):
     assert abs(np.ones(n) @ np.linalg.svd(A)[2][0]) <= 1e-12 * np.sqrt(n)
     s, it = orc.norm_est(inst["a_rowptr"], inst["a_colind"], sc["a_val"], n)
     assert abs(s - top) <= 1e-5 * top
+
+
+def test_tridiagonal_max_eigenvalue(orc):
+    # the Lanczos step's eigenvalue search against LAPACK on random, clustered and scaled cases
+    rng = np.random.default_rng(91)
+    cases = [(rng.normal(size=k), rng.normal(size=k - 1)) for k in (1, 2, 3, 7, 30, 200)]
+    cases += [(np.ones(20), 1e-12 * rng.normal(size=19)),                 # clustered
+              (np.abs(rng.normal(size=25)) * 1e150, rng.normal(size=24) * 1e150),
+              (rng.normal(size=25) * 1e-150, rng.normal(size=24) * 1e-150),
+              (np.zeros(10), np.ones(9))]                                   # +-2 cos(j pi / 11)
+    for a, b in cases:
+        T = np.diag(a) + np.diag(b, 1) + np.diag(b, -1)
+        ref = np.linalg.eigvalsh(T).max()
+        got = orc.tridiag_max_eig(a, b)
+        assert abs(got - ref) <= 1e-13 * max(np.abs(T).max(), 1e-300) * max(1, a.size), (a.size, got, ref)
+
+
+def test_norm_estimate_rank_one(orc):
+    # A = u v': the Krylov space is one-dimensional, so sigma = ||u|| ||v|| after one step (beta_1
+    # is rounding-level, and the relative-change stop ends the process within two more steps)
+    rng = np.random.default_rng(92)
+    u, v = rng.normal(size=40), rng.normal(size=30)
+    rp, ci, val = csr(np.outer(u, v))
+    s, it = orc.norm_est(rp, ci, val, 30)
+    assert it <= 3
+    assert abs(s - np.linalg.norm(u) * np.linalg.norm(v)) <= 1e-12 * np.linalg.norm(u) * np.linalg.norm(v)
