@@ -10,7 +10,7 @@
  * instance; a dual head on the mean of the last hidden layer gives the budget-row and
  * risk-row duals, and the remaining duals follow as lambda (w_F, w_D) with
  * lambda = y_t / sigma_bar.  The solver itself is unchanged; a cold start remains
- * the fallback and the solve is the judge of the start.
+ * the fallback, and the solve's own KKT test decides whether the start is good.
  *
  * Conventions as in cqp.h: int status, device pointers, caller-owned buffers,
  * stream NULL = default stream, nothing synchronises unless stated.  BF16 arrays are

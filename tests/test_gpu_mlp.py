@@ -6,7 +6,7 @@
   (oracle/mlp.py) evaluated on the same BF16-rounded weights and inputs;
 * what training buys: on held-out portfolio batches the warm-started batched
   solve needs fewer iterations than the cold start and still reaches rel-KKT
-  <= 1e-4 on every instance (the solver remains the judge of the start).
+  <= 1e-4 on every instance (the solver's own KKT test decides).
 """
 import numpy as np
 import pytest
