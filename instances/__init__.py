@@ -24,6 +24,8 @@ from __future__ import annotations
 import numpy as np
 
 CONE_FREE, CONE_NONNEG, CONE_SOC, CONE_RSOC, CONE_EXP, CONE_POW = 0, 1, 2, 3, 4, 5
+# exponential / power blocks whose middle coordinate is fixed at one (no affine row for it)
+CONE_EXP1, CONE_POW1 = 7, 8
 
 _M0 = np.uint64(0xD2511F53)
 _M1 = np.uint64(0xCD9E8D57)
@@ -274,17 +276,20 @@ def socp_mix(n=200_000, n_nonneg=100_000, n_soc=2000, soc_dim=(10, 50), n_rsoc=5
                          btype, bstart, bdim, balpha, q_diag=q_diag, q_R=q_R, q_D=q_D, x_feasible=x0)
 
 
-def fisher_market(n_buyers=10_000, n_goods=1000, density=0.05, seed=1003, pow_fraction=0.5):
+def fisher_market(n_buyers=10_000, n_goods=1000, density=0.05, seed=1003, pow_fraction=0.5, fixed_middle=True):
     """Config 3: quasilinear Fisher market with exponential and power cones.
 
     Variables, in order: allocations x_ij on the valuation graph E (nonneg),
-    retained money delta_i (nonneg), then one 3-D cone block per buyer:
+    retained money delta_i (nonneg), then one 3-D block per buyer:
     exponential (z_i, s_i, t_i) with s_i exp(z_i/s_i) <= t_i, or power
-    (t_i, s_i, z_i) with t_i^a s_i^(1-a) >= |z_i|.  Rows: supply
-    sum_i x_ij = 1 (one per good), utility t_i - sum_j u_ij x_ij - delta_i = 0
-    (one per buyer), and s_i = 1 (one per buyer).  Objective
-    sum_i (delta_i - w_i z_i), Q = 0.  Valuations lognormal(0,1) at the given
-    density, budgets w_i ~ U[0.5, 2], supplies 1, alpha ~ U[0.2, 0.8].
+    (t_i, s_i, z_i) with t_i^a s_i^(1-a) >= |z_i|, where s_i = 1.  Rows: supply
+    sum_i x_ij = 1 (one per good) and utility t_i - sum_j u_ij x_ij - delta_i = 0
+    (one per buyer).  With fixed_middle (the form of eq. fisher-conic: e + 4n
+    stored coordinates, m + n equations) s_i = 1 is part of the block type
+    (CONE_EXP1 / CONE_POW1); otherwise the blocks are cones and one row s_i = 1
+    per buyer is added (m + 2n rows).  Objective sum_i (delta_i - w_i z_i),
+    Q = 0.  Valuations lognormal(0,1) at the given density, budgets
+    w_i ~ U[0.5, 2], supplies 1, alpha ~ U[0.2, 0.8].
     """
     st = Stream(seed, 0)
     nb, ng = n_buyers, n_goods
@@ -311,8 +316,9 @@ def fisher_market(n_buyers=10_000, n_goods=1000, density=0.05, seed=1003, pow_fr
     off_delta = e
     off_cone = e + nb
     blist = [(CONE_NONNEG, e + nb, 0.0)]
+    t_exp, t_pow = (CONE_EXP1, CONE_POW1) if fixed_middle else (CONE_EXP, CONE_POW)
     for i in range(nb):
-        blist.append((CONE_POW, 3, float(alpha[i])) if is_pow[i] else (CONE_EXP, 3, 0.0))
+        blist.append((t_pow, 3, float(alpha[i])) if is_pow[i] else (t_exp, 3, 0.0))
     btype, bstart, bdim, balpha = blocks_from_list(blist)
     # coordinate of z_i, s_i, t_i inside block i
     zc = np.where(is_pow, 2, 0)
@@ -320,20 +326,27 @@ def fisher_market(n_buyers=10_000, n_goods=1000, density=0.05, seed=1003, pow_fr
     z_idx = off_cone + 3 * np.arange(nb) + zc
     s_idx = off_cone + 3 * np.arange(nb) + 1
     t_idx = off_cone + 3 * np.arange(nb) + tc
-    m = ng + 2 * nb
-    rows = [gj, ng + bi, ng + np.arange(nb), ng + np.arange(nb), ng + nb + np.arange(nb)]
-    cols = [np.arange(e), np.arange(e), t_idx, off_delta + np.arange(nb), s_idx]
-    vals = [np.ones(e), -u, np.ones(nb), -np.ones(nb), np.ones(nb)]
+    rows = [gj, ng + bi, ng + np.arange(nb), ng + np.arange(nb)]
+    cols = [np.arange(e), np.arange(e), t_idx, off_delta + np.arange(nb)]
+    vals = [np.ones(e), -u, np.ones(nb), -np.ones(nb)]
+    b = [np.ones(ng), np.zeros(nb)]
+    if not fixed_middle:
+        rows.append(ng + nb + np.arange(nb))
+        cols.append(s_idx)
+        vals.append(np.ones(nb))
+        b.append(np.ones(nb))
+    m = ng + nb * (1 if fixed_middle else 2)
     a_rowptr, a_colind, a_val = _coo_to_csr(m, n, np.concatenate(rows), np.concatenate(cols),
                                             np.concatenate(vals))
-    b = np.concatenate([np.ones(ng), np.zeros(nb), np.ones(nb)])
+    b = np.concatenate(b)
     c = np.zeros(n)
     c[off_delta:off_delta + nb] = 1.0
     c[z_idx] = -w
     return make_instance("fisher_b%d_g%d" % (nb, ng), m, n, a_rowptr, a_colind, a_val, c, b,
                          btype, bstart, bdim, balpha, q_diag=np.zeros(n),
                          fisher=dict(n_buyers=nb, n_goods=ng, edges=e, buyer=bi, good=gj, u=u, w=w,
-                                     is_pow=is_pow, alpha=alpha, z_idx=z_idx, t_idx=t_idx, s_idx=s_idx))
+                                     is_pow=is_pow, alpha=alpha, z_idx=z_idx, t_idx=t_idx, s_idx=s_idx,
+                                     fixed_middle=fixed_middle))
 
 
 

@@ -17,19 +17,26 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _HDR = os.path.join(_HERE, "oracle.h")
 _OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_OUT_OMP = os.path.join(_HERE, "_build", "liboracle_omp.so")
 
 FREE, NONNEG, SOC, RSOC, EXP, POW = 0, 1, 2, 3, 4, 5
+# slices with the middle coordinate fixed (eq. fisher-conic): {(r, f, t): f e^(r/f) <= t} and
+# {(x, f, z): x^a f^(1-a) >= |z|, x >= 0}, f = blk_fix (1 by default)
+EXP1, POW1 = 7, 8
 
 
-def build(force: bool = False) -> str:
-    """Compile oracle.c with gcc into oracle/_build/liboracle.so (if stale)."""
-    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile oracle.c with gcc into oracle/_build/liboracle.so, or with -fopenmp into
+    liboracle_omp.so (the same source; used to time the CPU baseline on all host cores)."""
+    out = _OUT_OMP if omp else _OUT
+    os.makedirs(os.path.dirname(out), exist_ok=True)
     newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
-    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < newest:
-        tmp = _OUT + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _OUT)
-    return _OUT
+    if force or not os.path.exists(out) or os.path.getmtime(out) < newest:
+        tmp = out + ".%d.tmp" % os.getpid()
+        flags = ["-fopenmp"] if omp else []
+        subprocess.check_call(["gcc", "-O2", "-std=c11", *flags, "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
 class Problem(C.Structure):
@@ -42,7 +49,8 @@ class Problem(C.Structure):
                 ("nblocks", C.c_int64),
                 ("blk_type", C.c_void_p), ("blk_start", C.c_void_p), ("blk_dim", C.c_void_p),
                 ("blk_alpha", C.c_void_p),
-                ("row_lo", C.c_void_p), ("row_hi", C.c_void_p), ("x_lo", C.c_void_p), ("x_hi", C.c_void_p)]
+                ("row_lo", C.c_void_p), ("row_hi", C.c_void_p), ("x_lo", C.c_void_p), ("x_hi", C.c_void_p),
+                ("blk_fix", C.c_void_p)]
 
 
 class Options(C.Structure):
@@ -72,44 +80,71 @@ class Info(C.Structure):
                 ("hist_E", C.c_void_p), ("hist_restart", C.c_void_p)]
 
 
-_lib = None
+_libs = {}
+_use_omp = False
+
+
+def use_openmp(flag: bool = True, threads: int = 0) -> int:
+    """Route the wrappers below to the OpenMP build (flag) with `threads` threads (0: the
+    runtime's default); returns the thread count a parallel loop will use."""
+    global _use_omp
+    _use_omp = bool(flag)
+    lb = lib()
+    if flag and threads > 0:
+        lb.orc_set_threads(int(threads))
+    return int(lb.orc_max_threads())
 
 
 def lib():
-    global _lib
-    if _lib is None:
-        _lib = C.CDLL(build())
-        _lib.orc_proj_block.restype = C.c_int
-        _lib.orc_in_cone.restype = C.c_int
-        _lib.orc_in_dual_cone.restype = C.c_int
-        _lib.orc_norm_est.restype = C.c_double
-        _lib.orc_pdhg_operator.restype = C.c_int
-        _lib.orc_prox.restype = C.c_int
-        _lib.orc_solve.restype = C.c_int
-        for fn in ("orc_in_cone", "orc_in_dual_cone"):
-            getattr(_lib, fn).argtypes = [C.c_int, C.c_int64, C.c_double, C.c_void_p, C.c_double]
-        _lib.orc_proj_block.argtypes = [C.c_int, C.c_int64, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]
-        _lib.orc_proj_block_scaled.restype = C.c_int
-        _lib.orc_proj_block_scaled.argtypes = [C.c_int, C.c_int64, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
-                                               C.c_void_p]
-        _lib.orc_power_start.argtypes = [C.c_int64, C.c_void_p]
-        _lib.orc_tridiag_max_eig.restype = C.c_double
-        _lib.orc_tridiag_max_eig.argtypes = [C.c_void_p, C.c_void_p, C.c_int]
-        _lib.orc_norm_est.argtypes = [C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
-                                      C.c_double, C.c_void_p]
-        _lib.orc_pdhg_operator.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
-                                           C.c_double, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]
-        _lib.orc_prox.argtypes = [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
-                                  C.c_int, C.c_int, C.c_void_p]
-        vp, i64 = C.c_void_p, C.c_int64
-        _lib.orc_default_options.argtypes = [vp]
-        _lib.orc_spmv.argtypes = [i64, vp, vp, vp, vp, vp]
-        _lib.orc_spmv_t.argtypes = [i64, i64, vp, vp, vp, vp, vp]
-        _lib.orc_q_apply.argtypes = [vp, vp, vp]
-        _lib.orc_proj_product.argtypes = [vp, vp, vp, vp]
-        _lib.orc_kkt.argtypes = [vp, vp, vp, vp]
-        _lib.orc_rescale.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
-        _lib.orc_solve.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    omp = _use_omp
+    if omp not in _libs:
+        _libs[omp] = _load(build(omp=omp))
+    return _libs[omp]
+
+
+def _load(path):
+    _lib = C.CDLL(path)
+    _lib.orc_proj_block.restype = C.c_int
+    _lib.orc_in_cone.restype = C.c_int
+    _lib.orc_in_dual_cone.restype = C.c_int
+    _lib.orc_norm_est.restype = C.c_double
+    _lib.orc_pdhg_operator.restype = C.c_int
+    _lib.orc_prox.restype = C.c_int
+    _lib.orc_solve.restype = C.c_int
+    for fn in ("orc_in_cone", "orc_in_dual_cone"):
+        getattr(_lib, fn).argtypes = [C.c_int, C.c_int64, C.c_double, C.c_void_p, C.c_double]
+    _lib.orc_proj_block.argtypes = [C.c_int, C.c_int64, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]
+    _lib.orc_proj_block_scaled.restype = C.c_int
+    _lib.orc_proj_block_scaled.argtypes = [C.c_int, C.c_int64, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                                           C.c_void_p]
+    _lib.orc_power_start.argtypes = [C.c_int64, C.c_void_p]
+    _lib.orc_tridiag_max_eig.restype = C.c_double
+    _lib.orc_tridiag_max_eig.argtypes = [C.c_void_p, C.c_void_p, C.c_int]
+    _lib.orc_norm_est.argtypes = [C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                  C.c_double, C.c_void_p]
+    _lib.orc_pdhg_operator.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
+                                       C.c_double, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]
+    _lib.orc_prox.argtypes = [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
+                              C.c_int, C.c_int, C.c_void_p]
+    vp, i64 = C.c_void_p, C.c_int64
+    _lib.orc_default_options.argtypes = [vp]
+    _lib.orc_spmv.argtypes = [i64, vp, vp, vp, vp, vp]
+    _lib.orc_spmv_t.argtypes = [i64, i64, vp, vp, vp, vp, vp]
+    _lib.orc_q_apply.argtypes = [vp, vp, vp]
+    _lib.orc_proj_product.argtypes = [vp, vp, vp, vp]
+    _lib.orc_kkt.argtypes = [vp, vp, vp, vp]
+    _lib.orc_rescale.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    _lib.orc_solve.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    _lib.orc_proj_slice.restype = C.c_int
+    _lib.orc_proj_slice.argtypes = [C.c_int, C.c_double, C.c_double, vp, vp, vp]
+    _lib.orc_restart_rule.restype = C.c_int
+    _lib.orc_restart_rule.argtypes = [C.c_double, C.c_double, C.c_double, i64, i64, vp]
+    _lib.orc_pid_update.restype = C.c_double
+    _lib.orc_pid_update.argtypes = [C.c_double, C.c_double, C.c_double, vp, vp]
+    _lib.orc_inner_tol.restype = C.c_double
+    _lib.orc_inner_tol.argtypes = [C.c_double, C.c_double, C.c_double, vp]
+    _lib.orc_set_threads.argtypes = [C.c_int]
+    _lib.orc_max_threads.restype = C.c_int
     return _lib
 
 
@@ -149,7 +184,8 @@ class _Prob:
             blk_type=_p(arr("blk_type", np.int32)), blk_start=_p(arr("blk_start", np.int64)),
             blk_dim=_p(arr("blk_dim", np.int64)), blk_alpha=_p(arr("blk_alpha", np.float64)),
             row_lo=_p(arr("row_lo", np.float64)), row_hi=_p(arr("row_hi", np.float64)),
-            x_lo=_p(arr("x_lo", np.float64)), x_hi=_p(arr("x_hi", np.float64)))
+            x_lo=_p(arr("x_lo", np.float64)), x_hi=_p(arr("x_hi", np.float64)),
+            blk_fix=_p(arr("blk_fix", np.float64)))
 
     @property
     def ptr(self):
@@ -215,6 +251,38 @@ def proj_block_scaled(ctype, sc, r, alpha=0.0, m=None):
     if rc != 0:
         raise ValueError("invalid cone block")
     return out
+
+
+def proj_slice(ctype, r, alpha=0.0, f=1.0, m=None):
+    """Projection onto the slice EXP1 / POW1 with middle coordinate f, metric m (None: Euclidean)."""
+    r = _f64(r)
+    mm = None if m is None else _f64(m)
+    out = np.zeros(3)
+    rc = lib().orc_proj_slice(int(ctype), float(alpha), float(f), _p(r), _p(mm), _p(out))
+    if rc != 0:
+        raise ValueError("invalid slice block")
+    return out
+
+
+def restart_rule(E, E0, Eprev, k, ktot, **opts):
+    """The oracle's restart decision (eq. practical-restart-rule)."""
+    o = default_options(**opts)
+    return bool(lib().orc_restart_rule(float(E), float(E0), float(Eprev), int(k), int(ktot), C.byref(o)))
+
+
+def pid_update(omega, dx, dy, state, **opts):
+    """The oracle's primal-weight update (eqs. pid-error, pid-weight); state = [I, e_prev] is updated."""
+    o = default_options(**opts)
+    st = np.ascontiguousarray(state, dtype=np.float64)
+    w = lib().orc_pid_update(float(omega), float(dx), float(dy), C.byref(o), _p(st))
+    state[:] = st
+    return w
+
+
+def inner_tol(eps_prev, mov, tau, **opts):
+    """The oracle's adaptive inner tolerance (eq. monotone-primal-inner-tol)."""
+    o = default_options(**opts)
+    return lib().orc_inner_tol(float(eps_prev), float(mov), float(tau), C.byref(o))
 
 
 def proj_product(inst, r, m=None):

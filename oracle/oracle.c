@@ -4,20 +4,69 @@
  * Paper: "PDHCG-CQP", arXiv 2608.09159.  Section numbers, equations and
  * tables cited below are the paper's.  Where the paper is silent the reading
  * taken is stated at the point of use.
+ *
+ * The same source builds twice: single-threaded (liboracle.so) and with OpenMP
+ * (liboracle_omp.so, -fopenmp), the latter only to time the CPU baseline on all
+ * host cores.  Parallel loops touch independent rows, coordinates or blocks, and
+ * every long sum is taken in fixed chunks of ORC_CHUNK terms whose totals are then
+ * added in index order, so both builds perform the same additions in the same order
+ * and return identical iterates with any thread count.
  */
 #include "oracle.h"
 
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define EULER_E 2.718281828459045235360287
+#define ORC_CHUNK 4096
 
 static double* dalloc(int64_t n) { return (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double)); }
-static double dot(int64_t n, const double* a, const double* b) {
+
+/* fixed-order sums (see the header comment): kind 0: sum a_i b_i, 1: sum (a_i - b_i)^2,
+ * 2: sum a_i w_i b_i, 3: sum a_i (b_i - w_i) */
+static double csum(int kind, int64_t n, const double* a, const double* b, const double* w) {
+  const int64_t nc = (n + ORC_CHUNK - 1) / ORC_CHUNK;
+  double part1[1];
+  double* part = nc <= 1 ? part1 : (double*)malloc((size_t)nc * sizeof(double));
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) if (nc > 1)
+#endif
+  for (int64_t c = 0; c < nc; ++c) {
+    const int64_t i1 = (c + 1) * ORC_CHUNK < n ? (c + 1) * ORC_CHUNK : n;
+    double t = 0.0;
+    for (int64_t i = c * ORC_CHUNK; i < i1; ++i) {
+      if (kind == 0) t += a[i] * b[i];
+      else if (kind == 1) { const double d = a[i] - b[i]; t += d * d; }
+      else if (kind == 2) t += a[i] * w[i] * b[i];
+      else t += a[i] * (b[i] - w[i]);
+    }
+    part[c] = t;
+  }
   double s = 0.0;
-  for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+  for (int64_t c = 0; c < nc; ++c) s += part[c];
+  if (part != part1) free(part);
   return s;
+}
+static double dot(int64_t n, const double* a, const double* b) { return csum(0, n, a, b, NULL); }
+static double dist2(int64_t n, const double* a, const double* b) { return csum(1, n, a, b, NULL); }
+
+void orc_set_threads(int t) {
+#ifdef _OPENMP
+  if (t > 0) omp_set_num_threads(t);
+#else
+  (void)t;
+#endif
+}
+int orc_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
 }
 static double nrm2(int64_t n, const double* a) { return sqrt(dot(n, a, a)); }
 static double sq(double a) { return a * a; }
@@ -28,6 +77,9 @@ static double sq(double a) { return a * a; }
 
 void orc_spmv(int64_t m, const int64_t* rowptr, const int64_t* colind, const double* val,
               const double* x, double* y) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 512)
+#endif
   for (int64_t i = 0; i < m; ++i) {
     double s = 0.0;
     for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) s += val[k] * x[colind[k]];
@@ -46,8 +98,14 @@ void orc_spmv_t(int64_t m, int64_t n, const int64_t* rowptr, const int64_t* coli
  * structured operator"). */
 static void q_apply_parts(int64_t n, const double* qd, const int64_t* pr, const int64_t* pc, const double* pv,
                           int64_t k, const double* R, const double* D, const double* x, double* out) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
   for (int64_t i = 0; i < n; ++i) out[i] = qd ? qd[i] * x[i] : 0.0;
   if (pr) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 512)
+#endif
     for (int64_t i = 0; i < n; ++i) {
       double s = 0.0;
       for (int64_t t = pr[i]; t < pr[i + 1]; ++t) s += pv[t] * x[pc[t]];
@@ -63,8 +121,11 @@ static void q_apply_parts(int64_t n, const double* qd, const int64_t* pr, const 
       for (int64_t j = 0; j < k; ++j) s += D[l * k + j] * t1[j];
       t2[l] = s;
     }
-    for (int64_t l = 0; l < k; ++l)
-      for (int64_t i = 0; i < n; ++i) out[i] += R[l * n + i] * t2[l];
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t l = 0; l < k; ++l) out[i] += R[l * n + i] * t2[l];
     free(t1);
     free(t2);
   }
@@ -102,6 +163,10 @@ int orc_in_cone(int type, int64_t d, double alpha, const double* r, double tol) 
     }
     case ORC_POW:
       return r[0] >= -tol && r[1] >= -tol && pow_geo(r[0], r[1], alpha) + tol >= fabs(r[2]);
+    case ORC_EXP1:
+      return fabs(r[1] - 1.0) <= tol && exp(r[0]) <= r[2] + tol;
+    case ORC_POW1:
+      return fabs(r[1] - 1.0) <= tol && r[0] >= -tol && pow(fmax(r[0], 0.0), alpha) + tol >= fabs(r[2]);
   }
   return 0;
 }
@@ -543,6 +608,78 @@ static void proj_pow_m(const double* r, const double* m, double alpha, double* o
   out[2] = rz > 0.0 ? rho : -rho;
 }
 
+/* --- slices with the middle coordinate fixed (Sec. 5.4, eq. fisher-conic) ---
+ * X_f = {(r, f, t): f e^{r/f} <= t} (exponential) and {(x, f, z): x^a f^(1-a) >= |z|, x >= 0}
+ * (power) for a fixed f > 0.  Both equal f X_1 with X_1 the slice at f = 1, and a projection in a
+ * diagonal metric commutes with a positive scalar: argmin_{u in f X_1} ||u - r||_M
+ * = f argmin_{v in X_1} ||v - r/f||_M.  On X_1 the middle coordinate is fixed, so the projection
+ * is that of the remaining pair onto a 2-D convex set, found from its normal-cone condition as
+ * the zero of a monotone scalar function (derived here; the paper gives no formula). */
+
+/* Exponential slice X_1 = {(a, 1, c): e^a <= c}.  Outside X_1 the projection (a, e^a) satisfies
+ * M (r - u) = lambda (e^a, -1) with lambda >= 0 (outward normal of e^a - c <= 0), i.e.
+ *   phi(a) = m_a (a0 - a) - m_c (e^a - c0) e^a = 0,   a <= a0,  e^a >= c0.
+ * On that range phi' = -m_a - m_c e^a (2 e^a - c0) < 0, phi(a0) < 0, and phi >= 0 at
+ * a0 - (m_c/m_a)(e^{a0} - c0) e^{a0} and (for c0 > 0) at log c0, so the zero is unique. */
+typedef struct { double a0, c0, ma, mc; } eslice_ctx;
+static double eslice_phi(double a, const void* vctx) {
+  const eslice_ctx* c = (const eslice_ctx*)vctx;
+  double ea = exp(a);
+  return c->ma * (c->a0 - a) - c->mc * (ea - c->c0) * ea;
+}
+
+/* Power slice X_1 = {(x, 1, z): x^a >= |z|, x >= 0}.  For z0 != 0 outside X_1 the projection is
+ * (x, sign(z0) x^a) with x in (max(x0, 0), |z0|^{1/a}) the zero of
+ *   psi(x) = m_x (x - x0) - m_z (|z0| - x^a) a x^{a-1},
+ * which tends to -infinity at 0+ (or is < 0 at x0 > 0) and is m_x (|z0|^{1/a} - x0) > 0 at the
+ * right end; psi' >= m_x > 0 there, so the zero is unique.  For z0 = 0 it is (max(x0, 0), 0). */
+typedef struct { double x0, Z, a, mx, mz; } pslice_ctx;
+static double pslice_psi(double x, const void* vctx) {
+  const pslice_ctx* c = (const pslice_ctx*)vctx;
+  return c->mx * (x - c->x0) - c->mz * (c->Z - pow(x, c->a)) * c->a * pow(x, c->a - 1.0);
+}
+
+int orc_proj_slice(int type, double alpha, double f, const double* r, const double* m, double* out) {
+  if (!(f > 0.0) || !isfinite(f)) return -1;
+  double m0 = m ? m[0] : 1.0, m2 = m ? m[2] : 1.0;
+  double a0 = r[0] / f, c0 = r[2] / f;
+  double u0, u2;
+  if (type == ORC_EXP1) {
+    if (exp(a0) <= c0) {
+      u0 = a0; u2 = c0;
+    } else {
+      eslice_ctx c = {a0, c0, m0, m2};
+      double ea = exp(a0);
+      double lo = a0 - (m2 / m0) * (ea - c0) * ea;
+      if (c0 > 0.0) lo = fmax(lo, log(c0));
+      if (!isfinite(lo)) {   /* e^{a0} overflowed: step left until phi >= 0 */
+        double step = 1.0;
+        lo = a0 - step;
+        while (eslice_phi(lo, &c) < 0.0 && step < 1e300) { step *= 2.0; lo = a0 - step; }
+      }
+      double a = bisect(eslice_phi, &c, lo, a0, 1);
+      u0 = a; u2 = exp(a);
+    }
+  } else if (type == ORC_POW1) {
+    if (!(alpha > 0.0 && alpha < 1.0)) return -1;
+    if (a0 >= 0.0 && pow(a0, alpha) >= fabs(c0)) {
+      u0 = a0; u2 = c0;
+    } else if (c0 == 0.0) {
+      u0 = fmax(a0, 0.0); u2 = 0.0;
+    } else {
+      pslice_ctx c = {a0, fabs(c0), alpha, m0, m2};
+      double x = bisect(pslice_psi, &c, fmax(a0, 0.0), pow(fabs(c0), 1.0 / alpha), 0);
+      u0 = x; u2 = (c0 > 0.0 ? 1.0 : -1.0) * pow(x, alpha);
+    }
+  } else {
+    return -1;
+  }
+  out[0] = f * u0;
+  out[1] = f;
+  out[2] = f * u2;
+  return 0;
+}
+
 int orc_proj_block(int type, int64_t d, double alpha, const double* r, const double* m, double* out) {
   switch (type) {
     case ORC_FREE: memcpy(out, r, (size_t)d * sizeof(double)); return 0;
@@ -566,15 +703,26 @@ int orc_proj_block(int type, int64_t d, double alpha, const double* r, const dou
       if (d != 3 || !(alpha > 0.0 && alpha < 1.0)) return -1;
       proj_pow_m(r, m, alpha, out);
       return 0;
+    case ORC_EXP1: case ORC_POW1:
+      if (d != 3) return -1;
+      return orc_proj_slice(type, alpha, 1.0, r, m, out);
   }
   return -1;
 }
 
 void orc_proj_product(const orc_problem* p, const double* r, const double* m, double* out) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
   for (int64_t j = 0; j < p->nblocks; ++j) {
     int64_t s = p->blk_start[j], d = p->blk_dim[j];
     if (p->blk_type[j] == ORC_BOX) {   /* coordinatewise clip: metric-independent (App. A.1) */
       for (int64_t i = s; i < s + d; ++i) out[i] = fmin(fmax(r[i], p->x_lo[i]), p->x_hi[i]);
+      continue;
+    }
+    if (p->blk_type[j] == ORC_EXP1 || p->blk_type[j] == ORC_POW1) {
+      orc_proj_slice(p->blk_type[j], p->blk_alpha[j], p->blk_fix ? p->blk_fix[j] : 1.0, r + s, m ? m + s : NULL,
+                     out + s);
       continue;
     }
     orc_proj_block(p->blk_type[j], d, p->blk_alpha[j], r + s, m ? m + s : NULL, out + s);
@@ -604,6 +752,33 @@ static double bound_norm(const orc_problem* p) {
 /* ------------------------------------------------------------------------- */
 /* KKT report (eq. kkt-cqp; relative measures as read in the build notes R1)  */
 /* ------------------------------------------------------------------------- */
+
+/* Support term of a slice block at f = 1: inf over X_1 of sl'x for the dual slack sl.
+ * Exponential, X_1 = {(r, 1, t): e^r <= t}: inf = sl_1 + inf_r (sl_0 r + sl_2 e^r), finite only for
+ * sl_0 <= 0 <= sl_2; then it is sl_1 + sl_0 (log(-sl_0/sl_2) - 1) (the minimiser e^r = -sl_0/sl_2),
+ * sl_1 for sl_0 = 0, and -infinity for sl_0 < 0 = sl_2.  Power, X_1 = {(x, 1, z): x^a >= |z|, x >= 0}:
+ * inf = sl_1 + inf_{x >= 0} (sl_0 x - |sl_2| x^a), finite only for sl_0 >= 0; with
+ * x* = (a |sl_2| / sl_0)^{1/(1-a)} it is sl_1 - (1-a)/a sl_0 x*, sl_1 for sl_2 = 0, and -infinity
+ * for sl_0 = 0 != sl_2.  D = {sl_0 <= 0, sl_2 >= 0} (exp) or {sl_0 >= 0} (pow) is the closed cone
+ * of slacks with a finite (or limiting) term; res receives sl - Pi_D(sl), the part counted as dual
+ * residual, and the term is evaluated at Pi_D(sl). */
+static double slice_support(int type, double alpha, const double* sl, double* res) {
+  res[0] = res[1] = res[2] = 0.0;
+  if (type == ORC_EXP1) {
+    double a = sl[0], c = sl[2];
+    if (a > 0.0) { res[0] = a; a = 0.0; }
+    if (c < 0.0) { res[2] = c; c = 0.0; }
+    if (a == 0.0) return sl[1];
+    if (c == 0.0) return -INFINITY;
+    return sl[1] + a * (log(-a / c) - 1.0);
+  }
+  double p = sl[0], w = fabs(sl[2]);
+  if (p < 0.0) { res[0] = p; p = 0.0; }
+  if (w == 0.0) return sl[1];
+  if (p == 0.0) return -INFINITY;
+  double xs = pow(alpha * w / p, 1.0 / (1.0 - alpha));
+  return sl[1] - (1.0 - alpha) / alpha * p * xs;
+}
 
 void orc_kkt(const orc_problem* p, const double* x, const double* y, orc_kkt_report* rep) {
   int64_t m = p->m, n = p->n;
@@ -642,14 +817,29 @@ void orc_kkt(const orc_problem* p, const double* x, const double* y, orc_kkt_rep
       ps[i] = r;
     }
   }
+  /* slice blocks (ORC_EXP1 / ORC_POW1, a convex set X_f = f X_1, not a cone): the dual objective
+   * gains inf_{x in X_f} s'x = f (s_mid + h(s)), which is finite only on a cone D of dual slacks;
+   * the distance of s to D joins the dual residual and h is taken at the projection onto D
+   * (reading, the slice analogue of the box terms above; derivation at slice_support) */
+  double sliceterm = 0.0;
+  for (int64_t j = 0; j < p->nblocks; ++j) {
+    int t = p->blk_type[j];
+    if (t != ORC_EXP1 && t != ORC_POW1) continue;
+    int64_t b0 = p->blk_start[j];
+    double sl[3] = {-s[b0], -s[b0 + 1], -s[b0 + 2]};   /* the slack Qx + c - A'y */
+    double res[3];
+    sliceterm += (p->blk_fix ? p->blk_fix[j] : 1.0) * slice_support(t, p->blk_alpha[j], sl, res);
+    for (int q = 0; q < 3; ++q) ps[b0 + q] = res[q];
+  }
   double rd = sqrt(dot(n, ps, ps) + rd2);
   double xqx = dot(n, x, qx), cx = dot(n, p->c, x);
-  double pobj = 0.5 * xqx + cx, dobj = by + boxterm - 0.5 * xqx;
+  double pobj = 0.5 * xqx + cx, dobj = by + boxterm + sliceterm - 0.5 * xqx;
   rep->norm_res_p = rp;
   rep->norm_res_d = rd;
   rep->eps_p = rp / (1.0 + bound_norm(p));
   rep->eps_d = rd / (1.0 + nrm2(n, p->c));
-  rep->eps_g = fabs(pobj - dobj) / (1.0 + fabs(pobj) + fabs(dobj));
+  /* an infinite support term (dual objective -inf) is the limit eps_g -> 1 */
+  rep->eps_g = isfinite(dobj) ? fabs(pobj - dobj) / (1.0 + fabs(pobj) + fabs(dobj)) : 1.0;
   rep->pobj = pobj;
   rep->dobj = dobj;
   rep->rel_kkt = fmax(rep->eps_p, fmax(rep->eps_d, rep->eps_g));
@@ -671,6 +861,8 @@ typedef struct {
   double *lo, *hi;                   /* row bounds (NULL: equality rows, b) */
   double *xlo, *xhi;                 /* box bounds (NULL: no box blocks) */
   double* csc;                       /* rescaled-cone mode: S_x on cone coordinates (NULL: blocks are cones) */
+  double* fix;                       /* per block: fixed middle coordinate of slice blocks (scaled) */
+  double beta_b;                     /* bound-objective factor of x (1 before rescaling) */
   orc_problem view;                  /* problem struct pointing at the arrays above */
 } wprob;
 
@@ -743,6 +935,9 @@ static void wprob_init(wprob* w, const orc_problem* p) {
     memcpy(w->xlo, p->x_lo, (size_t)w->n * sizeof(double));
     memcpy(w->xhi, p->x_hi, (size_t)w->n * sizeof(double));
   }
+  w->fix = dalloc(p->nblocks);
+  for (int64_t j = 0; j < p->nblocks; ++j) w->fix[j] = p->blk_fix ? p->blk_fix[j] : 1.0;
+  w->beta_b = 1.0;
   build_transpose(w);
   w->view = *p;
   w->view.a_rowptr = w->ar; w->view.a_colind = w->ac; w->view.a_val = w->av;
@@ -751,12 +946,13 @@ static void wprob_init(wprob* w, const orc_problem* p) {
   w->view.q_R = w->R; w->view.q_D = w->D;
   w->view.c = w->c; w->view.b = w->b;
   w->view.row_lo = w->lo; w->view.row_hi = w->hi; w->view.x_lo = w->xlo; w->view.x_hi = w->xhi;
+  w->view.blk_fix = w->fix;
 }
 
 static void wprob_free(wprob* w) {
   free(w->ar); free(w->ac); free(w->av); free(w->tr); free(w->tc); free(w->tv);
   free(w->qd); free(w->pr); free(w->pc); free(w->pv); free(w->R); free(w->D); free(w->c); free(w->b);
-  free(w->lo); free(w->hi); free(w->xlo); free(w->xhi); free(w->csc);
+  free(w->lo); free(w->hi); free(w->xlo); free(w->xhi); free(w->csc); free(w->fix);
 }
 
 static int q_is_diagonal(const wprob* w) { return w->pr == NULL && w->k == 0; }
@@ -878,6 +1074,12 @@ static void do_rescale(wprob* w, const orc_problem* p, const orc_options* o, sca
     for (int64_t t = 0; t < w->k * w->k; ++t) w->D[t] *= qs;
   }
   refresh_transpose_values(w);
+  /* a slice block X_f holds x~ = col x / beta_b; with one factor per block (cone-preserving mode)
+   * that is the slice with f~ = f col / beta_b (the set is f X_1 and scales as a whole) */
+  w->beta_b = sc->beta_b;
+  for (int64_t j = 0; j < p->nblocks; ++j)
+    if (!o->rescaled_cones && (p->blk_type[j] == ORC_EXP1 || p->blk_type[j] == ORC_POW1))
+      w->fix[j] *= sc->col[p->blk_start[j] + 1] / sc->beta_b;
   /* rescaled-cone mode: the scaled variable x~ = S_x x / beta_b lies in S_j K_j on each
    * cone block (beta_b is a positive scalar and drops out of the cone) */
   if (o->rescaled_cones) {
@@ -1031,6 +1233,20 @@ static void proj_scaled(const wprob* w, const double* r, const double* m, double
       orc_proj_product(&one, r, m, out);
       continue;
     }
+    if (t == ORC_EXP1 || t == ORC_POW1) {
+      /* a slice is not a cone, so beta_b stays: x~ lies in S X_f / beta_b, projected as
+       * S' Pi_{X_f}^{S' m S'}(S'^-1 r) with S' = S / beta_b (w->fix keeps the original f in
+       * this mode) */
+      double sc3[3], r3[3], m3[3], o3[3];
+      for (int q = 0; q < 3; ++q) {
+        sc3[q] = w->csc[s + q] / w->beta_b;
+        r3[q] = r[s + q] / sc3[q];
+        m3[q] = (m ? m[s + q] : 1.0) * sc3[q] * sc3[q];
+      }
+      orc_proj_slice(t, p->blk_alpha[j], w->fix[j], r3, m3, o3);
+      for (int q = 0; q < 3; ++q) out[s + q] = sc3[q] * o3[q];
+      continue;
+    }
     orc_proj_block_scaled(t, d, p->blk_alpha[j], w->csc + s, r + s, m ? m + s : NULL, out + s);
   }
 }
@@ -1044,6 +1260,9 @@ static void prox_diag(const wprob* w, double tau, const double* v, double* out) 
   int64_t n = w->n;
   double* mm = dalloc(n);
   double* xt = dalloc(n);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
   for (int64_t i = 0; i < n; ++i) {
     mm[i] = 1.0 + tau * w->qd[i];
     xt[i] = (v[i] - tau * w->c[i]) / mm[i];
@@ -1070,6 +1289,9 @@ static int prox_bb(const wprob* w, double tau, const double* v, const double* u0
   double* trial = dalloc(n);
   double jmax = 0.0;
   /* J = diag(Q) + I/tau with the full diagonal of Q = diag(q) + P + R'DR (eq. jacobi-inner-metric) */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) reduction(max : jmax)
+#endif
   for (int64_t i = 0; i < n; ++i) {
     double qi = w->qd[i];
     if (w->pr)
@@ -1082,25 +1304,31 @@ static int prox_bb(const wprob* w, double tau, const double* v, const double* u0
   }
   memcpy(u, u0, (size_t)n * sizeof(double));
   w_q_apply(w, u, q);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
   for (int64_t i = 0; i < n; ++i) g[i] = q[i] + w->c[i] + (u[i] - v[i]) / tau;
   double alpha = jacobi ? 1.0 : 1.0 / jmax;
   int it;
   double du = 0.0;
   for (it = 0; it < max_inner; ++it) {
+    #ifdef _OPENMP
+    #pragma omp parallel for schedule(static)
+    #endif
     for (int64_t i = 0; i < n; ++i) trial[i] = u[i] - alpha * g[i] / J[i];
     proj_scaled(w, trial, jacobi ? J : NULL, un);
-    du = 0.0;
-    for (int64_t i = 0; i < n; ++i) du += sq(un[i] - u[i]);
-    du = sqrt(du);
+    du = sqrt(dist2(n, un, u));
     if (du <= eps_in) { memcpy(u, un, (size_t)n * sizeof(double)); ++it; break; }
     w_q_apply(w, un, q);
-    for (int64_t i = 0; i < n; ++i) gn[i] = q[i] + w->c[i] + (un[i] - v[i]) / tau;
-    double sjs = 0.0, sdg = 0.0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
     for (int64_t i = 0; i < n; ++i) {
-      double s = un[i] - u[i];
-      sjs += s * J[i] * s;
-      sdg += s * (gn[i] - g[i]);
+      gn[i] = q[i] + w->c[i] + (un[i] - v[i]) / tau;
+      trial[i] = un[i] - u[i];          /* s = u^{j+1} - u^j */
     }
+    /* <s, J s> and <s, dg> with dg = g^{j+1} - g^j */
+    double sjs = csum(2, n, trial, trial, J), sdg = csum(3, n, trial, gn, g);
     if (sdg > 1e-30) alpha = sjs / sdg;
     if (alpha < 1e-10) alpha = 1e-10;
     if (alpha > 1e10) alpha = 1e10;
@@ -1126,10 +1354,19 @@ static int pdhg_operator(const wprob* w, double tau, double sigma, const double*
   int64_t m = w->m, n = w->n;
   double* v = scratch_n;
   orc_spmv(n, w->tr, w->tc, w->tv, y, v);            /* A'y via the transpose CSR */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
   for (int64_t i = 0; i < n; ++i) v[i] = x[i] + tau * v[i];
   int inner = do_prox(w, tau, v, x, eps_in, max_inner, jacobi, force_inner, xo);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
   for (int64_t i = 0; i < n; ++i) v[i] = 2.0 * xo[i] - x[i];
   orc_spmv(m, w->ar, w->ac, w->av, v, scratch_m);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
   for (int64_t i = 0; i < m; ++i) {
     double lo, hi;
     row_bounds(&w->view, i, &lo, &hi);
@@ -1192,21 +1429,50 @@ static void unscale(const wprob* w, const scaling* sc, const double* xs, const d
 static double fixed_point_error(const wprob* w, double omega, double eta, const double* hx, const double* hy,
                                 const double* wx, const double* wy, double* dxn, double* adx) {
   int64_t m = w->m, n = w->n;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
   for (int64_t j = 0; j < n; ++j) dxn[j] = hx[j] - wx[j];
   orc_spmv(m, w->ar, w->ac, w->av, dxn, adx);
-  double dx2 = dot(n, dxn, dxn), dy2 = 0.0, cross = 0.0;
-  for (int64_t i = 0; i < m; ++i) {
-    double dy = hy[i] - wy[i];
-    dy2 += dy * dy;
-    cross += adx[i] * dy;
-  }
+  double dx2 = dot(n, dxn, dxn), dy2 = dist2(m, hy, wy), cross = csum(3, m, adx, hy, wy);
   double e2 = omega * dx2 + dy2 / omega + 2.0 * eta * cross;
   return sqrt(fmax(e2, 0.0));
+}
+
+/* Adaptive restart (eq. practical-restart-rule): sufficient decay, necessary decay without local
+ * progress, or the artificial limit, tested from the epoch's second iteration on. */
+int orc_restart_rule(double E, double E0, double Eprev, int64_t k, int64_t ktot, const orc_options* o) {
+  if (k < 1) return 0;
+  if (E <= o->beta_s * E0) return 1;
+  if (E <= o->beta_n * E0 && E > Eprev) return 1;
+  if ((double)k >= o->beta_a * (double)ktot) return 1;
+  return 0;
+}
+
+/* PID primal weight (eqs. pid-error, pid-weight):
+ *   e_n = log(||dy|| / (omega_n ||dx||)),  I_n = beta_I I_{n-1} + e_n,
+ *   log omega_{n+1} = log omega_n + K_P e_n + K_I I_n + K_D (e_n - e_{n-1}). */
+double orc_pid_update(double omega, double dx, double dy, const orc_options* o, double* state) {
+  if (!o->pid || !(dx > 1e-10) || !(dy > 1e-10)) return omega;
+  double e = log(dy / (omega * dx));
+  state[0] = o->beta_I * state[0] + e;
+  double lw = log(omega) + o->K_P * e + o->K_I * state[0] + o->K_D * (e - state[1]);
+  state[1] = e;
+  return exp(lw);
+}
+
+/* Adaptive inner tolerance (eq. monotone-primal-inner-tol):
+ *   eps_k = min{eps_{k-1}, max{gamma_in ||x^{n,k} - x^{n,k-1}|| / tau_n, eps_min}}. */
+double orc_inner_tol(double eps_prev, double mov, double tau, const orc_options* o) {
+  return fmin(eps_prev, fmax(o->gamma_in * mov / tau, o->eps_min_in));
 }
 
 int orc_solve(const orc_problem* p, const orc_options* o, const double* x0, const double* y0, double* x_out,
               double* y_out, orc_info* info) {
   int64_t m = p->m, n = p->n;
+  for (int64_t j = 0; j < p->nblocks; ++j)
+    if ((p->blk_type[j] == ORC_EXP1 || p->blk_type[j] == ORC_POW1) && p->blk_fix && !(p->blk_fix[j] > 0.0))
+      return -1;
   wprob w;
   scaling sc;
   wprob_init(&w, p);
@@ -1231,7 +1497,7 @@ int orc_solve(const orc_problem* p, const orc_options* o, const double* x0, cons
   memcpy(ay, hy, (size_t)m * sizeof(double));
   memcpy(xprev, hx, (size_t)n * sizeof(double));
   double eps_in = o->eps0_in;
-  double pid_int = 0.0, err_prev = 0.0;
+  double pid_state[2] = {0.0, 0.0};   /* I_{n-1}, e_{n-1}; reading: both start at 0 */
   double E0 = 0.0, Eprev = 0.0;
   int64_t k = 0, ktot = 0, restarts = 0, inner_total = 0;
   double mov = 0.0;
@@ -1244,16 +1510,11 @@ int orc_solve(const orc_problem* p, const orc_options* o, const double* x0, cons
   while (ktot < o->max_iter) {
     /* adaptive inner tolerance (eq. monotone-primal-inner-tol) for k >= 1, with
      * x^{n,k} - x^{n,k-1} read as consecutive stored candidates */
-    if (k >= 1) {
-      double cand = fmax(o->gamma_in * mov / tau, o->eps_min_in);
-      if (cand < eps_in) eps_in = cand;
-    }
+    if (k >= 1) eps_in = orc_inner_tol(eps_in, mov, tau, o);
     int inner = pdhg_operator(&w, tau, sigma, hx, hy, eps_in, o->max_inner, o->jacobi, o->force_inner, wx, wy, sn,
                               sm);
     inner_total += inner;
-    double d2 = 0.0;
-    for (int64_t j = 0; j < n; ++j) d2 += sq(wx[j] - xprev[j]);
-    mov = sqrt(d2);
+    mov = sqrt(dist2(n, wx, xprev));
     memcpy(xprev, wx, (size_t)n * sizeof(double));
     ktot += 1;
     int check = (ktot % o->check_every) == 0 || ktot >= o->max_iter;
@@ -1304,11 +1565,7 @@ int orc_solve(const orc_problem* p, const orc_options* o, const double* x0, cons
         break;
       }
       /* restart rule (eq. practical-restart-rule) */
-      if (k >= 1) {
-        if (E <= o->beta_s * E0) do_restart = 1;
-        else if (E <= o->beta_n * E0 && E > Eprev) do_restart = 1;
-        else if ((double)k >= o->beta_a * (double)ktot) do_restart = 1;
-      }
+      do_restart = orc_restart_rule(E, E0, Eprev, k, ktot, o);
       Eprev = E;
       if (info && info->hist_iter && hist_len < o->hist_cap) {
         info->hist_iter[hist_len] = ktot; info->hist_kkt[hist_len] = rep.rel_kkt;
@@ -1320,20 +1577,10 @@ int orc_solve(const orc_problem* p, const orc_options* o, const double* x0, cons
       /* PID primal weight (eqs. pid-error, pid-weight) from the accepted endpoint
        * w^{n,N} against the epoch start z^{n,0} = a^n.  Reading: skipped when either
        * movement is below 1e-10. */
-      double dxn = 0.0, dyn = 0.0;
-      for (int64_t j = 0; j < n; ++j) dxn += sq(wx[j] - ax[j]);
-      for (int64_t i = 0; i < m; ++i) dyn += sq(wy[i] - ay[i]);
-      dxn = sqrt(dxn);
-      dyn = sqrt(dyn);
-      if (o->pid && dxn > 1e-10 && dyn > 1e-10) {
-        double e = log(dyn / (omega * dxn));
-        pid_int = o->beta_I * pid_int + e;
-        double lw = log(omega) + o->K_P * e + o->K_I * pid_int + o->K_D * (e - err_prev);
-        err_prev = e;
-        omega = exp(lw);
-        tau = eta / omega;
-        sigma = eta * omega;
-      }
+      double dxn = sqrt(dist2(n, wx, ax)), dyn = sqrt(dist2(m, wy, ay));
+      omega = orc_pid_update(omega, dxn, dyn, o, pid_state);
+      tau = eta / omega;
+      sigma = eta * omega;
       /* restart from the final stored candidate (eq. restart-output) */
       memcpy(ax, wx, (size_t)n * sizeof(double));
       memcpy(ay, wy, (size_t)m * sizeof(double));
@@ -1345,7 +1592,13 @@ int orc_solve(const orc_problem* p, const orc_options* o, const double* x0, cons
       /* anchored reflected-Halpern step (eq. rh-update) */
       double c1 = (double)(k + 1) / (double)(k + 2), c2 = 1.0 / (double)(k + 2), r2 = 2.0 * o->rho,
              r1 = 1.0 - 2.0 * o->rho;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
       for (int64_t j = 0; j < n; ++j) hx[j] = c1 * (r2 * wx[j] + r1 * hx[j]) + c2 * ax[j];
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
       for (int64_t i = 0; i < m; ++i) hy[i] = c1 * (r2 * wy[i] + r1 * hy[i]) + c2 * ay[i];
       k += 1;
     }

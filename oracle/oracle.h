@@ -13,13 +13,11 @@
  * Pins (tests/test_oracle_*.py): products against dense / exact integer
  * results, every projection against its KKT certificate, brute force and
  * closed forms, the PDHG step against the resolvent identity and Fejer /
- * Halpern bounds, and whole solves against closed-form optima.
- * Parity unpinned: the control heuristics inside orc_solve -- the adaptive
- * restart rule (eq. practical-restart-rule), the PID primal-weight update
- * (eqs. pid-error / pid-weight) and the adaptive inner tolerance (eq.
- * monotone-primal-inner-tol).  They change the path, not the fixed point, so
- * the closed-form solves cannot tell a deviation in them from the paper's
- * rule; they follow the paper's formulas as written.
+ * Halpern bounds, whole solves against closed-form optima, and the control
+ * rules of orc_solve (adaptive restart, PID primal weight, adaptive inner
+ * tolerance) against hand-computed cases of their printed formulas with the
+ * constants of Table practical-defaults (orc_restart_rule, orc_pid_update,
+ * orc_inner_tol are the functions orc_solve calls).
  */
 #ifndef CQP_ORACLE_H
 #define CQP_ORACLE_H
@@ -30,7 +28,13 @@ extern "C" {
 #endif
 
 /* Cone block types (a block is a contiguous slice of x). */
-enum { ORC_FREE = 0, ORC_NONNEG = 1, ORC_SOC = 2, ORC_RSOC = 3, ORC_EXP = 4, ORC_POW = 5, ORC_BOX = 6 };
+enum { ORC_FREE = 0, ORC_NONNEG = 1, ORC_SOC = 2, ORC_RSOC = 3, ORC_EXP = 4, ORC_POW = 5, ORC_BOX = 6,
+       /* slices with the middle coordinate fixed (Sec. 5.4, eq. fisher-conic and the coordinate
+        * count after it: each buyer's (z_i, 1, t_i) is one stored 3-D block with the middle entry
+        * held at one and no affine row for it):
+        * EXP1 = {(r, f, t): f exp(r/f) <= t}, POW1 = {(x, f, z): x^a f^(1-a) >= |z|, x >= 0},
+        * f = blk_fix of the block (1 when blk_fix is NULL); convex sets, not cones */
+       ORC_EXP1 = 7, ORC_POW1 = 8 };
 
 typedef struct {
   int64_t m, n;
@@ -47,6 +51,8 @@ typedef struct {
    * on ORC_BOX blocks, x_lo <= x <= x_hi (n entries, read on box coordinates only);
    * infinite entries mean no bound */
   const double* row_lo; const double* row_hi; const double* x_lo; const double* x_hi;
+  /* per block: the fixed middle coordinate f of ORC_EXP1 / ORC_POW1 blocks (NULL: f = 1) */
+  const double* blk_fix;
 } orc_problem;
 
 typedef struct {
@@ -94,6 +100,11 @@ typedef struct {
 
 void orc_default_options(orc_options* o);
 
+/* threads of the OpenMP build (liboracle_omp.so; no effect in the single-threaded build) and the
+ * number a parallel loop will use (1 in the single-threaded build) */
+void orc_set_threads(int t);
+int orc_max_threads(void);
+
 /* sparse products */
 void orc_spmv(int64_t m, const int64_t* rowptr, const int64_t* colind, const double* val,
               const double* x, double* y);
@@ -108,7 +119,10 @@ void orc_proj_product(const orc_problem* p, const double* r, const double* m, do
  * (NULL: Euclidean): S Pi_K^{S m S}(S^-1 r) (eq. scaling-induced-metric) */
 int orc_proj_block_scaled(int type, int64_t dim, double alpha, const double* sc, const double* r, const double* m,
                           double* out);
-/* 1 if r lies in the block's cone (tol absolute slack), for tests */
+/* projection onto the slice ORC_EXP1 / ORC_POW1 with middle coordinate f > 0 in the diagonal
+ * metric m (NULL: Euclidean); out[1] = f.  Returns -1 for a bad type, dim, alpha or f. */
+int orc_proj_slice(int type, double alpha, double f, const double* r, const double* m, double* out);
+/* 1 if r lies in the block's cone (tol absolute slack), for tests; slices use f = 1 */
 int orc_in_cone(int type, int64_t dim, double alpha, const double* r, double tol);
 int orc_in_dual_cone(int type, int64_t dim, double alpha, const double* r, double tol);
 
@@ -139,7 +153,22 @@ int orc_pdhg_operator(const orc_problem* p, double tau, double sigma, const doub
 int orc_prox(const orc_problem* p, double tau, const double* v, const double* u0, double eps_in,
              int max_inner, int jacobi, int force_inner, double* u_out);
 
-/* full solve; x_out (n), y_out (m) receive the unscaled final candidate */
+/* Control rules of orc_solve, exposed so that they can be pinned on hand-computed cases.
+ * orc_restart_rule: 1 if eq. practical-restart-rule restarts at epoch step k >= 1 with fixed-point
+ *   errors E = E_{n,k}, E0 = E_{n,0}, Eprev = E at the previous check of the epoch (E0 at its first),
+ *   k the epoch's iteration count and ktot the cumulative count; 0 at k = 0.
+ * orc_pid_update: eqs. pid-error / pid-weight at a restart with movements dx = ||w_x - x^{n,0}||,
+ *   dy = ||w_y - y^{n,0}||; state[0] = I_{n-1}, state[1] = e_{n-1} are updated in place; returns
+ *   omega_{n+1}.  Reading: omega is kept (and the state untouched) when o->pid is 0 or a movement
+ *   is <= 1e-10.
+ * orc_inner_tol: eq. monotone-primal-inner-tol, the tolerance of step k >= 1 from the previous one,
+ *   the movement mov = ||x^{n,k} - x^{n,k-1}|| and tau. */
+int orc_restart_rule(double E, double E0, double Eprev, int64_t k, int64_t ktot, const orc_options* o);
+double orc_pid_update(double omega, double dx, double dy, const orc_options* o, double* state);
+double orc_inner_tol(double eps_prev, double mov, double tau, const orc_options* o);
+
+/* full solve; x_out (n), y_out (m) receive the unscaled final candidate.  Returns 0 (converged),
+ * 1 (iteration limit) or -1 (invalid problem: a slice block with a non-positive blk_fix) */
 int orc_solve(const orc_problem* p, const orc_options* o, const double* x0, const double* y0,
               double* x_out, double* y_out, orc_info* info);
 

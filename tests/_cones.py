@@ -10,6 +10,7 @@ import numpy as np
 from scipy.optimize import minimize, minimize_scalar
 
 FREE, NONNEG, SOC, RSOC, EXP, POW = 0, 1, 2, 3, 4, 5
+EXP1, POW1 = 7, 8   # slices with the middle coordinate fixed at 1 (membership only)
 E = math.e
 
 
@@ -21,6 +22,8 @@ _INTERIOR = {
     EXP: lambda d: np.array([-1.0, 1.0, 1.0]),
     POW: lambda d: np.array([1.0, 1.0, 0.0]),
     NONNEG: lambda d: np.ones(d),
+    EXP1: lambda d: np.array([-1.0, 0.0, 1.0]),
+    POW1: lambda d: np.array([1.0, 0.0, 0.0]),
 }
 
 
@@ -44,6 +47,12 @@ def _in_cone_exact(t, u, alpha):
         if x < 0 or y < 0:
             return False
         return bool(x ** alpha * y ** (1 - alpha) >= abs(z))
+    # the fixed coordinate comes back from the scaled variables as beta_b (col / beta_b) / col,
+    # a few roundings from 1
+    if t == EXP1:
+        return bool(abs(u[1] - 1.0) <= 1e-14 and u[2] > 0 and u[0] <= math.log(u[2]))
+    if t == POW1:
+        return bool(abs(u[1] - 1.0) <= 1e-14 and u[0] >= 0 and u[0] ** alpha >= abs(u[2]))
     raise ValueError(t)
 
 

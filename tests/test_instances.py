@@ -45,13 +45,20 @@ def test_small_configs_structure_and_feasibility():
 
 
 def test_fisher_rows():
+    # eq. fisher-conic as counted after it: e + 4n stored coordinates and m + n equations with the
+    # middle coordinates fixed by the block type; one more row per buyer in the explicit-row form
     inst = I.small_config(3)
     f = inst["fisher"]
     nb, ng = f["n_buyers"], f["n_goods"]
-    assert inst["m"] == ng + 2 * nb
+    assert inst["m"] == ng + nb
     assert inst["n"] == f["edges"] + 4 * nb
+    assert set(inst["blk_type"][1:]) <= {I.CONE_EXP1, I.CONE_POW1}
     # every supply row and utility row is non-empty
     assert np.all(np.diff(inst["a_rowptr"]) > 0)
+    rw = I.fisher_market(n_buyers=200, n_goods=40, density=0.1, seed=2003, fixed_middle=False)
+    assert rw["m"] == ng + 2 * nb and rw["n"] == inst["n"]
+    assert set(rw["blk_type"][1:]) <= {I.CONE_EXP, I.CONE_POW}
+    assert np.all(np.diff(rw["a_rowptr"]) > 0)
 
 
 def test_portfolio_batch_structure():
