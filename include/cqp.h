@@ -62,6 +62,14 @@ extern "C" {
 #define CQP_CONE_EXP 4     /* cl{(r, s, t): s > 0, s exp(r/s) <= t}, d = 3 */
 #define CQP_CONE_POW 5     /* {(r, s, t): r, s >= 0, r^a s^(1-a) >= |t|}, d = 3, 0 < a < 1 */
 #define CQP_CONE_BOX 6     /* {x: x_lo <= x <= x_hi} coordinatewise (cqp_setup_general only), d >= 1 */
+/* Slices with the middle coordinate fixed at one (Sec. 5.4, eq. "fisher-conic" and the
+ * coordinate count after it: each buyer's (z, 1, t) is a stored 3-D block with no affine
+ * row for the one).  Convex sets, not cones; d = 3; the middle entry of x is always 1.
+ * Not available in batched mode or with rescaled_cones = 1 (CQP_ERR_UNSUPPORTED).  The KKT
+ * report adds inf over the slice of s'x to the dual objective and counts the part of the
+ * slack s outside that term's domain as dual residual (exp: s_r <= 0 <= s_t; pow: s_r >= 0). */
+#define CQP_CONE_EXP1 7    /* {(r, 1, t): exp(r) <= t} */
+#define CQP_CONE_POW1 8    /* {(r, 1, t): r >= 0, r^a >= |t|}, 0 < a < 1 */
 
 /* CSR matrix.  rowptr has nrows+1 entries (int64, rowptr[0] = 0), colind and
  * val have nnz entries; colind in [0, ncols).  nnz must be < 2^31. */
@@ -86,7 +94,7 @@ typedef struct {
 } cqp_qop;
 
 /* Cone blocks: nblocks contiguous slices (start, dim) that partition 0..n-1
- * in increasing order; alpha is used by CQP_CONE_POW only. */
+ * in increasing order; alpha is used by CQP_CONE_POW and CQP_CONE_POW1 only. */
 typedef struct {
   int64_t nblocks;
   const int32_t* type;
@@ -280,7 +288,8 @@ int cqp_spmv(int32_t precision, int64_t nrows, int64_t ncols, const int32_t* row
 
 /* out = Pi^M_K(r) blockwise (App. "cone-projections"): Euclidean when m is NULL,
  * otherwise the projection in the diagonal metric M = diag(m).  Cone blocks as
- * in cqp_setup but as device arrays.  r, m, out have n entries. */
+ * in cqp_setup but as device arrays (CQP_CONE_EXP1 / POW1 slices included; box
+ * blocks are not).  r, m, out have n entries. */
 int cqp_project(int32_t precision, int64_t n, const cqp_cones* K_device, const void* r, const void* m, void* out,
                 void* stream);
 
@@ -297,10 +306,14 @@ int cqp_project(int32_t precision, int64_t n, const cqp_cones* K_device, const v
  *   array (A->rowptr int64, A->colind int32, A->val double).  c (n), b (m),
  *   x (n), y (m): device arrays.  rep: host struct, filled on success.
  *   stream: cudaStream_t or NULL; the call synchronises it before returning.
+ * Cone blocks may include the slices CQP_CONE_EXP1 / POW1 (support terms as in
+ * cqp_kkt); box blocks are not accepted.
  * Errors: CQP_ERR_INVALID for NULL arguments, n < 1, n > CQP_KKT_STATIC_MAX_N,
- * rank > 64, or malformed A, P or cone blocks (the indices and block layout
- * are checked on the device; nothing is read out of bounds); CQP_ERR_CUDA;
- * CQP_ERR_NUMERICAL for a non-finite report.
+ * rank > 64, or malformed A, P or cone blocks (column indices, row pointers --
+ * rowptr[0] = 0, non-decreasing, at most nnz -- and the block layout are checked
+ * on the device; a bad row is skipped, so nothing is read out of bounds);
+ * CQP_ERR_UNSUPPORTED when its stream is being captured (the report is read back
+ * to the host); CQP_ERR_CUDA; CQP_ERR_NUMERICAL for a non-finite report.
  * The first call on each device looks up the array's device address, so make
  * it before any stream capture.  All calls on one device share the array:
  * calls that overlap on the GPU (two streams, two threads) race, so serialise

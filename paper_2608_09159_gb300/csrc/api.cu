@@ -288,7 +288,12 @@ struct Handle : HandleBase {
     for (int64_t j = 0; j < nb; ++j) {
       if (bs[j] != pos || bd[j] < 1) fail(CQP_ERR_INVALID, "cone blocks must partition 0..n-1 contiguously in order");
       const int t = bt[j];
-      if (t < 0 || t > 6) fail(CQP_ERR_INVALID, "unknown cone type");
+      if (t < 0 || t > 8) fail(CQP_ERR_INVALID, "unknown cone type");
+      const bool slice = t == CQP_CONE_EXP1 || t == CQP_CONE_POW1;
+      if (slice && B) fail(CQP_ERR_UNSUPPORTED, "slice blocks (EXP1/POW1) in a batch");
+      if (slice && o.rescaled_cones) fail(CQP_ERR_UNSUPPORTED, "slice blocks (EXP1/POW1) with rescaled_cones");
+      if (slice && bd[j] != 3) fail(CQP_ERR_INVALID, "EXP1/POW1 block dimension != 3");
+      if (t == CQP_CONE_POW1 && !(ba[j] > 0.0 && ba[j] < 1.0)) fail(CQP_ERR_INVALID, "power slice alpha outside (0,1)");
       if (t == CQP_CONE_BOX && (!G || !G->x_lo || !G->x_hi)) fail(CQP_ERR_INVALID, "box blocks need x_lo and x_hi");
       if (t == CQP_CONE_BOX && B) fail(CQP_ERR_UNSUPPORTED, "box blocks in a batch");
       if (t == CQP_CONE_SOC && bd[j] < 2) fail(CQP_ERR_INVALID, "SOC block dimension < 2");
@@ -303,10 +308,17 @@ struct Handle : HandleBase {
     if (B && o.rescaled_cones) fail(CQP_ERR_UNSUPPORTED, "rescaled-cone mode in a batch");
     std::vector<int64_t> soc_off{0}, rsoc_off{0};
     std::vector<double> pow_al;
+    std::vector<double> exp_sl, pow_sl;   // 1 for a slice block, 0 for a cone, in segment order
+    bool any_slice = false;
     int64_t cnt[6] = {0, 0, 0, 0, 0, 0};
-    // box blocks live in the free segment (their bounds are applied coordinatewise)
+    // box blocks live in the free segment (their bounds are applied coordinatewise); slices
+    // share the exponential / power segments with the cones and are told apart per block
     std::vector<int32_t> seg_of(nb);
-    for (int64_t j = 0; j < nb; ++j) seg_of[j] = bt[j] == CQP_CONE_BOX ? 0 : bt[j];
+    for (int64_t j = 0; j < nb; ++j) {
+      const int t = bt[j];
+      seg_of[j] = t == CQP_CONE_BOX ? 0 : (t == CQP_CONE_EXP1 ? 4 : (t == CQP_CONE_POW1 ? 5 : t));
+      if (t == CQP_CONE_EXP1 || t == CQP_CONE_POW1) any_slice = true;
+    }
     for (int64_t j = 0; j < nb; ++j) cnt[seg_of[j]] += bd[j];
     int64_t base[6];
     base[0] = 0;
@@ -321,6 +333,8 @@ struct Handle : HandleBase {
         if (t == CQP_CONE_SOC) soc_off.push_back(fill[t] + bd[j]);
         if (t == CQP_CONE_RSOC) rsoc_off.push_back(fill[t] + bd[j]);
         if (t == CQP_CONE_POW) pow_al.push_back(ba[j]);
+        if (t == CQP_CONE_EXP) exp_sl.push_back(bt[j] == CQP_CONE_EXP1 ? 1.0 : 0.0);
+        if (t == CQP_CONE_POW) pow_sl.push_back(bt[j] == CQP_CONE_POW1 ? 1.0 : 0.0);
         fill[t] += bd[j];
       }
     soc_off[0] = base[2];
@@ -392,6 +406,17 @@ struct Handle : HandleBase {
       fail(CQP_ERR_INVALID, "P must be n x n");
     if (k > 0 && (!Q->R || !Q->D)) fail(CQP_ERR_INVALID, "rank > 0 needs R and D");
     // ---- upload inputs (FP64) and validate ------------------------------------------
+    // host row pointers are checked before upload (rowptr[0] = 0, non-decreasing, last = nnz);
+    // device ones by k_validate_csr below, which reads only the caller's nnz entries
+    auto check_rowptr = [&](const int64_t* rp, int64_t rows, int64_t nz, const char* what) {
+      if (on_dev || !rp) return;
+      bool ok = rp[0] == 0 && rp[rows] == nz;
+      for (int64_t r = 0; r < rows && ok; ++r) ok = rp[r] <= rp[r + 1];
+      if (!ok) fail(CQP_ERR_INVALID, std::string(what) + ".rowptr must start at 0, not decrease and end at nnz");
+    };
+    if (!A->rowptr) fail(CQP_ERR_INVALID, "A.rowptr is required (nrows + 1 entries)");
+    check_rowptr(A->rowptr, m, nnz, "A");
+    if (has_p) check_rowptr(Q->P.rowptr, n, pnnz, "P");
     const int64_t* a_rp64 = (const int64_t*)upload(A->rowptr, (m + 1) * sizeof(int64_t));
     const int32_t* a_ci_in = (const int32_t*)upload(A->colind, nnz * sizeof(int32_t));
     const double* a_v_in = (const double*)upload(A->val, nnz * sizeof(double));
@@ -412,7 +437,7 @@ struct Handle : HandleBase {
     if (!c_d || (m > 0 && !b_d)) fail(CQP_ERR_INVALID, "c and b are required");
     int* bad = tmp.alloc<int>(1);
     CK(cudaMemsetAsync(bad, 0, sizeof(int), st));
-    count_launch(); cqp::k_validate_csr<<<cqp::grid_for(nnz + m), cqp::kSetupThreads, 0, st>>>(m, n, a_rp64, a_ci_in, a_v_in, bad);
+    count_launch(); cqp::k_validate_csr<<<cqp::grid_for(nnz + m), cqp::kSetupThreads, 0, st>>>(m, n, nnz, a_rp64, a_ci_in, a_v_in, bad);
     count_launch(); cqp::k_validate_vec<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, c_d, bad);
     if (m > 0 && !general) { count_launch(); cqp::k_validate_vec<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, b_d, bad); }
     if (m > 0 && general) { count_launch(); cqp::k_validate_bounds<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, b_d, bhi_d, nullptr, bad); }
@@ -427,7 +452,7 @@ struct Handle : HandleBase {
     }
     if (qd_in) { count_launch(); cqp::k_validate_vec<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, qd_in, bad); }
     if (R_in) { count_launch(); cqp::k_validate_vec<<<cqp::grid_for(k * n), cqp::kSetupThreads, 0, st>>>(k * n, R_in, bad); }
-    if (has_p) { count_launch(); cqp::k_validate_csr<<<cqp::grid_for(pnnz + n), cqp::kSetupThreads, 0, st>>>(n, n, p_rp64, p_ci_in, p_v_in, bad); }
+    if (has_p) { count_launch(); cqp::k_validate_csr<<<cqp::grid_for(pnnz + n), cqp::kSetupThreads, 0, st>>>(n, n, pnnz, p_rp64, p_ci_in, p_v_in, bad); }
     int hbad = 0;
     CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
     int64_t last_rp = 0;
@@ -668,6 +693,22 @@ struct Handle : HandleBase {
       palpha = mem.alloc<double>(pow_al.size());
       CK(cudaMemcpyAsync(palpha, pow_al.data(), pow_al.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     }
+    // slices: the fixed middle coordinate 1 of the caller's variables is col / beta_b in the
+    // scaled variable x~ = col x / beta_b (one factor per block: cone-preserving aggregation)
+    double* d_exp_fix = nullptr;
+    double* d_pow_fix = nullptr;
+    if (any_slice) {
+      if (n_exp > 0) {
+        d_exp_fix = mem.alloc<double>(n_exp);
+        CK(cudaMemcpyAsync(d_exp_fix, exp_sl.data(), n_exp * sizeof(double), cudaMemcpyHostToDevice, st));
+        count_launch(); cqp::k_slice_fix<<<cqp::grid_for(n_exp), cqp::kSetupThreads, 0, st>>>(n_exp, base[4], col, beta_b, d_exp_fix);
+      }
+      if (n_pow > 0) {
+        d_pow_fix = mem.alloc<double>(n_pow);
+        CK(cudaMemcpyAsync(d_pow_fix, pow_sl.data(), n_pow * sizeof(double), cudaMemcpyHostToDevice, st));
+        count_launch(); cqp::k_slice_fix<<<cqp::grid_for(n_pow), cqp::kSetupThreads, 0, st>>>(n_pow, base[5], col, beta_b, d_pow_fix);
+      }
+    }
     // Euclidean projections suffice when the diagonal Q vanishes on every cone coordinate
     double qcone = 0.0;
     {
@@ -766,6 +807,7 @@ struct Handle : HandleBase {
     P.n_free = cnt[0]; P.n_nonneg = cnt[1];
     P.n_soc = n_soc; P.soc_off = d_soc; P.n_rsoc = n_rsoc; P.rsoc_off = d_rsoc;
     P.n_exp = n_exp; P.exp_base = base[4]; P.n_pow = n_pow; P.pow_base = base[5]; P.pow_alpha = palpha;
+    P.exp_fix = d_exp_fix; P.pow_fix = d_pow_fix;
     if (has_p) P.qmode = cqp::kQSparse;
     else if (k > 0 || o.force_inner) P.qmode = cqp::kQLowRank;
     else P.qmode = cqp::kQDiag;

@@ -594,4 +594,123 @@ static __device__ __noinline__ void pow_proj(double rx, double ry, double rz, do
   out[2] = rz > 0.0 ? rho : -rho;
 }
 
+// --------------------------------------------------------------------------
+// Slices with the middle coordinate fixed (Sec. 5.4, eq. fisher-conic: each buyer's
+// (z, 1, t) block of the Fisher model stores the one and has no row for it):
+//   exponential X_f = {(r, f, t): f e^{r/f} <= t},
+//   power       X_f = {(x, f, z): x^a f^{1-a} >= |z|, x >= 0},   f > 0 fixed.
+// X_f = f X_1, and a projection in a diagonal metric commutes with the positive scalar
+// f, so the outer pair is divided by f, projected onto the 2-D set X_1 and scaled back.
+// Outside X_1 the projection is the zero of a monotone scalar function obtained from
+// the normal-cone condition M (z - u) = lambda * (outward normal); it is found in FP64
+// by Newton steps kept inside a sign-change bracket.  `guess` (optional) holds the
+// previous root of the block (exp: a, pow: x / |z|^{1/a}) and is updated.
+// --------------------------------------------------------------------------
+
+// exp: u = (a, 1, e^a) with phi(a) = m_r (a0 - a) - m_t (e^a - c0) e^a = 0; phi is
+// decreasing on the bracket [max(log c0, a0 - (m_t/m_r)(e^{a0} - c0) e^{a0}), a0],
+// positive at its left end and negative at its right end
+static __device__ __noinline__ void exp_slice_proj(double r0, double t0, double f, double mr, double mt, double* out,
+                                                  float* guess = nullptr) {
+  const double a0 = r0 / f, c0 = t0 / f;
+  out[1] = f;
+  const double ea0 = exp(a0);
+  if (ea0 <= c0) { out[0] = r0; out[2] = t0; return; }
+  auto phi = [&](double a, double* dphi) {
+    const double ea = exp(a);
+    *dphi = -mr - mt * ea * (2.0 * ea - c0);
+    return mr * (a0 - a) - mt * (ea - c0) * ea;
+  };
+  double lo = a0 - (mt / mr) * (ea0 - c0) * ea0;
+  if (c0 > 0.0) lo = fmax(lo, log(c0));
+  double hi = a0, d;
+  if (!isfinite(lo)) {
+    double step = 1.0;
+    lo = a0 - step;
+    while (phi(lo, &d) < 0.0 && step < 1e300) { step *= 2.0; lo = a0 - step; }
+  }
+  if (!isfinite(hi) || !(phi(hi, &d) < 0.0)) hi = a0;
+  double a = hi;
+  const double g0 = guess ? (double)*guess : NAN;
+  if (isfinite(g0) && g0 > lo && g0 < hi) {
+    if (phi(g0, &d) > 0.0) lo = g0; else hi = g0;
+    a = hi;
+  }
+  for (int it = 0; it < 200; ++it) {
+    const double v = phi(a, &d);
+    if (v == 0.0) break;
+    if (v > 0.0) lo = a; else hi = a;
+    double nx = (d != 0.0 && isfinite(d)) ? a - v / d : 0.5 * (lo + hi);
+    if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
+    const double step = fabs(nx - a);
+    a = nx;
+    if (step <= 4e-16 * fmax(1.0, fabs(a)) || (hi - lo) <= 4e-16 * fmax(1.0, fabs(a))) break;
+  }
+  if (guess) *guess = (float)a;
+  out[0] = f * a;
+  out[2] = f * exp(a);
+}
+
+// pow: u = (x, 1, sign(c0) x^a) with psi(x) = m_x (x - x0) - m_z (Z - x^a) a x^{a-1} = 0,
+// Z = |c0|; psi is increasing on (max(x0, 0), Z^{1/a}), negative at its left end (or
+// tending to -inf at 0+) and positive at its right end
+static __device__ __noinline__ void pow_slice_proj(double rx, double rz, double al, double f, double mx, double mz,
+                                                  double* out, float* guess = nullptr) {
+  const double x0 = rx / f, c0 = rz / f;
+  out[1] = f;
+  const double Z = fabs(c0);
+  if (x0 >= 0.0 && (Z == 0.0 || (x0 > 0.0 && al * log(x0) >= log(Z)))) { out[0] = rx; out[2] = rz; return; }
+  if (Z == 0.0) { out[0] = f * fmax(x0, 0.0); out[2] = 0.0; return; }
+  double lo = fmax(x0, 0.0), hi = exp(log(Z) / al);
+  auto psi = [&](double x, double* dpsi) {
+    const double lx = log(x);
+    const double xa = exp(al * lx), xam1 = exp((al - 1.0) * lx);
+    *dpsi = mx + mz * al * ((1.0 - al) * Z * xam1 / x + (2.0 * al - 1.0) * xam1 * xam1);
+    return mx * (x - x0) - mz * (Z - xa) * al * xam1;
+  };
+  double x = 0.5 * (lo + hi), d;
+  const double g0 = guess ? (double)*guess : NAN;
+  if (isfinite(g0) && g0 > 0.0 && g0 < 1.0 && g0 * hi > lo) x = g0 * hi;
+  for (int it = 0; it < 200; ++it) {
+    const double v = psi(x, &d);
+    if (v == 0.0) break;
+    if (v < 0.0) lo = x; else hi = x;
+    double nx = (d != 0.0 && isfinite(d)) ? x - v / d : 0.5 * (lo + hi);
+    if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
+    const double step = fabs(nx - x);
+    x = nx;
+    if (step <= 4e-16 * x || (hi - lo) <= 4e-16 * hi) break;
+  }
+  if (guess) *guess = (float)(x / exp(log(Z) / al));
+  out[0] = f * x;
+  out[2] = (c0 > 0.0 ? f : -f) * exp(al * log(x));
+}
+
+// Dual side of a slice block (unscaled, f = 1): the dual objective of the KKT report
+// gains inf_{x in X_1} sl'x, finite only when the slack sl lies in a closed cone D
+// (exp: sl_0 <= 0 <= sl_2, pow: sl_0 >= 0); res receives sl - Pi_D(sl), which counts as
+// dual residual, and the term is taken at Pi_D(sl):
+//   exp: sl_1 + sl_0 (log(-sl_0 / sl_2) - 1) (minimiser e^r = -sl_0 / sl_2), sl_1 at
+//        sl_0 = 0, -inf at sl_0 < 0 = sl_2;
+//   pow: sl_1 - (1-a)/a sl_0 x* with x* = (a |sl_2| / sl_0)^{1/(1-a)}, sl_1 at sl_2 = 0,
+//        -inf at sl_0 = 0 != sl_2.
+static __device__ double slice_support(bool is_pow, double al, const double* sl, double* res) {
+  res[0] = res[1] = res[2] = 0.0;
+  if (!is_pow) {
+    double a = sl[0], c = sl[2];
+    if (a > 0.0) { res[0] = a; a = 0.0; }
+    if (c < 0.0) { res[2] = c; c = 0.0; }
+    if (a == 0.0) return sl[1];
+    if (c == 0.0) return -INFINITY;
+    return sl[1] + a * (log(-a / c) - 1.0);
+  }
+  double p = sl[0];
+  const double w = fabs(sl[2]);
+  if (p < 0.0) { res[0] = p; p = 0.0; }
+  if (w == 0.0) return sl[1];
+  if (p == 0.0) return -INFINITY;
+  const double xs = exp(log(al * w / p) / (1.0 - al));
+  return sl[1] - (1.0 - al) / al * p * xs;
+}
+
 }  // namespace cqp

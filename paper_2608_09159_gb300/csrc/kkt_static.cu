@@ -51,7 +51,7 @@ constexpr int kThreads = 256;
 constexpr int kMaxGrid = 1024;
 constexpr int kRows = 3;   // ||Ax-b||^2, ||b||^2, b'y
 constexpr int kCols = 4;   // x'Qx, c'x, ||c||^2, ||Pi_K(-s)||^2 over free/nonneg coordinates
-constexpr int kCones = 1;  // ||Pi_K(-s)||^2 over SOC/RSOC/EXP/POW blocks
+constexpr int kCones = 2;  // ||Pi_K(-s)||^2 over SOC/RSOC/EXP/POW blocks (and slice residuals), slice support terms
 constexpr int64_t kMaxN = CQP_KKT_STATIC_MAX_N;
 constexpr int kMaxRank = 64;
 constexpr int64_t kOffRx = kMaxN;
@@ -68,8 +68,10 @@ __global__ void ks_clear(int64_t n, int k, double* __restrict__ s, double* __res
   if (t == 0) out[8] = 0.0;
 }
 
-// One warp per row of A: (Ax - b)_i, and A' y scattered into s by atomics.
-__global__ void __launch_bounds__(kThreads) ks_rows(int64_t m, int64_t n, const int64_t* __restrict__ rp,
+// One warp per row of A: (Ax - b)_i, and A' y scattered into s by atomics.  A row whose
+// pointers are out of order or outside [0, nnz] (or rowptr[0] != 0) is flagged and skipped,
+// so nothing past the caller's nnz entries is read.
+__global__ void __launch_bounds__(kThreads) ks_rows(int64_t m, int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
                                                     const int32_t* __restrict__ ci, const double* __restrict__ av,
                                                     const double* __restrict__ x, const double* __restrict__ y,
                                                     const double* __restrict__ b, double* __restrict__ s,
@@ -82,7 +84,7 @@ __global__ void __launch_bounds__(kThreads) ks_rows(int64_t m, int64_t n, const 
   double v[kRows] = {0.0, 0.0, 0.0};
   for (int64_t i = w0; i < m; i += nw) {
     const int64_t e0 = rp[i], e1 = rp[i + 1];
-    if (e0 < 0 || e1 < e0) {
+    if (e0 < 0 || e1 < e0 || e1 > nnz || (i == 0 && e0 != 0)) {
       if (lane == 0) out[8] = 1.0;
       continue;
     }
@@ -137,8 +139,9 @@ __device__ __forceinline__ int64_t block_of(int64_t j, int64_t nblocks, const in
 }
 
 // Per coordinate: (Qx)_j, s_j = (Qx)_j + c_j - (A'y)_j, objective sums, and the
-// dual residual of free / nonnegative coordinates.  Leaves -s in s.
-__global__ void __launch_bounds__(kThreads) ks_cols(int64_t n, const double* __restrict__ qd,
+// dual residual of free / nonnegative coordinates.  Leaves -s in s.  Rows of P are checked
+// like those of A (pointers within [0, pnnz], rowptr[0] = 0).
+__global__ void __launch_bounds__(kThreads) ks_cols(int64_t n, int64_t pnnz, const double* __restrict__ qd,
                                                     const int64_t* __restrict__ prp, const int32_t* __restrict__ pci,
                                                     const double* __restrict__ pv, int k, const double* __restrict__ R,
                                                     const double* __restrict__ D, const double* __restrict__ rx,
@@ -161,7 +164,7 @@ __global__ void __launch_bounds__(kThreads) ks_cols(int64_t n, const double* __r
     double qx = qd ? qd[j] * xj : 0.0;
     if (prp) {
       const int64_t e0 = prp[j], e1 = prp[j + 1];
-      if (e0 < 0 || e1 < e0) out[8] = 1.0;
+      if (e0 < 0 || e1 < e0 || e1 > pnnz || (j == 0 && e0 != 0)) out[8] = 1.0;
       else
         for (int64_t e = e0; e < e1; ++e) {
           const int32_t i = pci[e];
@@ -185,34 +188,43 @@ __global__ void __launch_bounds__(kThreads) ks_cols(int64_t n, const double* __r
 
 // One warp per cone block: check the block, project -s onto SOC / RSOC / EXP /
 // POW blocks in place (Euclidean projections of the cone library) and sum the
-// squared projection.
+// squared projection.  Slice blocks (EXP1 / POW1) add their support term to the dual
+// objective and the part of the slack outside its domain to the dual residual.
 __global__ void __launch_bounds__(kThreads) ks_cones(int64_t n, int64_t nblocks, const int32_t* __restrict__ type,
                                                      const int64_t* __restrict__ start, const int64_t* __restrict__ dim,
                                                      const double* __restrict__ alpha, double* __restrict__ s,
                                                      double* __restrict__ part, double* __restrict__ out) {
-  __shared__ double red[kThreads / 32];
-  __shared__ double tot[1];
+  __shared__ double red[kCones * (kThreads / 32)];
+  __shared__ double tot[kCones];
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  double v[1] = {0.0};
+  double v[kCones] = {0.0, 0.0};
   for (int64_t bk = w0; bk < nblocks; bk += nw) {
     const int32_t t = type[bk];
     const int64_t st = start[bk], d = dim[bk];
     const int64_t expect = bk == 0 ? 0 : start[bk - 1] + dim[bk - 1];
-    bool ok = st == expect && d >= 1 && st + d <= n && t >= CQP_CONE_FREE && t <= CQP_CONE_POW;
+    const bool slice = t == CQP_CONE_EXP1 || t == CQP_CONE_POW1;
+    bool ok = st == expect && d >= 1 && st + d <= n && ((t >= CQP_CONE_FREE && t <= CQP_CONE_POW) || slice);
     if (bk == nblocks - 1) ok = ok && st + d == n;
     if (t == CQP_CONE_SOC) ok = ok && d >= 2;
     if (t == CQP_CONE_RSOC) ok = ok && d >= 3;
-    if (t == CQP_CONE_EXP || t == CQP_CONE_POW) ok = ok && d == 3;
-    if (t == CQP_CONE_POW) ok = ok && alpha != nullptr && alpha[bk] > 0.0 && alpha[bk] < 1.0;
+    if (t == CQP_CONE_EXP || t == CQP_CONE_POW || slice) ok = ok && d == 3;
+    if (t == CQP_CONE_POW || t == CQP_CONE_POW1) ok = ok && alpha != nullptr && alpha[bk] > 0.0 && alpha[bk] < 1.0;
     if (!ok) {
       if (lane == 0) out[8] = 1.0;
       continue;
     }
     if (t == CQP_CONE_FREE || t == CQP_CONE_NONNEG) continue;  // done coordinate-wise in ks_cols
     double* z = s + st;
-    if (t == CQP_CONE_SOC) {
+    if (slice) {
+      if (lane == 0) {
+        const double sl[3] = {-z[0], -z[1], -z[2]};
+        double o[3];
+        v[1] += cqp::slice_support(t == CQP_CONE_POW1, t == CQP_CONE_POW1 ? alpha[bk] : 0.0, sl, o);
+        z[0] = o[0]; z[1] = o[1]; z[2] = o[2];
+      }
+    } else if (t == CQP_CONE_SOC) {
       cqp::warp_soc_euclid<double>(z, (int)d, lane);
     } else if (t == CQP_CONE_RSOC) {
       cqp::warp_rsoc_euclid<double>(z, (int)d, lane);
@@ -227,7 +239,7 @@ __global__ void __launch_bounds__(kThreads) ks_cones(int64_t n, int64_t nblocks,
     __syncwarp();
   }
   cqp::block_sum<kCones>(v, red, tot);
-  if (threadIdx.x == 0) part[blockIdx.x] = tot[0];
+  if (threadIdx.x < kCones) part[threadIdx.x * kMaxGrid + blockIdx.x] = tot[threadIdx.x];
 }
 
 // Fixed-order sums of the partials and the report (same definitions as cqp_kkt).
@@ -241,13 +253,16 @@ __global__ void ks_final(int g_rows, int g_cols, int g_cones, const double* __re
   for (int i = 0; i < kCols; ++i)
     for (int g = 0; g < g_cols; ++g) q[i] += pc[i * kMaxGrid + g];
   const double* pk = pc + kCols * kMaxGrid;
+  double sup = 0.0;
   for (int g = 0; g < g_cones; ++g) dc += pk[g];
+  for (int g = 0; g < g_cones; ++g) sup += pk[kMaxGrid + g];
   const double xqx = q[0], cx = q[1];
-  const double pobj = 0.5 * xqx + cx, dobj = r[2] - 0.5 * xqx;
+  const double pobj = 0.5 * xqx + cx, dobj = r[2] - 0.5 * xqx + sup;
   const double nrp = sqrt(r[0]), nrd = sqrt(q[3] + dc);
   out[0] = nrp / (1.0 + sqrt(r[1]));
   out[1] = nrd / (1.0 + sqrt(q[2]));
-  out[2] = fabs(pobj - dobj) / (1.0 + fabs(pobj) + fabs(dobj));
+  // an infinite slice support term (dual objective -inf) is the limit eps_g -> 1
+  out[2] = isfinite(dobj) ? fabs(pobj - dobj) / (1.0 + fabs(pobj) + fabs(dobj)) : 1.0;
   out[3] = fmax(out[0], fmax(out[1], out[2]));
   out[4] = pobj;
   out[5] = dobj;
@@ -299,8 +314,9 @@ extern "C" int cqp_kkt_static(const cqp_csr* A, const cqp_qop* Q, const double* 
   if (Q && (Q->rank < 0 || Q->rank > kMaxRank))
     return fail_with(CQP_ERR_INVALID, "cqp_kkt_static: rank must be in [0, 64]");
   if (k > 0 && (!Q->R || !Q->D)) return fail_with(CQP_ERR_INVALID, "cqp_kkt_static: R or D missing");
-  if (has_p && (!Q->P.colind || !Q->P.val || Q->P.nrows != n || Q->P.ncols != n))
-    return fail_with(CQP_ERR_INVALID, "cqp_kkt_static: P must be n x n");
+  if (has_p && (!Q->P.colind || !Q->P.val || Q->P.nrows != n || Q->P.ncols != n || Q->P.nnz < 0 ||
+                Q->P.nnz >= (1LL << 31)))
+    return fail_with(CQP_ERR_INVALID, "cqp_kkt_static: P must be n x n with 0 <= nnz < 2^31");
 
   int dev = 0;
   KS_CK(cudaGetDevice(&dev));
@@ -325,6 +341,14 @@ extern "C" int cqp_kkt_static(const cqp_csr* A, const cqp_qop* Q, const double* 
   double* part = base + kOffPart;
   double* out = base + kOffOut;
   cudaStream_t st = (cudaStream_t)stream;
+  {
+    // the report is read back to the host and the stream synchronised, which a stream
+    // capture does not allow
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    KS_CK(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone)
+      return fail_with(CQP_ERR_UNSUPPORTED, "cqp_kkt_static: called on a stream that is being captured");
+  }
 
   long long launches = 0;
   const int g_clear = grid_for(n, sms);
@@ -332,7 +356,7 @@ extern "C" int cqp_kkt_static(const cqp_csr* A, const cqp_qop* Q, const double* 
   ++launches;
   const int g_rows = m > 0 ? grid_for(m * 32, sms) : 0;
   if (g_rows > 0) {
-    ks_rows<<<g_rows, kThreads, 0, st>>>(m, n, A->rowptr, A->colind, A->val, x, y, b, s, part, out);
+    ks_rows<<<g_rows, kThreads, 0, st>>>(m, n, A->nnz, A->rowptr, A->colind, A->val, x, y, b, s, part, out);
     ++launches;
   }
   if (k > 0) {
@@ -340,7 +364,7 @@ extern "C" int cqp_kkt_static(const cqp_csr* A, const cqp_qop* Q, const double* 
     ++launches;
   }
   const int g_cols = grid_for(n, sms);
-  ks_cols<<<g_cols, kThreads, 0, st>>>(n, qd, has_p ? Q->P.rowptr : nullptr, has_p ? Q->P.colind : nullptr,
+  ks_cols<<<g_cols, kThreads, 0, st>>>(n, has_p ? Q->P.nnz : 0, qd, has_p ? Q->P.rowptr : nullptr, has_p ? Q->P.colind : nullptr,
                                        has_p ? Q->P.val : nullptr, k, k > 0 ? Q->R : nullptr, k > 0 ? Q->D : nullptr,
                                        rx, c, x, K->nblocks, K->type, K->start, s, part + kRows * kMaxGrid, out);
   const int g_cones = grid_for(K->nblocks * 32, sms);

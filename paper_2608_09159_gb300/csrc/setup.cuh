@@ -20,12 +20,15 @@ inline int grid_for(int64_t n, int threads = kSetupThreads, int cap = 152 * 32) 
 
 #define CQP_GRID_LOOP(i, n) for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
-// ---- validation: colind in range, values finite --------------------------------
-__global__ void k_validate_csr(int64_t nrows, int64_t ncols, const int64_t* rowptr, const int32_t* colind,
+// ---- validation: row pointers, colind in range, values finite -------------------
+// nnz is the caller's entry count (the length of colind and val), so a malformed
+// rowptr cannot make the check itself read past those arrays
+__global__ void k_validate_csr(int64_t nrows, int64_t ncols, int64_t nnz, const int64_t* rowptr, const int32_t* colind,
                                const double* val, int* bad) {
-  const int64_t nnz = rowptr[nrows];
-  CQP_GRID_LOOP(r, nrows) {
-    if (rowptr[r] > rowptr[r + 1]) atomicOr(bad, 1);
+  CQP_GRID_LOOP(r, nrows + 1) {
+    const int64_t p = rowptr[r];
+    if (p < 0 || p > nnz || (r < nrows && p > rowptr[r + 1])) atomicOr(bad, 1);
+    if ((r == 0 && p != 0) || (r == nrows && p != nnz)) atomicOr(bad, 1);
   }
   CQP_GRID_LOOP(k, nnz) {
     const int c = colind[k];
@@ -260,6 +263,12 @@ __global__ void k_sqrt_or_one(int64_t n, double* f) {
 }
 // cone blocks of the permuted layout: [b0, b1) coordinate ranges given by offsets
 // (SOC, RSOC) or by a base and width 3 (EXP, POW); max (mode 0) or RMS (mode 1)
+// slice blocks: fix[e] = flag[e] * col[base + 3 e + 1] / beta_b (flag 1 for a slice, 0 for a cone)
+__global__ void k_slice_fix(int64_t nblk, int64_t base, const double* col, double beta_b, double* fix) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < nblk && fix[e] != 0.0) fix[e] = col[base + 3 * e + 1] / beta_b;
+}
+
 __global__ void k_aggregate_blocks(int64_t nblk, const int64_t* off, int64_t base, int width, int mode, double* f) {
   CQP_GRID_LOOP(b, nblk) {
     const int64_t s = off ? off[b] : base + width * b;

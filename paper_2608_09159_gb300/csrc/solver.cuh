@@ -56,6 +56,9 @@ struct Prob {
   int64_t n_rsoc; const int64_t* rsoc_off;
   int64_t n_exp, exp_base;                            // exp cones at exp_base + 3 j
   int64_t n_pow, pow_base; const double* pow_alpha;
+  // slices (CQP_CONE_EXP1 / POW1): per exp / pow block the fixed middle coordinate in scaled
+  // variables, f~ = col / beta_b, or 0 for a full cone (null: no slices in the problem)
+  const double* exp_fix; const double* pow_fix;
   int qmode;
   int euclid_cones;                                   // diagonal mode with zero q on cone coordinates
   int tpr_a, tpr_t, tpr_p;                            // threads per row of A, A' and P
@@ -436,6 +439,13 @@ struct Solver {
         const int64_t s = P.exp_base + 3 * e;
         double o[3];
         float* gs = O.warm_roots ? W.root + P.n_soc + P.n_rsoc + e : nullptr;
+        const double fx = P.exp_fix ? P.exp_fix[e] : 0.0;
+        if (fx > 0.0) {   // slice {(r, f, t): f e^{r/f} <= t} (rejected with csc at setup)
+          exp_slice_proj((double)x[s], (double)x[s + 2], fx, (double)metric(kind, s, tau, itau),
+                         (double)metric(kind, s + 2, tau, itau), o, gs);
+          x[s] = T(o[0]); x[s + 1] = T(o[1]); x[s + 2] = T(o[2]);
+          continue;
+        }
         if (csc) {
           double sc3[3], z3[3], m3[3];
           for (int q = 0; q < 3; ++q) {
@@ -456,6 +466,14 @@ struct Solver {
       const int64_t e = own.p0 + (item - nexp);
       const int64_t s = P.pow_base + 3 * e;
       double o[3];
+      const double fx = P.pow_fix ? P.pow_fix[e] : 0.0;
+      if (fx > 0.0) {     // slice {(x, f, z): x^a f^{1-a} >= |z|, x >= 0}
+        pow_slice_proj((double)x[s], (double)x[s + 2], P.pow_alpha[e], fx, (double)metric(kind, s, tau, itau),
+                       (double)metric(kind, s + 2, tau, itau), o,
+                       O.warm_roots ? W.root + P.n_soc + P.n_rsoc + P.n_exp + e : nullptr);
+        x[s] = T(o[0]); x[s + 1] = T(o[1]); x[s + 2] = T(o[2]);
+        continue;
+      }
       if (csc) {
         double sc3[3], z3[3], m3[3];
         for (int q = 0; q < 3; ++q) {

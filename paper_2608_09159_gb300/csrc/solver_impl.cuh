@@ -284,7 +284,8 @@ __device__ bool Solver<T, Team, GEN>::kkt(const T* x, const T* y, bool have_rx) 
   apply_D(P, tk, wk);
   // K2: s~ = Q~x + c~ - A~'y on the owned coordinates, unscaled s = beta_c col s~,
   // ||Pi_K(-s)||^2 (free: K* = {0}; nonneg: max(-s, 0); cones below)
-  double v2[2] = {rd_rows, 0.0};   // dual residual^2, box term of the dual objective (scaled)
+  // dual residual^2, box term of the dual objective (scaled), slice term (unscaled)
+  double v2[3] = {rd_rows, 0.0, 0.0};
   for (int seg = 0; seg < 6; ++seg) {
     rows_loop_tpr<double>(
         own.g_t, P.t_rp, P.t_ci, P.t_v, own.x0[seg], own.x1[seg], [&](int j) { return y[j]; },
@@ -323,35 +324,48 @@ __device__ bool Solver<T, Team, GEN>::kkt(const T* x, const T* y, bool have_rx) 
         else warp_rsoc_euclid<double>(W.sd + s, d, lane);
       }
     }
+    // slices (unscaled middle coordinate 1): the support term joins the dual objective and
+    // the part of the slack outside its domain is left in W.sd as dual residual
     for (int64_t e = own.e0 + threadIdx.x; e < own.e1; e += blockDim.x) {
       double* z = W.sd + P.exp_base + 3 * e;
       double o[3];
-      exp_proj_euclid(z[0], z[1], z[2], o);
+      if (P.exp_fix && P.exp_fix[e] > 0.0) {
+        const double sl[3] = {-z[0], -z[1], -z[2]};
+        v2[2] += slice_support(false, 0.0, sl, o);
+      } else {
+        exp_proj_euclid(z[0], z[1], z[2], o);
+      }
       z[0] = o[0]; z[1] = o[1]; z[2] = o[2];
     }
     for (int64_t e = own.p0 + threadIdx.x; e < own.p1; e += blockDim.x) {
       double* z = W.sd + P.pow_base + 3 * e;
       double o[3];
-      pow_proj(z[0], z[1], z[2], P.pow_alpha[e], 1.0, 1.0, 1.0, o);
+      if (P.pow_fix && P.pow_fix[e] > 0.0) {
+        const double sl[3] = {-z[0], -z[1], -z[2]};
+        v2[2] += slice_support(true, P.pow_alpha[e], sl, o);
+      } else {
+        pow_proj(z[0], z[1], z[2], P.pow_alpha[e], 1.0, 1.0, 1.0, o);
+      }
       z[0] = o[0]; z[1] = o[1]; z[2] = o[2];
     }
     __syncthreads();
     for (int seg = 2; seg < 6; ++seg)
       for (int64_t i = own.x0[seg] + threadIdx.x; i < own.x1[seg]; i += blockDim.x) v2[0] += W.sd[i] * W.sd[i];
   }
-  publish<2>(v2, 0, false);
-  if (!sync_gather(2)) return false;
+  publish<3>(v2, 0, false);
+  if (!sync_gather(3)) return false;
   if (threadIdx.x == 0) {
     double rqr = 0.0;
     for (int l = 0; l < k; ++l) rqr += tk[l] * wk[l];
     const double xqx = xqdx + rqr + xpx;
     const double sc = P.beta_b * P.beta_c;
-    const double pobj = sc * (0.5 * xqx + cx), dobj = sc * (by + (GEN ? C.red[1] : 0.0) - 0.5 * xqx);
+    const double pobj = sc * (0.5 * xqx + cx), dobj = sc * (by + (GEN ? C.red[1] : 0.0) - 0.5 * xqx) + C.red[2];
     const double nrp = sqrt(rp2), nrd = sqrt(C.red[0]);
     double* K = C.s.kkt;
     K[0] = nrp / (1.0 + P.norm_b);
     K[1] = nrd / (1.0 + P.norm_c);
-    K[2] = fabs(pobj - dobj) / (1.0 + fabs(pobj) + fabs(dobj));
+    // an infinite slice support term (dual objective -inf) is the limit eps_g -> 1
+    K[2] = isfinite(dobj) ? fabs(pobj - dobj) / (1.0 + fabs(pobj) + fabs(dobj)) : 1.0;
     K[3] = fmax(K[0], fmax(K[1], K[2]));
     K[4] = pobj; K[5] = dobj; K[6] = nrp; K[7] = nrd;
     if (!isfinite(K[3])) C.s.err = kErrNumeric;

@@ -61,8 +61,8 @@ def test_spmv_parity(gpu, orc, rng, precision, tpr):
 def _blocks_sample(rng):
     blist = []
     for t, d in [(G.NONNEG, 7), (G.SOC, 5), (G.RSOC, 6), (G.EXP, 3), (G.POW, 3), (G.FREE, 4), (G.SOC, 2),
-                 (G.RSOC, 3), (G.SOC, 200), (G.RSOC, 150), (G.NONNEG, 1)]:
-        blist.append((t, d, float(rng.uniform(0.15, 0.85)) if t == G.POW else 0.0))
+                 (G.RSOC, 3), (G.SOC, 200), (G.RSOC, 150), (G.NONNEG, 1), (G.EXP1, 3), (G.POW1, 3)]:
+        blist.append((t, d, float(rng.uniform(0.15, 0.85)) if t in (G.POW, G.POW1) else 0.0))
     blist = blist * 40
     types = np.array([b[0] for b in blist], np.int32)
     dims = np.array([b[1] for b in blist], np.int64)
@@ -94,9 +94,7 @@ def test_projection_parity(gpu, orc, rng, precision, metric):
     for t, s, d, a in zip(types, starts, dims, alphas):
         ref = orc.proj_block(int(t), rr[s:s + d], alpha=a, m=None if mm is None else mm[s:s + d])
         scale = 1.0 + np.abs(rr[s:s + d]).max()
-        # root-finding cones in FP64: the oracle bisects to the last bit, the GPU stops its Newton
-        # iteration at 4e-16 relative steps; both are within a few ulps of the root
-        lim = tol * scale * (10 if (precision and t in (G.EXP, G.POW)) else 1)
+        lim = tol * scale
         assert np.abs(got[s:s + d] - ref).max() <= lim, (int(t), int(d), rr[s:s + d][:6], got[s:s + d][:6], ref[:6])
 
 
@@ -106,7 +104,12 @@ def test_projection_edge_cases(gpu, orc):
     cases = [(G.SOC, [0.3, 0.4, 1.0]), (G.SOC, [0.3, 0.4, -1.0]), (G.SOC, [3.0, 4.0, 5.0]), (G.SOC, [0.0, 0.0, 0.0]),
              (G.EXP, [0.0, 1.0, 2.0]), (G.EXP, [1.0, -1.0, -3.0]), (G.EXP, [-1.0, -2.0, 3.0]),
              (G.EXP, [-0.985, 0.00136, -1.83]), (G.POW, [-1.0, 2.0, 0.0]), (G.POW, [1.0, 1.0, 1.0]),
-             (G.RSOC, [1.0, 2.0, -2.0]), (G.RSOC, [0.0, 0.0, 1.0, -1.0]), (G.NONNEG, [-1.0, 0.0, 2.0])]
+             (G.RSOC, [1.0, 2.0, -2.0]), (G.RSOC, [0.0, 0.0, 1.0, -1.0]), (G.NONNEG, [-1.0, 0.0, 2.0]),
+             # slices: inside, c0 <= 0, large r0, z0 = 0, x0 < 0 with z0 != 0, on the boundary
+             (G.EXP1, [0.0, 5.0, 2.0]), (G.EXP1, [1.0, 0.0, -3.0]), (G.EXP1, [30.0, 1.0, 0.5]),
+             (G.EXP1, [-40.0, 1.0, -1e-3]), (G.EXP1, [0.5, 1.0, np.exp(0.5)]),
+             (G.POW1, [-1.0, 2.0, 0.0]), (G.POW1, [-2.0, 1.0, 0.3]), (G.POW1, [4.0, 1.0, 4.0 ** 0.4]),
+             (G.POW1, [1e-3, 1.0, -5.0]), (G.POW1, [50.0, 0.0, 1e-4])]
     for precision in (0, 1):
         dt = torch.float64 if precision else torch.float32
         for t, r in cases:
