@@ -17,9 +17,19 @@ host->device copies of the inputs and the device->host copy of (x, y) inside
 the timed region.  The FP64 plain-PDHG run (same code, precision = all FP64,
 cold start) is timed once as the comparison the metric names.
 
+The line also carries:
+  roofline      algorithmic bytes per solve (the per-unit figures of the scope table: the two
+                sparse products per outer iteration, R, R' or P and eight n-vectors per inner
+                step) over the solver kernel's CUDA-event time, against the measured HBM peak;
+  large         the HBM-bound workload: the large sparse QP (n = 2e8, m = 5e7, 1e9 nnz,
+                generated in device memory), one setup + solve to 1e-4 with its own roofline;
+  cpu_baseline  the FP64 oracle solving the same instance to 1e-4 on the host: the OpenMP
+                build on every core (value) and the single-threaded build (single_thread).
+
 With --gpus N under torchrun each rank solves its own instance (seed + rank):
 replicas, no collectives; rank 0 prints the max-over-ranks time.
---impl reference times the FP64 CPU oracle on the host cores instead.
+--impl reference times the FP64 CPU oracle (OpenMP build, every host core, one full solve
+to 1e-4 per step) instead.
 
 Other workloads (not the default line):
   --workload portfolio  4,096 uneven portfolio QPs solved in one batched launch
@@ -113,23 +123,27 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def algorithmic_bytes(inst, res, esize=4, isize=4):
-    """Bytes the method must move per solve (each array element touched once per pass),
-    from the iteration counts the solve reports:
-      A'y pass    : A' values + indices + row pointers, h_y gathered once, h_x read, v written
-      inner step  : u, v, c, q, diag(Q) read, u_next written, R (k x n) read
-      dual pass   : A values + indices + row pointers, w_x and h_x gathered once, h_y, b, a_y read,
-                    w_y, h_y written; w_x, h_x, a_x, w_x_prev read, w_x copy and h_x written
-      KKT check   : two products with A / A' and ten vectors, every check_every iterations."""
-    n, m = inst["n"], inst["m"]
+def algorithmic_bytes(n, m, nnz, iters, inner_total, k=0, pnnz=0, esize=4, isize=4, check_every=64):
+    """Bytes the method must move per solve, with the per-unit figures of the scope table's
+    measurement section (each array element counted once per pass):
+      per outer iteration, the two sparse products A'y (n rows) and A x (m rows):
+          values + indices (nnz (esize + isize)) + row pointers + gathered operand + output;
+      per inner BB step: R and R' (2 k n esize), the rows of a sparse P (pnnz (esize + isize) plus
+          row pointers) and eight n-vectors;
+      per KKT check (every check_every iterations): the same two sparse products again."""
+    spmv_at = nnz * (esize + isize) + (n + 1) * isize + m * esize + n * esize
+    spmv_a = nnz * (esize + isize) + (m + 1) * isize + n * esize + m * esize
+    per_iter = spmv_at + spmv_a
+    per_inner = 2 * k * n * esize + (pnnz * (esize + isize) + (n + 1) * isize if pnnz else 0) + 8 * n * esize
+    checks = iters // check_every + 1
+    return iters * per_iter + inner_total * per_inner + checks * per_iter
+
+
+def inst_bytes(inst, res, esize=4):
     nnz = int(inst["a_rowptr"][-1])
     k = 0 if inst.get("q_R") is None else int(inst["q_R"].shape[0])
-    aty = nnz * (esize + isize) + (n + 1) * isize + m * esize + 2 * n * esize
-    inner = (6 + k) * n * esize
-    dual = nnz * (esize + isize) + (m + 1) * isize + 2 * n * esize + 5 * m * esize + 6 * n * esize
-    kkt = 2 * nnz * (esize + isize) + (n + m + 2) * isize + 10 * (n + m) * esize
-    checks = res["iters"] // 64 + 1
-    return res["iters"] * (aty + dual) + res["inner_total"] * inner + checks * kkt
+    pnnz = 0 if inst.get("p_rowptr") is None else int(inst["p_rowptr"][-1])
+    return algorithmic_bytes(inst["n"], inst["m"], nnz, res["iters"], res["inner_total"], k, pnnz, esize)
 
 
 SOLVER_SOURCES = ("common.cuh", "cones.cuh", "solver.cuh", "solver_impl.cuh", "kernels.inc", "solver_f32.cu")
@@ -145,10 +159,10 @@ def _source_hash():
     return h.hexdigest()[:16]
 
 
-def _ncu_traffic():
-    """DRAM bytes per solve of the solver kernel from the committed ncu summary, if it was
-    captured on the current kernel sources."""
-    p = os.path.join(ROOT, "profiles", "pdhg_kernel_socp_mix.json")
+def _ncu_traffic(workload="socp_mix"):
+    """DRAM bytes per solve of the solver kernel from the committed ncu record of the workload,
+    if it was captured on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "pdhg_kernel_%s.json" % workload)
     try:
         with open(p) as f:
             d = json.load(f)
@@ -300,7 +314,7 @@ def run_ours(args, rank, world):
                 "rel_kkt": r64["kkt"]["rel_kkt"], "rc": r64["rc"]}
 
     peaks, src = _peaks()
-    alg = algorithmic_bytes(inst, res)
+    alg = inst_bytes(inst, res)
     kern_s = res["kernel_ms"] / 1e3
     achieved = alg / kern_s / 1e9 if kern_s > 0 else None
     traffic = _ncu_traffic()
@@ -311,7 +325,13 @@ def run_ours(args, rank, world):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(inst, fp64["iters"] if fp64 else res["iters"], args)
+        cpu = cpu_baseline(inst, args)
+    # the HBM half of the metric: the large sparse QP (one setup + solve, no warm-up) on rank 0
+    large = None
+    if rank == 0 and world == 1 and not args.no_large and not args.small:
+        del dinst
+        torch.cuda.empty_cache()
+        large = large_solve(args, 1, 0, flush)
 
     line = {
         "metric": METRIC, "value": step_s, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -322,6 +342,7 @@ def run_ours(args, rank, world):
         "e2e": {"value": statistics.mean(e2e_times), "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "roofline": roof,
+        "large": large,
         "cpu_baseline": cpu,
         "fp64_plain_pdhg": fp64,
         "speedup_vs_fp64": (fp64["time_s"] / step_s) if fp64 else None,
@@ -414,18 +435,22 @@ def run_portfolio(args):
     print(json.dumps(line), flush=True)
 
 
-def run_large(args):
+LARGE_DESC = ("large_qp: n=%d nonneg, m=%d, 20 nnz per row (about 5 per column) N(0,1), Q = diag(U[0,1]) + "
+              "Laplacian of a perfect matching (|N(0,1)| weights), c ~ N(0,1), b = A|N(0,1)|, seed 1005")
+
+
+def large_solve(args, steps, warmup, flush):
+    """The large sparse QP generated in device memory; each step is cqp_setup + cqp_solve to
+    relative KKT <= 1e-4 from the device-resident FP64 inputs (FP32 iterates)."""
     import torch
 
     import paper_2608_09159_gb300 as g
     from instances import gpu as G
-    g.build()
-    g.lib()
     n = int(args.large_n)
     n -= n % 2
     m = n // 4
     inst = G.large_qp_device(n=n, m=m, seed=1005)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
 
     def step():
         s = g.Solver(inst, device=True, precision=0, tol=1e-4, max_iter=1000000, time_limit_s=900.0)
@@ -435,29 +460,45 @@ def run_large(args):
 
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
-    times, (x, y, res), launches = _timed(step, args.steps, args.warmup, flush, g.cqp_kernel_launches)
+    times, (x, y, res), launches = _timed(step, steps, warmup, flush, g.cqp_kernel_launches)
+    clk = clocks.stop()
     nnz, pnnz = m * 20, 2 * n
-    # algorithmic bytes (FP32 values, int32 indices): A' and A passes with their vectors
-    # per outer iteration, P and 9 n-vectors per inner step
-    per_it = 2 * (nnz * 8 + (n + m) * 4) + 8 * n * 4 + 6 * m * 4
-    per_inner = pnnz * 8 + n * 4 + 8 * n * 4
-    alg = res["iters"] * per_it + res["inner_total"] * per_inner
+    alg = algorithmic_bytes(n, m, nnz, res["iters"], res["inner_total"], 0, pnnz)
     peaks, src = _peaks()
-    achieved = alg / (res["kernel_ms"] / 1e3) / 1e9
-    line = {"metric": "time to 1e-4 rel KKT", "value": statistics.mean(times), "unit": "s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(times) * 1e3,
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic (Philox-seeded, generated in device memory)",
-            "config": {"workload": "large_qp: n=%d nonneg, m=%d, 20 nnz per row, Q = diag(U[0,1]) + matching "
-                                   "Laplacian, seed 1005" % (n, m), "n": n, "m": m, "nnz": nnz, "pnnz": pnnz,
-                       "inputs": "device-resident FP64"},
+    kern_s = res["kernel_ms"] / 1e3
+    achieved = alg / kern_s / 1e9
+    del inst, x, y
+    torch.cuda.empty_cache()
+    return {"value": statistics.mean(times), "unit": "s", "steps": steps, "warmup": warmup,
+            "workload": LARGE_DESC % (n, m), "n": n, "m": m, "nnz": nnz, "pnnz": pnnz,
+            "inputs": "device-resident FP64, generated in device memory (Philox, index-addressed)",
             "gpu_launches": launches,
             "solve": {"rc": res["rc"], "iters": res["iters"], "inner_total": res["inner_total"],
-                      "rel_kkt": res["kkt"]["rel_kkt"], "setup_ms": res["setup_ms"], "kernel_ms": res["kernel_ms"]},
+                      "restarts": res["restarts"], "rel_kkt": res["kkt"]["rel_kkt"], "setup_ms": res["setup_ms"],
+                      "kernel_ms": res["kernel_ms"], "step_times_s": times},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
-                         "kernel": "pdhg_grid_kernel<float, false>", "algorithmic_bytes_per_solve": alg},
-            "clocks": clocks.stop()}
+                         "frac": achieved / peaks["hbm_gbs"], "traffic": _ncu_traffic("large"),
+                         "peak_source": src, "kernel": "pdhg_grid_kernel<float, false>",
+                         "algorithmic_bytes_per_solve": alg, "kernel_s_per_solve": kern_s},
+            "clocks": clk}
+
+
+def run_large(args):
+    import torch
+
+    import paper_2608_09159_gb300 as g
+    g.build()
+    g.lib()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    rec = large_solve(args, args.steps, args.warmup, flush)
+    line = {"metric": "time to 1e-4 rel KKT", "value": rec["value"], "unit": "s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": rec["value"] * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (Philox-seeded, generated in device memory)",
+            "config": {"workload": rec["workload"], "n": rec["n"], "m": rec["m"], "nnz": rec["nnz"],
+                       "pnnz": rec["pnnz"], "inputs": rec["inputs"]},
+            "gpu_launches": rec["gpu_launches"], "solve": rec["solve"], "roofline": rec["roofline"],
+            "clocks": rec["clocks"]}
     print(json.dumps(line), flush=True)
 
 
@@ -499,7 +540,7 @@ def run_frontend(args):
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
     times, (x, y, res), launches = _timed(step, args.steps, args.warmup, flush, g.cqp_kernel_launches)
-    alg = algorithmic_bytes(inst, res)
+    alg = inst_bytes(inst, res)
     peaks, src = _peaks()
     achieved = alg / (res["kernel_ms"] / 1e3) / 1e9
     kkt_check = None
@@ -577,44 +618,64 @@ def run_gemm(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(inst, iters_to_tol, args):
-    """The FP64 oracle (single thread) on a bounded sample of the same workload: setup plus
-    `sample_iters` outer iterations, extrapolated to the iteration count the FP64 method needs
-    on this instance (the FP64 trajectory of the GPU code, which follows the oracle's)."""
+def _oracle_solve_timed(inst, threads):
+    """One FP64 oracle solve of the instance to relative KKT <= 1e-4 (threads = 0: the
+    single-threaded build, else the OpenMP build with that many threads)."""
+    import oracle
+    used = oracle.use_openmp(threads > 0, threads)
+    try:
+        t0 = time.perf_counter()
+        _, _, info = oracle.solve(inst, tol=1e-4, max_iter=200000)
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.use_openmp(False)
+    return dt, used, info
+
+
+def cpu_baseline(inst, args):
+    """The FP64 oracle, as it stands, solving the same instance to relative KKT <= 1e-4 on the
+    host cores: once with the single-threaded build and once with the OpenMP build of the same
+    source on every core (the two builds return identical iterates)."""
     import oracle
     oracle.build()
-    t0 = time.perf_counter()
-    oracle.solve(inst, max_iter=1)
-    t_setup = time.perf_counter() - t0
-    M = args.cpu_iters
-    t0 = time.perf_counter()
-    oracle.solve(inst, max_iter=M)
-    t_m = time.perf_counter() - t0
-    per_iter = max(t_m - t_setup, 0.0) / max(M - 1, 1)
-    est = t_setup + per_iter * iters_to_tol
-    return {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": "setup + %d outer iterations of the full instance (%.1f s); time to 1e-4 extrapolated to %d "
-                      "iterations at %.3f s/iteration" % (M, t_m, iters_to_tol, per_iter),
-            "s_per_iter": per_iter, "setup_s": t_setup}
+    oracle.build(omp=True)
+    nproc = os.cpu_count() or 1
+    t_all, used, info = _oracle_solve_timed(inst, nproc)
+    out = {"value": t_all, "unit": "s", "cores": used, "kind": "oracle", "nproc": nproc,
+           "sample": "one full solve of the same instance to rel-KKT <= 1e-4 (%d iterations, %d inner steps, "
+                     "rel-KKT %.2e), OpenMP build on %d threads" % (info["iters"], info["inner_total"],
+                                                                     info["kkt"]["rel_kkt"], used),
+           "iters": info["iters"]}
+    if not args.cpu_all_only:
+        t1, _, info1 = _oracle_solve_timed(inst, 0)
+        out["single_thread"] = {"value": t1, "unit": "s", "cores": 1, "iters": info1["iters"]}
+    return out
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 CPU oracle on the bench's instance, each step one full solve to
+    relative KKT <= 1e-4 with the OpenMP build on every host core."""
     if rank != 0:
         return
-    import instances  # noqa: F401
+    import oracle
+    oracle.build(omp=True)
     inst = make_instance(args, 0)
-    vals = []
-    for _ in range(args.warmup + args.steps):
-        cb = cpu_baseline(inst, args.ref_iters, args)
-        vals.append(cb)
-    tim = vals[args.warmup:] or vals
-    v = statistics.mean(c["value"] for c in tim)
+    nproc = os.cpu_count() or 1
+    vals, used, info = [], 1, None
+    for i in range(args.warmup + args.steps):
+        t, used, info = _oracle_solve_timed(inst, nproc)
+        if i >= args.warmup:
+            vals.append(t)
+    v = statistics.mean(vals)
+    sample = ("each step one full FP64 oracle solve of the bench instance to rel-KKT <= 1e-4 (%d iterations), "
+              "OpenMP build on %d threads of %d host cores" % (info["iters"], used, nproc))
     line = {"metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic (Philox-seeded)", "impl": "reference",
             "config": {"workload": WORKLOAD, "tol": 1e-4},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": tim[-1]["sample"], "value": v, "unit": "s"},
-            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "cpu_baseline": {"kind": "oracle", "cores": used, "sample": sample, "value": v, "unit": "s"},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "step_times_s": vals}
     print(json.dumps(line), flush=True)
 
 
@@ -625,10 +686,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=1)
-    ap.add_argument("--cpu-iters", type=int, default=20)
-    ap.add_argument("--ref-iters", type=int, default=256,
-                    help="outer iterations the FP64 method needs on the default workload (reference arm)")
+    ap.add_argument("--cpu-all-only", action="store_true", help="cpu_baseline: skip the single-thread solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="leave the large sparse QP out of the default line")
     ap.add_argument("--no-oracle", action="store_true")
     ap.add_argument("--small", action="store_true", help="10x smaller instance (quick checks)")
     ap.add_argument("--workload", default="socp", choices=["socp", "portfolio", "large", "gemm", "lasso", "qcqp"])

@@ -136,10 +136,13 @@ typedef struct {
   double step_factor;       /* 0.998 */
   /* execution */
   int32_t input_on_device;  /* 1: every input pointer of cqp_setup is a device pointer */
-  int32_t team;             /* 0 auto, 1 whole-GPU cooperative kernel, 2 one thread block */
+  int32_t team;             /* 0 auto (n + m > 4096: 1, else 3 where a cluster fits, else 2), 1 whole-GPU
+                               cooperative kernel, 2 one thread block, 3 one thread-block cluster of up to
+                               16 CTAs (cluster barriers, distributed-shared-memory reductions) */
   int32_t threads;          /* threads per block, 0 = auto */
   int32_t blocks_per_sm;    /* 0 = auto (cooperative team only) */
-  int32_t tpr_a, tpr_at;    /* threads per CSR row for A and A', 0 = autotuned (timed per matrix shape, cached) */
+  int32_t tpr_a, tpr_at;    /* threads per CSR row for A and A' (1..32), -1 = one lane per row with four rows
+                               in flight, 0 = autotuned among these (timed per matrix shape, cached) */
   int32_t launch_iters;     /* outer iterations per kernel launch, 0 = auto */
   int32_t profile;          /* 1: record per-phase device time in cqp_result.phase_ms */
   int32_t warm_roots;       /* 1: start each cone block's root-finding from its previous root (default 1) */
@@ -281,7 +284,9 @@ int cqp_solve_batch(cqp_handle* h, const double* x0, const double* y0, double* x
  * bandwidth measurements).  `precision` selects FP32 (0) or FP64 (1) data:
  * val/x/y are float* or double* accordingly.  rowptr/colind are int32. ---- */
 
-/* y = A x with the CSR kernel of the solver (threads_per_row 0 = autotuned).
+/* y = A x with the CSR kernel of the solver (threads_per_row: 1, 2, 4, 8, 16 or 32 lanes per
+ * row; 0 = chosen from the mean row length; -1 = one lane per row with four rows in flight
+ * per lane, the solver's variant for short rows whose latency chains would otherwise bind).
  * Returns CQP_ERR_INVALID for bad sizes. */
 int cqp_spmv(int32_t precision, int64_t nrows, int64_t ncols, const int32_t* rowptr, const int32_t* colind,
              const void* val, const void* x, void* y, int32_t threads_per_row, void* stream);

@@ -220,7 +220,7 @@ struct Handle : HandleBase {
   int power_its = 0;                 // Lanczos steps of the norm estimate taken by setup
   long long setup_launches = 0;
   int64_t n_roots = 0;
-  bool grid = false;
+  int team = cqp::kTeamCta;          // how the solver's blocks cooperate (launch.h TeamKind)
   int blocks = 1, threads = 512;
   // batched mode (cqp_setup_batch): per-instance ranges, factors and step sizes
   bool batched = false;
@@ -725,7 +725,7 @@ struct Handle : HandleBase {
       double* zp = tmp.alloc<double>(n);   // previous Lanczos vector (zero at the start)
       CK(cudaMemsetAsync(zp, 0, n * sizeof(double), st));
       double* w = tmp.alloc<double>(std::max<int64_t>(m, 1));
-      double* ppart = tmp.alloc<double>(2 * (int64_t)nsm);
+      double* ppart = tmp.alloc<double>(2 * (int64_t)cqp::kMaxSlots * nsm);   // the grid team's two buffers
       unsigned* pcount = tmp.alloc<unsigned>(1);
       int* perr = tmp.alloc<int>(1);
       double* pout = tmp.alloc<double>(2);
@@ -837,8 +837,12 @@ struct Handle : HandleBase {
         // width within 5% of the fastest is taken: inside the solver narrow groups measured
         // better than the standalone timing shows (Lasso model: 1 lane 230 ms, tuned 2 lanes
         // 294 ms of kernel time; SOCP mix: 1 lane within 0.4% of the best)
-        float ms_of[5];
-        for (int t = 1, ti = 0; t <= 16; t <<= 1, ++ti) {
+        // candidate widths in order of preference: one lane per row, one lane with four rows in
+        // flight (cqp::kRowsBatched), then 2..16 lanes
+        const int cand[6] = {1, cqp::kRowsBatched, 2, 4, 8, 16};
+        float ms_of[6];
+        for (int ti = 0; ti < 6; ++ti) {
+          const int t = cand[ti];
           count_launch();
           CK(cqp::launch_spmv<T>(rows, rp, ci, v, xs, ys, t, st, nsm));
           float tot = 1e30f;
@@ -855,18 +859,18 @@ struct Handle : HandleBase {
           ms_of[ti] = tot;
         }
         float best_ms = 1e30f;
-        for (int ti = 0; ti < 5; ++ti) best_ms = std::min(best_ms, ms_of[ti]);
+        for (int ti = 0; ti < 6; ++ti) best_ms = std::min(best_ms, ms_of[ti]);
         int best = 16;
-        for (int ti = 4; ti >= 0; --ti)
-          if (ms_of[ti] <= 1.05f * best_ms) best = 1 << ti;
+        for (int ti = 5; ti >= 0; --ti)
+          if (ms_of[ti] <= 1.05f * best_ms) best = cand[ti];
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_tune_cache[key] = best;
         return best;
       };
-      P.tpr_a = o.tpr_a > 0 ? o.tpr_a : tune(m, nnz, a_rp, a_ci, a_v);
-      P.tpr_t = o.tpr_at > 0 ? o.tpr_at : tune(n, nnz, t_rp, t_ci, t_v);
+      P.tpr_a = o.tpr_a > 0 ? o.tpr_a : (o.tpr_a == -1 ? cqp::kRowsBatched : tune(m, nnz, a_rp, a_ci, a_v));
+      P.tpr_t = o.tpr_at > 0 ? o.tpr_at : (o.tpr_at == -1 ? cqp::kRowsBatched : tune(n, nnz, t_rp, t_ci, t_v));
       P.tpr_p = has_p ? tune(n, pnnz, p_rp, p_ci, pT) : 1;
     }
     // ---- work buffers and state -------------------------------------------------------------
@@ -888,21 +892,36 @@ struct Handle : HandleBase {
     // which hides more latency than one wide block per instance (measured on GB300:
     // 4,096 portfolio QPs 3.70 s at 512 threads, 2.34 s at 128, 2.22 s at 64)
     threads = o.threads > 0 ? o.threads : (batched ? 64 : 512);
+    // problems with more than 4096 coordinates and rows spread over the whole GPU; smaller
+    // ones run on one thread-block cluster (up to 16 SMs, cluster barriers and
+    // distributed-shared-memory reductions), or on one block where no cluster fits
     const int64_t size = n + m;
-    grid = !batched && (o.team == 1 || (o.team == 0 && size > 4096));
+    if (!batched) {
+      if (o.team == 1 || (o.team == 0 && size > 4096)) team = cqp::kTeamGrid;
+      else if (o.team == 2) team = cqp::kTeamCta;
+      else team = cqp::kTeamCluster;
+    }
     if (batched) {
       const int per = cqp::pdhg_blocks_per_sm<T>(threads);
       if (per < 1) fail(CQP_ERR_UNSUPPORTED, "solver kernel does not fit on an SM with this block size");
       blocks = (int)std::min<int64_t>((int64_t)nsm * per, bcount);
-    } else if (grid) {
+    } else if (team == cqp::kTeamGrid) {
       const int per = cqp::pdhg_blocks_per_sm<T>(threads);
       if (per < 1) fail(CQP_ERR_UNSUPPORTED, "solver kernel does not fit on an SM with this block size");
       const int want = o.blocks_per_sm > 0 ? std::min(o.blocks_per_sm, per) : 1;
       blocks = nsm * want;
+    } else if (team == cqp::kTeamCluster) {
+      blocks = cqp::pdhg_cluster_size<T>(threads);
+      if (blocks < 2) {
+        if (o.team == 3) fail(CQP_ERR_UNSUPPORTED, "no thread-block cluster of the solver kernel fits this device");
+        team = cqp::kTeamCta;
+        blocks = 1;
+      }
     } else {
       blocks = 1;
     }
-    W.part = mem.alloc<double>((int64_t)cqp::kMaxSlots * blocks);
+    // two buffers of block partials (the grid team alternates between them)
+    W.part = mem.alloc<double>(2 * (int64_t)cqp::kMaxSlots * blocks);
     S = mem.alloc<cqp::State>(batched ? bcount : 1);
     if (batched) {
       // largest instances first (coordinates + rows), so the tail of the queue is short
@@ -974,7 +993,7 @@ struct Handle : HandleBase {
       count_launch(); k_state_set_th<<<1, 32, 0, st>>>(S, t, (int)k);
     }
     CK(cudaMemsetAsync(dev_err, 0, sizeof(int), st));
-    long long per_launch = opt.launch_iters > 0 ? opt.launch_iters : (long long)O.check_every * (grid ? 4 : 16);
+    long long per_launch = opt.launch_iters > 0 ? opt.launch_iters : (long long)O.check_every * (team == cqp::kTeamGrid ? 4 : 16);
     int launches = 0;
     int status = CQP_ITER_LIMIT;
     double kernel_ms = 0.0;
@@ -986,7 +1005,7 @@ struct Handle : HandleBase {
       CK(cudaMemsetAsync(bar_count, 0, sizeof(unsigned), st));
       CK(cudaEventRecord(ev0, st));
       count_launch();
-      CK(cqp::launch_pdhg<T>(args(per_launch), grid, blocks, threads, st));
+      CK(cqp::launch_pdhg<T>(args(per_launch), team, blocks, threads, st));
       CK(cudaEventRecord(ev1, st));
       ++launches;
       CK(cudaMemcpyAsync(&back, S, sizeof(back), cudaMemcpyDeviceToHost, st));
@@ -1158,7 +1177,7 @@ struct Handle : HandleBase {
     CK(cudaMemsetAsync(bar_count, 0, sizeof(unsigned), st));
     CK(cudaMemsetAsync(dev_err, 0, sizeof(int), st));
     count_launch();
-    CK(cqp::launch_kkt<T>(args(0), tmp_x, tmp_y, kkt_out, grid, blocks, threads, st));
+    CK(cqp::launch_kkt<T>(args(0), tmp_x, tmp_y, kkt_out, team, blocks, threads, st));
     double h[8];
     CK(cudaMemcpyAsync(h, kkt_out, sizeof(h), cudaMemcpyDeviceToHost, st));
     int herr = 0;
@@ -1351,9 +1370,13 @@ int cqp_spmv(int32_t precision, int64_t nrows, int64_t ncols, const int32_t* row
              const void* val, const void* x, void* y, int32_t threads_per_row, void* stream) {
   if (nrows < 0 || ncols < 0 || !rowptr || (nrows > 0 && (!colind || !val || !x || !y))) return CQP_ERR_INVALID;
   int tpr = threads_per_row;
-  if (tpr != 0 && tpr != 1 && tpr != 2 && tpr != 4 && tpr != 8 && tpr != 16 && tpr != 32) return CQP_ERR_INVALID;
+  if (tpr != -1 && tpr != 0 && tpr != 1 && tpr != 2 && tpr != 4 && tpr != 8 && tpr != 16 && tpr != 32)
+    return CQP_ERR_INVALID;
+  const bool batched_rows = tpr == -1;
   return guarded([&]() {
-    if (tpr == 0) {
+    if (batched_rows) {
+      tpr = cqp::kRowsBatched;
+    } else if (tpr == 0) {
       int32_t last = 0;
       CK(cudaMemcpy(&last, rowptr + nrows, sizeof(int32_t), cudaMemcpyDeviceToHost));
       tpr = pow2_tpr(nrows > 0 ? (double)last / (double)nrows : 1.0);

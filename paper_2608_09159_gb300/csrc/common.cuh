@@ -91,6 +91,12 @@ __device__ __forceinline__ void block_sum_r(R (&v)[NS], double* scratch, double*
 //   publish(slot, v)       block total v of reduction slot `slot` (thread 0 only)
 //   gather(nslots, out)    after sync(): out[s] = sum over blocks of slot s, in a fixed
 //                          order, identical on every block (shared-memory `out`)
+//   finish()               before the kernel returns (the cluster team waits for every
+//                          block, whose shared memory the others may still read)
+// Every block runs the same publish / sync / gather sequence.  The partials alternate
+// between two buffers, one per gather: a block that has gathered and runs ahead writes
+// its next partials into the other buffer, and it cannot come back to this one before
+// the next barrier, which every block reaches only after its own gather.
 // ---------------------------------------------------------------------------
 
 struct GridBarrier {
@@ -103,15 +109,17 @@ struct GridBarrier {
 // through *err instead of hanging.
 struct GridTeam {
   GridBarrier bar;
-  double* part;      // [kMaxSlots][gridDim.x] block partials in global memory
+  double* part;      // [2][kMaxSlots][gridDim.x] block partials in global memory
   unsigned target;
   int failed;
+  int buf;           // buffer of the current publish / gather round
 
   __device__ void init(GridBarrier b, double* p) {
     bar = b;
     part = p;
     target = 0;
     failed = 0;
+    buf = 0;
   }
   __device__ __forceinline__ int nb() const { return gridDim.x; }
   __device__ __forceinline__ int bid() const { return blockIdx.x; }
@@ -134,18 +142,71 @@ struct GridTeam {
     failed = *(volatile int*)bar.err != 0;
     return !failed;
   }
-  __device__ __forceinline__ void publish(int slot, double v) { part[slot * gridDim.x + blockIdx.x] = v; }
+  __device__ __forceinline__ void publish(int slot, double v) {
+    part[(buf * kMaxSlots + slot) * gridDim.x + blockIdx.x] = v;
+  }
   // one warp per slot, lanes stride over blocks, then a fixed-order shuffle tree
+  __device__ void gather(int nslots, double* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const double* pb = part + (size_t)buf * kMaxSlots * gridDim.x;
+    for (int s = warp; s < nslots; s += nw) {
+      double t = 0.0;
+      for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(&pb[s * gridDim.x + b]);
+      t = warp_sum(t);
+      if (lane == 0) out[s] = t;
+    }
+    buf ^= 1;
+    __syncthreads();
+  }
+  __device__ __forceinline__ void finish() {}
+};
+
+// Thread-block-cluster team: the blocks of one cluster (launched as the whole grid),
+// synchronised by the hardware cluster barrier; every block keeps its partials in its
+// own shared memory and reads the others' through distributed shared memory, in rank
+// order.  Every block takes the same decisions from the same gathered sums, so all of
+// them pass the same barriers and none can wait for a block that has left.
+__device__ __forceinline__ double ld_cluster_f64(const double* local, unsigned rank) {
+  const unsigned addr = (unsigned)__cvta_generic_to_shared(local);
+  unsigned remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(addr), "r"(rank));
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(remote) : "memory");
+  return v;
+}
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+struct ClusterTeam {
+  double* part;      // shared memory of this block, [2][kMaxSlots]
+  int failed;
+  int buf;
+  __device__ void init(double* p) {
+    part = p;
+    failed = 0;
+    buf = 0;
+  }
+  __device__ __forceinline__ int nb() const { return gridDim.x; }
+  __device__ __forceinline__ int bid() const { return blockIdx.x; }
+  __device__ __forceinline__ bool sync() {
+    __syncthreads();
+    cluster_barrier();
+    return true;
+  }
+  __device__ __forceinline__ void publish(int slot, double v) { part[buf * kMaxSlots + slot] = v; }
   __device__ void gather(int nslots, double* out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int s = warp; s < nslots; s += nw) {
       double t = 0.0;
-      for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(&part[s * gridDim.x + b]);
+      for (int b = lane; b < (int)gridDim.x; b += 32) t += ld_cluster_f64(part + buf * kMaxSlots + s, (unsigned)b);
       t = warp_sum(t);
       if (lane == 0) out[s] = t;
     }
+    buf ^= 1;
     __syncthreads();
   }
+  __device__ __forceinline__ void finish() { cluster_barrier(); }
 };
 
 // One-CTA team: barriers are __syncthreads and block totals are final.
@@ -168,6 +229,7 @@ struct CtaTeam {
     for (int s = threadIdx.x; s < nslots; s += blockDim.x) out[s] = part[s];
     __syncthreads();
   }
+  __device__ __forceinline__ void finish() {}
 };
 
 // [lo, hi) share of `count` items for block b of nb
@@ -219,7 +281,7 @@ __device__ __forceinline__ void split_rows_by_nnz(const int* rowptr, int64_t nro
 // less than a quarter of it, then the largest power of two not above their mean length
 // (short rows under a wide group leave most lanes idle and serialise the block).
 __device__ __forceinline__ int block_group_width(int tuned, int64_t nnz, int64_t rows) {
-  if (rows <= 0 || 4 * nnz >= (int64_t)tuned * rows) return tuned;
+  if (tuned <= 1 || rows <= 0 || 4 * nnz >= (int64_t)tuned * rows) return tuned;   // 0: batched one-lane rows
   int g = 1;
   while (2 * g * rows <= nnz) g *= 2;
   return g;

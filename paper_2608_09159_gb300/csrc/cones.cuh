@@ -607,45 +607,60 @@ static __device__ __noinline__ void pow_proj(double rx, double ry, double rz, do
 // previous root of the block (exp: a, pow: x / |z|^{1/a}) and is updated.
 // --------------------------------------------------------------------------
 
+// Newton steps on a monotone function inside a sign-change bracket [lo, hi], with a
+// bisection step whenever two Newton steps have not halved the bracket (so far starts and
+// flat or steep stretches cannot stall it).  f(x, &df) returns the value and derivative;
+// up_at_lo: the function is negative at lo (increasing) or positive at lo (decreasing).
+template <typename F>
+static __device__ double bracketed_newton(F f, double lo, double hi, double x, bool neg_at_lo) {
+  if (!(x > lo && x < hi)) x = 0.5 * (lo + hi);
+  double w_old = hi - lo;
+  for (int it = 0; it < 200; ++it) {
+    double d;
+    const double v = f(x, &d);
+    if (v == 0.0) break;
+    if ((v < 0.0) == neg_at_lo) lo = x; else hi = x;
+    double nx = (d != 0.0 && isfinite(d)) ? x - v / d : 0.5 * (lo + hi);
+    if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
+    if ((it & 1) == 1) {
+      if (hi - lo > 0.5 * w_old) nx = 0.5 * (lo + hi);
+      w_old = hi - lo;
+    }
+    const double step = fabs(nx - x);
+    x = nx;
+    if (step <= 4e-16 * fmax(1.0, fabs(x)) || (hi - lo) <= 4e-16 * fmax(1.0, fabs(x))) break;
+  }
+  return x;
+}
+
 // exp: u = (a, 1, e^a) with phi(a) = m_r (a0 - a) - m_t (e^a - c0) e^a = 0; phi is
-// decreasing on the bracket [max(log c0, a0 - (m_t/m_r)(e^{a0} - c0) e^{a0}), a0],
-// positive at its left end and negative at its right end
+// decreasing where e^a >= c0.  Bracket: lo = log c0 for c0 > 0 (phi = m_r (a0 - log c0) > 0
+// there), else the first of min(a0, 0) - 2^k with phi >= 0 (phi grows without bound as
+// a -> -inf); hi = min(a0, log(S + max(c0, 0))) with S = sqrt((m_r/m_t)(a0 - lo)), where
+// e^a (e^a - c0) >= S^2 >= (m_r/m_t)(a0 - a) makes phi <= 0.
 static __device__ __noinline__ void exp_slice_proj(double r0, double t0, double f, double mr, double mt, double* out,
                                                   float* guess = nullptr) {
   const double a0 = r0 / f, c0 = t0 / f;
   out[1] = f;
-  const double ea0 = exp(a0);
-  if (ea0 <= c0) { out[0] = r0; out[2] = t0; return; }
+  if (exp(a0) <= c0) { out[0] = r0; out[2] = t0; return; }
   auto phi = [&](double a, double* dphi) {
     const double ea = exp(a);
     *dphi = -mr - mt * ea * (2.0 * ea - c0);
     return mr * (a0 - a) - mt * (ea - c0) * ea;
   };
-  double lo = a0 - (mt / mr) * (ea0 - c0) * ea0;
-  if (c0 > 0.0) lo = fmax(lo, log(c0));
-  double hi = a0, d;
-  if (!isfinite(lo)) {
+  double d, lo;
+  if (c0 > 0.0) {
+    lo = log(c0);
+  } else {
+    const double top = fmin(a0, 0.0);
     double step = 1.0;
-    lo = a0 - step;
-    while (phi(lo, &d) < 0.0 && step < 1e300) { step *= 2.0; lo = a0 - step; }
+    lo = top - step;
+    while (phi(lo, &d) < 0.0 && step < 1e300) { step *= 2.0; lo = top - step; }
   }
-  if (!isfinite(hi) || !(phi(hi, &d) < 0.0)) hi = a0;
-  double a = hi;
+  double hi = fmin(a0, log(sqrt((mr / mt) * (a0 - lo)) + fmax(c0, 0.0)));
+  if (!(hi > lo)) hi = a0;
   const double g0 = guess ? (double)*guess : NAN;
-  if (isfinite(g0) && g0 > lo && g0 < hi) {
-    if (phi(g0, &d) > 0.0) lo = g0; else hi = g0;
-    a = hi;
-  }
-  for (int it = 0; it < 200; ++it) {
-    const double v = phi(a, &d);
-    if (v == 0.0) break;
-    if (v > 0.0) lo = a; else hi = a;
-    double nx = (d != 0.0 && isfinite(d)) ? a - v / d : 0.5 * (lo + hi);
-    if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
-    const double step = fabs(nx - a);
-    a = nx;
-    if (step <= 4e-16 * fmax(1.0, fabs(a)) || (hi - lo) <= 4e-16 * fmax(1.0, fabs(a))) break;
-  }
+  const double a = bracketed_newton(phi, lo, hi, (isfinite(g0) && g0 > lo && g0 < hi) ? g0 : hi, false);
   if (guess) *guess = (float)a;
   out[0] = f * a;
   out[2] = f * exp(a);
@@ -653,7 +668,9 @@ static __device__ __noinline__ void exp_slice_proj(double r0, double t0, double 
 
 // pow: u = (x, 1, sign(c0) x^a) with psi(x) = m_x (x - x0) - m_z (Z - x^a) a x^{a-1} = 0,
 // Z = |c0|; psi is increasing on (max(x0, 0), Z^{1/a}), negative at its left end (or
-// tending to -inf at 0+) and positive at its right end
+// tending to -inf at 0+) and positive at its right end.  Since Z - x^a <= Z at the root,
+// x^{1-a} (x - x0) <= (m_z/m_x) a Z there, which bounds it by ((m_z/m_x) a Z)^{1/(2-a)} for
+// x0 <= 0 and by x0 + (m_z/m_x) a Z x0^{a-1} for x0 > 0.
 static __device__ __noinline__ void pow_slice_proj(double rx, double rz, double al, double f, double mx, double mz,
                                                   double* out, float* guess = nullptr) {
   const double x0 = rx / f, c0 = rz / f;
@@ -661,27 +678,20 @@ static __device__ __noinline__ void pow_slice_proj(double rx, double rz, double 
   const double Z = fabs(c0);
   if (x0 >= 0.0 && (Z == 0.0 || (x0 > 0.0 && al * log(x0) >= log(Z)))) { out[0] = rx; out[2] = rz; return; }
   if (Z == 0.0) { out[0] = f * fmax(x0, 0.0); out[2] = 0.0; return; }
-  double lo = fmax(x0, 0.0), hi = exp(log(Z) / al);
+  const double lo = fmax(x0, 0.0);
+  const double k = (mz / mx) * al * Z;
+  double hi = exp(log(Z) / al);
+  const double hb = x0 > 0.0 ? x0 + k * exp((al - 1.0) * log(x0)) : exp(log(k) / (2.0 - al));
+  if (hb > lo && hb < hi) hi = hb;
   auto psi = [&](double x, double* dpsi) {
     const double lx = log(x);
     const double xa = exp(al * lx), xam1 = exp((al - 1.0) * lx);
     *dpsi = mx + mz * al * ((1.0 - al) * Z * xam1 / x + (2.0 * al - 1.0) * xam1 * xam1);
     return mx * (x - x0) - mz * (Z - xa) * al * xam1;
   };
-  double x = 0.5 * (lo + hi), d;
   const double g0 = guess ? (double)*guess : NAN;
-  if (isfinite(g0) && g0 > 0.0 && g0 < 1.0 && g0 * hi > lo) x = g0 * hi;
-  for (int it = 0; it < 200; ++it) {
-    const double v = psi(x, &d);
-    if (v == 0.0) break;
-    if (v < 0.0) lo = x; else hi = x;
-    double nx = (d != 0.0 && isfinite(d)) ? x - v / d : 0.5 * (lo + hi);
-    if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
-    const double step = fabs(nx - x);
-    x = nx;
-    if (step <= 4e-16 * x || (hi - lo) <= 4e-16 * hi) break;
-  }
-  if (guess) *guess = (float)(x / exp(log(Z) / al));
+  const double x = bracketed_newton(psi, lo, hi, (isfinite(g0) && g0 > 0.0) ? g0 * hi : 0.5 * (lo + hi), true);
+  if (guess) *guess = (float)(x / hi);
   out[0] = f * x;
   out[2] = (c0 > 0.0 ? f : -f) * exp(al * log(x));
 }

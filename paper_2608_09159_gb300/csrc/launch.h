@@ -11,21 +11,31 @@ namespace cqp {
 template <typename T>
 struct KernelArgs;
 
-// Cooperative whole-GPU launch (grid = true) or one block (grid = false).
+// How the blocks of a solve cooperate: one block, the whole GPU (cooperative launch, one
+// block per SM) or one thread-block cluster.
+enum TeamKind : int { kTeamCta = 0, kTeamGrid = 1, kTeamCluster = 2 };
+
 template <typename T>
-cudaError_t launch_pdhg(const KernelArgs<T>& a, bool grid, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_pdhg(const KernelArgs<T>& a, int team, int blocks, int threads, cudaStream_t st);
 
 // KKT report of the scaled point (x, y) with the handle's data; out receives 8 doubles.
 template <typename T>
-cudaError_t launch_kkt(const KernelArgs<T>& a, const T* x, const T* y, double* out, bool grid, int blocks, int threads,
+cudaError_t launch_kkt(const KernelArgs<T>& a, const T* x, const T* y, double* out, int team, int blocks, int threads,
                        cudaStream_t st);
 
 // General-form variant of launch_pdhg (row bounds, box blocks), built in its own
 // translation unit; launch_pdhg forwards to it when P.rhi or P.xlo is set.
 template <typename T>
-cudaError_t launch_pdhg_general(const KernelArgs<T>& a, bool grid, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_pdhg_general(const KernelArgs<T>& a, int team, int blocks, int threads, cudaStream_t st);
 template <typename T>
 int pdhg_general_blocks_per_sm(int threads);
+template <typename T>
+int pdhg_general_cluster_size(int threads);
+
+// Largest cluster (16, 8, 4 or 2 CTAs of `threads` threads) every solver kernel variant of
+// this precision can be launched with; 0 if none.
+template <typename T>
+int pdhg_cluster_size(int threads);
 
 // Batched persistent solve (one block per instance at a time, work queue).
 template <typename T>

@@ -246,10 +246,71 @@ __device__ __forceinline__ void rows_loop(const int* rp, const int* ci, const T*
   (void)ngr;
 }
 
+// One lane per row, RB rows per lane at a time: the row pointers of all RB rows are loaded
+// first, then kMultiU entries of every row, then their gathers, so a lane keeps 2 RB + 2 RB
+// kMultiU independent loads in flight instead of one row's dependent chain (row pointer ->
+// entries -> gathered operands).  Short rows (a handful of entries) are otherwise bound by
+// that chain's latency.  Each row's entries are still summed in storage order.
+constexpr int kMultiRows = 4;
+constexpr int kMultiU = 4;
+template <int RB, typename Acc, typename T, typename X, typename F>
+__device__ __forceinline__ void rows_loop_multi(const int* rp, const int* ci, const T* v, int64_t r0, int64_t r1, X xf,
+                                                F f) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5;
+  const int64_t nrows = r1 - r0;
+  for (int64_t base = warp * 32 * RB; base < nrows; base += nwarps * 32 * RB) {
+    int beg[RB], end[RB];
+    Acc s[RB];
+    int len = 0;
+#pragma unroll
+    for (int q = 0; q < RB; ++q) {
+      const int64_t r = r0 + base + 32 * q + lane;
+      const bool ok = r < r1;
+      beg[q] = ok ? rp[r] : 0;
+      end[q] = ok ? rp[r + 1] : 0;
+      s[q] = Acc(0);
+    }
+#pragma unroll
+    for (int q = 0; q < RB; ++q) len = max(len, end[q] - beg[q]);
+    for (int k = 0; k < len; k += kMultiU) {
+      int j[RB][kMultiU];
+      T a[RB][kMultiU];
+#pragma unroll
+      for (int q = 0; q < RB; ++q)
+#pragma unroll
+        for (int u = 0; u < kMultiU; ++u) {
+          const int kk = beg[q] + k + u;
+          const bool ok = kk < end[q];
+          j[q][u] = ok ? __ldg(ci + kk) : -1;
+          a[q][u] = ok ? __ldg(v + kk) : T(0);
+        }
+      Acc g[RB][kMultiU];
+#pragma unroll
+      for (int q = 0; q < RB; ++q)
+#pragma unroll
+        for (int u = 0; u < kMultiU; ++u) g[q][u] = j[q][u] >= 0 ? (Acc)xf(j[q][u]) : Acc(0);
+#pragma unroll
+      for (int q = 0; q < RB; ++q)
+#pragma unroll
+        for (int u = 0; u < kMultiU; ++u) s[q] += (Acc)a[q][u] * g[q][u];
+    }
+#pragma unroll
+    for (int q = 0; q < RB; ++q) {
+      const int64_t r = r0 + base + 32 * q + lane;
+      if (r < r1) f(r, 0, s[q]);
+    }
+  }
+}
+
+// Row widths: tpr = G lanes per row (1..32), or kRowsBatched for one lane per row with
+// kMultiRows rows per lane in flight (rows_loop_multi).
+constexpr int kRowsBatched = 0;
 template <typename Acc, typename T, typename X, typename F>
 __device__ __forceinline__ void rows_loop_tpr(int tpr, const int* rp, const int* ci, const T* v, int64_t r0, int64_t r1,
                                               X xf, F f) {
   switch (tpr) {
+    case kRowsBatched: rows_loop_multi<kMultiRows, Acc>(rp, ci, v, r0, r1, xf, f); break;
     case 1: rows_loop<1, Acc>(rp, ci, v, r0, r1, xf, f); break;
     case 2: rows_loop<2, Acc>(rp, ci, v, r0, r1, xf, f); break;
     case 4: rows_loop<4, Acc>(rp, ci, v, r0, r1, xf, f); break;

@@ -51,6 +51,7 @@ template <typename Acc, typename T, typename X1, typename X2, typename F>
 __device__ __forceinline__ void rows_loop2_tpr(int tpr, const int* rp, const int* ci, const T* v, int64_t r0, int64_t r1,
                                                X1 x1, X2 x2, F f) {
   switch (tpr) {
+    case kRowsBatched:
     case 1: rows_loop2<1, Acc>(rp, ci, v, r0, r1, x1, x2, f); break;
     case 2: rows_loop2<2, Acc>(rp, ci, v, r0, r1, x1, x2, f); break;
     case 4: rows_loop2<4, Acc>(rp, ci, v, r0, r1, x1, x2, f); break;
@@ -670,6 +671,7 @@ __device__ __forceinline__ void solver_entry(const KernelArgs<T>& a, Team& team,
     if (team.failed) C.s.err = kErrBarrier;
     *a.S = C.s;
   }
+  team.finish();
 }
 
 template <typename T, bool GEN>
@@ -687,6 +689,67 @@ __global__ void __launch_bounds__(512, 1) pdhg_cta_kernel(KernelArgs<T> a) {
   CtaTeam team;
   team.init(part);
   solver_entry<T, CtaTeam, GEN>(a, team, smem);
+}
+
+// one thread-block cluster (the whole grid) for problems too small to spread over the
+// GPU: cluster barriers and distributed-shared-memory reductions instead of global ones
+template <typename T, bool GEN>
+__global__ void __launch_bounds__(512, 1) pdhg_cluster_kernel(KernelArgs<T> a) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ double part[2 * kMaxSlots];
+  ClusterTeam team;
+  team.init(part);
+  solver_entry<T, ClusterTeam, GEN>(a, team, smem);
+}
+
+// Launch of the cluster kernel: `blocks` CTAs forming one cluster (sizes above 8 need the
+// non-portable cluster attribute).
+template <typename K>
+cudaError_t launch_cluster(K kernel, void** args, int blocks, int threads, size_t smem, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (blocks > 8) {
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = blocks;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, (const void*)kernel, args);
+}
+
+// Largest cluster (16, 8, 4 or 2 CTAs) of the solver kernel that the device can place with
+// the given block size and shared memory; 0 if none.
+template <typename K>
+int cluster_size_for(K kernel, int threads, size_t smem) {
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  for (int c = 16; c >= 2; c /= 2) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = c;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, (const void*)kernel, &cfg) == cudaSuccess && nc >= 1) return c;
+    cudaGetLastError();
+  }
+  return 0;
 }
 
 }  // namespace cqp

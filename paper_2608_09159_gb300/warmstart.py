@@ -148,6 +148,8 @@ class WarmStartNet:
         cqp_gemm_bf16(0, 1, rows, HID, HID, _p(dZ2), HID, _p(self.bf["W2"]), HID, _p(dH1), HID, None, 4)
         cqp_relu_backward_bf16(rows, HID, _p(f["H1"]), _p(dH1), _p(self.g["b1"]))
         cqp_gemm_bf16(1, 0, FEAT, HID, rows, _p(f["X"]), FEAT, _p(dH1), HID, _p(self.g["W1"]), HID, None, 3, split)
+        # the intermediate derivatives stay available to the caller (layer-by-layer checks)
+        f.update(dscore=dscore, dyd=dyd, dZ2=dZ2, dZ1=dH1)
         return loss
 
     def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
@@ -208,15 +210,39 @@ def train(net: WarmStartNet, data: TrainingSet, steps: int, instances: int = 256
     return hist
 
 
-def solve_batch(batch, net: WarmStartNet | None = None, dual_mode: int = 1, **opts):
+def solve_batch(batch, net: WarmStartNet | None = None, dual_mode: int = 1, fallback: bool = True, **opts):
     """Batched solve of a portfolio batch, from the network's start when `net` is given,
-    else from zero.  Returns (x, y, per-instance results, summary)."""
+    else from zero.  Returns (x, y, per-instance results, summary).
+
+    Plain cold-start PDHG stays the fallback of the learned start: with `fallback`, every
+    instance whose warm-started solve ends unconverged (iteration or time limit, numerical
+    error) is solved again from zero, in one more batched launch in which the converged
+    instances start from their own solution (they stop at the first check).  The summary's
+    "fallback" entry counts those instances."""
     dbatch = to_device(batch)
     s = BatchSolver(dbatch, device=True, **opts)
     try:
         if net is None:
             return s.solve(out_device=True)
         x0, y0 = net.start(BatchDevice(dbatch), dual_mode=dual_mode)
-        return s.solve(x0=x0, y0=y0, out_device=True)
+        x, y, per, res = s.solve(x0=x0, y0=y0, out_device=True)
+        bad = [i for i, r in enumerate(per) if r["rc"] != 0]
+        res["fallback"] = len(bad)
+        if not bad or not fallback:
+            return x, y, per, res
+        xo, ro = dbatch["x_off"], dbatch["row_off"]
+        xs, ys = x.clone(), y.clone()
+        for i in bad:
+            xs[int(xo[i]):int(xo[i + 1])] = 0.0
+            ys[int(ro[i]):int(ro[i + 1])] = 0.0
+        x2, y2, per2, res2 = s.solve(x0=xs, y0=ys, out_device=True)
+        for i in bad:
+            x[int(xo[i]):int(xo[i + 1])] = x2[int(xo[i]):int(xo[i + 1])]
+            y[int(ro[i]):int(ro[i + 1])] = y2[int(ro[i]):int(ro[i + 1])]
+            per[i] = per2[i]
+        res["rc"] = max((r["rc"] for r in per), key=lambda v: (v != 0, abs(v)))
+        res["kernel_ms"] += res2["kernel_ms"]
+        res["fallback_kernel_ms"] = res2["kernel_ms"]
+        return x, y, per, res
     finally:
         s.close()

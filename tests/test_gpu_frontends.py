@@ -11,6 +11,8 @@ Each front-end instance is solved through cqp_setup_general on the GPU in FP32 a
 import numpy as np
 import pytest
 
+from _parity import REL_KKT, obj_close
+
 import instances as I
 from oracle import frontends as OF
 
@@ -52,9 +54,9 @@ def test_qcqp_frontend(gpu, orc, qcqp_case, precision):
     s.close()
     assert res["rc"] == 0, res
     rep = orc.kkt(inst, x, y)
-    assert rep["rel_kkt"] <= 1.5e-4, rep
+    assert rep["rel_kkt"] <= REL_KKT, rep
     xs = rec(x)
-    assert _rel(OF.qcqp_objective(prob, xs), OF.qcqp_objective(prob, xref)) <= 5e-4
+    assert obj_close(OF.qcqp_objective(prob, xs), OF.qcqp_objective(prob, xref))
     assert np.linalg.norm(xs - xref) <= 2e-2 * (1 + np.linalg.norm(xref))
 
 
@@ -77,8 +79,8 @@ def test_lasso_frontend(gpu, orc, lasso_case, precision):
     s.close()
     assert res["rc"] == 0, res
     rep = orc.kkt(inst, x, y)
-    assert rep["rel_kkt"] <= 1.5e-4, rep
+    assert rep["rel_kkt"] <= REL_KKT, rep
     xs = rec(x)
     f, fref = OF.lasso_objective(A, L["b"], L["lam"], xs), OF.lasso_objective(A, L["b"], L["lam"], xref)
-    assert _rel(f, fref) <= 5e-4
+    assert obj_close(f, fref), (f, fref)
     assert np.linalg.norm(xs - xref) <= 2e-2 * (1 + np.linalg.norm(xref))

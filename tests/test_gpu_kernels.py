@@ -37,7 +37,7 @@ def _csr_random(rng, m, n, density, long_rows=0):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("tpr", [0, 1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("tpr", [-1, 0, 1, 2, 4, 8, 16, 32])
 def test_spmv_parity(gpu, orc, rng, precision, tpr):
     import torch
     m, n = 1537, 1203                                               # ragged tail over many tiles
@@ -109,7 +109,10 @@ def test_projection_edge_cases(gpu, orc):
              (G.EXP1, [0.0, 5.0, 2.0]), (G.EXP1, [1.0, 0.0, -3.0]), (G.EXP1, [30.0, 1.0, 0.5]),
              (G.EXP1, [-40.0, 1.0, -1e-3]), (G.EXP1, [0.5, 1.0, np.exp(0.5)]),
              (G.POW1, [-1.0, 2.0, 0.0]), (G.POW1, [-2.0, 1.0, 0.3]), (G.POW1, [4.0, 1.0, 4.0 ** 0.4]),
-             (G.POW1, [1e-3, 1.0, -5.0]), (G.POW1, [50.0, 0.0, 1e-4])]
+             (G.POW1, [1e-3, 1.0, -5.0]), (G.POW1, [50.0, 0.0, 1e-4]),
+             # slices far outside: e^{r0} overflowing the naive bracket, |t0| >> 1
+             (G.EXP1, [108.9, 18.0, -62.6]), (G.EXP1, [300.0, 1.0, 1e10]), (G.EXP1, [-5.0, 1.0, -1e4]),
+             (G.POW1, [-3.0, 1.0, 1e4]), (G.POW1, [0.5, 1.0, -1e3]), (G.POW1, [1e4, 1.0, 1e6])]
     for precision in (0, 1):
         dt = torch.float64 if precision else torch.float32
         for t, r in cases:

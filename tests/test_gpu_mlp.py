@@ -3,7 +3,9 @@
 * the BF16 tensor-core GEMM against the exact product of the same BF16 values,
   for every transpose combination and epilogue, at ragged sizes;
 * features, forward pass and gradients of the network against the FP64 oracle
-  (oracle/mlp.py) evaluated on the same BF16-rounded weights and inputs;
+  (oracle/mlp.py), layer by layer and element by element: each layer's reference takes the
+  same BF16 weights and the GPU's own BF16-rounded input of that layer, and the bound is one
+  BF16 rounding of the output plus the FP32 accumulation error;
 * what training buys: on held-out portfolio batches the warm-started batched
   solve needs fewer iterations than the cold start and still reaches rel-KKT
   <= 1e-4 on every instance (the solver's own KKT test decides).
@@ -67,18 +69,32 @@ def test_gemm_bf16(gpu, ta, tb, epi):
 
 
 def _net_params_numpy(net):
-    import torch
     p = {k: v.double().cpu().numpy().copy() for k, v in net.p.items()}
     for k in ("W1", "W2"):
         p[k] = net.bf[k].float().cpu().numpy().astype(np.float64)   # the GEMMs use the BF16 copies
     return p
 
 
-def _relerr(a, b):
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+def _np(t):
+    return t.float().cpu().numpy().astype(np.float64)
 
 
-def test_forward_and_gradients_match_oracle(gpu):
+U32 = 2.0 ** -24        # FP32 unit roundoff
+BF16 = 2.0 ** -8        # one BF16 rounding (round to nearest: 2^-9 relative), with margin
+
+
+def _check(name, got, ref, terms, k, bf16_out):
+    """Elementwise: |got - ref| <= (BF16 rounding of ref if the kernel writes BF16) + k u32 * terms,
+    with terms the sum of |products| of each entry's FP32 accumulation of length k."""
+    bound = (BF16 * np.abs(ref) if bf16_out else 0.0) + 2.0 * k * U32 * terms + 1e-30
+    err = np.abs(got - ref)
+    assert np.all(err <= bound), (name, float(err.max()), float((err / bound).max()))
+
+
+def test_forward_and_gradients_match_oracle_elementwise(gpu):
+    """Every layer of the BF16 network, forward and backward, against oracle/mlp.py evaluated in FP64
+    on the same BF16 weights and on the GPU's own (BF16-rounded) inputs of that layer, element by
+    element, with a bound from one BF16 rounding of the output and the FP32 accumulation."""
     import torch
     from oracle import mlp as M
     from paper_2608_09159_gb300 import warmstart as W
@@ -86,31 +102,71 @@ def test_forward_and_gradients_match_oracle(gpu):
     dev = W.BatchDevice(b)
     X = dev.features()
     Xo = M.features(b, b["n_factors"])
-    Xg = X.float().cpu().numpy().astype(np.float64)
-    assert np.all(np.abs(Xg - Xo) <= 2.0 ** -8 * np.abs(Xo) + 1e-30)
+    Xg = _np(X)
+    assert np.all(np.abs(Xg - Xo) <= BF16 * np.abs(Xo) + 1e-30)
     net = W.WarmStartNet(seed=5)
     rng = np.random.default_rng(6)
     # a non-trivial dual head and score layer
     net.p["Wd"].copy_(torch.from_numpy(rng.normal(size=(W.HID, 2)).astype(np.float32) * 0.05))
     net.p["w3"].copy_(torch.from_numpy(rng.normal(size=W.HID).astype(np.float32) * 0.05))
+    net.p["b1"].copy_(torch.from_numpy(rng.normal(size=W.HID).astype(np.float32) * 0.05))
+    net.p["b2"].copy_(torch.from_numpy(rng.normal(size=W.HID).astype(np.float32) * 0.05))
     off = dev.asset_off_h
-    f = net.forward(X, dev.asset_off, dev.count)
+    count, rows = dev.count, Xg.shape[0]
+    f = net.forward(X, dev.asset_off, count)
     p = _net_params_numpy(net)
-    fo = M.forward(p, Xg, off)
-    assert _relerr(f["x0"].double().cpu().numpy(), fo["x0"]) <= 2e-2
-    assert _relerr(f["ydual"].double().cpu().numpy(), fo["yd"]) <= 2e-2
+    A = np.abs
+    # layer 1 from the features, layer 2 from the GPU's BF16 H1, head from the GPU's BF16 H2
+    _, H1r = M.layer(Xg, p["W1"], p["b1"])
+    H1g = _np(f["H1"])
+    _check("H1", H1g, H1r, A(Xg) @ A(p["W1"]) + A(p["b1"]), Xg.shape[1] + 1, True)
+    _, H2r = M.layer(H1g, p["W2"], p["b2"])
+    H2g = _np(f["H2"])
+    _check("H2", H2g, H2r, A(H1g) @ A(p["W2"]) + A(p["b2"]), W.HID + 1, True)
+    hr = M.head_forward(p, H2g, off)
+    sg = _np(f["score"])
+    _check("score", sg, hr["s"], A(H2g) @ A(p["w3"]) + A(p["b3"][0]), W.HID + 1, False)
+    # softmax of the GPU's own scores, and the pooled mean / dual head of its H2
+    hs = M.head_forward(p, H2g, off)
+    x0g = _np(f["x0"])
+    xs_ref = np.empty_like(sg)
+    for i in range(count):
+        z = np.exp(sg[off[i]:off[i + 1]] - sg[off[i]:off[i + 1]].max())
+        xs_ref[off[i]:off[i + 1]] = z / z.sum()
+    assert np.all(np.abs(x0g - xs_ref) <= 256 * U32 * xs_ref + 1e-12)
+    pg = _np(f["pooled"])
+    assert np.all(np.abs(pg - hs["pooled"]) <= 2 * 64 * U32 * (A(H2g).max() + 1e-30))
+    _check("ydual", _np(f["ydual"]), pg @ p["Wd"] + p["bd"], A(pg) @ A(p["Wd"]) + A(p["bd"]), W.HID + 1, False)
+    # backward: loss gradients of the mean loss (scale 1/count) from the GPU's forward values
     xs = np.concatenate([rng.dirichlet(np.ones(int(n))) for n in b["n_assets"]]).astype(np.float32)
-    ys = rng.normal(size=(dev.count, 2)).astype(np.float32)
+    ys = rng.normal(size=(count, 2)).astype(np.float32)
     loss = net.backward(f, torch.from_numpy(xs).cuda(), torch.from_numpy(ys).cuda(), lam=1.0)
-    go = M.backward(p, Xg, fo, xs.astype(np.float64), ys.astype(np.float64), off, 1.0)
-    assert abs(loss.item() - M.loss(fo, xs, ys, off, 1.0)) <= 2e-2 * abs(M.loss(fo, xs, ys, off, 1.0))
-    for k in W.PARAMS:
-        gk = net.g[k].double().cpu().numpy() * dev.count          # the GPU gradient is of the mean loss
-        if k == "b3":
-            # a common shift of the scores leaves every softmax unchanged: the exact gradient is 0
-            assert abs(gk[0]) <= 1e-4 * np.abs(go["w3"]).max(), gk
-            continue
-        assert _relerr(gk.reshape(go[k].shape), go[k]) <= 6e-2, k
+    fg = dict(s=sg, x0=x0g, pooled=pg, yd=_np(f["ydual"]), H2=H2g)
+    ds, dyd, _, gh = M.head_backward(p, fg, xs.astype(np.float64), ys.astype(np.float64), off, 1.0)
+    assert abs(loss.item() - M.loss(fg, xs, ys, off, 1.0)) <= 1e-5 * M.loss(fg, xs, ys, off, 1.0)
+    dsg, dydg = _np(f["dscore"]), _np(f["dyd"])
+    big = 1.0 + max(A(ds).max(), A(dyd).max()) / count
+    assert np.all(A(dsg - ds / count) <= 256 * U32 * big), float(A(dsg - ds / count).max())
+    assert np.all(A(dydg - dyd / count) <= 16 * U32 * big)
+    # head parameter gradients from the GPU's own dscore and dydual
+    gw3r, gb3r, _ = M.layer_backward(H2g, dsg[:, None])
+    gWdr, gbdr, _ = M.layer_backward(pg, dydg)
+    for k, ref, terms, K in (("w3", gw3r[:, 0], A(H2g).T @ A(dsg), rows), ("b3", gb3r, A(dsg).sum(keepdims=True), rows),
+                             ("Wd", gWdr, A(pg).T @ A(dydg), count), ("bd", gbdr, A(dydg).sum(axis=0), count)):
+        _check("g" + k, _np(net.g[k]).reshape(ref.shape), ref, terms, K + 8, False)
+    assert np.all(A(gw3r[:, 0] - gh["w3"] / count) <= 1e-4 * (A(gh["w3"]).max() / count + 1e-30))
+    # the masked dZ2 from the GPU's ds, dyd; layer-2 gradients and dZ1 from the GPU's BF16 dZ2
+    dZ2r = M.head_input_grad(p, dsg, dydg, off) * (H2g > 0)
+    dZ2g = _np(f["dZ2"])
+    _check("dZ2", dZ2g, dZ2r, (A(dsg)[:, None] * A(p["w3"])[None, :] + A(dydg @ p["Wd"].T).max()) * (H2g > 0), 4, True)
+    gW2r, gb2r, dZ1r = M.layer_backward(H1g, dZ2g, p["W2"], H1g > 0)
+    _check("gW2", _np(net.g["W2"]), gW2r, A(H1g).T @ A(dZ2g), rows, False)
+    _check("gb2", _np(net.g["b2"]), gb2r, A(dZ2g).sum(axis=0), rows, False)
+    dZ1g = _np(f["dZ1"])
+    _check("dZ1", dZ1g, dZ1r, (A(dZ2g) @ A(p["W2"]).T) * (H1g > 0), W.HID, True)
+    gW1r, gb1r, _ = M.layer_backward(Xg, dZ1g)
+    _check("gW1", _np(net.g["W1"]), gW1r, A(Xg).T @ A(dZ1g), rows, False)
+    _check("gb1", _np(net.g["b1"]), gb1r, A(dZ1g).sum(axis=0), rows, False)
 
 
 def test_trained_start_needs_fewer_iterations(gpu):
@@ -136,3 +192,26 @@ def test_trained_start_needs_fewer_iterations(gpu):
         iw = np.mean([r["iters"] for r in warm])
         print("dual_mode %d: mean iterations cold %.1f warm %.1f" % (mode, ic, iw))
         assert iw < 0.95 * ic
+
+
+def test_unconverged_warm_start_falls_back_to_cold_start(gpu):
+    """A network whose dual head is far off (bias 1e4) leaves its warm-started instances unconverged
+    within the iteration cap; solve_batch then solves them again from zero, the plain method."""
+    import torch
+    from paper_2608_09159_gb300 import warmstart as W
+    test = I.portfolio_batch(count=40, n_range=(20, 60), k_range=(3, 8), seed=598)
+    _, _, cold, rc = W.solve_batch(test, None, precision=0, tol=1e-4, max_iter=100000, time_limit_s=120.0)
+    assert rc["rc"] == 0
+    cap = max(r["iters"] for r in cold)
+    net = W.WarmStartNet(seed=3)
+    net.p["bd"].copy_(torch.tensor([1e4, -1e4], dtype=torch.float32))
+    opts = dict(precision=0, tol=1e-4, max_iter=cap, time_limit_s=120.0)
+    _, _, warm, rw = W.solve_batch(test, net, dual_mode=1, fallback=False, **opts)
+    failed = [i for i, r in enumerate(warm) if r["rc"] != 0]
+    assert rw["fallback"] == len(failed) > 0
+    x, y, per, rf = W.solve_batch(test, net, dual_mode=1, **opts)
+    assert rf["fallback"] == len(failed)
+    assert all(r["rc"] == 0 for r in per) and rf["rc"] == 0
+    for i in failed:                      # the fallback instances are the cold solves
+        assert per[i]["iters"] == cold[i]["iters"]
+        assert per[i]["kkt"]["rel_kkt"] <= 1e-4

@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import instances as I
+from _parity import REL_KKT, TIGHT_TOL, obj_close
 
 pytestmark = pytest.mark.gpu
 
@@ -40,14 +41,32 @@ def test_small_configs_solve(gpu, orc, k, precision, team):
     x, y, res = s.solve()
     assert res["rc"] == 0, res
     rep = orc.kkt(inst, x, y)                 # independent FP64 CPU measurement of the same point
-    assert rep["rel_kkt"] <= 1.5e-4, rep
-    assert abs(rep["rel_kkt"] - res["kkt"]["rel_kkt"]) <= 1e-5 + 0.05 * rep["rel_kkt"]
-    xo, yo, info = orc.solve(inst, max_iter=200000, tol=1e-4)
-    assert _rel(rep["pobj"], info["kkt"]["pobj"]) <= 1e-4 * 5
-    if k in (1, 2):                           # Q positive definite: x* unique
-        xs, ys, _ = orc.solve(inst, max_iter=400000, tol=1e-9)
+    assert rep["rel_kkt"] <= REL_KKT, rep
+    assert abs(rep["rel_kkt"] - res["kkt"]["rel_kkt"]) <= 1e-7 + 1e-3 * rep["rel_kkt"]
+    xs, ys, info = orc.solve(inst, max_iter=1000000, tol=TIGHT_TOL)
+    assert info["status"] == 0
+    assert obj_close(rep["pobj"], info["kkt"]["pobj"]), (rep["pobj"], info["kkt"]["pobj"])
+    if k in (1, 2):                           # Q positive definite: x* unique (an extra check, not the bar)
         assert np.linalg.norm(x - xs) <= 2e-2 * (1 + np.linalg.norm(xs))
     s.close()
+
+
+def test_config1_full_size_fp64(gpu, orc):
+    """The sparse nonnegative QP at its full size (n = 1,000, m = 500) in FP64, the precision
+    this workload is measured in, through the automatic team choice.  At the first check below
+    rel-KKT 1e-4 (7e-5) this instance's objective is still 2.4e-4 from the optimum, so the
+    solve runs to 1e-5: rel-KKT <= 1e-4 then holds with the objective within 1e-4."""
+    inst = I.sparse_qp_nonneg()
+    s = gpu.Solver(inst, precision=1, max_iter=400000, tol=1e-5, time_limit_s=120.0)
+    x, y, res = s.solve()
+    s.close()
+    assert res["rc"] == 0, res
+    rep = orc.kkt(inst, x, y)
+    assert rep["rel_kkt"] <= REL_KKT, rep
+    assert abs(rep["rel_kkt"] - res["kkt"]["rel_kkt"]) <= 1e-7 + 1e-3 * rep["rel_kkt"]
+    xs, ys, info = orc.solve(inst, max_iter=1000000, tol=TIGHT_TOL)
+    assert info["status"] == 0
+    assert obj_close(rep["pobj"], info["kkt"]["pobj"]), (rep["pobj"], info["kkt"]["pobj"])
 
 
 def test_one_step_fp64_matches_oracle_operator(gpu, orc):
@@ -91,7 +110,7 @@ def test_averaged_variant(gpu, orc):
     s = gpu.Solver(inst, precision=1, update=1, avg_epoch=64, max_iter=400000, tol=1e-4, time_limit_s=120.0)
     x, y, res = s.solve()
     assert res["rc"] == 0, res
-    assert orc.kkt(inst, x, y)["rel_kkt"] <= 1.5e-4
+    assert orc.kkt(inst, x, y)["rel_kkt"] <= REL_KKT
     s.close()
 
 
@@ -118,9 +137,14 @@ def test_invalid_inputs(gpu):
     with pytest.raises(gpu.CQPError) as e:
         gpu.Solver(bad)
     assert e.value.code == -1
-    bad = I.small_config(3)
-    bad["blk_alpha"] = bad["blk_alpha"].copy()
-    bad["blk_alpha"][bad["blk_type"] == 5] = 1.5        # power cone alpha outside (0, 1)
+    for fixed_middle in (True, False):                  # power slice / power cone alpha outside (0, 1)
+        bad = I.fisher_market(n_buyers=200, n_goods=40, density=0.1, seed=2003, fixed_middle=fixed_middle)
+        bad["blk_alpha"] = bad["blk_alpha"].copy()
+        bad["blk_alpha"][np.isin(bad["blk_type"], (I.CONE_POW, I.CONE_POW1))] = 1.5
+        with pytest.raises(gpu.CQPError) as e:
+            gpu.Solver(bad)
+        assert e.value.code == -1
+    sl = I.small_config(3)                              # slices are not available in the rescaled-cone mode
     with pytest.raises(gpu.CQPError) as e:
-        gpu.Solver(bad)
-    assert e.value.code == -1
+        gpu.Solver(sl, rescaled_cones=1)
+    assert e.value.code == -6

@@ -78,8 +78,8 @@ def _close(got, ref):
 
 
 @pytest.mark.parametrize("k", [1, 2, 3])
-def test_two_calls_match_handle_kkt(gpu, k):
-    inst = I.small_config(k)
+def test_two_calls_match_handle_kkt(gpu, orc, k):
+    inst = I.small_config(k)      # k = 3: exponential and power slice blocks
     x, y = _point(inst, 40 + k)
     s = gpu.Solver(inst, precision=1)
     ref = s.kkt(x, y)
@@ -89,6 +89,23 @@ def test_two_calls_match_handle_kkt(gpu, k):
     second = _static_report(gpu, prob, x, y)
     _close(first, ref)
     _close(second, ref)
+    _close(first, orc.kkt(inst, x, y))          # and the FP64 oracle's report of the same point
+
+
+def test_malformed_row_pointers_are_reported(gpu):
+    # a row pointer past nnz (or a first entry other than 0) is flagged and its row skipped:
+    # the call reads only the caller's nnz entries and returns CQP_ERR_INVALID
+    import torch
+    inst = I.small_config(1)
+    x, y = _point(inst, 9)
+    for bad_at, value in ((inst["m"], int(inst["a_rowptr"][-1]) + 64), (0, 1)):
+        A, Q, K, t = _device_problem(gpu, inst)
+        t["a_rowptr"][bad_at] = value
+        xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+        rep = gpu.KKTReport()
+        with pytest.raises(gpu.CQPError) as e:
+            gpu.cqp_kkt_static(A, Q, t["c"].data_ptr(), t["b"].data_ptr(), K, xd.data_ptr(), yd.data_ptr(), rep)
+        assert e.value.code == -1 and "malformed" in str(e.value)
 
 
 def test_back_to_back_sizes_clear_the_scratch(gpu):
