@@ -619,8 +619,11 @@ static void proj_pow_m(const double* r, const double* m, double alpha, double* o
 /* Exponential slice X_1 = {(a, 1, c): e^a <= c}.  Outside X_1 the projection (a, e^a) satisfies
  * M (r - u) = lambda (e^a, -1) with lambda >= 0 (outward normal of e^a - c <= 0), i.e.
  *   phi(a) = m_a (a0 - a) - m_c (e^a - c0) e^a = 0,   a <= a0,  e^a >= c0.
- * On that range phi' = -m_a - m_c e^a (2 e^a - c0) < 0, phi(a0) < 0, and phi >= 0 at
- * a0 - (m_c/m_a)(e^{a0} - c0) e^{a0} and (for c0 > 0) at log c0, so the zero is unique. */
+ * On that range phi' = -m_a - m_c e^a (2 e^a - c0) < 0, so the zero is unique.  Bracket:
+ * lo = log c0 for c0 > 0 (phi = m_a (a0 - log c0) > 0 there), else the first of
+ * min(a0, 0) - 2^k with phi >= 0 (phi -> +inf as a -> -inf); hi = min(a0, log(S + max(c0, 0)))
+ * with S^2 = (m_a/m_c)(a0 - lo): there e^a (e^a - c0) >= S^2 >= (m_a/m_c)(a0 - a), so phi <= 0.
+ * (The bracket stays a few units wide even when e^{a0} is huge.) */
 typedef struct { double a0, c0, ma, mc; } eslice_ctx;
 static double eslice_phi(double a, const void* vctx) {
   const eslice_ctx* c = (const eslice_ctx*)vctx;
@@ -632,7 +635,9 @@ static double eslice_phi(double a, const void* vctx) {
  * (x, sign(z0) x^a) with x in (max(x0, 0), |z0|^{1/a}) the zero of
  *   psi(x) = m_x (x - x0) - m_z (|z0| - x^a) a x^{a-1},
  * which tends to -infinity at 0+ (or is < 0 at x0 > 0) and is m_x (|z0|^{1/a} - x0) > 0 at the
- * right end; psi' >= m_x > 0 there, so the zero is unique.  For z0 = 0 it is (max(x0, 0), 0). */
+ * right end; psi' >= m_x > 0 there, so the zero is unique.  At the zero |z0| - x^a <= |z0|, so
+ * x^{1-a} (x - x0) <= k = (m_z/m_x) a |z0|: the right end can be lowered to k^{1/(2-a)} (x0 <= 0)
+ * or x0 + k x0^{a-1} (x0 > 0).  For z0 = 0 the projection is (max(x0, 0), 0). */
 typedef struct { double x0, Z, a, mx, mz; } pslice_ctx;
 static double pslice_psi(double x, const void* vctx) {
   const pslice_ctx* c = (const pslice_ctx*)vctx;
@@ -649,15 +654,17 @@ int orc_proj_slice(int type, double alpha, double f, const double* r, const doub
       u0 = a0; u2 = c0;
     } else {
       eslice_ctx c = {a0, c0, m0, m2};
-      double ea = exp(a0);
-      double lo = a0 - (m2 / m0) * (ea - c0) * ea;
-      if (c0 > 0.0) lo = fmax(lo, log(c0));
-      if (!isfinite(lo)) {   /* e^{a0} overflowed: step left until phi >= 0 */
-        double step = 1.0;
-        lo = a0 - step;
-        while (eslice_phi(lo, &c) < 0.0 && step < 1e300) { step *= 2.0; lo = a0 - step; }
+      double lo;
+      if (c0 > 0.0) {
+        lo = log(c0);
+      } else {
+        double top = fmin(a0, 0.0), step = 1.0;
+        lo = top - step;
+        while (eslice_phi(lo, &c) < 0.0 && step < 1e300) { step *= 2.0; lo = top - step; }
       }
-      double a = bisect(eslice_phi, &c, lo, a0, 1);
+      double hi = fmin(a0, log(sqrt((m0 / m2) * (a0 - lo)) + fmax(c0, 0.0)));
+      if (!(hi > lo)) hi = a0;
+      double a = bisect(eslice_phi, &c, lo, hi, 1);
       u0 = a; u2 = exp(a);
     }
   } else if (type == ORC_POW1) {
@@ -668,7 +675,11 @@ int orc_proj_slice(int type, double alpha, double f, const double* r, const doub
       u0 = fmax(a0, 0.0); u2 = 0.0;
     } else {
       pslice_ctx c = {a0, fabs(c0), alpha, m0, m2};
-      double x = bisect(pslice_psi, &c, fmax(a0, 0.0), pow(fabs(c0), 1.0 / alpha), 0);
+      double lo = fmax(a0, 0.0), hi = pow(fabs(c0), 1.0 / alpha);
+      double k = (m2 / m0) * alpha * fabs(c0);
+      double hb = a0 > 0.0 ? a0 + k * pow(a0, alpha - 1.0) : pow(k, 1.0 / (2.0 - alpha));
+      if (hb > lo && hb < hi) hi = hb;
+      double x = bisect(pslice_psi, &c, lo, hi, 0);
       u0 = x; u2 = (c0 > 0.0 ? 1.0 : -1.0) * pow(x, alpha);
     }
   } else {
