@@ -146,6 +146,8 @@ typedef struct {
   int32_t launch_iters;     /* outer iterations per kernel launch, 0 = auto */
   int32_t profile;          /* 1: record per-phase device time in cqp_result.phase_ms */
   int32_t warm_roots;       /* 1: start each cone block's root-finding from its previous root (default 1) */
+  int32_t col_blocks;       /* dual step's product A z over column blocks whose slice of z stays in L2:
+                               0 auto (on when z exceeds 64 MB: 8 blocks), 1 off, K >= 2 forces K blocks (<= 64) */
   void* stream;             /* cudaStream_t, NULL = default stream */
 } cqp_options;
 

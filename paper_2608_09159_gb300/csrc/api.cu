@@ -709,6 +709,30 @@ struct Handle : HandleBase {
         count_launch(); cqp::k_slice_fix<<<cqp::grid_for(n_pow), cqp::kSetupThreads, 0, st>>>(n_pow, base[5], col, beta_b, d_pow_fix);
       }
     }
+    // column blocks of A for the dual step: the gathered vector z = 2 w_x - h_x (n entries) is read
+    // at random columns; when it is larger than a good part of L2, the product runs over blocks of
+    // columns whose slice of z stays in L2 (reading: 8 slices above 64 MB)
+    int cb_n = 0;
+    int* cb_rp = nullptr;
+    int* cb_ci = nullptr;
+    T* cb_v = nullptr;
+    {
+      const double zbytes = (double)n * sizeof(T);
+      if (o.col_blocks >= 2) cb_n = std::min(o.col_blocks, 64);
+      else if (o.col_blocks == 0 && zbytes > 64.0 * 1024 * 1024) cb_n = 8;
+      if (batched || m == 0 || nnz == 0) cb_n = 0;
+      if ((int64_t)cb_n * m >= (int64_t(1) << 31)) cb_n = 0;
+      if (cb_n > 1) {
+        const int64_t width = (n + cb_n - 1) / cb_n;
+        int* cnt = tmp.alloc<int>((int64_t)cb_n * m);
+        cb_rp = mem.alloc<int>((int64_t)cb_n * m + 1);
+        cb_ci = mem.alloc<int>(nnz);
+        cb_v = mem.alloc<T>(nnz);
+        count_launch(); cqp::k_cb_count<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp, a_ci, width, cb_n, cnt);
+        dev_scan(cnt, cb_rp, (int64_t)cb_n * m, tmp, st);
+        count_launch(); cqp::k_cb_scatter<T><<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp, a_ci, a_v, width, cb_n, cb_rp, cb_ci, cb_v);
+      }
+    }
     // Euclidean projections suffice when the diagonal Q vanishes on every cone coordinate
     double qcone = 0.0;
     {
@@ -808,6 +832,19 @@ struct Handle : HandleBase {
     P.n_soc = n_soc; P.soc_off = d_soc; P.n_rsoc = n_rsoc; P.rsoc_off = d_rsoc;
     P.n_exp = n_exp; P.exp_base = base[4]; P.n_pow = n_pow; P.pow_base = base[5]; P.pow_alpha = palpha;
     P.exp_fix = d_exp_fix; P.pow_fix = d_pow_fix;
+    P.cb_n = cb_n; P.cb_rp = cb_rp; P.cb_ci = cb_ci; P.cb_v = cb_v;
+    // rows of P of one common length (a matching Laplacian has two per row): their entries are
+    // addressed without reading the row pointers
+    P.p_ulen = 0;
+    if (has_p && n > 0 && pnnz % n == 0 && pnnz / n > 0 && pnnz / n <= 64) {
+      int* ubad = tmp.alloc<int>(1);
+      CK(cudaMemsetAsync(ubad, 0, sizeof(int), st));
+      count_launch(); cqp::k_check_uniform<<<cqp::grid_for(n + 1), cqp::kSetupThreads, 0, st>>>(n, p_rp, (int)(pnnz / n), ubad);
+      int hb = 1;
+      CK(cudaMemcpyAsync(&hb, ubad, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (!hb) P.p_ulen = (int)(pnnz / n);
+    }
     if (has_p) P.qmode = cqp::kQSparse;
     else if (k > 0 || o.force_inner) P.qmode = cqp::kQLowRank;
     else P.qmode = cqp::kQDiag;
@@ -819,7 +856,10 @@ struct Handle : HandleBase {
       T* xs = tmp.alloc<T>(n);
       T* ys = tmp.alloc<T>(std::max<int64_t>(std::max(m, n), 1));
       count_launch(); cqp::k_convert<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, jdv, xs);
-      auto tune = [&](int64_t rows, int64_t nz, const int32_t* rp, const int32_t* ci, const T* v) {
+      // ncols: length of the gathered operand; one lane with four rows in flight is only a
+      // candidate when that operand does not fit in a good part of L2 (there the gathers' DRAM
+      // latency binds; inside L2 the plain loop measured faster in the solver)
+      auto tune = [&](int64_t rows, int64_t ncols, int64_t nz, const int32_t* rp, const int32_t* ci, const T* v) {
         if (rows == 0) return 1;
         int dev = 0;
         CK(cudaGetDevice(&dev));
@@ -840,9 +880,11 @@ struct Handle : HandleBase {
         // candidate widths in order of preference: one lane per row, one lane with four rows in
         // flight (cqp::kRowsBatched), then 2..16 lanes
         const int cand[6] = {1, cqp::kRowsBatched, 2, 4, 8, 16};
+        const bool batched_ok = (double)ncols * sizeof(T) > 32.0 * 1024 * 1024;
         float ms_of[6];
         for (int ti = 0; ti < 6; ++ti) {
           const int t = cand[ti];
+          if (t == cqp::kRowsBatched && !batched_ok) { ms_of[ti] = 1e30f; continue; }
           count_launch();
           CK(cqp::launch_spmv<T>(rows, rp, ci, v, xs, ys, t, st, nsm));
           float tot = 1e30f;
@@ -869,9 +911,9 @@ struct Handle : HandleBase {
         g_tune_cache[key] = best;
         return best;
       };
-      P.tpr_a = o.tpr_a > 0 ? o.tpr_a : (o.tpr_a == -1 ? cqp::kRowsBatched : tune(m, nnz, a_rp, a_ci, a_v));
-      P.tpr_t = o.tpr_at > 0 ? o.tpr_at : (o.tpr_at == -1 ? cqp::kRowsBatched : tune(n, nnz, t_rp, t_ci, t_v));
-      P.tpr_p = has_p ? tune(n, pnnz, p_rp, p_ci, pT) : 1;
+      P.tpr_a = o.tpr_a > 0 ? o.tpr_a : (o.tpr_a == -1 ? cqp::kRowsBatched : tune(m, n, nnz, a_rp, a_ci, a_v));
+      P.tpr_t = o.tpr_at > 0 ? o.tpr_at : (o.tpr_at == -1 ? cqp::kRowsBatched : tune(n, m, nnz, t_rp, t_ci, t_v));
+      P.tpr_p = has_p ? tune(n, n, pnnz, p_rp, p_ci, pT) : 1;
     }
     // ---- work buffers and state -------------------------------------------------------------
     const int64_t mm = std::max<int64_t>(m, 1);
@@ -884,6 +926,7 @@ struct Handle : HandleBase {
     W.avx = o.update == 1 ? mem.alloc<T>(n) : nullptr;
     W.avy = o.update == 1 ? mem.alloc<T>(mm) : nullptr;
     W.mbuf = mem.alloc<T>(n);
+    W.cb_acc = cb_n > 1 ? mem.alloc<T>(m) : nullptr;
     W.sd = mem.alloc<double>(n);
     n_roots = n_soc + n_rsoc + n_exp + n_pow;
     W.root = mem.alloc<float>(std::max<int64_t>(n_roots, 1));
@@ -1252,6 +1295,7 @@ int cqp_default_options(cqp_options* o) {
   o->power_tol = 1e-6;
   o->step_factor = 0.998;
   o->warm_roots = 1;
+  o->col_blocks = 0;
   return CQP_OK;
 }
 

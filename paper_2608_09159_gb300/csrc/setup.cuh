@@ -263,6 +263,41 @@ __global__ void k_sqrt_or_one(int64_t n, double* f) {
 }
 // cone blocks of the permuted layout: [b0, b1) coordinate ranges given by offsets
 // (SOC, RSOC) or by a base and width 3 (EXP, POW); max (mode 0) or RMS (mode 1)
+// ---- column blocks of A for the dual step's product (entry (r, c) is in block c / width) ----
+// cnt[b * rows + r] = number of entries of row r in block b
+__global__ void k_cb_count(int64_t rows, const int* rp, const int* ci, int64_t width, int nb, int* cnt) {
+  CQP_GRID_LOOP(r, rows) {
+    const int e0 = rp[r], e1 = rp[r + 1];
+    for (int b = 0; b < nb; ++b) {
+      int c = 0;
+      for (int e = e0; e < e1; ++e) c += (int64_t)ci[e] / width == b;
+      cnt[(int64_t)b * rows + r] = c;
+    }
+  }
+}
+// entries of row r in block b, in row order, to out[bp[b * rows + r] ...]
+template <typename T>
+__global__ void k_cb_scatter(int64_t rows, const int* rp, const int* ci, const T* v, int64_t width, int nb,
+                             const int* bp, int* oci, T* ov) {
+  CQP_GRID_LOOP(r, rows) {
+    const int e0 = rp[r], e1 = rp[r + 1];
+    for (int b = 0; b < nb; ++b) {
+      int pos = bp[(int64_t)b * rows + r];
+      for (int e = e0; e < e1; ++e)
+        if ((int64_t)ci[e] / width == b) {
+          oci[pos] = ci[e];
+          ov[pos] = v[e];
+          ++pos;
+        }
+    }
+  }
+}
+
+// *bad = 1 unless rp[r] = L r for every r <= rows (rows of exactly L entries)
+__global__ void k_check_uniform(int64_t rows, const int* rp, int L, int* bad) {
+  CQP_GRID_LOOP(r, rows + 1) if ((int64_t)rp[r] != (int64_t)L * r) *bad = 1;
+}
+
 // slice blocks: fix[e] = flag[e] * col[base + 3 e + 1] / beta_b (flag 1 for a slice, 0 for a cone)
 __global__ void k_slice_fix(int64_t nblk, int64_t base, const double* col, double beta_b, double* fix) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;

@@ -59,6 +59,10 @@ struct Prob {
   // slices (CQP_CONE_EXP1 / POW1): per exp / pow block the fixed middle coordinate in scaled
   // variables, f~ = col / beta_b, or 0 for a full cone (null: no slices in the problem)
   const double* exp_fix; const double* pow_fix;
+  // column blocks of A for the dual step's product between checks (cb_n <= 1: not used):
+  // block b's rows are rows of the CSR with row pointers cb_rp + b m (into cb_ci, cb_v)
+  int cb_n; const int* cb_rp; const int* cb_ci; const T* cb_v;
+  int p_ulen;                                         // > 0: every row of P has exactly p_ulen entries
   int qmode;
   int euclid_cones;                                   // diagonal mode with zero q on cone coordinates
   int tpr_a, tpr_t, tpr_p;                            // threads per row of A, A' and P
@@ -78,6 +82,7 @@ struct Work {
   T* g[2];              // gradients (sparse-P mode)
   T* avx; T* avy;       // running averages (averaged variant)
   T* mbuf;              // metric of cone blocks too large for shared staging
+  T* cb_acc;            // partial row sums of the column-blocked product (m)
   float* root;          // last scalar root per cone block (warm starts): SOC, RSOC, exp, pow
   double* sd;           // FP64 dual slack of cone coordinates (KKT)
   double* part;         // block partials [kMaxSlots][nb]
@@ -253,9 +258,10 @@ __device__ __forceinline__ void rows_loop(const int* rp, const int* ci, const T*
 // that chain's latency.  Each row's entries are still summed in storage order.
 constexpr int kMultiRows = 4;
 constexpr int kMultiU = 4;
+// ulen > 0: every row has exactly ulen entries (rp[r] = ulen r), so the row pointers are not read.
 template <int RB, typename Acc, typename T, typename X, typename F>
 __device__ __forceinline__ void rows_loop_multi(const int* rp, const int* ci, const T* v, int64_t r0, int64_t r1, X xf,
-                                                F f) {
+                                                F f, int ulen = 0) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5;
   const int64_t nrows = r1 - r0;
@@ -267,8 +273,13 @@ __device__ __forceinline__ void rows_loop_multi(const int* rp, const int* ci, co
     for (int q = 0; q < RB; ++q) {
       const int64_t r = r0 + base + 32 * q + lane;
       const bool ok = r < r1;
-      beg[q] = ok ? rp[r] : 0;
-      end[q] = ok ? rp[r + 1] : 0;
+      if (ulen > 0) {
+        beg[q] = ok ? (int)(ulen * r) : 0;
+        end[q] = ok ? beg[q] + ulen : 0;
+      } else {
+        beg[q] = ok ? rp[r] : 0;
+        end[q] = ok ? rp[r + 1] : 0;
+      }
       s[q] = Acc(0);
     }
 #pragma unroll
@@ -308,9 +319,9 @@ __device__ __forceinline__ void rows_loop_multi(const int* rp, const int* ci, co
 constexpr int kRowsBatched = 0;
 template <typename Acc, typename T, typename X, typename F>
 __device__ __forceinline__ void rows_loop_tpr(int tpr, const int* rp, const int* ci, const T* v, int64_t r0, int64_t r1,
-                                              X xf, F f) {
+                                              X xf, F f, int ulen = 0) {
   switch (tpr) {
-    case kRowsBatched: rows_loop_multi<kMultiRows, Acc>(rp, ci, v, r0, r1, xf, f); break;
+    case kRowsBatched: rows_loop_multi<kMultiRows, Acc>(rp, ci, v, r0, r1, xf, f, ulen); break;
     case 1: rows_loop<1, Acc>(rp, ci, v, r0, r1, xf, f); break;
     case 2: rows_loop<2, Acc>(rp, ci, v, r0, r1, xf, f); break;
     case 4: rows_loop<4, Acc>(rp, ci, v, r0, r1, xf, f); break;
@@ -754,7 +765,8 @@ struct Solver {
                            gout[i] = g;
                            if (!first) acc += (u[i] - uprev[i]) * (g - gprev[i]);
                          }
-                       });
+                       },
+                       P.p_ulen);
     }
     v2[0] = (double)acc;
     v2[1] = 0.0;

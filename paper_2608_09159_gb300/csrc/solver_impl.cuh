@@ -452,8 +452,25 @@ __device__ void Solver<T, Team, GEN>::run(long long budget) {
       for (int seg = 0; seg < 6; ++seg)
         for (int64_t i = own.x0[seg] + threadIdx.x; i < own.x1[seg]; i += blockDim.x) zv[i] = T(2) * wxn[i] - hx[i];
       if (!team.sync()) return;
-      rows_loop_tpr<T>(own.g_a, P.a_rp, P.a_ci, P.a_v, own.row0, own.row1, [&](int j) { return zv[j]; },
-                       [&](int64_t r, int gl, T s1) { dual_row(r, gl, s1, T(0)); });
+      if (P.cb_n > 1) {
+        // column blocks: every block of the team works on the same slice of z (one barrier per
+        // slice), so the slice stays in L2 while its entries stream past; a row keeps its lane
+        // in every slice, which adds its partial sums in slice order
+        T* acc = W.cb_acc;
+        for (int b = 0; b < P.cb_n; ++b) {
+          const bool first = b == 0, last = b == P.cb_n - 1;
+          rows_loop_tpr<T>(kRowsBatched, P.cb_rp + (int64_t)b * P.m, P.cb_ci, P.cb_v, own.row0, own.row1,
+                           [&](int j) { return zv[j]; }, [&](int64_t r, int gl, T s1) {
+                             if (gl != 0) return;
+                             if (last) dual_row(r, 0, first ? s1 : acc[r] + s1, T(0));
+                             else acc[r] = first ? s1 : acc[r] + s1;
+                           });
+          if (!last && !team.sync()) return;
+        }
+      } else {
+        rows_loop_tpr<T>(own.g_a, P.a_rp, P.a_ci, P.a_v, own.row0, own.row1, [&](int j) { return zv[j]; },
+                         [&](int64_t r, int gl, T s1) { dual_row(r, gl, s1, T(0)); });
+      }
     }
     T* hxn = W.hx[hb ^ 1];
     T* wxs = W.wx[wb ^ 1];

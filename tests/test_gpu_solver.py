@@ -69,6 +69,30 @@ def test_config1_full_size_fp64(gpu, orc):
     assert obj_close(rep["pobj"], info["kkt"]["pobj"]), (rep["pobj"], info["kkt"]["pobj"])
 
 
+@pytest.mark.parametrize("precision", [1, 0])
+def test_column_blocked_dual_step(gpu, orc, precision):
+    """The dual step's product over column blocks (forced on a small problem: 5 blocks) reaches
+    the same bars; in FP64 its first iterations equal the plain product's to rounding."""
+    inst = I.small_config(2)
+    s = gpu.Solver(inst, precision=precision, max_iter=200000, tol=1e-4, time_limit_s=120.0, col_blocks=5)
+    x, y, res = s.solve()
+    s.close()
+    assert res["rc"] == 0, res
+    rep = orc.kkt(inst, x, y)
+    assert rep["rel_kkt"] <= REL_KKT, rep
+    xs, ys, info = orc.solve(inst, max_iter=1000000, tol=TIGHT_TOL)
+    assert obj_close(rep["pobj"], info["kkt"]["pobj"]), (rep["pobj"], info["kkt"]["pobj"])
+    if precision == 1:
+        a = gpu.Solver(inst, precision=1, max_iter=10, col_blocks=5)
+        b = gpu.Solver(inst, precision=1, max_iter=10, col_blocks=1)
+        xa, ya, _ = a.solve()
+        xb, yb, _ = b.solve()
+        a.close()
+        b.close()
+        assert np.abs(xa - xb).max() <= 1e-9 * (1 + np.abs(xb).max())
+        assert np.abs(ya - yb).max() <= 1e-9 * (1 + np.abs(yb).max())
+
+
 def test_one_step_fp64_matches_oracle_operator(gpu, orc):
     # scaling off, one outer iteration, prox solved to 1e-13: the candidate is T(z0), z0 = 0
     for k in (1, 2, 3):
