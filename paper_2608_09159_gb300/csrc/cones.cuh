@@ -611,24 +611,30 @@ static __device__ __noinline__ void pow_proj(double rx, double ry, double rz, do
 // bisection step whenever two Newton steps have not halved the bracket (so far starts and
 // flat or steep stretches cannot stall it).  f(x, &df) returns the value and derivative;
 // up_at_lo: the function is negative at lo (increasing) or positive at lo (decreasing).
-template <typename F>
-static __device__ double bracketed_newton(F f, double lo, double hi, double x, bool neg_at_lo) {
-  if (!(x > lo && x < hi)) x = 0.5 * (lo + hi);
-  double w_old = hi - lo;
+// rtol: stop once a step or the bracket is below rtol max(1, |x|).  f(x, &d, &sc) also returns
+// the size sc of the terms it sums: once |f| <= 8 u sc (u the unit roundoff of R) the value is
+// rounding noise and further steps cannot improve x, so the iteration stops there too.
+template <typename R, typename F>
+static __device__ R bracketed_newton(F f, R lo, R hi, R x, bool neg_at_lo, R rtol) {
+  const R u = sizeof(R) == 4 ? R(5.9604645e-08) : R(1.1102230246251565e-16);
+  if (!(x > lo && x < hi)) x = R(0.5) * (lo + hi);
+  R w_old = hi - lo, step_old = hi - lo;
   for (int it = 0; it < 200; ++it) {
-    double d;
-    const double v = f(x, &d);
-    if (v == 0.0) break;
-    if ((v < 0.0) == neg_at_lo) lo = x; else hi = x;
-    double nx = (d != 0.0 && isfinite(d)) ? x - v / d : 0.5 * (lo + hi);
-    if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
+    R d, sc;
+    const R v = f(x, &d, &sc);
+    if (v == R(0) || fabs(v) <= R(8) * u * sc) break;
+    if ((v < R(0)) == neg_at_lo) lo = x; else hi = x;
+    R nx = (d != R(0) && isfinite(d)) ? x - v / d : R(0.5) * (lo + hi);
+    if (!(nx > lo && nx < hi)) nx = R(0.5) * (lo + hi);
+    // bisect when two steps have not halved the bracket and Newton is not converging fast
     if ((it & 1) == 1) {
-      if (hi - lo > 0.5 * w_old) nx = 0.5 * (lo + hi);
+      if (hi - lo > R(0.5) * w_old && fabs(nx - x) > R(0.25) * step_old) nx = R(0.5) * (lo + hi);
       w_old = hi - lo;
     }
-    const double step = fabs(nx - x);
+    const R step = fabs(nx - x);
+    step_old = step;
     x = nx;
-    if (step <= 4e-16 * fmax(1.0, fabs(x)) || (hi - lo) <= 4e-16 * fmax(1.0, fabs(x))) break;
+    if (step <= rtol * fmax(R(1), fabs(x)) || (hi - lo) <= rtol * fmax(R(1), fabs(x))) break;
   }
   return x;
 }
@@ -643,24 +649,39 @@ static __device__ __noinline__ void exp_slice_proj(double r0, double t0, double 
   const double a0 = r0 / f, c0 = t0 / f;
   out[1] = f;
   if (exp(a0) <= c0) { out[0] = r0; out[2] = t0; return; }
-  auto phi = [&](double a, double* dphi) {
+  auto phi = [&](double a, double* dphi, double* sc) {
     const double ea = exp(a);
     *dphi = -mr - mt * ea * (2.0 * ea - c0);
+    *sc = mr * (fabs(a0) + fabs(a)) + mt * ea * (ea + fabs(c0));
     return mr * (a0 - a) - mt * (ea - c0) * ea;
   };
-  double d, lo;
+  double d, sc, lo;
   if (c0 > 0.0) {
     lo = log(c0);
   } else {
     const double top = fmin(a0, 0.0);
     double step = 1.0;
     lo = top - step;
-    while (phi(lo, &d) < 0.0 && step < 1e300) { step *= 2.0; lo = top - step; }
+    while (phi(lo, &d, &sc) < 0.0 && step < 1e300) { step *= 2.0; lo = top - step; }
   }
   double hi = fmin(a0, log(sqrt((mr / mt) * (a0 - lo)) + fmax(c0, 0.0)));
   if (!(hi > lo)) hi = a0;
   const double g0 = guess ? (double)*guess : NAN;
-  const double a = bracketed_newton(phi, lo, hi, (isfinite(g0) && g0 > lo && g0 < hi) ? g0 : hi, false);
+  double start = (isfinite(g0) && g0 > lo && g0 < hi) ? g0 : hi;
+  // the bulk of the iteration in FP32 (GB300's FP64 rate is a small fraction of its FP32
+  // rate), then FP64 Newton steps from its result inside the FP64 bracket
+  if (fabs(lo) < 60.0 && fabs(hi) < 60.0 && fabs(a0) < 1e6 && fabs(c0) < 1e30) {
+    const float a0f = (float)a0, c0f = (float)c0, mrf = (float)mr, mtf = (float)mt;
+    auto phif = [&](float a, float* dphi, float* scf) {
+      const float ea = expf(a);
+      *dphi = -mrf - mtf * ea * (2.0f * ea - c0f);
+      *scf = mrf * (fabsf(a0f) + fabsf(a)) + mtf * ea * (ea + fabsf(c0f));
+      return mrf * (a0f - a) - mtf * (ea - c0f) * ea;
+    };
+    const float af = bracketed_newton<float>(phif, (float)lo, (float)hi, (float)start, false, 2e-6f);
+    if (isfinite(af) && (double)af > lo && (double)af < hi) start = (double)af;
+  }
+  const double a = bracketed_newton<double>(phi, lo, hi, start, false, 4e-16);
   if (guess) *guess = (float)a;
   out[0] = f * a;
   out[2] = f * exp(a);
@@ -683,14 +704,29 @@ static __device__ __noinline__ void pow_slice_proj(double rx, double rz, double 
   double hi = exp(log(Z) / al);
   const double hb = x0 > 0.0 ? x0 + k * exp((al - 1.0) * log(x0)) : exp(log(k) / (2.0 - al));
   if (hb > lo && hb < hi) hi = hb;
-  auto psi = [&](double x, double* dpsi) {
+  auto psi = [&](double x, double* dpsi, double* sc) {
     const double lx = log(x);
     const double xa = exp(al * lx), xam1 = exp((al - 1.0) * lx);
     *dpsi = mx + mz * al * ((1.0 - al) * Z * xam1 / x + (2.0 * al - 1.0) * xam1 * xam1);
+    *sc = mx * (fabs(x) + fabs(x0)) + mz * (Z + xa) * al * xam1;
     return mx * (x - x0) - mz * (Z - xa) * al * xam1;
   };
   const double g0 = guess ? (double)*guess : NAN;
-  const double x = bracketed_newton(psi, lo, hi, (isfinite(g0) && g0 > 0.0) ? g0 * hi : 0.5 * (lo + hi), true);
+  double start = (isfinite(g0) && g0 > 0.0 && g0 * hi > lo && g0 < 1.0) ? g0 * hi : 0.5 * (lo + hi);
+  // FP32 bulk, FP64 finish (as for the exponential slice)
+  if (hi < 1e30 && fabs(x0) < 1e30 && Z < 1e30 && lo < 1e30) {
+    const float x0f = (float)x0, Zf = (float)Z, alf = (float)al, mxf = (float)mx, mzf = (float)mz;
+    auto psif = [&](float x, float* dpsi, float* scf) {
+      const float lx = logf(x);
+      const float xa = expf(alf * lx), xam1 = expf((alf - 1.0f) * lx);
+      *dpsi = mxf + mzf * alf * ((1.0f - alf) * Zf * xam1 / x + (2.0f * alf - 1.0f) * xam1 * xam1);
+      *scf = mxf * (fabsf(x) + fabsf(x0f)) + mzf * (Zf + xa) * alf * xam1;
+      return mxf * (x - x0f) - mzf * (Zf - xa) * alf * xam1;
+    };
+    const float xf = bracketed_newton<float>(psif, (float)lo, (float)hi, (float)start, true, 2e-6f);
+    if (isfinite(xf) && (double)xf > lo && (double)xf < hi) start = (double)xf;
+  }
+  const double x = bracketed_newton<double>(psi, lo, hi, start, true, 4e-16);
   if (guess) *guess = (float)(x / hi);
   out[0] = f * x;
   out[2] = (c0 > 0.0 ? f : -f) * exp(al * log(x));

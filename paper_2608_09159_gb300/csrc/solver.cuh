@@ -317,6 +317,22 @@ __device__ __forceinline__ void rows_loop_multi(const int* rp, const int* ci, co
 // Row widths: tpr = G lanes per row (1..32), or kRowsBatched for one lane per row with
 // kMultiRows rows per lane in flight (rows_loop_multi).
 constexpr int kRowsBatched = 0;
+// The same without the batched variant (it runs as one lane per row), for the rarely run
+// passes (KKT checks), so the persistent kernel carries fewer copies of the row loops.
+template <typename Acc, typename T, typename X, typename F>
+__device__ __forceinline__ void rows_loop_tpr_plain(int tpr, const int* rp, const int* ci, const T* v, int64_t r0,
+                                                    int64_t r1, X xf, F f) {
+  switch (tpr) {
+    case kRowsBatched:
+    case 1: rows_loop<1, Acc>(rp, ci, v, r0, r1, xf, f); break;
+    case 2: rows_loop<2, Acc>(rp, ci, v, r0, r1, xf, f); break;
+    case 4: rows_loop<4, Acc>(rp, ci, v, r0, r1, xf, f); break;
+    case 8: rows_loop<8, Acc>(rp, ci, v, r0, r1, xf, f); break;
+    case 16: rows_loop<16, Acc>(rp, ci, v, r0, r1, xf, f); break;
+    default: rows_loop<32, Acc>(rp, ci, v, r0, r1, xf, f); break;
+  }
+}
+
 template <typename Acc, typename T, typename X, typename F>
 __device__ __forceinline__ void rows_loop_tpr(int tpr, const int* rp, const int* ci, const T* v, int64_t r0, int64_t r1,
                                               X xf, F f, int ulen = 0) {
@@ -632,7 +648,43 @@ struct Solver {
     auto jm = [&](int64_t i) -> T { return jac ? jd[i] + itau : T(1); };
     T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
     unsigned long long tsub = (O.profile && team.bid() == 0 && threadIdx.x == 0) ? now_ns() : 0ull;
-    // elementwise segments (free, nonneg)
+    // elementwise segments (free, nonneg).  Without a low-rank part four elements per thread are
+    // loaded together (a streaming pass over n-vectors is otherwise bound by the few loads each
+    // of the 16 warps has in flight); the partial sums take the same order as the loop below.
+    if (KM == 0) {
+      constexpr int EU = 4;
+      const int64_t B = blockDim.x;
+      for (int seg = 0; seg < 2; ++seg)
+        for (int64_t i0 = own.x0[seg] + threadIdx.x; i0 < own.x1[seg]; i0 += EU * B) {
+          T uu[EU], qq[EU], gg[EU], jj[EU], ca[EU], va[EU];
+#pragma unroll
+          for (int e = 0; e < EU; ++e) {
+            const int64_t i = i0 + e * B;
+            const bool ok = i < own.x1[seg];
+            uu[e] = ok ? uc[i] : T(0);
+            qq[e] = ok ? qd[i] : T(0);
+            gg[e] = (ok && gs) ? gs[i] : T(0);
+            ca[e] = (ok && !gs) ? cc[i] : T(0);
+            va[e] = (ok && !gs) ? vv[i] : T(0);
+            jj[e] = ok ? jm(i) : T(1);
+          }
+#pragma unroll
+          for (int e = 0; e < EU; ++e) {
+            const int64_t i = i0 + e * B;
+            if (i >= own.x1[seg]) break;
+            const T u = uu[e], qi = qq[e];
+            const T g = gs ? gg[e] : qi * u + ca[e] + (u - va[e]) * itau;
+            const T J = jj[e];
+            const T un = proj_elem(i, u - alpha * g / J);
+            un_out[i] = un;
+            const T sd = un - u;
+            a0 += sd * sd;
+            a1 += J * sd * sd;
+            a2 += (qi + itau) * sd * sd;
+            a3 += un * un;
+          }
+        }
+    } else
     for (int seg = 0; seg < 2; ++seg)
       for (int64_t i = own.x0[seg] + threadIdx.x; i < own.x1[seg]; i += blockDim.x) {
         T rr[KM > 0 ? KM : 1];
@@ -751,11 +803,92 @@ struct Solver {
 
   // ---- sparse-P mode: gradient at u (P u by the owned rows of P), dots -------
   // writes g(u) to gout; v2 = {<s, dg>} with s = u - uprev, dg = g(u) - gprev
+  // The same gradient over rows [r0, r1) with one lane per row and kMultiRows rows in flight
+  // (no low-rank part): each row's vector operands are loaded with its entries, ahead of the
+  // gathers, instead of after the row sum and behind the previous row's store.  Same
+  // arithmetic in the same order as the generic loop.
+  __device__ T grad_rows_batched(const T* u, const T* uprev, const T* gprev, T* gout, T itau, bool first, int64_t r0,
+                                 int64_t r1) {
+    constexpr int RB = kMultiRows, U = kMultiU;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5;
+    const int ulen = P.p_ulen;
+    const int* __restrict__ rp = P.p_rp;
+    const int* __restrict__ ci = P.p_ci;
+    const T* __restrict__ pv = P.p_v;
+    T acc = T(0);
+    for (int64_t base = warp * 32 * RB; base < r1 - r0; base += nwarps * 32 * RB) {
+      int beg[RB], end[RB];
+      T uu[RB], qq[RB], cc[RB], vv[RB], up[RB], gp[RB], s[RB];
+      int len = 0;
+#pragma unroll
+      for (int q = 0; q < RB; ++q) {
+        const int64_t r = r0 + base + 32 * q + lane;
+        const bool ok = r < r1;
+        if (ulen > 0) {
+          beg[q] = ok ? (int)(ulen * r) : 0;
+          end[q] = ok ? beg[q] + ulen : 0;
+        } else {
+          beg[q] = ok ? rp[r] : 0;
+          end[q] = ok ? rp[r + 1] : 0;
+        }
+        uu[q] = ok ? u[r] : T(0);
+        qq[q] = ok ? __ldg(P.qd + r) : T(0);
+        cc[q] = ok ? __ldg(P.c + r) : T(0);
+        vv[q] = ok ? W.v[r] : T(0);
+        up[q] = (ok && !first) ? uprev[r] : T(0);
+        gp[q] = (ok && !first) ? gprev[r] : T(0);
+        s[q] = T(0);
+      }
+#pragma unroll
+      for (int q = 0; q < RB; ++q) len = max(len, end[q] - beg[q]);
+      for (int k = 0; k < len; k += U) {
+        int j[RB][U];
+        T a[RB][U];
+#pragma unroll
+        for (int q = 0; q < RB; ++q)
+#pragma unroll
+          for (int t = 0; t < U; ++t) {
+            const int kk = beg[q] + k + t;
+            const bool ok = kk < end[q];
+            j[q][t] = ok ? __ldg(ci + kk) : -1;
+            a[q][t] = ok ? __ldg(pv + kk) : T(0);
+          }
+        T gth[RB][U];
+#pragma unroll
+        for (int q = 0; q < RB; ++q)
+#pragma unroll
+          for (int t = 0; t < U; ++t) gth[q][t] = j[q][t] >= 0 ? u[j[q][t]] : T(0);
+#pragma unroll
+        for (int q = 0; q < RB; ++q)
+#pragma unroll
+          for (int t = 0; t < U; ++t) s[q] += a[q][t] * gth[q][t];
+      }
+#pragma unroll
+      for (int q = 0; q < RB; ++q) {
+        const int64_t r = r0 + base + 32 * q + lane;
+        if (r < r1) {
+          const T g = s[q] + qq[q] * uu[q] + cc[q] + (uu[q] - vv[q]) * itau;
+          gout[r] = g;
+          if (!first) acc += (uu[q] - up[q]) * (g - gp[q]);
+        }
+      }
+    }
+    return acc;
+  }
+
   __device__ void grad_pass(const T* u, const T* uprev, const T* gprev, T* gout, double tau, double (&v2)[2],
                             bool first) {
     const T itau = T(1.0 / tau);
     const T* w = wvec();
     T acc = T(0);
+    if (own.g_p == kRowsBatched && P.k == 0) {
+      for (int seg = 0; seg < 6; ++seg) acc += grad_rows_batched(u, uprev, gprev, gout, itau, first, own.x0[seg], own.x1[seg]);
+      v2[0] = (double)acc;
+      v2[1] = 0.0;
+      __syncthreads();
+      return;
+    }
     for (int seg = 0; seg < 6; ++seg) {
       rows_loop_tpr<T>(own.g_p, P.p_rp, P.p_ci, P.p_v, own.x0[seg], own.x1[seg], [&](int j) { return u[j]; },
                        [&](int64_t i, int gl, T pu) {

@@ -227,7 +227,7 @@ __device__ bool Solver<T, Team, GEN>::kkt(const T* x, const T* y, bool have_rx) 
   // dual-sign residual of rows with an infinite side (added to the dual residual in K2)
   double v4[4] = {0.0, 0.0, 0.0, 0.0};
   double rd_rows = 0.0;
-  rows_loop_tpr<double>(own.g_a, P.a_rp, P.a_ci, P.a_v, own.row0, own.row1, [&](int j) { return x[j]; },
+  rows_loop_tpr_plain<double>(own.g_a, P.a_rp, P.a_ci, P.a_v, own.row0, own.row1, [&](int j) { return x[j]; },
                         [&](int64_t r, int gl, double ax) {
                           if (gl == 0) {
                             if (GEN && P.rhi) {
@@ -269,7 +269,7 @@ __device__ bool Solver<T, Team, GEN>::kkt(const T* x, const T* y, bool have_rx) 
   if (sparse) {
     // (P~ x)_i on the owned coordinates, kept in W.sd until K2 reads it
     for (int seg = 0; seg < 6; ++seg)
-      rows_loop_tpr<double>(own.g_p, P.p_rp, P.p_ci, P.p_v, own.x0[seg], own.x1[seg], [&](int j) { return x[j]; },
+      rows_loop_tpr_plain<double>(own.g_p, P.p_rp, P.p_ci, P.p_v, own.x0[seg], own.x1[seg], [&](int j) { return x[j]; },
                             [&](int64_t i, int gl, double px) {
                               if (gl == 0) {
                                 W.sd[i] = px;
@@ -288,7 +288,7 @@ __device__ bool Solver<T, Team, GEN>::kkt(const T* x, const T* y, bool have_rx) 
   // dual residual^2, box term of the dual objective (scaled), slice term (unscaled)
   double v2[3] = {rd_rows, 0.0, 0.0};
   for (int seg = 0; seg < 6; ++seg) {
-    rows_loop_tpr<double>(
+    rows_loop_tpr_plain<double>(
         own.g_t, P.t_rp, P.t_ci, P.t_v, own.x0[seg], own.x1[seg], [&](int j) { return y[j]; },
         [&](int64_t i, int gl, double aty) {
           if (gl == 0) {
@@ -450,7 +450,20 @@ __device__ void Solver<T, Team, GEN>::run(long long budget) {
       // coordinates, it is gathered as one operand instead of two
       T* zv = W.z;
       for (int seg = 0; seg < 6; ++seg)
-        for (int64_t i = own.x0[seg] + threadIdx.x; i < own.x1[seg]; i += blockDim.x) zv[i] = T(2) * wxn[i] - hx[i];
+        for (int64_t i0 = own.x0[seg] + threadIdx.x; i0 < own.x1[seg]; i0 += 4 * (int64_t)blockDim.x) {
+          T w4[4], h4[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int64_t i = i0 + e * (int64_t)blockDim.x;
+            w4[e] = i < own.x1[seg] ? wxn[i] : T(0);
+            h4[e] = i < own.x1[seg] ? hx[i] : T(0);
+          }
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int64_t i = i0 + e * (int64_t)blockDim.x;
+            if (i < own.x1[seg]) zv[i] = T(2) * w4[e] - h4[e];
+          }
+        }
       if (!team.sync()) return;
       if (P.cb_n > 1) {
         // column blocks: every block of the team works on the same slice of z (one barrier per
@@ -459,7 +472,7 @@ __device__ void Solver<T, Team, GEN>::run(long long budget) {
         T* acc = W.cb_acc;
         for (int b = 0; b < P.cb_n; ++b) {
           const bool first = b == 0, last = b == P.cb_n - 1;
-          rows_loop_tpr<T>(kRowsBatched, P.cb_rp + (int64_t)b * P.m, P.cb_ci, P.cb_v, own.row0, own.row1,
+          rows_loop_multi<kMultiRows, T>(P.cb_rp + (int64_t)b * P.m, P.cb_ci, P.cb_v, own.row0, own.row1,
                            [&](int j) { return zv[j]; }, [&](int64_t r, int gl, T s1) {
                              if (gl != 0) return;
                              if (last) dual_row(r, 0, first ? s1 : acc[r] + s1, T(0));
@@ -475,6 +488,37 @@ __device__ void Solver<T, Team, GEN>::run(long long budget) {
     T* hxn = W.hx[hb ^ 1];
     T* wxs = W.wx[wb ^ 1];
     const T* wxp = W.wx[wb];
+    if (halpern_now && !needE && !check && !avg) {
+      // between checks: four coordinates per thread with their loads issued together (same
+      // arithmetic; the movement sum takes the same order as the general loop below)
+      constexpr int EU = 4;
+      const int64_t B = blockDim.x;
+      const T* __restrict__ axp = W.ax;
+      for (int seg = 0; seg < 6; ++seg) {
+        const int64_t a = own.x0[seg], b = own.x1[seg];
+        for (int64_t i0 = a + threadIdx.x; i0 < b; i0 += EU * B) {
+          T w[EU], h[EU], p[EU], an[EU];
+#pragma unroll
+          for (int e = 0; e < EU; ++e) {
+            const int64_t i = i0 + e * B;
+            const bool ok = i < b;
+            w[e] = ok ? wxn[i] : T(0);
+            h[e] = ok ? hx[i] : T(0);
+            p[e] = ok ? wxp[i] : T(0);
+            an[e] = ok ? axp[i] : T(0);
+          }
+#pragma unroll
+          for (int e = 0; e < EU; ++e) {
+            const int64_t i = i0 + e * B;
+            if (i >= b) break;
+            const T mv = w[e] - p[e];
+            mov_acc += mv * mv;
+            wxs[i] = w[e];
+            hxn[i] = tc1 * (tr2 * w[e] + tr1 * h[e]) + tc2 * an[e];
+          }
+        }
+      }
+    } else
     for (int seg = 0; seg < 6; ++seg) {
       const int64_t a = own.x0[seg], b = own.x1[seg];
       for (int64_t base = a + (threadIdx.x - lane); base < b; base += blockDim.x) {
