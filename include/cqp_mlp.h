@@ -45,10 +45,34 @@ int cqp_ws_features(int64_t count, const int64_t* x_off, const int64_t* n_assets
  * inputs, FP32 accumulation.  epilogue: 0 C = result (FP32), 1 C = result + bias
  * (FP32, bias has N entries), 2 C = ReLU(result + bias) (BF16), 3 C += result (FP32,
  * atomic; split_k slices of K run in parallel; C must be initialised), 4 C = result
- * (BF16).  Errors: CQP_ERR_INVALID for bad sizes or more than 65535 row tiles. */
+ * (BF16).  The product A B' (trans_a = 0, trans_b = 1) with N a multiple of 256, K a
+ * multiple of 64, lda, ldb, ldc multiples of 8, 16-byte aligned A, B, C and epilogue
+ * 0, 1, 2 or 4 runs on the fifth-generation tensor cores (tcgen05.mma into tensor
+ * memory, operands loaded by tiled tensor copies); the other forms on the warp-level
+ * tensor-core kernel.  Errors: CQP_ERR_INVALID for bad sizes or more than 65535 row
+ * tiles; asynchronous on `stream` (see cqp_gemm_check). */
 int cqp_gemm_bf16(int32_t trans_a, int32_t trans_b, int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t lda,
                   const uint16_t* B, int64_t ldb, void* C, int64_t ldc, const float* bias, int32_t epilogue,
                   int32_t split_k, void* stream);
+
+/* CQP_ERR_WAIT if a bounded wait inside one of the tensor-core GEMMs issued so far on the
+ * current device expired (it then stored nothing); CQP_OK otherwise.  Synchronises stream and
+ * clears the record. */
+int cqp_gemm_check(void* stream);
+
+/* out (cols x rows, BF16, row-major) = in' (in: rows x cols, BF16, row-major). */
+int cqp_transpose_bf16(int64_t rows, int64_t cols, const uint16_t* in, uint16_t* out, void* stream);
+
+/* Encoders of the tensor-core GEMM's descriptors, exposed for host tests (PTX ISA tcgen05
+ * shared-memory descriptor: start address, leading / stride byte offsets, version bits 46-48 =
+ * 0b001, swizzle mode in bits 61-63; instruction descriptor of kind::f16 with BF16 A and B, FP32
+ * accumulator, K-major operands, M x N). */
+uint64_t cqp_umma_smem_desc(uint32_t smem_addr, uint32_t lbo_bytes, uint32_t sbo_bytes, int32_t swizzle);
+uint32_t cqp_umma_instr_desc_bf16(int32_t m, int32_t n);
+
+/* Number of tensor-memory GEMM kernels launched by this process so far (the forms of
+ * cqp_gemm_bf16 that take the tcgen05 path); lets callers confirm which kernel ran. */
+long long cqp_gemm_tc_launches(void);
 
 /* Head forward: score_j = H2_j . w3 + b3 (FP32), x0 = softmax of the scores within each
  * instance, pooled_i = mean of H2 over the instance's assets (count x 512), ydual_i =

@@ -133,11 +133,19 @@ def lib():
         L.cqp_relu_backward_bf16.argtypes = [i64, i64, vp, vp, vp, vp]
         L.cqp_adam_step.argtypes = [i64, vp, vp, vp, vp, f32, f32, f32, f32, i64, vp, vp]
         L.cqp_ws_start.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, i64, vp, vp, vp, f32, i32, vp, vp, vp]
+        L.cqp_gemm_check.argtypes = [vp]
+        L.cqp_transpose_bf16.argtypes = [i64, i64, vp, vp, vp]
+        L.cqp_umma_smem_desc.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, i32]
+        L.cqp_umma_smem_desc.restype = C.c_uint64
+        L.cqp_umma_instr_desc_bf16.argtypes = [i32, i32]
+        L.cqp_umma_instr_desc_bf16.restype = C.c_uint32
+        L.cqp_gemm_tc_launches.argtypes = []
+        L.cqp_gemm_tc_launches.restype = C.c_longlong
         for f in ("cqp_default_options", "cqp_setup", "cqp_solve", "cqp_kkt", "cqp_spmv", "cqp_project",
                   "cqp_kkt_static", "cqp_setup_batch", "cqp_solve_batch", "cqp_setup_general", "cqp_ws_features",
                   "cqp_gemm_bf16",
                   "cqp_ws_head_forward", "cqp_ws_loss", "cqp_ws_head_backward", "cqp_relu_backward_bf16",
-                  "cqp_adam_step", "cqp_ws_start"):
+                  "cqp_adam_step", "cqp_ws_start", "cqp_gemm_check", "cqp_transpose_bf16"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -239,6 +247,15 @@ def cqp_ws_start(count, x_off, row_off, n_assets, asset_off, rank, q, R, ldr, b,
                  y0, stream=None) -> int:
     return _check(lib().cqp_ws_start(count, x_off, row_off, n_assets, asset_off, rank, q, R, ldr, b, xw, ydual,
                                      yb_scale, dual_mode, x0, y0, stream))
+
+
+def cqp_gemm_check(stream=None) -> int:
+    """Raises if a bounded wait inside a tensor-memory GEMM expired since the last check."""
+    return _check(lib().cqp_gemm_check(stream))
+
+
+def cqp_transpose_bf16(rows, cols, src, dst, stream=None) -> int:
+    return _check(lib().cqp_transpose_bf16(rows, cols, src, dst, stream))
 
 
 def cqp_free(h) -> None:

@@ -25,6 +25,10 @@
 namespace cqp {
 void record_error(const std::string& msg);
 void record_launches(long long k);
+int gemm_tc_try(int32_t trans_a, int32_t trans_b, int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t lda,
+                const uint16_t* B, int64_t ldb, void* C, int64_t ldc, const float* bias, int32_t epilogue,
+                cudaStream_t st, int* rc);
+int gemm_tc_status(cudaStream_t st);
 }  // namespace cqp
 
 namespace {
@@ -600,6 +604,11 @@ int cqp_gemm_bf16(int32_t trans_a, int32_t trans_b, int64_t M, int64_t N, int64_
   if (M < 0 || N < 0 || K < 0 || !A || !B || !C || epilogue < 0 || epilogue > 4)
     return fail_with(CQP_ERR_INVALID, "cqp_gemm_bf16: bad arguments");
   if (M == 0 || N == 0) return CQP_OK;
+  {
+    int rc = CQP_OK;
+    if (cqp::gemm_tc_try(trans_a, trans_b, M, N, K, A, lda, B, ldb, C, ldc, bias, epilogue, (cudaStream_t)stream, &rc))
+      return rc;
+  }
   const int splits = epilogue == 3 ? std::max(1, split_k) : 1;
   int64_t kc = (K + splits - 1) / splits;
   kc = (kc + TK - 1) / TK * TK;
@@ -706,3 +715,36 @@ int cqp_ws_start(int64_t count, const int64_t* x_off, const int64_t* row_off, co
 }
 
 }  // extern "C"
+
+int cqp_gemm_check(void* stream) { return cqp::gemm_tc_status((cudaStream_t)stream); }
+
+namespace {
+// 32 x 32 tiles through shared memory (padded against bank conflicts)
+__global__ void __launch_bounds__(256) k_transpose_bf16(int64_t rows, int64_t cols, const bf16* in, bf16* out) {
+  __shared__ bf16 t[32][33];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int64_t r = r0 + i, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) t[i][threadIdx.x] = in[r * cols + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int64_t c = c0 + i, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) out[c * rows + r] = t[threadIdx.x][i];
+  }
+}
+}  // namespace
+
+int cqp_transpose_bf16(int64_t rows, int64_t cols, const uint16_t* in, uint16_t* out, void* stream) {
+  if (rows < 0 || cols < 0 || (rows > 0 && cols > 0 && (!in || !out)))
+    return fail_with(CQP_ERR_INVALID, "cqp_transpose_bf16: bad arguments");
+  if (rows == 0 || cols == 0) return CQP_OK;
+  if ((cols + 31) / 32 > 2147483647 || (rows + 31) / 32 > 65535)
+    return fail_with(CQP_ERR_INVALID, "cqp_transpose_bf16: too many tiles");
+  dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32)), block(32, 8);
+  k_transpose_bf16<<<grid, block, 0, (cudaStream_t)stream>>>(rows, cols, reinterpret_cast<const bf16*>(in),
+                                                             reinterpret_cast<bf16*>(out));
+  cqp::record_launches(1);
+  MLP_CK(cudaGetLastError());
+  return CQP_OK;
+}

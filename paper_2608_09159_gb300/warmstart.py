@@ -16,7 +16,7 @@ import math
 
 import numpy as np
 
-from . import (BatchSolver, cqp_adam_step, cqp_gemm_bf16, cqp_relu_backward_bf16, cqp_ws_features,
+from . import (BatchSolver, cqp_adam_step, cqp_gemm_bf16, cqp_relu_backward_bf16, cqp_transpose_bf16, cqp_ws_features,
                cqp_ws_head_backward, cqp_ws_head_forward, cqp_ws_loss, cqp_ws_start)
 
 HID = 512
@@ -104,11 +104,15 @@ class WarmStartNet:
         self.m = {k: torch.zeros_like(v) for k, v in self.p.items()}
         self.v = {k: torch.zeros_like(v) for k, v in self.p.items()}
         self.bf = {k: torch.empty(self.p[k].shape, dtype=torch.bfloat16, device="cuda") for k in ("W1", "W2")}
+        # W2' in BF16: layer 2's forward product H1 W2 = H1 (W2')' takes the tensor-memory GEMM
+        # (A times the transpose of a K-contiguous B)
+        self.w2t = torch.empty(HID, HID, dtype=torch.bfloat16, device="cuda")
         self.step = 0
         # BF16 copies of the initial weights through the Adam kernel with a zero step
         for k in ("W1", "W2"):
             cqp_adam_step(self.p[k].numel(), _p(self.p[k]), _p(self.g[k]), _p(self.m[k]), _p(self.v[k]), 0.0, 0.9,
                           0.999, 1e-8, 1, _p(self.bf[k]))
+        cqp_transpose_bf16(HID, HID, _p(self.bf["W2"]), _p(self.w2t))
 
     def forward(self, X, asset_off, count):
         torch = self.torch
@@ -116,7 +120,7 @@ class WarmStartNet:
         H1 = torch.empty(rows, HID, dtype=torch.bfloat16, device="cuda")
         H2 = torch.empty(rows, HID, dtype=torch.bfloat16, device="cuda")
         cqp_gemm_bf16(0, 0, rows, HID, FEAT, _p(X), FEAT, _p(self.bf["W1"]), HID, _p(H1), HID, _p(self.p["b1"]), 2)
-        cqp_gemm_bf16(0, 0, rows, HID, HID, _p(H1), HID, _p(self.bf["W2"]), HID, _p(H2), HID, _p(self.p["b2"]), 2)
+        cqp_gemm_bf16(0, 1, rows, HID, HID, _p(H1), HID, _p(self.w2t), HID, _p(H2), HID, _p(self.p["b2"]), 2)
         score = torch.empty(rows, dtype=torch.float32, device="cuda")
         x0 = torch.empty(rows, dtype=torch.float32, device="cuda")
         pooled = torch.empty(count, HID, dtype=torch.float32, device="cuda")
@@ -157,6 +161,7 @@ class WarmStartNet:
         for k in PARAMS:
             cqp_adam_step(self.p[k].numel(), _p(self.p[k]), _p(self.g[k]), _p(self.m[k]), _p(self.v[k]), lr, beta1,
                           beta2, eps, self.step, _p(self.bf.get(k)))
+        cqp_transpose_bf16(HID, HID, _p(self.bf["W2"]), _p(self.w2t))
 
     def start(self, dev: BatchDevice, X=None, dual_mode: int = 1):
         """(x0, y0) of the batch (FP64 device tensors) from the network.  dual_mode: 0 primal

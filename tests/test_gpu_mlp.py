@@ -68,6 +68,67 @@ def test_gemm_bf16(gpu, ta, tb, epi):
     assert np.all(np.abs(got - ref) <= tol * bound), np.abs(got - ref).max()
 
 
+@pytest.mark.parametrize("shape", [(128, 256, 64), (300, 512, 128), (1000, 256, 576), (4100, 768, 512)])
+@pytest.mark.parametrize("epi", [0, 1, 2, 4])
+def test_gemm_tensor_memory_path(gpu, shape, epi):
+    """C = A B' with A (M x K) and B (N x K) row-major: the form that runs on tcgen05.mma with
+    the accumulator in tensor memory.  One tile (128 x 256 x 64), ragged row tiles (M = 300,
+    1000, 4100), several K slices through the four-stage ring (K = 576: nine slices, the ring
+    wraps twice), several column tiles; compared with the exact product of the same BF16
+    values, and the launch counter shows the tensor-memory kernel ran."""
+    import torch
+    M, N, K = shape
+    rng = np.random.default_rng(M + N + K + epi)
+    A = rng.normal(size=(M, K))
+    B = rng.normal(size=(N, K))
+    At, Bt = _bf16(torch, A), _bf16(torch, B)
+    Ab = At.float().cpu().numpy().astype(np.float64)
+    Bb = Bt.float().cpu().numpy().astype(np.float64)
+    ref = Ab @ Bb.T
+    bias = rng.normal(size=N).astype(np.float32)
+    bt = torch.from_numpy(bias).cuda()
+    if epi in (2, 4):
+        C = torch.full((M, N), float("nan"), dtype=torch.bfloat16, device="cuda")
+    else:
+        C = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    before = gpu.lib().cqp_gemm_tc_launches()
+    gpu.cqp_gemm_bf16(0, 1, M, N, K, At.data_ptr(), K, Bt.data_ptr(), K, C.data_ptr(), N,
+                      bt.data_ptr() if epi in (1, 2) else None, epi, 1)
+    gpu.cqp_gemm_check()
+    assert gpu.lib().cqp_gemm_tc_launches() == before + 1
+    got = C.float().cpu().numpy().astype(np.float64)
+    if epi in (1, 2):
+        ref = ref + bias
+    if epi == 2:
+        ref = np.maximum(ref, 0.0)
+    bound = np.abs(Ab) @ np.abs(Bb.T) + 1.0
+    tol = 2.0 ** -8 if epi in (2, 4) else 1e-5
+    assert np.all(np.isfinite(got))
+    assert np.all(np.abs(got - ref) <= tol * bound), np.abs(got - ref).max()
+
+
+def test_gemm_tensor_memory_path_strided(gpu):
+    """Leading dimensions above the row lengths (lda = K + 64, ldb = K + 8, ldc = N + 256): the
+    tensor maps' row strides and the epilogue's stores honour them, and the padding of C is
+    left untouched."""
+    import torch
+    M, N, K = 260, 256, 128
+    rng = np.random.default_rng(77)
+    A = _bf16(torch, rng.normal(size=(M, K + 64)))
+    B = _bf16(torch, rng.normal(size=(N, K + 8)))
+    C = torch.full((M, N + 256), 7.0, dtype=torch.float32, device="cuda")
+    before = gpu.lib().cqp_gemm_tc_launches()
+    gpu.cqp_gemm_bf16(0, 1, M, N, K, A.data_ptr(), K + 64, B.data_ptr(), K + 8, C.data_ptr(), N + 256, None, 0, 1)
+    gpu.cqp_gemm_check()
+    assert gpu.lib().cqp_gemm_tc_launches() == before + 1
+    Ab = _np(A)[:, :K]
+    Bb = _np(B)[:, :K]
+    got = C.cpu().numpy().astype(np.float64)
+    ref = Ab @ Bb.T
+    assert np.all(np.abs(got[:, :N] - ref) <= 1e-5 * (np.abs(Ab) @ np.abs(Bb.T) + 1.0))
+    assert np.all(got[:, N:] == 7.0)
+
+
 def _net_params_numpy(net):
     p = {k: v.double().cpu().numpy().copy() for k, v in net.p.items()}
     for k in ("W1", "W2"):
