@@ -584,10 +584,10 @@ def run_gemm(args):
     cases = [
         ("forward Z2 = H1 (W2')' (+bias, ReLU, BF16 out)",
          lambda: g.cqp_gemm_bf16(0, 1, rows, H, H, H1.data_ptr(), H, Wt.data_ptr(), H, out.data_ptr(), H,
-                                 bias.data_ptr(), 2), "k_gemm_tc"),
+                                 bias.data_ptr(), 2), "k_gemm_tc_persistent"),
         ("backward dH1 = dZ2 W2' (BF16 out)",
          lambda: g.cqp_gemm_bf16(0, 1, rows, H, H, H1.data_ptr(), H, Wt.data_ptr(), H, out.data_ptr(), H, None, 4),
-         "k_gemm_tc"),
+         "k_gemm_tc_persistent"),
         ("forward Z2 = H1 W2, untransposed weight (+bias, ReLU, BF16 out)",
          lambda: g.cqp_gemm_bf16(0, 0, rows, H, H, H1.data_ptr(), H, Wt.data_ptr(), H, out.data_ptr(), H,
                                  bias.data_ptr(), 2), "k_gemm_bf16"),

@@ -46,11 +46,13 @@ int cqp_ws_features(int64_t count, const int64_t* x_off, const int64_t* n_assets
  * (FP32, bias has N entries), 2 C = ReLU(result + bias) (BF16), 3 C += result (FP32,
  * atomic; split_k slices of K run in parallel; C must be initialised), 4 C = result
  * (BF16).  The product A B' (trans_a = 0, trans_b = 1) with N a multiple of 256, K a
- * multiple of 64, lda, ldb, ldc multiples of 8, 16-byte aligned A, B, C and epilogue
- * 0, 1, 2 or 4 runs on the fifth-generation tensor cores (tcgen05.mma into tensor
- * memory, operands loaded by tiled tensor copies); the other forms on the warp-level
- * tensor-core kernel.  Errors: CQP_ERR_INVALID for bad sizes or more than 65535 row
- * tiles; asynchronous on `stream` (see cqp_gemm_check). */
+ * multiple of 64, lda >= K, ldb >= K, ldc >= N all multiples of 8, 16-byte aligned A,
+ * B, C (and bias, for epilogues 1 and 2) and epilogue 0, 1, 2 or 4 runs on the
+ * fifth-generation tensor cores: a persistent kernel, tcgen05.mma into two accumulators
+ * in tensor memory, operands loaded and C stored by tiled tensor copies.  The other forms
+ * run on the warp-level tensor-core kernel.  Errors: CQP_ERR_INVALID for bad sizes, or
+ * (warp-level kernel) more than 65535 row tiles; asynchronous on `stream` (see
+ * cqp_gemm_check). */
 int cqp_gemm_bf16(int32_t trans_a, int32_t trans_b, int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t lda,
                   const uint16_t* B, int64_t ldb, void* C, int64_t ldc, const float* bias, int32_t epilogue,
                   int32_t split_k, void* stream);

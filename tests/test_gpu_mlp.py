@@ -68,14 +68,16 @@ def test_gemm_bf16(gpu, ta, tb, epi):
     assert np.all(np.abs(got - ref) <= tol * bound), np.abs(got - ref).max()
 
 
-@pytest.mark.parametrize("shape", [(128, 256, 64), (300, 512, 128), (1000, 256, 576), (4100, 768, 512)])
+@pytest.mark.parametrize("shape", [(128, 256, 64), (300, 512, 128), (1000, 256, 576), (4100, 768, 512),
+                                   (40000, 512, 256)])
 @pytest.mark.parametrize("epi", [0, 1, 2, 4])
 def test_gemm_tensor_memory_path(gpu, shape, epi):
     """C = A B' with A (M x K) and B (N x K) row-major: the form that runs on tcgen05.mma with
     the accumulator in tensor memory.  One tile (128 x 256 x 64), ragged row tiles (M = 300,
     1000, 4100), several K slices through the four-stage ring (K = 576: nine slices, the ring
-    wraps twice), several column tiles; compared with the exact product of the same BF16
-    values, and the launch counter shows the tensor-memory kernel ran."""
+    wraps twice), several column tiles, and more tiles than SMs (M = 40,000: 626 tiles, so each
+    persistent block alternates its two tensor-memory accumulators); compared with the exact
+    product of the same BF16 values, and the launch counter shows the tensor-memory kernel ran."""
     import torch
     M, N, K = shape
     rng = np.random.default_rng(M + N + K + epi)
@@ -127,6 +129,15 @@ def test_gemm_tensor_memory_path_strided(gpu):
     ref = Ab @ Bb.T
     assert np.all(np.abs(got[:, :N] - ref) <= 1e-5 * (np.abs(Ab) @ np.abs(Bb.T) + 1.0))
     assert np.all(got[:, N:] == 7.0)
+    # a bias pointer off the 16-byte grid takes the warp-level kernel, with the same result
+    bias = torch.from_numpy(rng.normal(size=N + 1).astype(np.float32)).cuda()
+    C2 = torch.empty(M, N, dtype=torch.float32, device="cuda")
+    before = gpu.lib().cqp_gemm_tc_launches()
+    gpu.cqp_gemm_bf16(0, 1, M, N, K, A.data_ptr(), K + 64, B.data_ptr(), K + 8, C2.data_ptr(), N,
+                      bias[1:].data_ptr(), 1, 1)
+    assert gpu.lib().cqp_gemm_tc_launches() == before
+    ref1 = ref + bias[1:].cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(C2.cpu().numpy() - ref1) <= 1e-5 * (np.abs(Ab) @ np.abs(Bb.T) + 1.0))
 
 
 def _net_params_numpy(net):
