@@ -123,18 +123,20 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def algorithmic_bytes(n, m, nnz, iters, inner_total, k=0, pnnz=0, esize=4, isize=4, check_every=64):
+def algorithmic_bytes(n, m, nnz, iters, inner_total, k=0, pnnz=0, esize=4, isize=4, check_every=64, vsize=None):
     """Bytes the method must move per solve, with the per-unit figures of the scope table's
     measurement section (each array element counted once per pass):
       per outer iteration, the two sparse products A'y (n rows) and A x (m rows):
           values + indices (nnz (esize + isize)) + row pointers + gathered operand + output;
       per inner BB step: R and R' (2 k n esize), the rows of a sparse P (pnnz (esize + isize) plus
           row pointers) and eight n-vectors;
-      per KKT check (every check_every iterations): the same two sparse products again."""
-    spmv_at = nnz * (esize + isize) + (n + 1) * isize + m * esize + n * esize
-    spmv_a = nnz * (esize + isize) + (m + 1) * isize + n * esize + m * esize
+      per KKT check (every check_every iterations): the same two sparse products again.
+    vsize: bytes of a stored matrix value of A, A' and P (default esize; 2 with BF16 storage)."""
+    vs = esize if vsize is None else vsize
+    spmv_at = nnz * (vs + isize) + (n + 1) * isize + m * esize + n * esize
+    spmv_a = nnz * (vs + isize) + (m + 1) * isize + n * esize + m * esize
     per_iter = spmv_at + spmv_a
-    per_inner = 2 * k * n * esize + (pnnz * (esize + isize) + (n + 1) * isize if pnnz else 0) + 8 * n * esize
+    per_inner = 2 * k * n * esize + (pnnz * (vs + isize) + (n + 1) * isize if pnnz else 0) + 8 * n * esize
     checks = iters // check_every + 1
     return iters * per_iter + inner_total * per_inner + checks * per_iter
 
@@ -452,8 +454,10 @@ def large_solve(args, steps, warmup, flush):
     inst = G.large_qp_device(n=n, m=m, seed=1005)
     torch.cuda.synchronize()
 
+    bf = int(getattr(args, "matrix_bf16", 0))
+
     def step():
-        s = g.Solver(inst, device=True, precision=0, tol=1e-4, max_iter=1000000, time_limit_s=900.0)
+        s = g.Solver(inst, device=True, precision=0, tol=1e-4, max_iter=1000000, time_limit_s=900.0, matrix_bf16=bf)
         out = s.solve(out_device=True)
         s.close()
         return out
@@ -463,7 +467,9 @@ def large_solve(args, steps, warmup, flush):
     times, (x, y, res), launches = _timed(step, steps, warmup, flush, g.cqp_kernel_launches)
     clk = clocks.stop()
     nnz, pnnz = m * 20, 2 * n
-    alg = algorithmic_bytes(n, m, nnz, res["iters"], res["inner_total"], 0, pnnz)
+    # mode 2 (A and P in BF16) is the one this workload takes: its rounded P stays a diagonal plus
+    # a weighted matching Laplacian, positive semidefinite
+    alg = algorithmic_bytes(n, m, nnz, res["iters"], res["inner_total"], 0, pnnz, vsize=2 if bf else None)
     peaks, src = _peaks()
     kern_s = res["kernel_ms"] / 1e3
     achieved = alg / kern_s / 1e9
@@ -472,12 +478,14 @@ def large_solve(args, steps, warmup, flush):
     return {"value": statistics.mean(times), "unit": "s", "steps": steps, "warmup": warmup,
             "workload": LARGE_DESC % (n, m), "n": n, "m": m, "nnz": nnz, "pnnz": pnnz,
             "inputs": "device-resident FP64, generated in device memory (Philox, index-addressed)",
+            "matrix_values": ("BF16 (A and P rounded to BF16 at setup; the rounded problem is solved and "
+                              "measured)") if bf else "FP32",
             "gpu_launches": launches,
             "solve": {"rc": res["rc"], "iters": res["iters"], "inner_total": res["inner_total"],
                       "restarts": res["restarts"], "rel_kkt": res["kkt"]["rel_kkt"], "setup_ms": res["setup_ms"],
                       "kernel_ms": res["kernel_ms"], "step_times_s": times},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": achieved / peaks["hbm_gbs"], "traffic": _ncu_traffic("large"),
+                         "frac": achieved / peaks["hbm_gbs"], "traffic": None if bf else _ncu_traffic("large"),
                          "peak_source": src, "kernel": "pdhg_grid_kernel<float, false>",
                          "algorithmic_bytes_per_solve": alg, "kernel_s_per_solve": kern_s},
             "clocks": clk}
@@ -496,7 +504,7 @@ def run_large(args):
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (Philox-seeded, generated in device memory)",
             "config": {"workload": rec["workload"], "n": rec["n"], "m": rec["m"], "nnz": rec["nnz"],
-                       "pnnz": rec["pnnz"], "inputs": rec["inputs"]},
+                       "pnnz": rec["pnnz"], "inputs": rec["inputs"], "matrix_values": rec["matrix_values"]},
             "gpu_launches": rec["gpu_launches"], "solve": rec["solve"], "roofline": rec["roofline"],
             "clocks": rec["clocks"]}
     print(json.dumps(line), flush=True)
@@ -706,6 +714,8 @@ def main():
     ap.add_argument("--ws-train", type=int, default=0, help="portfolio: instances to train the warm start on")
     ap.add_argument("--ws-steps", type=int, default=3000, help="portfolio: warm-start training steps")
     ap.add_argument("--large-n", type=float, default=2e8, help="large: number of variables")
+    ap.add_argument("--matrix-bf16", type=int, default=0,
+                    help="large: 2 = BF16-stored values of A, A' and P (the BF16-rounded problem is solved)")
     args = ap.parse_args()
     if args.workload != "socp" and args.impl == "ours":
         {"portfolio": run_portfolio, "large": run_large, "gemm": run_gemm, "lasso": run_frontend,

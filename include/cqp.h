@@ -148,6 +148,17 @@ typedef struct {
   int32_t warm_roots;       /* 1: start each cone block's root-finding from its previous root (default 1) */
   int32_t col_blocks;       /* dual step's product A z over column blocks whose slice of z stays in L2:
                                0 auto (on when z exceeds 64 MB: 8 blocks), 1 off, K >= 2 forces K blocks (<= 64) */
+  int32_t matrix_bf16;      /* 1: BF16-stored values of A and A'; 2: of A, A' and the sparse part P of Q.
+                               FP32 accumulation; precision 0, single problems, whole-GPU team only.  The
+                               stored values are rounded to BF16 at setup (to FP32, then to BF16,
+                               nearest-even each): the problem solved and reported by cqp_kkt is the one
+                               with those rounded values.  With 2 the caller must know the rounded P is
+                               still positive semidefinite: it is when P is diagonal or a weighted graph
+                               Laplacian (both signs of a weight round alike), not in general (entrywise
+                               rounding of a matrix with small eigenvalues can make it indefinite).  The
+                               Ruiz, Pock-Chambolle and bound-objective factors are rounded to powers of
+                               two, so the scaled values stay exactly representable.  0 (default): values
+                               in the iterate precision */
   void* stream;             /* cudaStream_t, NULL = default stream */
 } cqp_options;
 
@@ -289,7 +300,8 @@ int cqp_solve_batch(cqp_handle* h, const double* x0, const double* y0, double* x
 /* y = A x with the CSR kernel of the solver (threads_per_row: 1, 2, 4, 8, 16 or 32 lanes per
  * row; 0 = chosen from the mean row length; -1 = one lane per row with four rows in flight
  * per lane, the solver's variant for short rows whose latency chains would otherwise bind).
- * Returns CQP_ERR_INVALID for bad sizes. */
+ * precision 2: val holds BF16 values (uint16 bit patterns), x and y are float*, sums in FP32
+ * (the product of the matrix_bf16 mode).  Returns CQP_ERR_INVALID for bad sizes. */
 int cqp_spmv(int32_t precision, int64_t nrows, int64_t ncols, const int32_t* rowptr, const int32_t* colind,
              const void* val, const void* x, void* y, int32_t threads_per_row, void* stream);
 

@@ -623,6 +623,31 @@ CONFIGS = {
 # config 5 (n = 2e8, m = 5e7, 1e9 nonzeros) is generated on the device: instances.gpu.large_qp_device
 
 
+def round_bf16(a) -> np.ndarray:
+    """Values rounded to FP32, then to BF16 (round to nearest, ties to even, at each step),
+    returned as FP64: the matrix values a solve with BF16 matrix storage works with."""
+    f = np.ascontiguousarray(a, dtype=np.float64).astype(np.float32)
+    bits = f.view(np.uint32).astype(np.uint64)
+    bits = (bits + 0x7FFF + ((bits >> 16) & 1)) & 0xFFFF0000
+    return bits.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def bf16_bits(a) -> np.ndarray:
+    """The BF16 bit patterns (uint16) of round_bf16(a)."""
+    r = round_bf16(a).astype(np.float32)
+    return (r.view(np.uint32) >> 16).astype(np.uint16)
+
+
+def with_bf16_matrices(inst: dict, p: bool = True) -> dict:
+    """A copy of the instance with the values of A (and, if p, of the sparse part P of Q)
+    rounded as round_bf16 rounds them."""
+    out = dict(inst)
+    out["a_val"] = round_bf16(inst["a_val"])
+    if p and inst.get("p_val") is not None:
+        out["p_val"] = round_bf16(inst["p_val"])
+    return out
+
+
 def small_config(k: int):
     """Scaled-down copies with the same structure, for oracle-speed parity tests."""
     if k == 1:

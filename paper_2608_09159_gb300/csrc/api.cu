@@ -12,6 +12,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -306,6 +307,11 @@ struct Handle : HandleBase {
     // segment table in the new order: free, nonneg, soc, rsoc, exp, pow (stable within a type)
     std::vector<int64_t> seg_new, seg_old;
     if (B && o.rescaled_cones) fail(CQP_ERR_UNSUPPORTED, "rescaled-cone mode in a batch");
+    if (o.matrix_bf16 < 0 || o.matrix_bf16 > 2) fail(CQP_ERR_INVALID, "matrix_bf16 must be 0, 1 or 2");
+    const bool bf = o.matrix_bf16 != 0;      // A and A' values in BF16
+    const bool bfp = o.matrix_bf16 == 2;     // and the sparse part P of Q
+    if (bf && (B || !std::is_same<T, float>::value))
+      fail(CQP_ERR_UNSUPPORTED, "matrix_bf16 needs FP32 iterates (precision 0) and a single problem");
     std::vector<int64_t> soc_off{0}, rsoc_off{0};
     std::vector<double> pow_al;
     std::vector<double> exp_sl, pow_sl;   // 1 for a slice block, 0 for a cone, in segment order
@@ -511,6 +517,7 @@ struct Handle : HandleBase {
     count_launch(); cqp::k_copy_rowptr32<<<cqp::grid_for(m + 1), cqp::kSetupThreads, 0, st>>>(m + 1, a_rp64, a_rp);
     count_launch(); cqp::k_remap_cols<<<cqp::grid_for(nnz), cqp::kSetupThreads, 0, st>>>(nnz, iperm, a_ci_in, a_ci);
     CK(cudaMemcpyAsync(av, a_v_in, nnz * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (bf && nnz > 0) { count_launch(); cqp::k_round_bf16<<<cqp::grid_for(nnz), cqp::kSetupThreads, 0, st>>>(nnz, av); }
     double* cv = tmp.alloc<double>(n);
     double* qv = tmp.alloc<double>(n);
     double* bv = tmp.alloc<double>(std::max<int64_t>(m, 1));
@@ -542,6 +549,7 @@ struct Handle : HandleBase {
       dev_scan(len, p_rp, n, tmp, st);
       count_launch(); cqp::k_copy_rows_perm<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, perm, iperm, p_rp64, p_ci_in, p_v_in,
                                                                                 p_rp, p_ci, pv);
+      if (bfp && pnnz > 0) { count_launch(); cqp::k_round_bf16<<<cqp::grid_for(pnnz), cqp::kSetupThreads, 0, st>>>(pnnz, pv); }
     }
     // ---- transpose of A (deterministic: every row of A' sorted by row of A) ------------
     int32_t* t_rp = mem.alloc<int32_t>(n + 1);
@@ -589,6 +597,10 @@ struct Handle : HandleBase {
       if (n_pow) { count_launch(); cqp::k_aggregate_blocks<<<cqp::grid_for(n_pow), cqp::kSetupThreads, 0, st>>>(n_pow, nullptr, base[5], 3, mode, colf); }
     };
     auto scale_step = [&]() {
+      if (bf) {   // power-of-two factors keep the BF16 values of A and P exact
+        count_launch(); cqp::k_pow2_round<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, colf);
+        if (m > 0) { count_launch(); cqp::k_pow2_round<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, rowf); }
+      }
       count_launch(); cqp::k_scale_matrix<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp, a_ci, av, rowf, colf);
       count_launch(); cqp::k_mul<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, col, colf);
       if (m > 0) { count_launch(); cqp::k_mul<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, row, rowf); }
@@ -631,6 +643,10 @@ struct Handle : HandleBase {
     } else if (o.bound_obj) {
       beta_b = bound_norm(bv, bhv) + 1.0;
       beta_c = std::sqrt(dev_dot(cv, nullptr, n, part, one, st)) + 1.0;
+      if (bf) {
+        beta_b = cqp::pow2_round(beta_b);
+        beta_c = cqp::pow2_round(beta_c);
+      }
       if (m > 0) { count_launch(); cqp::k_scal<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, bv, 1.0 / beta_b); }
       if (bhv) { count_launch(); cqp::k_scal<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, bhv, 1.0 / beta_b); }
       count_launch(); cqp::k_scal<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, cv, 1.0 / beta_c);
@@ -642,10 +658,20 @@ struct Handle : HandleBase {
     // full diagonal of Q~ (Jacobi metric) and conversion to the iterate precision
     double* jdv = tmp.alloc<double>(n);
     count_launch(); cqp::k_full_diag<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, qv, p_rp, p_ci, pv, k, Rv, Dv, jdv);
-    T* a_v = mem.alloc<T>(nnz);
-    T* t_v = mem.alloc<T>(nnz);
+    // in the BF16 mode the iterate-precision copies serve only the norm estimate and the
+    // autotuner during setup; the handle keeps the BF16 ones
+    T* a_v = bf ? tmp.alloc<T>(nnz) : mem.alloc<T>(nnz);
+    T* t_v = bf ? tmp.alloc<T>(nnz) : mem.alloc<T>(nnz);
     count_launch(); cqp::k_convert<T><<<cqp::grid_for(nnz), cqp::kSetupThreads, 0, st>>>(nnz, av, a_v);
     count_launch(); cqp::k_gather_convert<T><<<cqp::grid_for(nnz), cqp::kSetupThreads, 0, st>>>(nnz, tmap, av, t_v);
+    __nv_bfloat16* a_vb = nullptr;
+    __nv_bfloat16* t_vb = nullptr;
+    if (bf && nnz > 0) {
+      a_vb = mem.alloc<__nv_bfloat16>(nnz);
+      t_vb = mem.alloc<__nv_bfloat16>(nnz);
+      count_launch(); cqp::k_to_bf16<<<cqp::grid_for(nnz), cqp::kSetupThreads, 0, st>>>(nnz, nullptr, av, a_vb);
+      count_launch(); cqp::k_to_bf16<<<cqp::grid_for(nnz), cqp::kSetupThreads, 0, st>>>(nnz, tmap, av, t_vb);
+    }
     T* cT = mem.alloc<T>(n);
     T* bT = mem.alloc<T>(std::max<int64_t>(m, 1));
     T* qT = mem.alloc<T>(n);
@@ -684,9 +710,14 @@ struct Handle : HandleBase {
       count_launch(); cqp::k_convert<T><<<cqp::grid_for(k * n), cqp::kSetupThreads, 0, st>>>(k * n, Rv, RT);
     }
     T* pT = nullptr;
+    __nv_bfloat16* pTb = nullptr;
     if (has_p) {
-      pT = mem.alloc<T>(pnnz);
+      pT = bfp ? tmp.alloc<T>(pnnz) : mem.alloc<T>(pnnz);
       count_launch(); cqp::k_convert<T><<<cqp::grid_for(pnnz), cqp::kSetupThreads, 0, st>>>(pnnz, pv, pT);
+      if (bfp && pnnz > 0) {
+        pTb = mem.alloc<__nv_bfloat16>(pnnz);
+        count_launch(); cqp::k_to_bf16<<<cqp::grid_for(pnnz), cqp::kSetupThreads, 0, st>>>(pnnz, nullptr, pv, pTb);
+      }
     }
     double* palpha = nullptr;
     if (!pow_al.empty()) {
@@ -716,6 +747,7 @@ struct Handle : HandleBase {
     int* cb_rp = nullptr;
     int* cb_ci = nullptr;
     T* cb_v = nullptr;
+    __nv_bfloat16* cb_vb = nullptr;
     {
       const double zbytes = (double)n * sizeof(T);
       if (o.col_blocks >= 2) cb_n = std::min(o.col_blocks, 64);
@@ -727,10 +759,15 @@ struct Handle : HandleBase {
         int* cnt = tmp.alloc<int>((int64_t)cb_n * m);
         cb_rp = mem.alloc<int>((int64_t)cb_n * m + 1);
         cb_ci = mem.alloc<int>(nnz);
-        cb_v = mem.alloc<T>(nnz);
         count_launch(); cqp::k_cb_count<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp, a_ci, width, cb_n, cnt);
         dev_scan(cnt, cb_rp, (int64_t)cb_n * m, tmp, st);
-        count_launch(); cqp::k_cb_scatter<T><<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp, a_ci, a_v, width, cb_n, cb_rp, cb_ci, cb_v);
+        if (a_vb) {
+          cb_vb = mem.alloc<__nv_bfloat16>(nnz);
+          count_launch(); cqp::k_cb_scatter<__nv_bfloat16><<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp, a_ci, a_vb, width, cb_n, cb_rp, cb_ci, cb_vb);
+        } else {
+          cb_v = mem.alloc<T>(nnz);
+          count_launch(); cqp::k_cb_scatter<T><<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp, a_ci, a_v, width, cb_n, cb_rp, cb_ci, cb_v);
+        }
       }
     }
     // Euclidean projections suffice when the diagonal Q vanishes on every cone coordinate
@@ -810,8 +847,9 @@ struct Handle : HandleBase {
     }
     // ---- problem descriptor ----------------------------------------------------------------
     P.n = n; P.m = m;
-    P.a_rp = a_rp; P.a_ci = a_ci; P.a_v = a_v;
-    P.t_rp = t_rp; P.t_ci = t_ci; P.t_v = t_v;
+    P.a_rp = a_rp; P.a_ci = a_ci; P.a_v = bf ? nullptr : a_v;
+    P.t_rp = t_rp; P.t_ci = t_ci; P.t_v = bf ? nullptr : t_v;
+    P.a_vb = a_vb; P.t_vb = t_vb; P.p_vb = pTb; P.cb_vb = cb_vb;
     P.qd = qT; P.jd = jT; P.k = (int)k; P.kpad = (int)kpad; P.R = RT; P.D = Dv;
     // D = d I (the common case) lets the kernel skip the k x k products
     P.d_scale = 0.0;
@@ -825,7 +863,7 @@ struct Handle : HandleBase {
           if ((a == b2 && hD[a * k + b2] != hD[0]) || (a != b2 && hD[a * k + b2] != 0.0)) ident = false;
       if (ident) P.d_scale = hD[0];
     }
-    P.p_rp = p_rp; P.p_ci = p_ci; P.p_v = pT;
+    P.p_rp = p_rp; P.p_ci = p_ci; P.p_v = bfp ? nullptr : pT;
     P.c = cT; P.b = bT; P.col = col; P.row = row; P.beta_b = beta_b; P.beta_c = beta_c;
     P.rhi = rhiT; P.xlo = xloT; P.xhi = xhiT; P.csc = cscT;
     P.n_free = cnt[0]; P.n_nonneg = cnt[1];
@@ -940,7 +978,9 @@ struct Handle : HandleBase {
     // distributed-shared-memory reductions), or on one block where no cluster fits
     const int64_t size = n + m;
     if (!batched) {
-      if (o.team == 1 || (o.team == 0 && size > 4096)) team = cqp::kTeamGrid;
+      if (bf && o.team != 0 && o.team != 1)
+        fail(CQP_ERR_UNSUPPORTED, "matrix_bf16 runs on the whole-GPU team (team 0 or 1)");
+      if (o.team == 1 || (o.team == 0 && (size > 4096 || bf))) team = cqp::kTeamGrid;
       else if (o.team == 2) team = cqp::kTeamCta;
       else team = cqp::kTeamCluster;
     }
@@ -1296,6 +1336,7 @@ int cqp_default_options(cqp_options* o) {
   o->step_factor = 0.998;
   o->warm_roots = 1;
   o->col_blocks = 0;
+  o->matrix_bf16 = 0;
   return CQP_OK;
 }
 
@@ -1430,6 +1471,9 @@ int cqp_spmv(int32_t precision, int64_t nrows, int64_t ncols, const int32_t* row
     count_launch();
     if (precision == 1)
       CK(cqp::launch_spmv<double>(nrows, rowptr, colind, (const double*)val, (const double*)x, (double*)y, tpr, st));
+    else if (precision == 2)
+      CK(cqp::launch_spmv_bf16<float>(nrows, rowptr, colind, (const __nv_bfloat16*)val, (const float*)x, (float*)y, tpr,
+                                      st));
     else
       CK(cqp::launch_spmv<float>(nrows, rowptr, colind, (const float*)val, (const float*)x, (float*)y, tpr, st));
     CK(cudaStreamSynchronize(st));

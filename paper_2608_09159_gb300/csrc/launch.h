@@ -55,6 +55,9 @@ template <typename T>
 cudaError_t launch_spmv(int64_t nrows, const int* rp, const int* ci, const T* v, const T* x, T* y, int tpr,
                         cudaStream_t st, int blocks = 0);
 template <typename T>
+cudaError_t launch_spmv_bf16(int64_t nrows, const int* rp, const int* ci, const __nv_bfloat16* v, const T* x, T* y,
+                             int tpr, cudaStream_t st, int blocks = 0);
+template <typename T>
 cudaError_t launch_project(int64_t nblocks, const int32_t* type, const int64_t* start, const int64_t* dim,
                            const double* alpha, const T* r, const T* m, T* out, int64_t n, cudaStream_t st);
 

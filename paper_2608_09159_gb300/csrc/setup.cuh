@@ -5,6 +5,8 @@
 
 #include <cstdint>
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace cqp {
@@ -296,6 +298,28 @@ __global__ void k_cb_scatter(int64_t rows, const int* rp, const int* ci, const T
 // *bad = 1 unless rp[r] = L r for every r <= rows (rows of exactly L entries)
 __global__ void k_check_uniform(int64_t rows, const int* rp, int L, int* bad) {
   CQP_GRID_LOOP(r, rows + 1) if ((int64_t)rp[r] != (int64_t)L * r) *bad = 1;
+}
+
+// BF16 matrix storage: v <- BF16(FP32(v)), rounding to nearest even at each step
+__global__ void k_round_bf16(int64_t n, double* v) {
+  CQP_GRID_LOOP(i, n) v[i] = (double)__bfloat162float(__float2bfloat16_rn((float)v[i]));
+}
+
+// f <- 2^round(log2 f) for positive finite f (the power of two nearest in ratio: a mantissa
+// m in [1/2, 1) rounds up at m >= 1/sqrt 2); scaling by such factors keeps BF16 values exact
+__host__ __device__ inline double pow2_round(double f) {
+  if (!(f > 0.0) || !isfinite(f)) return f;
+  int e = 0;
+  const double m = frexp(f, &e);
+  return ldexp(1.0, m >= 0.70710678118654752440 ? e : e - 1);
+}
+__global__ void k_pow2_round(int64_t n, double* f) {
+  CQP_GRID_LOOP(i, n) f[i] = pow2_round(f[i]);
+}
+
+// out[i] = BF16(in[map[i]]) (map null: in[i]); the values are exactly representable here
+__global__ void k_to_bf16(int64_t n, const int32_t* map, const double* in, __nv_bfloat16* out) {
+  CQP_GRID_LOOP(i, n) out[i] = __float2bfloat16_rn((float)in[map ? map[i] : i]);
 }
 
 // slice blocks: fix[e] = flag[e] * col[base + 3 e + 1] / beta_b (flag 1 for a slice, 0 for a cone)

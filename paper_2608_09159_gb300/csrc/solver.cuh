@@ -30,6 +30,10 @@
 // uses two passes per iteration.
 #pragma once
 
+#include <cuda_bf16.h>
+
+#include <type_traits>
+
 #include "common.cuh"
 #include "cones.cuh"
 
@@ -48,6 +52,9 @@ struct Prob {
   int kpad;                                            // rows of R as stored: k rounded up to 8, rows >= k zero
   double d_scale;                                     // D = d_scale * I when > 0 (else general D)
   const int* p_rp; const int* p_ci; const T* p_v;     // scaled sparse P (n rows) or null
+  // BF16-stored matrix values (FP32 iterates only): when set, the products read these in place of
+  // a_v, t_v, p_v, cb_v (the same scaled values, exactly representable in BF16)
+  const __nv_bfloat16* a_vb; const __nv_bfloat16* t_vb; const __nv_bfloat16* p_vb; const __nv_bfloat16* cb_vb;
   const T* c; const T* b;                             // scaled c, b (general form: b holds the row lower bounds)
   const double* col; const double* row;               // x = beta_b x~/col, y = beta_c y~/row
   double beta_b, beta_c, norm_b, norm_c;              // ||b||, ||c|| of the unscaled data
@@ -198,6 +205,14 @@ __device__ void make_own(const Prob<T>& P, int b, int nb, Own& o) {
 constexpr int kUnroll = 4;
 template <int G> struct RowBatch { static constexpr int value = G <= 2 ? 8 : 4; };
 
+// A stored matrix value in the accumulation type (FP32, FP64 or BF16 storage).
+template <typename Acc>
+__device__ __forceinline__ Acc ld_val(const float* p) { return (Acc)__ldg(p); }
+template <typename Acc>
+__device__ __forceinline__ Acc ld_val(const double* p) { return (Acc)__ldg(p); }
+template <typename Acc>
+__device__ __forceinline__ Acc ld_val(const __nv_bfloat16* p) { return (Acc)__bfloat162float(__ldg(p)); }
+
 template <int G, typename Acc, typename T, typename X>
 __device__ __forceinline__ Acc seg_dot(const int* __restrict__ ci, const T* __restrict__ v, int beg, int end, int gl,
                                        X xf) {
@@ -205,19 +220,19 @@ __device__ __forceinline__ Acc seg_dot(const int* __restrict__ ci, const T* __re
   Acc s = Acc(0);
   for (int k = beg + gl; k < end; k += U * G) {
     int j[U];
-    T a[U];
+    Acc a[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int kk = k + u * G;
       const bool ok = kk < end;
       j[u] = ok ? __ldg(ci + kk) : -1;
-      a[u] = ok ? __ldg(v + kk) : T(0);
+      a[u] = ok ? ld_val<Acc>(v + kk) : Acc(0);
     }
     Acc g[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) g[u] = j[u] >= 0 ? (Acc)xf(j[u]) : Acc(0);
 #pragma unroll
-    for (int u = 0; u < U; ++u) s += (Acc)a[u] * g[u];
+    for (int u = 0; u < U; ++u) s += a[u] * g[u];
   }
   return s;
 }
@@ -286,7 +301,7 @@ __device__ __forceinline__ void rows_loop_multi(const int* rp, const int* ci, co
     for (int q = 0; q < RB; ++q) len = max(len, end[q] - beg[q]);
     for (int k = 0; k < len; k += kMultiU) {
       int j[RB][kMultiU];
-      T a[RB][kMultiU];
+      Acc a[RB][kMultiU];
 #pragma unroll
       for (int q = 0; q < RB; ++q)
 #pragma unroll
@@ -294,7 +309,7 @@ __device__ __forceinline__ void rows_loop_multi(const int* rp, const int* ci, co
           const int kk = beg[q] + k + u;
           const bool ok = kk < end[q];
           j[q][u] = ok ? __ldg(ci + kk) : -1;
-          a[q][u] = ok ? __ldg(v + kk) : T(0);
+          a[q][u] = ok ? ld_val<Acc>(v + kk) : Acc(0);
         }
       Acc g[RB][kMultiU];
 #pragma unroll
@@ -304,7 +319,7 @@ __device__ __forceinline__ void rows_loop_multi(const int* rp, const int* ci, co
 #pragma unroll
       for (int q = 0; q < RB; ++q)
 #pragma unroll
-        for (int u = 0; u < kMultiU; ++u) s[q] += (Acc)a[q][u] * g[q][u];
+        for (int u = 0; u < kMultiU; ++u) s[q] += a[q][u] * g[q][u];
     }
 #pragma unroll
     for (int q = 0; q < RB; ++q) {
@@ -373,6 +388,20 @@ struct Solver {
 
   // ---- small helpers -------------------------------------------------------
   __device__ __forceinline__ int nwarps() const { return blockDim.x >> 5; }
+  // Runs fn(values) with the BF16 copy of a matrix's values when there is one, else with the
+  // iterate-precision copy.  BF16 storage is compiled into the whole-GPU FP32 solver only (the
+  // setup runs matrix_bf16 handles on that team).
+  static constexpr bool kBf16 = std::is_same<T, float>::value && std::is_same<Team, GridTeam>::value;
+  template <typename F>
+  __device__ __forceinline__ void vals(const T* v, const __nv_bfloat16* vb, F&& fn) const {
+    if constexpr (kBf16) {
+      if (vb) {
+        fn(vb);
+        return;
+      }
+    }
+    fn(v);
+  }
   static __device__ __forceinline__ unsigned long long now_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -594,12 +623,14 @@ struct Solver {
 
   // ---- A' products: v = h_x + tau A' h_y on the owned coordinates -----------
   __device__ void phase_aty(const T* hx, const T* hy, double tau) {
-    for (int seg = 0; seg < 6; ++seg) {
-      rows_loop_tpr<T>(own.g_t, P.t_rp, P.t_ci, P.t_v, own.x0[seg], own.x1[seg], [&](int j) { return hy[j]; },
-                       [&](int64_t i, int gl, T s) {
-                         if (gl == 0) W.v[i] = hx[i] + T(tau) * s;
-                       });
-    }
+    vals(P.t_v, P.t_vb, [&](auto tv) {
+      for (int seg = 0; seg < 6; ++seg) {
+        rows_loop_tpr<T>(own.g_t, P.t_rp, P.t_ci, tv, own.x0[seg], own.x1[seg], [&](int j) { return hy[j]; },
+                         [&](int64_t i, int gl, T s) {
+                           if (gl == 0) W.v[i] = hx[i] + T(tau) * s;
+                         });
+      }
+    });
     __syncthreads();
   }
 
@@ -807,15 +838,15 @@ struct Solver {
   // (no low-rank part): each row's vector operands are loaded with its entries, ahead of the
   // gathers, instead of after the row sum and behind the previous row's store.  Same
   // arithmetic in the same order as the generic loop.
-  __device__ T grad_rows_batched(const T* u, const T* uprev, const T* gprev, T* gout, T itau, bool first, int64_t r0,
-                                 int64_t r1) {
+  template <typename V>
+  __device__ T grad_rows_batched(const V* __restrict__ pv, const T* u, const T* uprev, const T* gprev, T* gout, T itau,
+                                 bool first, int64_t r0, int64_t r1) {
     constexpr int RB = kMultiRows, U = kMultiU;
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5;
     const int ulen = P.p_ulen;
     const int* __restrict__ rp = P.p_rp;
     const int* __restrict__ ci = P.p_ci;
-    const T* __restrict__ pv = P.p_v;
     T acc = T(0);
     for (int64_t base = warp * 32 * RB; base < r1 - r0; base += nwarps * 32 * RB) {
       int beg[RB], end[RB];
@@ -852,7 +883,7 @@ struct Solver {
             const int kk = beg[q] + k + t;
             const bool ok = kk < end[q];
             j[q][t] = ok ? __ldg(ci + kk) : -1;
-            a[q][t] = ok ? __ldg(pv + kk) : T(0);
+            a[q][t] = ok ? ld_val<T>(pv + kk) : T(0);
           }
         T gth[RB][U];
 #pragma unroll
@@ -883,23 +914,28 @@ struct Solver {
     const T* w = wvec();
     T acc = T(0);
     if (own.g_p == kRowsBatched && P.k == 0) {
-      for (int seg = 0; seg < 6; ++seg) acc += grad_rows_batched(u, uprev, gprev, gout, itau, first, own.x0[seg], own.x1[seg]);
+      vals(P.p_v, P.p_vb, [&](auto pv) {
+        for (int seg = 0; seg < 6; ++seg)
+          acc += grad_rows_batched(pv, u, uprev, gprev, gout, itau, first, own.x0[seg], own.x1[seg]);
+      });
       v2[0] = (double)acc;
       v2[1] = 0.0;
       __syncthreads();
       return;
     }
     for (int seg = 0; seg < 6; ++seg) {
-      rows_loop_tpr<T>(own.g_p, P.p_rp, P.p_ci, P.p_v, own.x0[seg], own.x1[seg], [&](int j) { return u[j]; },
-                       [&](int64_t i, int gl, T pu) {
-                         if (gl == 0) {
-                           T g = pu + P.qd[i] * u[i] + P.c[i] + (u[i] - W.v[i]) * itau;
-                           if (P.k > 0) g += rtw(i, w);
-                           gout[i] = g;
-                           if (!first) acc += (u[i] - uprev[i]) * (g - gprev[i]);
-                         }
-                       },
-                       P.p_ulen);
+      vals(P.p_v, P.p_vb, [&](auto pv) {
+        rows_loop_tpr<T>(own.g_p, P.p_rp, P.p_ci, pv, own.x0[seg], own.x1[seg], [&](int j) { return u[j]; },
+                         [&](int64_t i, int gl, T pu) {
+                           if (gl == 0) {
+                             T g = pu + P.qd[i] * u[i] + P.c[i] + (u[i] - W.v[i]) * itau;
+                             if (P.k > 0) g += rtw(i, w);
+                             gout[i] = g;
+                             if (!first) acc += (u[i] - uprev[i]) * (g - gprev[i]);
+                           }
+                         },
+                         P.p_ulen);
+      });
     }
     v2[0] = (double)acc;
     v2[1] = 0.0;

@@ -20,13 +20,13 @@ __device__ __forceinline__ void rows_loop2(const int* rp, const int* ci, const T
       constexpr int U = RowBatch<G>::value;
       for (int k = beg + gl; k < end; k += U * G) {
         int j[U];
-        T a[U];
+        Acc a[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int kk = k + u * G;
           const bool okk = kk < end;
           j[u] = okk ? __ldg(ci + kk) : -1;
-          a[u] = okk ? __ldg(v + kk) : T(0);
+          a[u] = okk ? ld_val<Acc>(v + kk) : Acc(0);
         }
         Acc g1[U], g2[U];
 #pragma unroll
@@ -36,8 +36,8 @@ __device__ __forceinline__ void rows_loop2(const int* rp, const int* ci, const T
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          s1 += (Acc)a[u] * g1[u];
-          s2 += (Acc)a[u] * g2[u];
+          s1 += a[u] * g1[u];
+          s2 += a[u] * g2[u];
         }
       }
     }
@@ -227,28 +227,30 @@ __device__ bool Solver<T, Team, GEN>::kkt(const T* x, const T* y, bool have_rx) 
   // dual-sign residual of rows with an infinite side (added to the dual residual in K2)
   double v4[4] = {0.0, 0.0, 0.0, 0.0};
   double rd_rows = 0.0;
-  rows_loop_tpr_plain<double>(own.g_a, P.a_rp, P.a_ci, P.a_v, own.row0, own.row1, [&](int j) { return x[j]; },
-                        [&](int64_t r, int gl, double ax) {
-                          if (gl == 0) {
-                            if (GEN && P.rhi) {
-                              const double lo = (double)P.b[r], hi = (double)P.rhi[r];
-                              const double res = P.beta_b * P.row[r] * (ax - fmin(fmax(ax, lo), hi));
-                              v4[0] += res * res;
-                              const double yr = (double)y[r];
-                              if (lo == hi) {
-                                v4[1] += lo * yr;
-                              } else if (yr != 0.0) {
-                                const double bd = yr > 0.0 ? lo : hi;
-                                if (isfinite(bd)) v4[1] += bd * yr;
-                                else { const double yu = P.beta_c * yr / P.row[r]; rd_rows += yu * yu; }
+  vals(P.a_v, P.a_vb, [&](auto av) {
+    rows_loop_tpr_plain<double>(own.g_a, P.a_rp, P.a_ci, av, own.row0, own.row1, [&](int j) { return x[j]; },
+                          [&](int64_t r, int gl, double ax) {
+                            if (gl == 0) {
+                              if (GEN && P.rhi) {
+                                const double lo = (double)P.b[r], hi = (double)P.rhi[r];
+                                const double res = P.beta_b * P.row[r] * (ax - fmin(fmax(ax, lo), hi));
+                                v4[0] += res * res;
+                                const double yr = (double)y[r];
+                                if (lo == hi) {
+                                  v4[1] += lo * yr;
+                                } else if (yr != 0.0) {
+                                  const double bd = yr > 0.0 ? lo : hi;
+                                  if (isfinite(bd)) v4[1] += bd * yr;
+                                  else { const double yu = P.beta_c * yr / P.row[r]; rd_rows += yu * yu; }
+                                }
+                              } else {
+                                const double res = P.beta_b * P.row[r] * (ax - (double)P.b[r]);
+                                v4[0] += res * res;
+                                v4[1] += (double)P.b[r] * (double)y[r];
                               }
-                            } else {
-                              const double res = P.beta_b * P.row[r] * (ax - (double)P.b[r]);
-                              v4[0] += res * res;
-                              v4[1] += (double)P.b[r] * (double)y[r];
                             }
-                          }
-                        });
+                          });
+  });
   const bool need_r = k > 0 && !have_rx;
   const int lane = threadIdx.x & 31;
   for (int seg = 0; seg < 6; ++seg) {
@@ -269,13 +271,15 @@ __device__ bool Solver<T, Team, GEN>::kkt(const T* x, const T* y, bool have_rx) 
   if (sparse) {
     // (P~ x)_i on the owned coordinates, kept in W.sd until K2 reads it
     for (int seg = 0; seg < 6; ++seg)
-      rows_loop_tpr_plain<double>(own.g_p, P.p_rp, P.p_ci, P.p_v, own.x0[seg], own.x1[seg], [&](int j) { return x[j]; },
-                            [&](int64_t i, int gl, double px) {
-                              if (gl == 0) {
-                                W.sd[i] = px;
-                                v5[4] += (double)x[i] * px;
-                              }
-                            });
+      vals(P.p_v, P.p_vb, [&](auto pv) {
+        rows_loop_tpr_plain<double>(own.g_p, P.p_rp, P.p_ci, pv, own.x0[seg], own.x1[seg], [&](int j) { return x[j]; },
+                              [&](int64_t i, int gl, double px) {
+                                if (gl == 0) {
+                                  W.sd[i] = px;
+                                  v5[4] += (double)x[i] * px;
+                                }
+                              });
+      });
   }
   __syncthreads();
   publish<5>(v5, 0, need_r);
@@ -288,28 +292,30 @@ __device__ bool Solver<T, Team, GEN>::kkt(const T* x, const T* y, bool have_rx) 
   // dual residual^2, box term of the dual objective (scaled), slice term (unscaled)
   double v2[3] = {rd_rows, 0.0, 0.0};
   for (int seg = 0; seg < 6; ++seg) {
-    rows_loop_tpr_plain<double>(
-        own.g_t, P.t_rp, P.t_ci, P.t_v, own.x0[seg], own.x1[seg], [&](int j) { return y[j]; },
-        [&](int64_t i, int gl, double aty) {
-          if (gl == 0) {
-            double qx = (double)P.qd[i] * (double)x[i];
-            if (k > 0) qx += rtw_d(i, wk);
-            if (sparse) qx += W.sd[i];
-            const double st = qx + (double)P.c[i] - aty;
-            const double ss = P.beta_c * P.col[i] * st;
-            if (seg == 0 && GEN && P.xlo) {
-              // box coordinate: min_{x in [lo,hi]} s x joins the dual objective; an infinite
-              // side demands the matching sign of s
-              if (st != 0.0) {
-                const double bd = st > 0.0 ? (double)P.xlo[i] : (double)P.xhi[i];
-                if (isfinite(bd)) v2[1] += st * bd;
-                else v2[0] += ss * ss;
-              }
-            } else if (seg == 0) v2[0] += ss * ss;
-            else if (seg == 1) { const double t = fmax(-ss, 0.0); v2[0] += t * t; }
-            else W.sd[i] = -ss;
-          }
-        });
+    vals(P.t_v, P.t_vb, [&](auto tv) {
+      rows_loop_tpr_plain<double>(
+          own.g_t, P.t_rp, P.t_ci, tv, own.x0[seg], own.x1[seg], [&](int j) { return y[j]; },
+          [&](int64_t i, int gl, double aty) {
+            if (gl == 0) {
+              double qx = (double)P.qd[i] * (double)x[i];
+              if (k > 0) qx += rtw_d(i, wk);
+              if (sparse) qx += W.sd[i];
+              const double st = qx + (double)P.c[i] - aty;
+              const double ss = P.beta_c * P.col[i] * st;
+              if (seg == 0 && GEN && P.xlo) {
+                // box coordinate: min_{x in [lo,hi]} s x joins the dual objective; an infinite
+                // side demands the matching sign of s
+                if (st != 0.0) {
+                  const double bd = st > 0.0 ? (double)P.xlo[i] : (double)P.xhi[i];
+                  if (isfinite(bd)) v2[1] += st * bd;
+                  else v2[0] += ss * ss;
+                }
+              } else if (seg == 0) v2[0] += ss * ss;
+              else if (seg == 1) { const double t = fmax(-ss, 0.0); v2[0] += t * t; }
+              else W.sd[i] = -ss;
+            }
+          });
+    });
   }
   __syncthreads();
   // cone coordinates: project -s onto each cone (Euclidean, FP64, in place in W.sd)
@@ -442,9 +448,11 @@ __device__ void Solver<T, Team, GEN>::run(long long budget) {
       }
     };
     if (needE) {
-      rows_loop2_tpr<T>(own.g_a, P.a_rp, P.a_ci, P.a_v, own.row0, own.row1,
-                        [&](int j) { return T(2) * wxn[j] - hx[j]; }, [&](int j) { return hx[j] - wxn[j]; },
-                        dual_row);
+      vals(P.a_v, P.a_vb, [&](auto av) {
+        rows_loop2_tpr<T>(own.g_a, P.a_rp, P.a_ci, av, own.row0, own.row1,
+                          [&](int j) { return T(2) * wxn[j] - hx[j]; }, [&](int j) { return hx[j] - wxn[j]; },
+                          dual_row);
+      });
     } else {
       // between checks the row products need only 2 w_x - h_x: written once for the owned
       // coordinates, it is gathered as one operand instead of two
@@ -472,17 +480,21 @@ __device__ void Solver<T, Team, GEN>::run(long long budget) {
         T* acc = W.cb_acc;
         for (int b = 0; b < P.cb_n; ++b) {
           const bool first = b == 0, last = b == P.cb_n - 1;
-          rows_loop_multi<kMultiRows, T>(P.cb_rp + (int64_t)b * P.m, P.cb_ci, P.cb_v, own.row0, own.row1,
-                           [&](int j) { return zv[j]; }, [&](int64_t r, int gl, T s1) {
-                             if (gl != 0) return;
-                             if (last) dual_row(r, 0, first ? s1 : acc[r] + s1, T(0));
-                             else acc[r] = first ? s1 : acc[r] + s1;
-                           });
+          vals(P.cb_v, P.cb_vb, [&](auto cbv) {
+            rows_loop_multi<kMultiRows, T>(P.cb_rp + (int64_t)b * P.m, P.cb_ci, cbv, own.row0, own.row1,
+                             [&](int j) { return zv[j]; }, [&](int64_t r, int gl, T s1) {
+                               if (gl != 0) return;
+                               if (last) dual_row(r, 0, first ? s1 : acc[r] + s1, T(0));
+                               else acc[r] = first ? s1 : acc[r] + s1;
+                             });
+          });
           if (!last && !team.sync()) return;
         }
       } else {
-        rows_loop_tpr<T>(own.g_a, P.a_rp, P.a_ci, P.a_v, own.row0, own.row1, [&](int j) { return zv[j]; },
-                         [&](int64_t r, int gl, T s1) { dual_row(r, gl, s1, T(0)); });
+        vals(P.a_v, P.a_vb, [&](auto av) {
+          rows_loop_tpr<T>(own.g_a, P.a_rp, P.a_ci, av, own.row0, own.row1, [&](int j) { return zv[j]; },
+                           [&](int64_t r, int gl, T s1) { dual_row(r, gl, s1, T(0)); });
+        });
       }
     }
     T* hxn = W.hx[hb ^ 1];

@@ -82,3 +82,49 @@ def test_portfolio_batch_structure():
         assert np.allclose(I.csr_matvec(m["a_rowptr"], m["a_colind"], m["a_val"], z), m["b"], atol=1e-12)
         assert abs(np.linalg.norm(z[n_as:-1]) - z[-1]) <= 1e-12
         assert list(m["blk_type"]) == [I.CONE_NONNEG, I.CONE_SOC]
+
+
+def test_round_bf16_is_round_to_nearest_even():
+    # against torch's FP32 -> BF16 conversion (round to nearest, ties to even) on random values,
+    # exact ties, values next to a power of two and signed zeros
+    import torch
+    rng = np.random.default_rng(3)
+    x = np.concatenate([rng.normal(size=20000) * 10.0 ** rng.integers(-30, 30, size=20000),
+                        [0.0, -0.0, 1.0, -1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, 1.0 + 2.0 ** -9, 2.0 - 2.0 ** -9]])
+    got = I.round_bf16(x)
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).double().numpy()
+    assert np.array_equal(got, ref)
+    assert np.array_equal(np.signbit(got), np.signbit(ref))
+    # the ties: 1 + 2^-8 lies halfway between 1 and 1 + 2^-7 and goes to the even 1; 1 + 3 2^-8 goes up
+    assert got[-4] == 1.0 and got[-3] == 1.0 + 2.0 ** -6
+    # the bit patterns reproduce the rounded values
+    bits = I.bf16_bits(x).astype(np.uint32) << 16
+    assert np.array_equal(bits.view(np.float32).astype(np.float64), got)
+
+
+def test_bf16_rounding_and_positive_semidefiniteness_of_p():
+    # BF16 storage of P (matrix_bf16 = 2) solves the problem with P rounded entrywise.  For the
+    # large QP's P (a diagonal plus a weighted matching Laplacian: rows (i, j) hold d_i + w, -w) both
+    # signs of a weight round alike, so every 2 x 2 block stays positive semidefinite; for the
+    # sparse QP's P = M'M + 1e-2 I at full size the rounded matrix is indefinite
+    inst = I.small_config(5)
+    n = inst["n"]
+    rp, ci, v = inst["p_rowptr"], inst["p_colind"], I.round_bf16(inst["p_val"])
+    assert np.all(np.diff(rp) == 2)
+    rows = np.repeat(np.arange(n), 2)
+    diag = np.zeros(n)
+    off = np.zeros(n)
+    mate = np.full(n, -1)
+    on = ci == rows
+    diag[rows[on]] = v[on]
+    off[rows[~on]] = v[~on]
+    mate[rows[~on]] = ci[~on]
+    assert np.all(mate >= 0) and np.all(mate[mate] == np.arange(n))
+    assert np.all(off == off[mate])                                # symmetric after rounding
+    assert np.all(diag >= 0) and np.all(diag * diag[mate] >= off * off)
+    full = I.sparse_qp_nonneg()
+    m = full["n"]
+    P = np.zeros((m, m))
+    r = np.repeat(np.arange(m), np.diff(full["p_rowptr"]))
+    P[r, full["p_colind"]] = I.round_bf16(full["p_val"])
+    assert np.linalg.eigvalsh(P).min() < 0.0
