@@ -39,6 +39,8 @@ Other workloads (not the default line):
   --workload large      the large sparse QP (n = --large-n, m = n/4, 20 nnz per
                         row), generated in device memory; setup + solve per step.
   --workload gemm       the warm-start network's BF16 GEMMs at the training shape.
+  --workload spmv       the sparse product in each layout (CSR row widths, merge path, sliced
+                        ELL) on the large QP's A and an A'-shaped matrix at a tenth of its size.
   --workload lasso      a Lasso with the shape and density of rcv1_test (677,399 x 47,236,
                         density 1.55e-3), reformulated by frontends.lasso_to_qp; setup + solve.
   --workload qcqp       a synthetic convex QCQP (n = 200,000, 50,000 linear rows, 50 quadratic
@@ -637,6 +639,85 @@ def run_gemm(args):
     print(json.dumps(line), flush=True)
 
 
+def run_spmv(args):
+    """The sparse product y = A x in each layout of the library, on the large QP's A (20 entries per
+    row) and on a matrix with A''s shape and row-length profile (n rows, Poisson(5) entries per row,
+    random columns over m), at n = --large-n / 10 by default (2e7: 1e8 entries, operands well
+    above L2).  Throughput in algorithmic bytes: entries (value + index), row pointers, the output
+    and one pass over the input vector."""
+    import torch
+
+    import paper_2608_09159_gb300 as g
+    from instances import gpu as G
+    g.build()
+    g.lib()
+    n = int(args.large_n / 10)
+    n -= n % 2
+    m = n // 4
+    inst = G.large_qp_device(n=n, m=m, seed=1005)
+    A = (m, n, inst["a_rowptr"].to(torch.int32), inst["a_colind"], inst["a_val"].to(torch.float32))
+    del inst
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    lens = torch.poisson(torch.full((n,), 5.0, device="cuda"), generator=gen).to(torch.int64)
+    rp = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
+    rp[1:] = torch.cumsum(lens, 0)
+    nz = int(rp[-1])
+    T = (n, m, rp.to(torch.int32), torch.randint(0, m, (nz,), device="cuda", generator=gen, dtype=torch.int32),
+         torch.randn(nz, device="cuda", generator=gen))
+    del lens, rp
+    peaks, src = _peaks()
+    res = {}
+    launches = 0
+    for mname, (rows, cols, rpt, cit, vt) in (("A (m x n, 20 per row)", A), ("A'-shaped (n x m, Poisson(5) per row)", T)):
+        x = torch.randn(cols, device="cuda", generator=gen)
+        y = torch.empty(rows, device="cuda")
+        nnz = int(vt.numel())
+        alg = nnz * 8 + (rows + 1) * 4 + rows * 4 + cols * 4
+        sell = g.Sell(0, rows, cols, rpt.data_ptr(), cit.data_ptr(), vt.data_ptr())
+        variants = {"csr 1 lane/row": lambda: g.cqp_spmv(0, rows, cols, rpt.data_ptr(), cit.data_ptr(), vt.data_ptr(),
+                                                        x.data_ptr(), y.data_ptr(), 1),
+                    "csr 1 lane/row, 4 rows in flight": lambda: g.cqp_spmv(0, rows, cols, rpt.data_ptr(), cit.data_ptr(),
+                                                                          vt.data_ptr(), x.data_ptr(), y.data_ptr(), -1),
+                    "csr 4 lanes/row": lambda: g.cqp_spmv(0, rows, cols, rpt.data_ptr(), cit.data_ptr(), vt.data_ptr(),
+                                                         x.data_ptr(), y.data_ptr(), 4),
+                    "csr 32 lanes/row": lambda: g.cqp_spmv(0, rows, cols, rpt.data_ptr(), cit.data_ptr(), vt.data_ptr(),
+                                                          x.data_ptr(), y.data_ptr(), 32),
+                    "merge path": lambda: g.cqp_spmv_merge(0, rows, cols, rpt.data_ptr(), cit.data_ptr(), vt.data_ptr(),
+                                                           x.data_ptr(), y.data_ptr()),
+                    "sliced ELL-32": lambda: sell.spmv(x.data_ptr(), y.data_ptr())}
+        out = {}
+        for vname, fn in variants.items():
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            c0 = g.cqp_kernel_launches()
+            ts = []
+            for _ in range(args.steps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn()
+                e1.record()
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            launches += g.cqp_kernel_launches() - c0
+            ms = statistics.median(ts)
+            out[vname] = {"ms": ms, "gbs": alg / ms / 1e6}
+        out["sell_stored_over_nnz"] = sell.stored / nnz
+        sell.close()
+        res[mname] = {"rows": rows, "cols": cols, "nnz": nnz, "algorithmic_bytes": alg, "variants": out}
+    best = max((v["gbs"], mn, vn) for mn, r in res.items() for vn, v in r["variants"].items() if isinstance(v, dict))
+    line = {"metric": "SpMV throughput (algorithmic bytes)", "value": best[0], "unit": "GB/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic (Philox / torch generator, device memory)",
+            "config": {"workload": "large QP A and an A'-shaped matrix at n = %d, m = %d" % (n, m),
+                       "l2": "operands larger than L2 (no flush needed)"},
+            "matrices": res, "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "achieved": best[0], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": best[0] / peaks["hbm_gbs"], "peak_source": src, "case": "%s, %s" % (best[1], best[2])}}
+    print(json.dumps(line), flush=True)
+
+
 def _oracle_solve_timed(inst, threads):
     """One FP64 oracle solve of the instance to relative KKT <= 1e-4 (threads = 0: the
     single-threaded build, else the OpenMP build with that many threads)."""
@@ -710,7 +791,7 @@ def main():
     ap.add_argument("--no-large", action="store_true", help="leave the large sparse QP out of the default line")
     ap.add_argument("--no-oracle", action="store_true")
     ap.add_argument("--small", action="store_true", help="10x smaller instance (quick checks)")
-    ap.add_argument("--workload", default="socp", choices=["socp", "portfolio", "large", "gemm", "lasso", "qcqp"])
+    ap.add_argument("--workload", default="socp", choices=["socp", "portfolio", "large", "gemm", "lasso", "qcqp", "spmv"])
     ap.add_argument("--ws-train", type=int, default=0, help="portfolio: instances to train the warm start on")
     ap.add_argument("--ws-steps", type=int, default=3000, help="portfolio: warm-start training steps")
     ap.add_argument("--large-n", type=float, default=2e8, help="large: number of variables")
@@ -718,7 +799,7 @@ def main():
                     help="large: 2 = BF16-stored values of A, A' and P (the BF16-rounded problem is solved)")
     args = ap.parse_args()
     if args.workload != "socp" and args.impl == "ours":
-        {"portfolio": run_portfolio, "large": run_large, "gemm": run_gemm, "lasso": run_frontend,
+        {"portfolio": run_portfolio, "large": run_large, "gemm": run_gemm, "spmv": run_spmv, "lasso": run_frontend,
          "qcqp": run_frontend}[args.workload](args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))

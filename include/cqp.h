@@ -305,6 +305,28 @@ int cqp_solve_batch(cqp_handle* h, const double* x0, const double* y0, double* x
 int cqp_spmv(int32_t precision, int64_t nrows, int64_t ncols, const int32_t* rowptr, const int32_t* colind,
              const void* val, const void* x, void* y, int32_t threads_per_row, void* stream);
 
+/* The same product with two other layouts (kernel-level; device pointers; precision 0, 1 or
+ * 2 as in cqp_spmv; well-formed CSR: rowptr non-decreasing from 0 to nnz, columns in range).
+ * cqp_spmv_merge: merge-based row splitting (Merrill and Garland, SC 2016): every thread takes
+ * an equal share of the m + nnz items of the merge of row ends and entries, so rows of any
+ * length are balanced; carries of rows split between threads are added in thread order by a
+ * second kernel (deterministic).  Allocates and frees its carry buffers (stream-ordered) and
+ * synchronises the stream.  Errors: CQP_ERR_INVALID, CQP_ERR_CUDA. */
+int cqp_spmv_merge(int32_t precision, int64_t nrows, int64_t ncols, const int32_t* rowptr, const int32_t* colind,
+                   const void* val, const void* x, void* y, void* stream);
+
+/* Sliced ELL with slices of 32 rows: each slice padded to its longest row and stored
+ * column-major inside the slice (coalesced 32-row steps; padded slots skipped).  cqp_sell_build
+ * copies a device CSR matrix into that layout (the handle owns the copy; synchronises the
+ * stream); cqp_sell_stored reports the stored entries (nnz plus padding); cqp_spmv_sell
+ * computes y = A x asynchronously on `stream`; cqp_sell_free releases the handle. */
+typedef struct cqp_sell cqp_sell;
+int cqp_sell_build(int32_t precision, int64_t nrows, int64_t ncols, const int32_t* rowptr, const int32_t* colind,
+                   const void* val, void* stream, cqp_sell** out);
+int cqp_sell_stored(const cqp_sell* A, int64_t* stored);
+int cqp_spmv_sell(const cqp_sell* A, const void* x, void* y, void* stream);
+void cqp_sell_free(cqp_sell* A);
+
 /* out = Pi^M_K(r) blockwise (App. "cone-projections"): Euclidean when m is NULL,
  * otherwise the projection in the diagonal metric M = diag(m).  Cone blocks as
  * in cqp_setup but as device arrays (CQP_CONE_EXP1 / POW1 slices included; box

@@ -140,13 +140,20 @@ def lib():
         L.cqp_umma_smem_desc.restype = C.c_uint64
         L.cqp_umma_instr_desc_bf16.argtypes = [i32, i32]
         L.cqp_umma_instr_desc_bf16.restype = C.c_uint32
+        L.cqp_spmv_merge.argtypes = [i32, i64, i64, vp, vp, vp, vp, vp, vp]
+        L.cqp_sell_build.argtypes = [i32, i64, i64, vp, vp, vp, vp, vp]
+        L.cqp_sell_stored.argtypes = [vp, vp]
+        L.cqp_spmv_sell.argtypes = [vp, vp, vp, vp]
+        L.cqp_sell_free.argtypes = [vp]
+        L.cqp_sell_free.restype = None
         L.cqp_gemm_tc_launches.argtypes = []
         L.cqp_gemm_tc_launches.restype = C.c_longlong
         for f in ("cqp_default_options", "cqp_setup", "cqp_solve", "cqp_kkt", "cqp_spmv", "cqp_project",
                   "cqp_kkt_static", "cqp_setup_batch", "cqp_solve_batch", "cqp_setup_general", "cqp_ws_features",
                   "cqp_gemm_bf16",
                   "cqp_ws_head_forward", "cqp_ws_loss", "cqp_ws_head_backward", "cqp_relu_backward_bf16",
-                  "cqp_adam_step", "cqp_ws_start", "cqp_gemm_check", "cqp_transpose_bf16"):
+                  "cqp_adam_step", "cqp_ws_start", "cqp_gemm_check", "cqp_transpose_bf16", "cqp_spmv_merge",
+                  "cqp_sell_build", "cqp_sell_stored", "cqp_spmv_sell"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -257,6 +264,35 @@ def cqp_gemm_check(stream=None) -> int:
 
 def cqp_transpose_bf16(rows, cols, src, dst, stream=None) -> int:
     return _check(lib().cqp_transpose_bf16(rows, cols, src, dst, stream))
+
+
+def cqp_spmv_merge(precision, nrows, ncols, rowptr, colind, val, x, y, stream=None) -> int:
+    return _check(lib().cqp_spmv_merge(precision, nrows, ncols, rowptr, colind, val, x, y, stream))
+
+
+class Sell:
+    """Sliced-ELL copy of a device CSR matrix (cqp_sell_build / cqp_spmv_sell / cqp_sell_free)."""
+
+    def __init__(self, precision, nrows, ncols, rowptr, colind, val, stream=None):
+        self.h = C.c_void_p()
+        _check(lib().cqp_sell_build(precision, nrows, ncols, rowptr, colind, val, stream, C.byref(self.h)))
+        n = C.c_int64()
+        _check(lib().cqp_sell_stored(self.h, C.byref(n)))
+        self.stored = n.value
+
+    def spmv(self, x, y, stream=None):
+        return _check(lib().cqp_spmv_sell(self.h, x, y, stream))
+
+    def close(self):
+        if self.h:
+            lib().cqp_sell_free(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def cqp_free(h) -> None:
