@@ -20,6 +20,10 @@ namespace cqp {
 template <typename T> struct Tol;
 template <> struct Tol<float> { static constexpr double rel = 4e-7; };
 template <> struct Tol<double> { static constexpr double rel = 4e-16; };
+// unit roundoff of the element sums' precision
+template <typename T> struct Unit;
+template <> struct Unit<float> { static constexpr double u = 5.9604644775390625e-08; };
+template <> struct Unit<double> { static constexpr double u = 1.1102230246251565e-16; };
 
 // FP64 on this GPU runs at about 1/57 of the FP32 rate, so the warp-level
 // projections keep element work and warp trees in the iterate precision T and
@@ -112,9 +116,13 @@ __device__ __noinline__ void warp_soc_metric(T* x, const T* m, int d, int lane, 
       int done = 0;
       if (lane == 0) {
         const T nrm = sqrt(s2t);
-        const T psi = (mt - lam) * inv_mtzt - T(1) / nrm;
+        const T a = (mt - lam) * inv_mtzt, b = T(1) / nrm;
+        const T psi = a - b;
         const T dpsi = -inv_mtzt - s3t / (s2t * nrm);
-        if (psi == T(0)) {
+        // psi within a few roundings of its terms is noise: its sign no longer tells the side of
+        // the root, so the iteration stops
+        const T noise = T(8.0 * Unit<T>::u) * ((a < T(0) ? -a : a) + b);
+        if (psi == T(0) || (psi < T(0) ? -psi : psi) <= noise) {
           done = 1;
         } else {
           if ((psi > T(0)) == lo_pos) lo = lam; else hi = lam;
@@ -295,7 +303,9 @@ __device__ __noinline__ void warp_rsoc_metric(T* x, const T* m, int d, int lane,
       int done = 0;
       if (lane == 0) {
         const double f = fval(xx, (double)sv, (double)sv3, &dfv);
-        if (f == 0.0) {
+        // f = sv - 2 s t with sv a sum in T: within a few roundings of its terms f is noise
+        const double noise = 8.0 * Unit<T>::u * ((double)sv + fabs((double)sv - f));
+        if (f == 0.0 || fabs(f) <= noise) {
           done = 1;
         } else {
           if ((f > 0.0) == lo_pos) lo = xx; else hi = xx;
