@@ -146,8 +146,10 @@ typedef struct {
   int32_t launch_iters;     /* outer iterations per kernel launch, 0 = auto */
   int32_t profile;          /* 1: record per-phase device time in cqp_result.phase_ms */
   int32_t warm_roots;       /* 1: start each cone block's root-finding from its previous root (default 1) */
-  int32_t col_blocks;       /* dual step's product A z over column blocks whose slice of z stays in L2:
-                               0 auto (on when z exceeds 64 MB: 8 blocks), 1 off, K >= 2 forces K blocks (<= 64) */
+  int32_t col_blocks;       /* sparse products over column slices whose slice of the gathered vector stays
+                               in L2: the dual step's A z (0 auto: 8 slices when z exceeds 64 MB) and the
+                               A'y pass (0 auto: slices of at most 100 MB of y when y exceeds 64 MB);
+                               1 off; K >= 2 forces K slices for both (<= 64) */
   int32_t matrix_bf16;      /* 1: BF16-stored values of A and A'; 2: of A, A' and the sparse part P of Q.
                                FP32 accumulation; precision 0, single problems, whole-GPU team only.  The
                                stored values are rounded to BF16 at setup (to FP32, then to BF16,

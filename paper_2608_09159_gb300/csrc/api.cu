@@ -770,6 +770,36 @@ struct Handle : HandleBase {
         }
       }
     }
+    // column slices of A' for the A'y pass: its gathered vector y (m entries) is read at random
+    // columns; above 64 MB the pass runs over slices of at most 100 MB of y (reading), or over the
+    // forced count of col_blocks
+    int tcb_n = 0;
+    int* tcb_rp = nullptr;
+    int* tcb_ci = nullptr;
+    T* tcb_v = nullptr;
+    __nv_bfloat16* tcb_vb = nullptr;
+    {
+      const double ybytes = (double)m * sizeof(T);
+      if (o.col_blocks >= 2) tcb_n = std::min(o.col_blocks, 64);
+      else if (o.col_blocks == 0 && ybytes > 64.0 * 1024 * 1024) tcb_n = (int)std::ceil(ybytes / (100.0 * 1024 * 1024));
+      if (tcb_n < 2 || batched || m == 0 || nnz == 0) tcb_n = 0;
+      if ((int64_t)tcb_n * n >= (int64_t(1) << 31)) tcb_n = 0;
+      if (tcb_n > 1) {
+        const int64_t width = (m + tcb_n - 1) / tcb_n;
+        int* cnt = tmp.alloc<int>((int64_t)tcb_n * n);
+        tcb_rp = mem.alloc<int>((int64_t)tcb_n * n + 1);
+        tcb_ci = mem.alloc<int>(nnz);
+        count_launch(); cqp::k_cb_count<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, t_rp, t_ci, width, tcb_n, cnt);
+        dev_scan(cnt, tcb_rp, (int64_t)tcb_n * n, tmp, st);
+        if (t_vb) {
+          tcb_vb = mem.alloc<__nv_bfloat16>(nnz);
+          count_launch(); cqp::k_cb_scatter<__nv_bfloat16><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, t_rp, t_ci, t_vb, width, tcb_n, tcb_rp, tcb_ci, tcb_vb);
+        } else {
+          tcb_v = mem.alloc<T>(nnz);
+          count_launch(); cqp::k_cb_scatter<T><<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, t_rp, t_ci, t_v, width, tcb_n, tcb_rp, tcb_ci, tcb_v);
+        }
+      }
+    }
     // Euclidean projections suffice when the diagonal Q vanishes on every cone coordinate
     double qcone = 0.0;
     {
@@ -850,6 +880,7 @@ struct Handle : HandleBase {
     P.a_rp = a_rp; P.a_ci = a_ci; P.a_v = bf ? nullptr : a_v;
     P.t_rp = t_rp; P.t_ci = t_ci; P.t_v = bf ? nullptr : t_v;
     P.a_vb = a_vb; P.t_vb = t_vb; P.p_vb = pTb; P.cb_vb = cb_vb;
+    P.tcb_n = tcb_n; P.tcb_rp = tcb_rp; P.tcb_ci = tcb_ci; P.tcb_v = tcb_v; P.tcb_vb = tcb_vb;
     P.qd = qT; P.jd = jT; P.k = (int)k; P.kpad = (int)kpad; P.R = RT; P.D = Dv;
     // D = d I (the common case) lets the kernel skip the k x k products
     P.d_scale = 0.0;
@@ -965,6 +996,7 @@ struct Handle : HandleBase {
     W.avy = o.update == 1 ? mem.alloc<T>(mm) : nullptr;
     W.mbuf = mem.alloc<T>(n);
     W.cb_acc = cb_n > 1 ? mem.alloc<T>(m) : nullptr;
+    W.tcb_acc = P.tcb_n > 1 ? mem.alloc<T>(n) : nullptr;
     W.sd = mem.alloc<double>(n);
     n_roots = n_soc + n_rsoc + n_exp + n_pow;
     W.root = mem.alloc<float>(std::max<int64_t>(n_roots, 1));

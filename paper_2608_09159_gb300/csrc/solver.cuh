@@ -69,6 +69,9 @@ struct Prob {
   // column blocks of A for the dual step's product between checks (cb_n <= 1: not used):
   // block b's rows are rows of the CSR with row pointers cb_rp + b m (into cb_ci, cb_v)
   int cb_n; const int* cb_rp; const int* cb_ci; const T* cb_v;
+  // column slices of A' for the A'y pass (tcb_n <= 1: not used): slice b's rows are rows of the
+  // CSR with row pointers tcb_rp + b n (into tcb_ci, tcb_v), columns in the b-th range of y
+  int tcb_n; const int* tcb_rp; const int* tcb_ci; const T* tcb_v; const __nv_bfloat16* tcb_vb;
   int p_ulen;                                         // > 0: every row of P has exactly p_ulen entries
   int qmode;
   int euclid_cones;                                   // diagonal mode with zero q on cone coordinates
@@ -90,6 +93,7 @@ struct Work {
   T* avx; T* avy;       // running averages (averaged variant)
   T* mbuf;              // metric of cone blocks too large for shared staging
   T* cb_acc;            // partial row sums of the column-blocked product (m)
+  T* tcb_acc;           // partial row sums of the column-sliced A'y pass (n)
   float* root;          // last scalar root per cone block (warm starts): SOC, RSOC, exp, pow
   double* sd;           // FP64 dual slack of cone coordinates (KKT)
   double* part;         // block partials [kMaxSlots][nb]
@@ -622,7 +626,29 @@ struct Solver {
   }
 
   // ---- A' products: v = h_x + tau A' h_y on the owned coordinates -----------
-  __device__ void phase_aty(const T* hx, const T* hy, double tau) {
+  __device__ bool phase_aty(const T* hx, const T* hy, double tau) {
+    if (P.tcb_n > 1) {
+      // column slices: every block of the team works on the same slice of y (one barrier per
+      // slice), so the slice stays in L2 while the entries stream past; a row adds its partial
+      // sums in slice order
+      T* acc = W.tcb_acc;
+      for (int b = 0; b < P.tcb_n; ++b) {
+        const bool first = b == 0, last = b == P.tcb_n - 1;
+        vals(P.tcb_v, P.tcb_vb, [&](auto tv) {
+          for (int seg = 0; seg < 6; ++seg)
+            rows_loop_multi<kMultiRows, T>(P.tcb_rp + (int64_t)b * P.n, P.tcb_ci, tv, own.x0[seg], own.x1[seg],
+                                           [&](int j) { return hy[j]; }, [&](int64_t i, int gl, T s) {
+                                             if (gl != 0) return;
+                                             const T t = first ? s : acc[i] + s;
+                                             if (last) W.v[i] = hx[i] + T(tau) * t;
+                                             else acc[i] = t;
+                                           });
+        });
+        if (!last && !team.sync()) return false;
+      }
+      __syncthreads();
+      return true;
+    }
     vals(P.t_v, P.t_vb, [&](auto tv) {
       for (int seg = 0; seg < 6; ++seg) {
         rows_loop_tpr<T>(own.g_t, P.t_rp, P.t_ci, tv, own.x0[seg], own.x1[seg], [&](int j) { return hy[j]; },
@@ -632,6 +658,7 @@ struct Solver {
       }
     });
     __syncthreads();
+    return true;
   }
 
   // ---- one projected (Jacobi-)BB step on the owned coordinates --------------
@@ -682,7 +709,69 @@ struct Solver {
     // elementwise segments (free, nonneg).  Without a low-rank part four elements per thread are
     // loaded together (a streaming pass over n-vectors is otherwise bound by the few loads each
     // of the 16 warps has in flight); the partial sums take the same order as the loop below.
-    if (KM == 0) {
+    if constexpr (KM == 0 && sizeof(T) == 4) {
+      // FP32: 16-byte loads of four consecutive coordinates, two such chunks in flight per
+      // thread (the pass streams five n-vectors; scalar loads leave too few bytes in flight
+      // per SM to cover the HBM latency).  Head and tail of a segment off the 4-element grid
+      // take the scalar path.
+      constexpr int CU = 2;
+      const int64_t B = blockDim.x;
+      auto elem = [&](int64_t i, T u, T qi, T gv, T cv, T vi, T J) {
+        const T g = gs ? gv : qi * u + cv + (u - vi) * itau;
+        const T un = proj_elem(i, u - alpha * g / J);
+        const T sd = un - u;
+        a0 += sd * sd;
+        a1 += J * sd * sd;
+        a2 += (qi + itau) * sd * sd;
+        a3 += un * un;
+        return un;
+      };
+      auto scalar = [&](int64_t i) {
+        un_out[i] = elem(i, uc[i], qd[i], gs ? gs[i] : T(0), gs ? T(0) : cc[i], gs ? T(0) : vv[i], jm(i));
+      };
+      for (int seg = 0; seg < 2; ++seg) {
+        const int64_t a = own.x0[seg], b = own.x1[seg];
+        const int64_t ah = ((a + 3) & ~int64_t(3)) < b ? ((a + 3) & ~int64_t(3)) : b;
+        const int64_t c0 = ah >> 2, c1 = b >> 2 > c0 ? b >> 2 : c0;
+        for (int64_t i = a + threadIdx.x; i < ah; i += B) scalar(i);
+        for (int64_t i = (c1 << 2) > ah ? (c1 << 2) + threadIdx.x : ah + threadIdx.x; i < b; i += B) scalar(i);
+        const float4* __restrict__ u4 = reinterpret_cast<const float4*>(uc);
+        const float4* __restrict__ q4 = reinterpret_cast<const float4*>(qd);
+        const float4* __restrict__ g4 = reinterpret_cast<const float4*>(gs);
+        const float4* __restrict__ c4 = reinterpret_cast<const float4*>(cc);
+        const float4* __restrict__ v4 = reinterpret_cast<const float4*>(vv);
+        const float4* __restrict__ j4 = reinterpret_cast<const float4*>(jd);
+        float4* __restrict__ o4 = reinterpret_cast<float4*>(un_out);
+        for (int64_t cq = c0 + threadIdx.x; cq < c1; cq += CU * B) {
+          float4 uu[CU], qq[CU], gg[CU], ca[CU], va[CU], jj[CU];
+          const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int e = 0; e < CU; ++e) {
+            const int64_t c = cq + e * B;
+            const bool ok = c < c1;
+            uu[e] = ok ? u4[c] : z4;
+            qq[e] = ok ? q4[c] : z4;
+            gg[e] = (ok && gs) ? g4[c] : z4;
+            ca[e] = (ok && !gs) ? c4[c] : z4;
+            va[e] = (ok && !gs) ? v4[c] : z4;
+            jj[e] = (ok && jac) ? j4[c] : z4;
+          }
+#pragma unroll
+          for (int e = 0; e < CU; ++e) {
+            const int64_t c = cq + e * B;
+            if (c >= c1) break;
+            const T J0 = jac ? jj[e].x + itau : T(1), J1 = jac ? jj[e].y + itau : T(1);
+            const T J2 = jac ? jj[e].z + itau : T(1), J3 = jac ? jj[e].w + itau : T(1);
+            float4 o;
+            o.x = elem(4 * c, uu[e].x, qq[e].x, gg[e].x, ca[e].x, va[e].x, J0);
+            o.y = elem(4 * c + 1, uu[e].y, qq[e].y, gg[e].y, ca[e].y, va[e].y, J1);
+            o.z = elem(4 * c + 2, uu[e].z, qq[e].z, gg[e].z, ca[e].z, va[e].z, J2);
+            o.w = elem(4 * c + 3, uu[e].w, qq[e].w, gg[e].w, ca[e].w, va[e].w, J3);
+            o4[c] = o;
+          }
+        }
+      }
+    } else if (KM == 0) {
       constexpr int EU = 4;
       const int64_t B = blockDim.x;
       for (int seg = 0; seg < 2; ++seg)

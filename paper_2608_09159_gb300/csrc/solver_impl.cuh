@@ -91,7 +91,7 @@ template <typename T, class Team, bool GEN>
 __device__ bool Solver<T, Team, GEN>::prox_diag(const T* hx) {
   using S = Solver<T, Team, GEN>;
   const double tau = C.s.tau;
-  phase_aty(hx, W.hy[C.s.hb], tau);
+  if (!phase_aty(hx, W.hy[C.s.hb], tau)) return false;
   tick(0);
   T* u = W.u[0];
   const T tt = T(tau);
@@ -119,7 +119,7 @@ __device__ bool Solver<T, Team, GEN>::prox_bb(const T* hx, int& ub) {
   const double tau = C.s.tau;
   const int k = P.k;
   const bool sparse = P.qmode == kQSparse;
-  phase_aty(hx, W.hy[C.s.hb], tau);
+  if (!phase_aty(hx, W.hy[C.s.hb], tau)) return false;
   tick(0);
   // t = R h_x from the state; w = D t
   for (int l = threadIdx.x; l < k; l += blockDim.x) C.tcur[l] = C.s.t_h[l];

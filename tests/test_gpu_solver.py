@@ -71,8 +71,9 @@ def test_config1_full_size_fp64(gpu, orc):
 
 @pytest.mark.parametrize("precision", [1, 0])
 def test_column_blocked_dual_step(gpu, orc, precision):
-    """The dual step's product over column blocks (forced on a small problem: 5 blocks) reaches
-    the same bars; in FP64 its first iterations equal the plain product's to rounding."""
+    """The dual step's A z and the A'y pass over column slices (forced on a small problem: 5
+    slices each) reach the same bars; in FP64 the first iterations equal the plain products' to
+    rounding."""
     inst = I.small_config(2)
     s = gpu.Solver(inst, precision=precision, max_iter=200000, tol=1e-4, time_limit_s=120.0, col_blocks=5)
     x, y, res = s.solve()
