@@ -997,6 +997,78 @@ struct Solver {
     return acc;
   }
 
+  // The same for FP32 iterates and rows of exactly ulen entries, four consecutive rows per thread:
+  // 16-byte loads of the row vectors and of the rows' entries (ulen = 2: eight entries, two int4
+  // and two float4 or one uint4 of BF16), the gathers and the store of g likewise four at a time.
+  // Rows off the 4-row grid at either end of the range take grad_rows_batched.  Each row's sum is
+  // in storage order, as there.
+  template <typename V>
+  __device__ T grad_rows_vec4(const V* __restrict__ pv, const T* u, const T* uprev, const T* gprev, T* gout, T itau,
+                              bool first, int64_t r0, int64_t r1) {
+    const int ulen = P.p_ulen;
+    const int64_t rh = ((r0 + 3) & ~int64_t(3)) < r1 ? ((r0 + 3) & ~int64_t(3)) : r1;
+    const int64_t c0 = rh >> 2, c1 = (r1 >> 2) > c0 ? (r1 >> 2) : c0;
+    T acc = grad_rows_batched(pv, u, uprev, gprev, gout, itau, first, r0, rh);
+    acc += grad_rows_batched(pv, u, uprev, gprev, gout, itau, first, (c1 << 2) > rh ? (c1 << 2) : rh, r1);
+    const int* __restrict__ ci = P.p_ci;
+    const float4* __restrict__ u4 = reinterpret_cast<const float4*>(u);
+    const float4* __restrict__ q4 = reinterpret_cast<const float4*>(P.qd);
+    const float4* __restrict__ cc4 = reinterpret_cast<const float4*>(P.c);
+    const float4* __restrict__ v4 = reinterpret_cast<const float4*>(W.v);
+    const float4* __restrict__ up4 = reinterpret_cast<const float4*>(uprev);
+    const float4* __restrict__ gp4 = reinterpret_cast<const float4*>(gprev);
+    float4* __restrict__ g4 = reinterpret_cast<float4*>(gout);
+    for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+      const float4 uu = u4[c], qq = q4[c], cv = cc4[c], vv = v4[c];
+      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 up = first ? z4 : up4[c], gp = first ? z4 : gp4[c];
+      const int64_t base = (int64_t)ulen * 4 * c;
+      float sr[4] = {0.f, 0.f, 0.f, 0.f};
+      if (ulen == 2) {
+        const int4 ja = reinterpret_cast<const int4*>(ci + base)[0], jb = reinterpret_cast<const int4*>(ci + base)[1];
+        float a[8];
+        if constexpr (std::is_same<V, __nv_bfloat16>::value) {
+          const uint4 w = *reinterpret_cast<const uint4*>(pv + base);
+          const unsigned ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            a[2 * t] = __uint_as_float(ws[t] << 16);
+            a[2 * t + 1] = __uint_as_float(ws[t] & 0xFFFF0000u);
+          }
+        } else {
+          const float4 pa = reinterpret_cast<const float4*>(pv + base)[0], pb = reinterpret_cast<const float4*>(pv + base)[1];
+          a[0] = pa.x; a[1] = pa.y; a[2] = pa.z; a[3] = pa.w; a[4] = pb.x; a[5] = pb.y; a[6] = pb.z; a[7] = pb.w;
+        }
+        const int j[8] = {ja.x, ja.y, ja.z, ja.w, jb.x, jb.y, jb.z, jb.w};
+        float gv[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) gv[t] = u[j[t]];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          sr[q] += a[2 * q] * gv[2 * q];
+          sr[q] += a[2 * q + 1] * gv[2 * q + 1];
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          for (int t = 0; t < ulen; ++t) {
+            const int64_t e = base + (int64_t)q * ulen + t;
+            sr[q] += ld_val<float>(pv + e) * u[__ldg(ci + e)];
+          }
+      }
+      const float uq[4] = {uu.x, uu.y, uu.z, uu.w}, qv[4] = {qq.x, qq.y, qq.z, qq.w}, cq[4] = {cv.x, cv.y, cv.z, cv.w};
+      const float vq[4] = {vv.x, vv.y, vv.z, vv.w}, pq[4] = {up.x, up.y, up.z, up.w}, gq[4] = {gp.x, gp.y, gp.z, gp.w};
+      float go[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        go[q] = sr[q] + qv[q] * uq[q] + cq[q] + (uq[q] - vq[q]) * itau;
+        if (!first) acc += (uq[q] - pq[q]) * (go[q] - gq[q]);
+      }
+      g4[c] = make_float4(go[0], go[1], go[2], go[3]);
+    }
+    return acc;
+  }
+
   __device__ void grad_pass(const T* u, const T* uprev, const T* gprev, T* gout, double tau, double (&v2)[2],
                             bool first) {
     const T itau = T(1.0 / tau);
@@ -1004,8 +1076,15 @@ struct Solver {
     T acc = T(0);
     if (own.g_p == kRowsBatched && P.k == 0) {
       vals(P.p_v, P.p_vb, [&](auto pv) {
-        for (int seg = 0; seg < 6; ++seg)
+        for (int seg = 0; seg < 6; ++seg) {
+          if constexpr (sizeof(T) == 4) {
+            if (P.p_ulen > 0) {
+              acc += grad_rows_vec4(pv, u, uprev, gprev, gout, itau, first, own.x0[seg], own.x1[seg]);
+              continue;
+            }
+          }
           acc += grad_rows_batched(pv, u, uprev, gprev, gout, itau, first, own.x0[seg], own.x1[seg]);
+        }
       });
       v2[0] = (double)acc;
       v2[1] = 0.0;
