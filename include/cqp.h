@@ -179,8 +179,10 @@ typedef struct {
   /* with opt.profile: device time (block 0) per phase of the iteration: A'y product,
    * prox work, prox barriers, dual step, its barrier, KKT checks, restart/Halpern at
    * checks, whole loop; then the inner BB step split into its elementwise part, cone
-   * gradient, cone projection and cone bookkeeping */
-  double phase_ms[12];
+   * gradient, cone projection and cone bookkeeping; then the dual step split into the
+   * z = 2 w_x - h_x pass (with its barrier), the row products (with the barriers between
+   * column slices) and the Halpern update of x; the last entry is unused */
+  double phase_ms[16];
   double kernel_ms;                /* CUDA-event time of the solver kernel launches of this solve */
   int64_t setup_launches;          /* kernels launched by cqp_setup for this handle */
 } cqp_result;

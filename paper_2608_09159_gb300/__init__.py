@@ -88,7 +88,7 @@ class Result(C.Structure):
     _fields_ = [("status", C.c_int32), ("iters", C.c_int64), ("restarts", C.c_int64), ("inner_total", C.c_int64),
                 ("kernel_launches", C.c_int64), ("kkt", KKTReport), ("eta", C.c_double), ("norm_A", C.c_double),
                 ("omega", C.c_double), ("setup_ms", C.c_double), ("solve_ms", C.c_double),
-                ("phase_ms", C.c_double * 12), ("kernel_ms", C.c_double), ("setup_launches", C.c_int64)]
+                ("phase_ms", C.c_double * 16), ("kernel_ms", C.c_double), ("setup_launches", C.c_int64)]
 
 
 _lib = None

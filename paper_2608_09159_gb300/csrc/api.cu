@@ -1164,7 +1164,7 @@ struct Handle : HandleBase {
       res->omega = back.omega;
       res->setup_ms = setup_ms;
       res->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-      for (int i = 0; i < 12; ++i) res->phase_ms[i] = back.prof[i] * 1e-6;
+      for (int i = 0; i < 16; ++i) res->phase_ms[i] = back.prof[i] * 1e-6;
       res->kernel_ms = kernel_ms;
       res->setup_launches = setup_launches;
     }

@@ -115,9 +115,10 @@ struct State {
   double t_h[kMaxRank];            // R~ h_x of the current Halpern state
   double kkt[8];                   // eps_p, eps_d, eps_g, rel_kkt, pobj, dobj, ||r_p||, ||r_d||
   double lastE;
-  double prof[12];                 // ns per phase: A'y, prox work, prox barriers, dual step, its barrier,
+  double prof[16];                 // ns per phase: A'y, prox work, prox barriers, dual step, its barrier,
                                    // KKT, restart/Halpern at checks, whole loop; inner-step split:
-                                   // elementwise, cone gradient, cone projection, cone bookkeeping
+                                   // elementwise, cone gradient, cone projection, cone bookkeeping;
+                                   // dual-step split: z pass, row products, Halpern update of x
   long long k, ktot, restarts, inner_total;
   int hb, wb;                      // current Halpern / candidate buffer
   int status;                      // 0 running, 1 converged, 2 iteration limit
@@ -278,7 +279,7 @@ __device__ __forceinline__ void rows_loop(const int* rp, const int* ci, const T*
 constexpr int kMultiRows = 4;
 constexpr int kMultiU = 4;
 // ulen > 0: every row has exactly ulen entries (rp[r] = ulen r), so the row pointers are not read.
-template <int RB, typename Acc, typename T, typename X, typename F>
+template <int RB, typename Acc, int U = kMultiU, typename T, typename X, typename F>
 __device__ __forceinline__ void rows_loop_multi(const int* rp, const int* ci, const T* v, int64_t r0, int64_t r1, X xf,
                                                 F f, int ulen = 0) {
   const int lane = threadIdx.x & 31;
@@ -303,27 +304,27 @@ __device__ __forceinline__ void rows_loop_multi(const int* rp, const int* ci, co
     }
 #pragma unroll
     for (int q = 0; q < RB; ++q) len = max(len, end[q] - beg[q]);
-    for (int k = 0; k < len; k += kMultiU) {
-      int j[RB][kMultiU];
-      Acc a[RB][kMultiU];
+    for (int k = 0; k < len; k += U) {
+      int j[RB][U];
+      Acc a[RB][U];
 #pragma unroll
       for (int q = 0; q < RB; ++q)
 #pragma unroll
-        for (int u = 0; u < kMultiU; ++u) {
+        for (int u = 0; u < U; ++u) {
           const int kk = beg[q] + k + u;
           const bool ok = kk < end[q];
           j[q][u] = ok ? __ldg(ci + kk) : -1;
           a[q][u] = ok ? ld_val<Acc>(v + kk) : Acc(0);
         }
-      Acc g[RB][kMultiU];
+      Acc g[RB][U];
 #pragma unroll
       for (int q = 0; q < RB; ++q)
 #pragma unroll
-        for (int u = 0; u < kMultiU; ++u) g[q][u] = j[q][u] >= 0 ? (Acc)xf(j[q][u]) : Acc(0);
+        for (int u = 0; u < U; ++u) g[q][u] = j[q][u] >= 0 ? (Acc)xf(j[q][u]) : Acc(0);
 #pragma unroll
       for (int q = 0; q < RB; ++q)
 #pragma unroll
-        for (int u = 0; u < kMultiU; ++u) s[q] += a[q][u] * g[q][u];
+        for (int u = 0; u < U; ++u) s[q] += a[q][u] * g[q][u];
     }
 #pragma unroll
     for (int q = 0; q < RB; ++q) {

@@ -447,6 +447,7 @@ __device__ void Solver<T, Team, GEN>::run(long long budget) {
         v6[5] += e * e;
       }
     };
+    unsigned long long tsub = (O.profile && team.bid() == 0 && threadIdx.x == 0) ? now_ns() : 0ull;
     if (needE) {
       vals(P.a_v, P.a_vb, [&](auto av) {
         rows_loop2_tpr<T>(own.g_a, P.a_rp, P.a_ci, av, own.row0, own.row1,
@@ -473,6 +474,7 @@ __device__ void Solver<T, Team, GEN>::run(long long budget) {
           }
         }
       if (!team.sync()) return;
+      subtick(12, tsub);
       if (P.cb_n > 1) {
         // column blocks: every block of the team works on the same slice of z (one barrier per
         // slice), so the slice stays in L2 while its entries stream past; a row keeps its lane
@@ -497,6 +499,7 @@ __device__ void Solver<T, Team, GEN>::run(long long budget) {
         });
       }
     }
+    subtick(13, tsub);
     T* hxn = W.hx[hb ^ 1];
     T* wxs = W.wx[wb ^ 1];
     const T* wxp = W.wx[wb];
@@ -558,6 +561,7 @@ __device__ void Solver<T, Team, GEN>::run(long long budget) {
     if (halpern_now && k > 0) rx_lmajor(hxn);
     v6[0] = (double)mov_acc;
     __syncthreads();
+    subtick(14, tsub);
     if (needE || check) {
       publish<6>(v6, 0, halpern_now && k > 0);
     } else {
