@@ -158,8 +158,9 @@ typedef struct {
                                still positive semidefinite: it is when P is diagonal or a weighted graph
                                Laplacian (both signs of a weight round alike), not in general (entrywise
                                rounding of a matrix with small eigenvalues can make it indefinite).  The
-                               Ruiz, Pock-Chambolle and bound-objective factors are rounded to powers of
-                               two, so the scaled values stay exactly representable.  0 (default): values
+                               cumulative Ruiz and Pock-Chambolle factors and the bound-objective factors
+                               are rounded to powers of two, so the scaled values stay exactly
+                               representable.  0 (default): values
                                in the iterate precision */
   void* stream;             /* cudaStream_t, NULL = default stream */
 } cqp_options;

@@ -597,10 +597,6 @@ struct Handle : HandleBase {
       if (n_pow) { count_launch(); cqp::k_aggregate_blocks<<<cqp::grid_for(n_pow), cqp::kSetupThreads, 0, st>>>(n_pow, nullptr, base[5], 3, mode, colf); }
     };
     auto scale_step = [&]() {
-      if (bf) {   // power-of-two factors keep the BF16 values of A and P exact
-        count_launch(); cqp::k_pow2_round<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, colf);
-        if (m > 0) { count_launch(); cqp::k_pow2_round<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, rowf); }
-      }
       count_launch(); cqp::k_scale_matrix<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp, a_ci, av, rowf, colf);
       count_launch(); cqp::k_mul<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, col, colf);
       if (m > 0) { count_launch(); cqp::k_mul<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, row, rowf); }
@@ -621,6 +617,13 @@ struct Handle : HandleBase {
       if (m > 0) { count_launch(); cqp::k_sqrt_or_one<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, rowf); }
       if (!o.rescaled_cones) aggregate(1);
       scale_step();
+    }
+    if (bf) {
+      // power-of-two factors keep the BF16 values of A and P exact: the cumulative Ruiz and
+      // Pock-Chambolle factors are rounded once, and A is brought to the rounded factors
+      count_launch(); cqp::k_pow2_ratio<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, col, colf);
+      if (m > 0) { count_launch(); cqp::k_pow2_ratio<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, row, rowf); }
+      if (m > 0) { count_launch(); cqp::k_scale_matrix<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, a_rp, a_ci, av, rowf, colf); }
     }
     count_launch(); cqp::k_div<<<cqp::grid_for(n), cqp::kSetupThreads, 0, st>>>(n, cv, col);
     if (m > 0) { count_launch(); cqp::k_div<<<cqp::grid_for(m), cqp::kSetupThreads, 0, st>>>(m, bv, row); }

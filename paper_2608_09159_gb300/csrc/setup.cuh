@@ -313,8 +313,13 @@ __host__ __device__ inline double pow2_round(double f) {
   const double m = frexp(f, &e);
   return ldexp(1.0, m >= 0.70710678118654752440 ? e : e - 1);
 }
-__global__ void k_pow2_round(int64_t n, double* f) {
-  CQP_GRID_LOOP(i, n) f[i] = pow2_round(f[i]);
+// c <- its power of two (pow2_round), f <- the ratio new / old that brings a scaled matrix along
+__global__ void k_pow2_ratio(int64_t n, double* c, double* f) {
+  CQP_GRID_LOOP(i, n) {
+    const double p = pow2_round(c[i]);
+    f[i] = p / c[i];
+    c[i] = p;
+  }
 }
 
 // out[i] = BF16(in[map[i]]) (map null: in[i]); the values are exactly representable here
