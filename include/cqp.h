@@ -141,8 +141,10 @@ typedef struct {
                                16 CTAs (cluster barriers, distributed-shared-memory reductions) */
   int32_t threads;          /* threads per block, 0 = auto */
   int32_t blocks_per_sm;    /* 0 = auto (cooperative team only) */
-  int32_t tpr_a, tpr_at;    /* threads per CSR row for A and A' (1..32), -1 = one lane per row with four rows
-                               in flight, 0 = autotuned among these (timed per matrix shape, cached) */
+  int32_t tpr_a, tpr_at, tpr_p; /* threads per CSR row for A, A' and the sparse part P of Q (1..32), -1 = one
+                               lane per row with four rows in flight (P: with 16-byte loads of four rows
+                               when its rows all have the same length), 0 = autotuned among these (timed
+                               per matrix shape, cached) */
   int32_t launch_iters;     /* outer iterations per kernel launch, 0 = auto */
   int32_t profile;          /* 1: record per-phase device time in cqp_result.phase_ms */
   int32_t warm_roots;       /* 1: start each cone block's root-finding from its previous root (default 1) */

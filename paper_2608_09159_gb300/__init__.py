@@ -60,7 +60,7 @@ class Options(C.Structure):
                 ("time_limit_s", C.c_double),
                 ("power_iters", C.c_int32), ("power_tol", C.c_double), ("step_factor", C.c_double),
                 ("input_on_device", C.c_int32), ("team", C.c_int32), ("threads", C.c_int32),
-                ("blocks_per_sm", C.c_int32), ("tpr_a", C.c_int32), ("tpr_at", C.c_int32),
+                ("blocks_per_sm", C.c_int32), ("tpr_a", C.c_int32), ("tpr_at", C.c_int32), ("tpr_p", C.c_int32),
                 ("launch_iters", C.c_int32), ("profile", C.c_int32), ("warm_roots", C.c_int32), ("col_blocks", C.c_int32),
                 ("matrix_bf16", C.c_int32),
                 ("stream", C.c_void_p)]

@@ -985,7 +985,7 @@ struct Handle : HandleBase {
       };
       P.tpr_a = o.tpr_a > 0 ? o.tpr_a : (o.tpr_a == -1 ? cqp::kRowsBatched : tune(m, n, nnz, a_rp, a_ci, a_v));
       P.tpr_t = o.tpr_at > 0 ? o.tpr_at : (o.tpr_at == -1 ? cqp::kRowsBatched : tune(n, m, nnz, t_rp, t_ci, t_v));
-      P.tpr_p = has_p ? tune(n, n, pnnz, p_rp, p_ci, pT) : 1;
+      P.tpr_p = !has_p ? 1 : (o.tpr_p > 0 ? o.tpr_p : (o.tpr_p == -1 ? cqp::kRowsBatched : tune(n, n, pnnz, p_rp, p_ci, pT)));
     }
     // ---- work buffers and state -------------------------------------------------------------
     const int64_t mm = std::max<int64_t>(m, 1);

@@ -90,6 +90,27 @@ def test_bf16_solves_the_rounded_problem(gpu, orc, k, mode):
         assert np.linalg.norm(x - xs) <= 2e-2 * (1 + np.linalg.norm(xs))
 
 
+@pytest.mark.parametrize("mode", [0, 2])
+def test_forced_one_lane_rows_and_column_slices(gpu, orc, mode):
+    """The large QP's small copy with the paths its full size takes forced on: one lane per row
+    with four rows in flight for A, A' and P (P, with exactly two entries per row, then takes the
+    16-byte four-row gradient, head and tail rows the one-row loop) and 5 column slices for A z and
+    A'y; FP32 values (mode 0) and BF16 values (mode 2).  Oracle-measured rel-KKT <= 1e-4 on the
+    problem solved, and the oracle's tight objective."""
+    inst = I.small_config(5)
+    s = gpu.Solver(inst, precision=0, matrix_bf16=mode, tpr_a=-1, tpr_at=-1, tpr_p=-1, col_blocks=5, team=1,
+                   max_iter=200000, tol=1e-4, time_limit_s=120.0)
+    x, y, res = s.solve()
+    s.close()
+    assert res["rc"] == 0, res
+    solved = I.with_bf16_matrices(inst) if mode == 2 else inst
+    rep = orc.kkt(solved, x, y)
+    assert rep["rel_kkt"] <= REL_KKT, rep
+    xs, ys, info = orc.solve(solved, max_iter=1000000, tol=TIGHT_TOL)
+    assert obj_close(rep["pobj"], info["kkt"]["pobj"]), (rep["pobj"], info["kkt"]["pobj"])
+    assert np.linalg.norm(x - xs) <= 2e-2 * (1 + np.linalg.norm(xs))
+
+
 def test_bf16_values_already_representable_give_the_same_problem(gpu, orc):
     # an instance whose values are BF16 already: rounding changes nothing, so the KKT report of a
     # point through a BF16 handle equals the oracle's on the instance itself
