@@ -171,7 +171,7 @@ def inst_bytes(inst, res, esize=4):
     return algorithmic_bytes(inst["n"], inst["m"], nnz, res["iters"], res["inner_total"], k, pnnz, esize)
 
 
-SOLVER_SOURCES = ("common.cuh", "cones.cuh", "solver.cuh", "solver_impl.cuh", "kernels.inc", "solver_f32.cu")
+SOLVER_SOURCES = ("common.cuh", "cones.cuh", "solver.cuh", "solver_impl.cuh", "kernels.inc", "solver_grid_f32.cu")
 
 
 def _source_hash():

@@ -37,6 +37,18 @@ int pdhg_general_cluster_size(int threads);
 template <typename T>
 int pdhg_cluster_size(int threads);
 
+// The whole-GPU team's kernels, compiled in their own translation units (CQP_GRID_PART):
+// the equality-form solver and KKT kernels and the general-form solver kernel.
+template <typename T>
+cudaError_t launch_pdhg_grid(const KernelArgs<T>& a, int blocks, int threads, cudaStream_t st);
+template <typename T>
+cudaError_t launch_kkt_grid(const KernelArgs<T>& a, const T* x, const T* y, double* out, int blocks, int threads,
+                            cudaStream_t st);
+template <typename T>
+int pdhg_grid_blocks_per_sm(int threads);
+template <typename T>
+cudaError_t launch_pdhg_general_grid(const KernelArgs<T>& a, int blocks, int threads, cudaStream_t st);
+
 // Batched persistent solve (one block per instance at a time, work queue).
 template <typename T>
 cudaError_t launch_pdhg_batch(const KernelArgs<T>& a, const BatchArgs& b, int blocks, int threads, cudaStream_t st);

@@ -1,0 +1,4 @@
+// FP32 instantiation of the whole-GPU general-form solver kernel.
+#define CQP_T float
+#define CQP_GRID_PART
+#include "general.inc"
