@@ -20,7 +20,10 @@ cold start) is timed once as the comparison the metric names.
 The line also carries:
   roofline      algorithmic bytes per solve (the per-unit figures of the scope table: the two
                 sparse products per outer iteration, R, R' or P and eight n-vectors per inner
-                step) over the solver kernel's CUDA-event time, against the measured HBM peak;
+                step) over the solver kernel's CUDA-event time, against the measured HBM peak,
+                with `traffic` (ncu DRAM bytes per solve from profiles/, when captured on the
+                current kernel sources) and `l2` (the same rate against a measured copy between
+                two L2-resident 32 MB buffers: this workload's working set stays in L2);
   large         the HBM-bound workload: the large sparse QP (n = 2e8, m = 5e7, 1e9 nnz,
                 generated in device memory), one setup + solve to 1e-4 with its own roofline;
   cpu_baseline  the FP64 oracle solving the same instance to 1e-4 on the host: the OpenMP
@@ -37,10 +40,12 @@ Other workloads (not the default line):
                         --ws-train N a warm-start network is first trained on N
                         solved instances and the warm-started step is timed too.
   --workload large      the large sparse QP (n = --large-n, m = n/4, 20 nnz per
-                        row), generated in device memory; setup + solve per step.
+                        row), generated in device memory; setup + solve per step;
+                        --matrix-bf16 2 stores A, A' and P as BF16 (the rounded problem).
   --workload gemm       the warm-start network's BF16 GEMMs at the training shape.
   --workload spmv       the sparse product in each layout (CSR row widths, merge path, sliced
-                        ELL) on the large QP's A and an A'-shaped matrix at a tenth of its size.
+                        ELL) on the large QP's A and an A'-shaped matrix at a tenth of its size
+                        (--large-n 2e9: full size).
   --workload lasso      a Lasso with the shape and density of rcv1_test (677,399 x 47,236,
                         density 1.55e-3), reformulated by frontends.lasso_to_qp; setup + solve.
   --workload qcqp       a synthetic convex QCQP (n = 200,000, 50,000 linear rows, 50 quadratic
