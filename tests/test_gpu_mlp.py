@@ -68,12 +68,14 @@ def test_gemm_bf16(gpu, ta, tb, epi):
     assert np.all(np.abs(got - ref) <= tol * bound), np.abs(got - ref).max()
 
 
-@pytest.mark.parametrize("shape", [(128, 256, 64), (300, 512, 128), (1000, 256, 576), (4100, 768, 512),
-                                   (40000, 512, 256)])
+@pytest.mark.parametrize("shape", [(1, 256, 64), (77, 512, 192), (128, 256, 64), (300, 512, 128), (1000, 256, 576),
+                                   (4100, 768, 512), (40000, 512, 256)])
 @pytest.mark.parametrize("epi", [0, 1, 2, 4])
 def test_gemm_tensor_memory_path(gpu, shape, epi):
     """C = A B' with A (M x K) and B (N x K) row-major: the form that runs on tcgen05.mma with
-    the accumulator in tensor memory.  One tile (128 x 256 x 64), ragged row tiles (M = 300,
+    the accumulator in tensor memory.  A single row and 77 rows (one partial tile: the tensor
+    copies fill rows past M with zeros and the tiled stores clip them), one tile (128 x 256 x
+    64), ragged row tiles (M = 300,
     1000, 4100), several K slices through the four-stage ring (K = 576: nine slices, the ring
     wraps twice), several column tiles, and more tiles than SMs (M = 40,000: 626 tiles, so each
     persistent block alternates its two tensor-memory accumulators); compared with the exact
