@@ -65,3 +65,40 @@ def test_oracle_not_imported_by_product():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".inc")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "oracle.h" not in txt, f
+
+
+def _header_fields(header, struct_name):
+    """(name, C type, array length) of the fields of `typedef struct { ... } struct_name;`."""
+    import re
+    end = header.index("} %s;" % struct_name)
+    start = header.rindex("typedef struct {", 0, end)
+    body = re.sub(r"/\*.*?\*/", "", header[start + len("typedef struct {"):end], flags=re.S)
+    out = []
+    for line in body.splitlines():
+        m = re.match(r"\s*(int32_t|int64_t|double|void\*|cqp_kkt_report|const \w+\*)\s+(.+);", line)
+        if not m:
+            continue
+        for nm in m.group(2).split(","):
+            nm = nm.strip()
+            a = re.match(r"(\w+)\[(\d+)\]", nm)
+            out.append((a.group(1), m.group(1), int(a.group(2))) if a else (nm, m.group(1), 1))
+    return out
+
+
+def test_ctypes_mirrors_follow_the_header():
+    # the binding's option and result structures must match include/cqp.h field by field
+    # (order, C type, array length); a mismatch would shift every later field across the ABI
+    import ctypes as C
+    import paper_2608_09159_gb300 as g
+    header = open(os.path.join(ROOT, "include", "cqp.h")).read()
+    ctype = {"int32_t": C.c_int32, "int64_t": C.c_int64, "double": C.c_double, "void*": C.c_void_p}
+    for struct_name, py in (("cqp_options", g.Options), ("cqp_result", g.Result), ("cqp_kkt_report", g.KKTReport)):
+        fields = _header_fields(header, struct_name)
+        assert [f[0] for f in fields] == [f for f, _ in py._fields_], struct_name
+        for (name, ty, n), (_, pty) in zip(fields, py._fields_):
+            if ty == "cqp_kkt_report":
+                assert pty is g.KKTReport, name
+            elif n > 1:
+                assert pty._type_ is ctype[ty] and pty._length_ == n, name
+            else:
+                assert pty is ctype[ty], (struct_name, name)
