@@ -75,7 +75,7 @@ def _header_fields(header, struct_name):
     body = re.sub(r"/\*.*?\*/", "", header[start + len("typedef struct {"):end], flags=re.S)
     out = []
     for line in body.splitlines():
-        m = re.match(r"\s*(int32_t|int64_t|double|void\*|cqp_kkt_report|const \w+\*)\s+(.+);", line)
+        m = re.match(r"\s*(int32_t|int64_t|double|void\*|cqp_kkt_report|cqp_csr|const \w+\*)\s+(.+);", line)
         if not m:
             continue
         for nm in m.group(2).split(","):
@@ -92,12 +92,18 @@ def test_ctypes_mirrors_follow_the_header():
     import paper_2608_09159_gb300 as g
     header = open(os.path.join(ROOT, "include", "cqp.h")).read()
     ctype = {"int32_t": C.c_int32, "int64_t": C.c_int64, "double": C.c_double, "void*": C.c_void_p}
-    for struct_name, py in (("cqp_options", g.Options), ("cqp_result", g.Result), ("cqp_kkt_report", g.KKTReport)):
+    for struct_name, py in (("cqp_options", g.Options), ("cqp_result", g.Result), ("cqp_kkt_report", g.KKTReport),
+                            ("cqp_csr", g.CSR), ("cqp_qop", g.QOp), ("cqp_cones", g.Cones), ("cqp_bounds", g.Bounds),
+                            ("cqp_batch", g.Batch), ("cqp_instance_result", g.InstanceResult)):
         fields = _header_fields(header, struct_name)
         assert [f[0] for f in fields] == [f for f, _ in py._fields_], struct_name
         for (name, ty, n), (_, pty) in zip(fields, py._fields_):
             if ty == "cqp_kkt_report":
                 assert pty is g.KKTReport, name
+            elif ty == "cqp_csr":
+                assert pty is g.CSR, name
+            elif ty.startswith("const "):
+                assert pty is C.c_void_p, (struct_name, name)   # device or host pointer
             elif n > 1:
                 assert pty._type_ is ctype[ty] and pty._length_ == n, name
             else:
