@@ -279,29 +279,43 @@ __device__ __forceinline__ void rows_loop(const int* rp, const int* ci, const T*
 constexpr int kMultiRows = 4;
 constexpr int kMultiU = 4;
 // ulen > 0: every row has exactly ulen entries (rp[r] = ulen r), so the row pointers are not read.
-template <int RB, typename Acc, int U = kMultiU, typename T, typename X, typename F>
+template <int RB, typename Acc, int U = kMultiU, bool PF = false, typename T, typename X, typename F>
 __device__ __forceinline__ void rows_loop_multi(const int* rp, const int* ci, const T* v, int64_t r0, int64_t r1, X xf,
                                                 F f, int ulen = 0) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5;
   const int64_t nrows = r1 - r0;
-  for (int64_t base = warp * 32 * RB; base < nrows; base += nwarps * 32 * RB) {
+  const int64_t stride = nwarps * 32 * RB;
+  // PF: the row pointers of the lane's next RB rows are loaded while the current rows are summed
+  // (measured faster for the column slices of A, slower for those of A')
+  int nbeg[RB], nend[RB];
+  auto load_ptrs = [&](int64_t bs) {
+#pragma unroll
+    for (int q = 0; q < RB; ++q) {
+      const int64_t r = r0 + bs + 32 * q + lane;
+      const bool ok = bs < nrows && r < r1;
+      if (ulen > 0) {
+        nbeg[q] = ok ? (int)(ulen * r) : 0;
+        nend[q] = ok ? nbeg[q] + ulen : 0;
+      } else {
+        nbeg[q] = ok ? rp[r] : 0;
+        nend[q] = ok ? rp[r + 1] : 0;
+      }
+    }
+  };
+  if (PF) load_ptrs(warp * 32 * RB);
+  for (int64_t base = warp * 32 * RB; base < nrows; base += stride) {
     int beg[RB], end[RB];
     Acc s[RB];
     int len = 0;
+    if (!PF) load_ptrs(base);
 #pragma unroll
     for (int q = 0; q < RB; ++q) {
-      const int64_t r = r0 + base + 32 * q + lane;
-      const bool ok = r < r1;
-      if (ulen > 0) {
-        beg[q] = ok ? (int)(ulen * r) : 0;
-        end[q] = ok ? beg[q] + ulen : 0;
-      } else {
-        beg[q] = ok ? rp[r] : 0;
-        end[q] = ok ? rp[r + 1] : 0;
-      }
+      beg[q] = nbeg[q];
+      end[q] = nend[q];
       s[q] = Acc(0);
     }
+    if (PF) load_ptrs(base + stride);
 #pragma unroll
     for (int q = 0; q < RB; ++q) len = max(len, end[q] - beg[q]);
     for (int k = 0; k < len; k += U) {

@@ -483,7 +483,7 @@ __device__ void Solver<T, Team, GEN>::run(long long budget) {
         for (int b = 0; b < P.cb_n; ++b) {
           const bool first = b == 0, last = b == P.cb_n - 1;
           vals(P.cb_v, P.cb_vb, [&](auto cbv) {
-            rows_loop_multi<kMultiRows, T>(P.cb_rp + (int64_t)b * P.m, P.cb_ci, cbv, own.row0, own.row1,
+            rows_loop_multi<kMultiRows, T, kMultiU, true>(P.cb_rp + (int64_t)b * P.m, P.cb_ci, cbv, own.row0, own.row1,
                              [&](int j) { return zv[j]; }, [&](int64_t r, int gl, T s1) {
                                if (gl != 0) return;
                                if (last) dual_row(r, 0, first ? s1 : acc[r] + s1, T(0));
