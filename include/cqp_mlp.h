@@ -57,9 +57,9 @@ int cqp_gemm_bf16(int32_t trans_a, int32_t trans_b, int64_t M, int64_t N, int64_
                   const uint16_t* B, int64_t ldb, void* C, int64_t ldc, const float* bias, int32_t epilogue,
                   int32_t split_k, void* stream);
 
-/* CQP_ERR_WAIT if a bounded wait inside one of the tensor-core GEMMs issued so far on the
- * current device expired (it then stored nothing); CQP_OK otherwise.  Synchronises stream and
- * clears the record. */
+/* CQP_ERR_WAIT if a bounded wait (one second) inside one of the tensor-core GEMMs issued so far
+ * on the current device expired (that GEMM's output is then incomplete: the blocks stop at the
+ * failed wait); CQP_OK otherwise.  Synchronises stream and clears the record. */
 int cqp_gemm_check(void* stream);
 
 /* out (cols x rows, BF16, row-major) = in' (in: rows x cols, BF16, row-major). */
